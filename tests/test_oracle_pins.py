@@ -1,0 +1,408 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each test names the passage of the paper it pins and the outside fact used:
+textbook matrices and conjugation tables, closed forms, algebraic invariants,
+floating-point evaluations through numpy's Kronecker products, and brute force
+on tiny instances.  A plausible slip in the oracle (a dropped sqrt2, a wrong
+sign or phase, a transposed product, a wrong half-split order) fails at least
+one of them.
+"""
+
+import numpy as np
+import pytest
+
+from paper_1606_07413_gb300 import workloads as W
+
+R2 = np.sqrt(2.0)
+w8 = np.exp(1j * np.pi / 4)
+
+# textbook one-qubit matrices
+I2 = np.eye(2, dtype=complex)
+SX = np.array([[0, 1], [1, 0]], dtype=complex)
+SY = np.array([[0, -1j], [1j, 0]], dtype=complex)
+SZ = np.array([[1, 0], [0, -1]], dtype=complex)
+GH = np.array([[1, 1], [1, -1]], dtype=complex) / R2
+GS = np.diag([1, 1j])
+GT = np.diag([1, w8])
+
+
+def kron_pauli(n, code):
+    """P(code) as a Kronecker product of textbook Paulis; qubit q is bit q of
+    the basis index (the most significant factor is qubit n-1)."""
+    x, z = code >> n, code & ((1 << n) - 1)
+    table = {(0, 0): I2, (0, 1): SZ, (1, 0): SX, (1, 1): SY}
+    m = np.eye(1, dtype=complex)
+    for q in reversed(range(n)):
+        m = np.kron(m, table[((x >> q) & 1, (z >> q) & 1)])
+    return m
+
+
+def embed(n, q, g):
+    m = np.eye(1, dtype=complex)
+    for t in reversed(range(n)):
+        m = np.kron(m, g if t == q else I2)
+    return m
+
+
+def float_unitary(n, gates):
+    """Unitary of a gate list from textbook gate matrices (numpy, complex128)."""
+    d = 1 << n
+    U = np.eye(d, dtype=complex)
+    for op, a, b in np.asarray(gates).reshape(-1, 3):
+        if op == W.OP_CNOT:
+            G = np.zeros((d, d), complex)
+            for c in range(d):
+                G[c ^ (((c >> a) & 1) << b), c] = 1
+        elif op == W.OP_RP:
+            P = kron_pauli(n, int(a))
+            G = 0.5 * (1 + w8) * np.eye(d) + 0.5 * (1 - w8) * P
+        else:
+            g = {W.OP_H: GH, W.OP_S: GS, W.OP_T: GT, W.OP_X: SX, W.OP_Z: SZ,
+                 W.OP_SDG: GS.conj(), W.OP_TDG: GT.conj()}[int(op)]
+            G = embed(n, int(a), g)
+        U = G @ U
+    return U
+
+
+def float_channel(n, U):
+    D = 4 ** n
+    Ps = [kron_pauli(n, j) for j in range(D)]
+    C = np.zeros((D, D))
+    for i in range(D):
+        for j in range(D):
+            C[i, j] = np.trace(Ps[i] @ U @ Ps[j] @ U.conj().T).real / 2 ** n
+    return C
+
+
+def random_circuit(rng, n, length, t_gates=True):
+    rows = []
+    ops = [W.OP_H, W.OP_S, W.OP_T] if t_gates else [W.OP_H, W.OP_S]
+    for _ in range(length):
+        kind = int(rng.integers(len(ops) + (1 if n > 1 else 0)))
+        if kind < len(ops):
+            rows.append((ops[kind], int(rng.integers(n)), 0))
+        else:
+            c, t = rng.choice(n, 2, replace=False)
+            rows.append((W.OP_CNOT, int(c), int(t)))
+    return np.asarray(rows, np.int32).reshape(-1, 3)
+
+
+# ---------------------------------------------------------------- Paulis (Sec. 4.1)
+
+@pytest.mark.parametrize("n", [1, 2])
+def test_pauli_product_phase_matches_kronecker_matrices(orc, n):
+    """P(p) P(q) = i^lambda P(p^q) with lambda from textbook matrix products."""
+    D = 4 ** n
+    for p in range(D):
+        for q in range(D):
+            lhs = kron_pauli(n, p) @ kron_pauli(n, q)
+            lam = orc.pauli_phase(n, p, q)
+            assert np.allclose(lhs, (1j ** lam) * kron_pauli(n, p ^ q)), (p, q)
+
+
+def test_unitary_builder_matches_textbook_gates(orc):
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 3):
+        gates = random_circuit(rng, n, 40)
+        gates = np.concatenate([gates, np.asarray([(W.OP_RP, int(rng.integers(1, 4 ** n)), 0)], np.int32)])
+        u, e = orc.unitary_from_circuit(n, gates)
+        exact = (u[..., 0] + u[..., 1] * w8 + u[..., 2] * w8 ** 2 + u[..., 3] * w8 ** 3) / R2 ** e
+        assert np.allclose(exact, float_unitary(n, gates))
+
+
+# ------------------------------------------------------- channel representation (Sec. 4.1)
+
+def test_channel_of_H_S_CNOT_follow_textbook_conjugation_tables(orc):
+    # n = 1 codes: I=0, Z=1, X=2, Y=3
+    H = orc.channel_from_circuit(1, [(W.OP_H, 0, 0)]).values()
+    assert np.allclose(H, [[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, -1]])  # X<->Z, Y->-Y
+    S = orc.channel_from_circuit(1, [(W.OP_S, 0, 0)]).values()
+    assert np.allclose(S[:, 2], [0, 0, 0, 1])   # S X S^dag = Y
+    assert np.allclose(S[:, 3], [0, 0, -1, 0])  # S Y S^dag = -X
+    assert np.allclose(S[:, 1], [0, 1, 0, 0])   # Z fixed
+    # CNOT with control qubit 0, target qubit 1 (n = 2; code = x << 2 | z)
+    C = orc.channel_from_circuit(2, [(W.OP_CNOT, 0, 1)]).values()
+
+    def code(x, z):
+        return (x << 2) | z
+
+    assert C[code(0b11, 0), code(0b01, 0)] == pytest.approx(1)  # X_c -> X_c X_t
+    assert C[code(0b10, 0), code(0b10, 0)] == pytest.approx(1)  # X_t -> X_t
+    assert C[code(0, 0b11), code(0, 0b10)] == pytest.approx(1)  # Z_t -> Z_c Z_t
+    assert C[code(0, 0b01), code(0, 0b01)] == pytest.approx(1)  # Z_c -> Z_c
+
+
+def test_T_closed_form(orc):
+    """R(Z) on one qubit is T; T X T^dag = (X + Y)/sqrt2 and T Y T^dag = (Y - X)/sqrt2."""
+    T = orc.channel_from_circuit(1, [(W.OP_T, 0, 0)])
+    assert T.equals(orc.rhat(1, 1))
+    v = T.values()
+    assert np.allclose(v[:, 2], [0, 0, 1 / R2, 1 / R2])
+    assert np.allclose(v[:, 3], [0, 0, -1 / R2, 1 / R2])
+    assert np.allclose(v[:, 1], [0, 1, 0, 0])
+    assert T.reduced().E == 1
+
+
+@pytest.mark.parametrize("n", [1, 2])
+def test_channel_matches_float_trace_over_kronecker_paulis(orc, n):
+    rng = np.random.default_rng(10 + n)
+    for _ in range(3):
+        gates = random_circuit(rng, n, 30)
+        C = orc.channel_from_circuit(n, gates)
+        assert np.allclose(C.values(), float_channel(n, float_unitary(n, gates)), atol=1e-9)
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_channel_is_a_homomorphism(orc, n):
+    """(UV)^ = U^ V^ (used implicitly when the paper writes Eq. tcount_synthesis in channel form)."""
+    rng = np.random.default_rng(20 + n)
+    for _ in range(2):
+        g1 = random_circuit(rng, n, 25)
+        g2 = random_circuit(rng, n, 25)
+        both = orc.channel_from_circuit(n, np.concatenate([g1, g2]))  # g1 acts first
+        prod = orc.channel_from_circuit(n, g2) @ orc.channel_from_circuit(n, g1)
+        assert both.equals(prod)
+        swapped = orc.channel_from_circuit(n, g1) @ orc.channel_from_circuit(n, g2)
+        assert not both.equals(swapped)
+
+
+# ------------------------------------------------------------ R^(P) (Sec. 4.1)
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_rhat_columns_equal_trace_definition(orc, n):
+    for p in range(1, 4 ** n):
+        assert orc.rhat(n, p).equals(orc.rhat_trace(n, p)), p
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_rhat_invariants(orc, n):
+    ident = orc.identity(n)
+    rng = np.random.default_rng(30 + n)
+    for p in rng.choice(np.arange(1, 4 ** n), size=min(8, 4 ** n - 1), replace=False):
+        R, Rt = orc.rhat(n, int(p)), orc.rhat(n, int(p), transpose=True)
+        assert (R @ Rt).equals(ident)                   # orthogonal
+        assert Rt.equals(orc.Chan(n, R.a.T.copy(), R.b.T.copy(), R.E))
+        R2m = R @ R
+        assert orc.is_clifford(R2m) and not orc.is_clifford(R)  # R^2 Clifford, R not
+        R8 = R2m @ R2m
+        R8 = R8 @ R8
+        assert R8.equals(ident)                          # R^8 = I
+        # at most two nonzeros per column, and exactly half the columns are split
+        nz = (R.a != 0) | (R.b != 0)
+        assert nz.sum(axis=0).max() <= 2
+        assert (nz.sum(axis=0) == 2).sum() == 4 ** n // 2
+
+
+def test_rp_gate_channel_equals_rhat(orc):
+    for n in (1, 2, 3):
+        for p in (1, 4 ** n - 1, 5 % (4 ** n - 1) + 1):
+            assert orc.channel_from_circuit(n, [(W.OP_RP, p, 0)]).equals(orc.rhat(n, p))
+
+
+# ------------------------------------------------------ canonical form modulo Clifford
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_canonical_form_and_walk_hash_are_clifford_invariant(orc, n):
+    rng = np.random.default_rng(40 + n)
+    gates, _ = W.seeded_target(n, 3, 99 + n)
+    C = orc.channel_from_circuit(n, gates)
+    for _ in range(3):
+        Dc = orc.channel_from_circuit(n, W.clifford_word(rng, n, 60))
+        CD = C @ Dc
+        assert orc.same_coset(C, CD)
+        assert orc.matrix_hash(C, 4, 0, 5, 48) == orc.matrix_hash(CD, 4, 0, 5, 48)
+    # a different coset: multiply by one more rotation
+    other = C @ orc.rhat(n, 3)
+    assert not orc.same_coset(C, other)
+    assert orc.matrix_hash(C, 4, 0, 5, 48) != orc.matrix_hash(other, 4, 0, 5, 48)
+
+
+def test_hash_depends_on_version_and_tag(orc):
+    gates, _ = W.seeded_target(2, 3, 5)
+    C = orc.channel_from_circuit(2, gates)
+    h = {orc.matrix_hash(C, 4, c, v, 64) for v in range(3) for c in range(3)}
+    assert len(h) == 9
+
+
+# --------------------------------------------------------------- T-count (Sec. 4.1)
+
+def test_tcount_of_single_T_is_one(orc):
+    C = orc.channel_from_circuit(1, [(W.OP_T, 0, 0)])
+    assert orc.mitm_tcount(C, 3)[0] == 1
+    assert orc.brute_tcount(C, 3)[0] == 1
+
+
+def test_tcount_of_clifford_is_zero(orc):
+    rng = np.random.default_rng(7)
+    for n in (1, 2, 3):
+        C = orc.channel_from_circuit(n, W.clifford_word(rng, n, 80))
+        assert orc.is_clifford(C) and orc.sde(C) == 0
+        assert orc.mitm_tcount(C, 2)[0] == 0
+
+
+def test_rotation_squared_is_clifford(orc):
+    for p in (1, 6, 15):
+        C = orc.channel_from_circuit(2, [(W.OP_RP, p, 0), (W.OP_RP, p, 0)])
+        assert orc.mitm_tcount(C, 2)[0] == 0
+        assert orc.brute_tcount(C, 2)[0] == 0
+
+
+def test_every_single_rotation_has_tcount_one(orc):
+    for p in range(1, 16):
+        C = orc.channel_from_circuit(2, [(W.OP_RP, p, 0), (W.OP_H, 1, 0), (W.OP_CNOT, 1, 0)])
+        t, paulis = orc.mitm_tcount(C, 2)
+        assert t == 1 and orc.verify(C, paulis)
+
+
+def test_mitm_matches_brute_force_on_tiny_instances(orc):
+    """Exhaustive MITM (Eq. mitm) agrees with brute force over all products (Sec. 3)."""
+    rng = np.random.default_rng(11)
+    seen = set()
+    for trial in range(10):
+        t = int(rng.integers(1, 4))
+        # repeated or commuting factors make some instances collapse below t
+        ps = [int(v) for v in rng.integers(1, 16, size=t)]
+        if trial % 3 == 0 and t >= 2:
+            ps[1] = ps[0]
+        rows = [(W.OP_RP, p, 0) for p in ps] + [tuple(r) for r in W.clifford_word(rng, 2, 30)]
+        C = orc.channel_from_circuit(2, np.asarray(rows, np.int32))
+        tb, pb = orc.brute_tcount(C, 3)
+        tm, pm = orc.mitm_tcount(C, 3)
+        assert tb == tm and tm <= t
+        assert orc.sde(C) <= tm
+        assert orc.verify(C, pm) and orc.verify(C, pb)
+        seen.add(tm)
+    assert len(seen) >= 2
+
+
+def test_construction_bound_and_sde_lower_bound(orc):
+    for cfg in (1, 2):
+        c = W.CONFIGS[cfg]
+        gates, _ = W.config_target(cfg)
+        C = orc.channel_from_circuit(c["n"], gates)
+        assert orc.sde(C) <= c["t"]
+    gates, _ = W.config_target(1)
+    C = orc.channel_from_circuit(2, gates)
+    t, paulis = orc.mitm_tcount(C, 3)
+    assert orc.sde(C) <= t <= 3 and orc.verify(C, paulis)
+
+
+def test_verify_rejects_wrong_decompositions(orc):
+    gates, _ = W.config_target(1)
+    C = orc.channel_from_circuit(2, gates)
+    t, paulis = orc.mitm_tcount(C, 3)
+    assert orc.verify(C, paulis)
+    assert not orc.verify(C, paulis[::-1]) or paulis == paulis[::-1]
+    bad = list(paulis)
+    bad[0] = bad[0] % 15 + 1
+    assert not orc.verify(C, bad)
+
+
+# --------------------------------------------------- walk, claws and re-walking (Sec. 3)
+
+def test_claw_halves_hash_equal(orc):
+    """A decomposition split as in Eq. mitm gives V and W in one coset, so the
+    walk maps both sides to the same next state."""
+    for cfg in (1, 2):
+        c = W.CONFIGS[cfg]
+        gates, _ = W.config_target(cfg)
+        C = orc.channel_from_circuit(c["n"], gates)
+        if cfg == 1:
+            t, p = orc.mitm_tcount(C, 3)
+        else:
+            t, p = orc.mitm_level(C, 5) and (5, orc.mitm_level(C, 5))
+        h = t // 2
+        chunk = p[2 * h] if t & 1 else 0
+        V = orc.half_product(C, t, chunk, 0, p[:h])
+        Wm = orc.half_product(C, t, chunk, 1, p[h:2 * h])
+        assert V.E == Wm.E == orc.sde(C) + (t & 1) + h
+        assert orc.same_coset(V, Wm)
+        assert orc.matrix_hash(V, t, chunk, 3, c["L"]) == orc.matrix_hash(Wm, t, chunk, 3, c["L"])
+        # the states that decode to these halves step to the same point
+        xi = 4 ** c["n"] - 1
+        r_v = sum((q - 1) * xi ** j for j, q in enumerate(p[:h]))
+        r_w = sum((q - 1) * xi ** j for j, q in enumerate(p[h:2 * h]))
+        xv, xw = (r_v << 1) | 0, (r_w << 1) | 1
+        assert orc.decode(c["n"], t, xv) == (0, p[:h])
+        y = orc.walk_step(C, t, chunk, 3, c["L"], [xv, xw])
+        assert y[0] == y[1]
+        cls, a, b, paulis = orc.rewalk(C, t, chunk, 3, c["L"], xv, 1, xw, 1)
+        assert cls == orc.CLAW and orc.verify(C, paulis)
+
+
+def test_walk_step_is_a_function_of_the_decoded_point(orc):
+    gates, _ = W.config_target(1)
+    C = orc.channel_from_circuit(2, gates)
+    xi_h = 15
+    x = np.asarray([7, 7 + 2 * xi_h, 7 + 2 * xi_h * 1000], np.uint64)
+    y = orc.walk_step(C, 2, 0, 1, 32, x)
+    assert y[0] == y[1] == y[2]
+    assert orc.classify(C, 2, 0, int(x[0]), int(x[1]))[0] == orc.TRIVIAL
+    y = orc.walk_step(C, 2, 0, 1, 32, np.asarray([6, 7], np.uint64))
+    assert y[0] != y[1]
+
+
+def test_serial_walk_search_finds_the_optimal_tcount(orc):
+    rng = np.random.default_rng(12)
+    for trial in range(3):
+        gates, _ = W.seeded_target(2, 3, 500 + trial)
+        C = orc.channel_from_circuit(2, gates)
+        t_exact, _ = orc.mitm_tcount(C, 3)
+        t, paulis, st = orc.vow_search(C, 3, dtheta=2, L=32, max_len=400, per_version=4000,
+                                       per_level=2_000_000, table_log2=14, seed=int(rng.integers(1 << 40)))
+        assert t == t_exact and orc.verify(C, paulis)
+        assert st["claws"] >= 1 and st["no_merge"] == 0
+
+
+def test_dp_predicate(orc):
+    y = np.asarray([0, 1 << 20, (1 << 26) - 1, 1 << 26, (1 << 31) | 5], np.uint64)
+    assert orc.is_dp(y, 32, 6).tolist() == [True, True, True, False, False]
+
+
+def _noncommuting_chain(orc, rng, n, t):
+    """t Pauli codes with every neighbour pair anticommuting."""
+    ps = [int(rng.integers(1, 4 ** n))]
+    while len(ps) < t:
+        q = int(rng.integers(1, 4 ** n))
+        if orc.pauli_phase(n, ps[-1], q) != orc.pauli_phase(n, q, ps[-1]):
+            ps.append(q)
+    return ps
+
+
+@pytest.mark.parametrize("n,t", [(2, 4), (2, 5), (3, 4), (3, 5)])
+def test_known_normal_form_is_a_claw(orc, n, t):
+    """Build C = R(P_t)...R(P_1) D directly (Eq. tcount_synthesis) with
+    non-commuting neighbours; then V_(P_1..P_h) and W_(P_h+1..P_2h) (chunk P_t
+    for odd t) are one coset (Eq. mitm), and the half products equal the
+    explicit products of the (trace-pinned) R^ matrices."""
+    rng = np.random.default_rng(100 * n + t)
+    ps = _noncommuting_chain(orc, rng, n, t)
+    rows = [tuple(r) for r in W.clifford_word(rng, n, 40)] + [(W.OP_RP, p, 0) for p in ps]
+    C = orc.channel_from_circuit(n, np.asarray(rows, np.int32))
+    h = t // 2
+    chunk = ps[2 * h] if t & 1 else 0
+    V = orc.half_product(C, t, chunk, 0, ps[:h])
+    Wm = orc.half_product(C, t, chunk, 1, ps[h:2 * h])
+    # explicit products
+    Vx = orc.identity(n)
+    for p in ps[:h]:
+        Vx = orc.rhat(n, p) @ Vx
+    Wx = C
+    if t & 1:
+        Wx = orc.rhat(n, chunk, transpose=True) @ Wx
+    for p in reversed(ps[h:2 * h]):
+        Wx = orc.rhat(n, p, transpose=True) @ Wx
+    assert V.equals(Vx) and Wm.equals(Wx)
+    assert orc.same_coset(V, Wm)
+    assert orc.verify(C, ps)
+    # swapping the two W-side factors breaks the claw (they do not commute)
+    Wswap = orc.half_product(C, t, chunk, 1, ps[h:2 * h][::-1])
+    assert not orc.same_coset(V, Wswap)
+    xi = 4 ** n - 1
+    xv = sum((q - 1) * xi ** j for j, q in enumerate(ps[:h])) << 1
+    xw = (sum((q - 1) * xi ** j for j, q in enumerate(ps[h:2 * h])) << 1) | 1
+    L = {2: 32, 3: 48}[n]
+    y = orc.walk_step(C, t, chunk, 9, L, [xv, xw])
+    assert y[0] == y[1]
+    cls, paulis = orc.classify(C, t, chunk, xv, xw)
+    assert cls == orc.CLAW and paulis == ps
