@@ -1,0 +1,219 @@
+/*
+ * qcs.h -- C ABI of libqcs, a GB300 (sm_103a) implementation of the
+ * deterministic-walk optimal T-count search of Di Matteo & Mosca,
+ * "Parallelizing quantum circuit synthesis".
+ *
+ * The library finds, for a target unitary C over Clifford+T, the smallest t
+ * and Paulis P_1..P_t with  C = e^{i phi} R(P_t) ... R(P_1) D,  D Clifford
+ * (Sec. 4.1, Eq. tcount_synthesis), by a parallel claw search between the two
+ * halves of Eq. mitm (Sec. 3) on one GPU.
+ *
+ * Conventions shared by every entry point:
+ *  - Pauli code j in [0, 4^n): x = j >> n, z = j & (2^n - 1), qubit q is bit q;
+ *    P(j) = i^{|x&z|} X^x Z^z.  Basis state c has qubit q in bit q of c.
+ *  - Exact targets are 2^n x 2^n row-major matrices of Z[omega] numbers, four
+ *    int64 per entry (c0 + c1 w + c2 w^2 + c3 w^3, w = e^{i pi/4}), all divided
+ *    by sqrt2^exp.
+ *  - Channel matrices (Sec. 4.1, U^_ij = Tr(P_i U P_j U^dag)/2^n) are 4^n x 4^n
+ *    row-major, two int64 per entry (a, b) meaning (a + b sqrt2)/sqrt2^exp.
+ *  - Walk states are L-bit strings in uint64 (L = params.state_bits).  A state
+ *    x names side x & 1 (0: V = R(q_h)..R(q_1), 1: W = R(q_1)^T..R(q_h)^T
+ *    [R(c)^T] C^ in channel form) and rotations q_j = digit_j + 1, the digits
+ *    of (x >> 1) mod xi^h in base xi = 4^n - 1, least significant first
+ *    (Sec. 2 mappings mu, nu and h; Sec. 3 chunks c for odd k).
+ *
+ * Ownership: every pointer argument stays owned by the caller; the library
+ * copies what it keeps.  The library owns every device allocation it makes and
+ * frees it in qcs_destroy_problem.  Errors are returned as status codes, never
+ * thrown across the ABI.  A problem handle may be used by one host thread at a
+ * time (qcs_poll_collisions and qcs_cancel may be called concurrently with a
+ * running search).
+ */
+#ifndef QCS_H
+#define QCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define QCS_API __attribute__((visibility("default")))
+#else
+#define QCS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define QCS_OK 0
+#define QCS_ERR_ARG (-1)         /* argument out of range or inconsistent */
+#define QCS_ERR_NOT_UNITARY (-2) /* target is not an exact unitary / channel */
+#define QCS_ERR_NOMEM (-3)       /* host or device allocation failed */
+#define QCS_ERR_CUDA (-4)        /* a CUDA call failed (see qcs_last_cuda_error) */
+#define QCS_ERR_MISMATCH (-5)    /* decomposition does not reproduce the target */
+#define QCS_ERR_OVERFLOW (-6)    /* exact arithmetic would overflow int64 */
+#define QCS_ERR_BUSY (-7)        /* a search is already running on this problem */
+#define QCS_ERR_TIMEOUT (-8)     /* qcs_wait ran out of time */
+#define QCS_ERR_DEVICE (-9)      /* a device-side bounded wait gave up */
+
+/* search status reported by qcs_poll_collisions */
+#define QCS_IDLE 0
+#define QCS_SEARCHING 1
+#define QCS_FOUND 2
+#define QCS_BUDGET_EXHAUSTED 3
+#define QCS_CANCELLED 4
+#define QCS_ERROR 5
+
+/* gate ops of the circuit input format: rows (op, a, b) in time order */
+#define QCS_GATE_H 0    /* H on qubit a */
+#define QCS_GATE_S 1    /* S = diag(1, i) on qubit a */
+#define QCS_GATE_CNOT 2 /* control a, target b */
+#define QCS_GATE_T 3    /* T = diag(1, w) on qubit a */
+#define QCS_GATE_RP 4   /* R(P_a) of Sec. 4.1, a = Pauli code in [1, 4^n) */
+#define QCS_GATE_X 5
+#define QCS_GATE_Z 6
+#define QCS_GATE_SDG 7
+#define QCS_GATE_TDG 8
+
+/* merge classes of a re-walked collision (Sec. 3, Fig. 2) */
+#define QCS_MERGE_ROBIN_HOOD 0 /* one start lies on the other trail */
+#define QCS_MERGE_TRIVIAL 1    /* both states decode to the same point */
+#define QCS_MERGE_SAME_SIDE 2  /* both sides V (or both W): no solution */
+#define QCS_MERGE_CLAW 3       /* V meets W: a decomposition */
+#define QCS_MERGE_FALSE_HASH 4 /* V meets W by hash only, not exactly */
+#define QCS_MERGE_NO_MERGE 5   /* trails did not meet (inconsistent input) */
+
+typedef struct qcs_params {
+    int32_t state_bits;       /* L, 32..64 */
+    int32_t dp_bits;          /* d_theta, theta = 2^-d_theta (Sec. 3), 1 .. L-1 */
+    int32_t walks;            /* concurrent walks (one warp each) */
+    int32_t table_log2;       /* distinguished-point table holds 2^table_log2 slots (32 B each) */
+    int32_t steps_per_launch; /* walk steps each walk advances per kernel launch */
+    int32_t max_trail_factor; /* a trail is abandoned after max_trail_factor * 2^d_theta steps */
+    int32_t queue_capacity;   /* collision pairs kept per launch */
+    int32_t budget_factor;    /* a level gives up after budget_factor * (points at that level) steps */
+    int32_t theta_policy;     /* 0: d_theta fixed; 1: raise theta on small levels (time to solution) */
+    int32_t version_factor;   /* new function version every version_factor * points steps (0: never) */
+    uint64_t seed;            /* seed of trail starting points */
+} qcs_params;
+
+typedef struct qcs_result {
+    int32_t status;      /* QCS_IDLE .. QCS_ERROR */
+    int32_t error;       /* status code when status == QCS_ERROR */
+    int32_t k;           /* level (T-count candidate) being searched or found */
+    int32_t t_count;     /* optimal T-count when FOUND, else -1 */
+    uint32_t paulis[16]; /* P_1 .. P_t when FOUND */
+    int32_t sde;         /* smallest denominator exponent of C^ (lower bound on t) */
+    uint32_t version;    /* current function version */
+    int64_t steps;       /* walk steps taken (all levels) */
+    int64_t dps;         /* distinguished points reached */
+    int64_t merges;      /* trail pairs re-walked */
+    int64_t robin_hood, trivial, same_side, claws, false_hash, no_merge;
+    int64_t abandoned;   /* trails cut at the maximum length */
+    int64_t dropped;     /* distinguished points lost to a full table neighbourhood */
+    int64_t queue_overflow;
+    int64_t launches;    /* walk-kernel launches */
+    double seconds;      /* wall time since qcs_run_walks */
+} qcs_result;
+
+typedef struct qcs_problem qcs_problem;
+
+/* Fill *p with the defaults for n qubits (L = 32/48/64, d_theta = 6/10/12 ...). */
+QCS_API void qcs_default_params(int n_qubits, qcs_params *p);
+
+/* Create a search problem from an exact target unitary (see conventions).
+ * Checks exact unitarity, forms C^ (Sec. 4.1) exactly and reduces it to its
+ * smallest denominator exponent, then uploads it.  k_max in [0, 15] bounds the
+ * T-count ladder.  p may be NULL for defaults.  Errors: QCS_ERR_ARG (n not in
+ * 1..4, k_max out of range, bad params), QCS_ERR_NOT_UNITARY, QCS_ERR_OVERFLOW,
+ * QCS_ERR_NOMEM, QCS_ERR_CUDA.  On success *out owns device memory. */
+QCS_API int qcs_create_problem(int n_qubits, const int64_t *target, int32_t target_exp, int k_max,
+                       const qcs_params *p, qcs_problem **out);
+
+/* Same, from a 4^n x 4^n channel matrix given as (a, b) pairs over sqrt2^exp
+ * (chan_ab[2*(i*4^n + j)] = a_ij, [.. + 1] = b_ij).  Checks exact
+ * orthogonality and that row and column 0 are e_0; it does not check that the
+ * matrix is the channel of a unitary. */
+QCS_API int qcs_create_problem_channel(int n_qubits, const int64_t *chan_ab, int32_t exp, int k_max,
+                               const qcs_params *p, qcs_problem **out);
+
+/* Same, from a gate list of n_gates rows (op, a, b) in time order (QCS_GATE_*);
+ * the target is the product of the gates' textbook matrices. */
+QCS_API int qcs_create_problem_circuit(int n_qubits, const int32_t *gates, int n_gates, int k_max,
+                               const qcs_params *p, qcs_problem **out);
+
+/* Start the T-count ladder (levels sde(C^) .. k_max) on the given CUDA stream
+ * (a cudaStream_t; NULL = legacy default stream; a PyTorch stream handle is
+ * fine).  Returns at once: a library-owned host thread drives the launches.
+ * step_budget bounds the total walk steps (0 = no bound).  The stream must
+ * stay valid until the search ends (qcs_wait, or status != SEARCHING).
+ * Errors: QCS_ERR_BUSY if a search is running, QCS_ERR_ARG. */
+QCS_API int qcs_run_walks(qcs_problem *prob, uint64_t step_budget, void *cuda_stream);
+
+/* Non-blocking snapshot of the search (status, level, counters, and the
+ * decomposition once FOUND). */
+QCS_API int qcs_poll_collisions(qcs_problem *prob, qcs_result *out);
+
+/* Block until the running search ends or timeout_ms passes (< 0: forever);
+ * fills *out like qcs_poll_collisions.  QCS_ERR_TIMEOUT on time-out. */
+QCS_API int qcs_wait(qcs_problem *prob, int64_t timeout_ms, qcs_result *out);
+
+/* Ask a running search to stop before its next launch; qcs_wait then reports
+ * QCS_CANCELLED. */
+QCS_API int qcs_cancel(qcs_problem *prob);
+
+/* Once FOUND: the Clifford D of Eq. tcount_synthesis as a signed permutation of
+ * Pauli codes, D P_j D^dag = sign[j] P_perm[j] (arrays of 4^n entries). */
+QCS_API int qcs_get_clifford(qcs_problem *prob, int32_t *perm, int8_t *sign);
+
+/* Exact host check that C = e^{i phi} R(P_t)..R(P_1) D for a Clifford D
+ * (Sec. 4.1): forms D^ = R^(P_1)^T..R^(P_t)^T C^ and tests that it is a signed
+ * permutation.  target as in qcs_create_problem; paulis[0] is P_1.  Pure host,
+ * no GPU.  QCS_OK or QCS_ERR_MISMATCH (or QCS_ERR_ARG / QCS_ERR_NOT_UNITARY /
+ * QCS_ERR_OVERFLOW). */
+QCS_API int qcs_verify_decomposition(int n_qubits, const int64_t *target, int32_t target_exp,
+                             const uint32_t *paulis, int t);
+
+/* One walk step f = h o nu o mu (Sec. 2, Fig. 1; Sec. 3 z_b) for count states
+ * at level k (chunk c in 1..4^n-1 for odd k, 0 for even k) and function
+ * version `version`: out[i] = f(in[i]), is_dp[i] = 1 when out[i] is
+ * distinguished (its top d_theta of L bits are zero).  in, out, is_dp are
+ * DEVICE pointers (is_dp may be NULL); asynchronous on `stream`.  count = 0 is
+ * a no-op.  Errors: QCS_ERR_ARG (k > k_max or chunk out of range), QCS_ERR_CUDA. */
+QCS_API int qcs_walk_step(qcs_problem *prob, int k, int chunk, uint32_t version, const uint64_t *in,
+                  uint64_t *out, uint8_t *is_dp, size_t count, void *stream);
+
+/* Re-walk count trail pairs on the device (Sec. 3, Fig. 2): pair i is
+ * (start_a[i], len_a[i]) and (start_b[i], len_b[i]) ending at one
+ * distinguished point, at level k, chunk, version.  cls[i] gets a
+ * QCS_MERGE_* class (claw candidates are reported as QCS_MERGE_CLAW before the
+ * exact check), ab[2i], ab[2i+1] the two distinct states whose images
+ * coincide.  Lengths above 2^20 are reported as QCS_MERGE_NO_MERGE without
+ * walking.  All pointers are DEVICE pointers; asynchronous on `stream`. */
+QCS_API int qcs_rewalk(qcs_problem *prob, int k, int chunk, uint32_t version, const uint64_t *start_a,
+               const uint32_t *len_a, const uint64_t *start_b, const uint32_t *len_b,
+               size_t count, int32_t *cls, uint64_t *ab, void *stream);
+
+/* Facts about a created problem: sde of C^ (smallest denominator exponent),
+ * and the number of walk points 2 xi^h at level k (per chunk). */
+QCS_API int qcs_problem_sde(const qcs_problem *prob);
+QCS_API uint64_t qcs_level_points(const qcs_problem *prob, int k);
+
+/* Copy C^ (reduced) to host arrays a, b (4^n x 4^n) and its exponent. */
+QCS_API int qcs_get_channel(const qcs_problem *prob, int64_t *a, int64_t *b, int32_t *exp);
+
+/* Synchronises and frees everything the problem owns.  NULL is a no-op. */
+QCS_API void qcs_destroy_problem(qcs_problem *prob);
+
+/* Text for a status code; never NULL. */
+QCS_API const char *qcs_strerror(int code);
+
+/* Last CUDA error string seen by this thread's calls into the library. */
+QCS_API const char *qcs_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCS_H */

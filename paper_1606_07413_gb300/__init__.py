@@ -1,0 +1,266 @@
+"""Python binding of libqcs (include/qcs.h): GB300-native deterministic-walk
+optimal T-count synthesis (Di Matteo & Mosca, "Parallelizing quantum circuit
+synthesis", Sec. 2-4).
+
+Argument marshalling only: every step of the search runs in the CUDA kernels
+of ``csrc/``; device buffers are PyTorch CUDA tensors passed by pointer.  There
+is no CPU fallback: importing the binding fails loudly when ``libqcs.so`` has
+not been built (``python -c "import __graft_entry__ as g; g.build()"``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build_mod
+
+__all__ = ["lib", "Params", "Result", "Problem", "default_params", "verify_decomposition",
+           "strerror", "QcsError"]
+
+OK = 0
+ERR_ARG, ERR_NOT_UNITARY, ERR_NOMEM, ERR_CUDA, ERR_MISMATCH, ERR_OVERFLOW, ERR_BUSY, ERR_TIMEOUT, ERR_DEVICE = \
+    -1, -2, -3, -4, -5, -6, -7, -8, -9
+IDLE, SEARCHING, FOUND, BUDGET_EXHAUSTED, CANCELLED, ERROR = range(6)
+MERGE_ROBIN_HOOD, MERGE_TRIVIAL, MERGE_SAME_SIDE, MERGE_CLAW, MERGE_FALSE_HASH, MERGE_NO_MERGE = range(6)
+STATUS_NAMES = {IDLE: "idle", SEARCHING: "searching", FOUND: "found", BUDGET_EXHAUSTED: "budget_exhausted",
+                CANCELLED: "cancelled", ERROR: "error"}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("state_bits", ctypes.c_int32), ("dp_bits", ctypes.c_int32), ("walks", ctypes.c_int32),
+                ("table_log2", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32),
+                ("max_trail_factor", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
+                ("budget_factor", ctypes.c_int32), ("theta_policy", ctypes.c_int32),
+                ("version_factor", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("error", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("t_count", ctypes.c_int32), ("paulis", ctypes.c_uint32 * 16), ("sde", ctypes.c_int32),
+                ("version", ctypes.c_uint32), ("steps", ctypes.c_int64), ("dps", ctypes.c_int64),
+                ("merges", ctypes.c_int64), ("robin_hood", ctypes.c_int64), ("trivial", ctypes.c_int64),
+                ("same_side", ctypes.c_int64), ("claws", ctypes.c_int64), ("false_hash", ctypes.c_int64),
+                ("no_merge", ctypes.c_int64), ("abandoned", ctypes.c_int64), ("dropped", ctypes.c_int64),
+                ("queue_overflow", ctypes.c_int64), ("launches", ctypes.c_int64), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["paulis"] = [int(v) for v in self.paulis[: max(self.t_count, 0)]]
+        d["status_name"] = STATUS_NAMES.get(self.status, "?")
+        return d
+
+
+class QcsError(RuntimeError):
+    def __init__(self, code, where=""):
+        msg = strerror(code)
+        if code == ERR_CUDA:
+            msg += ": " + lib().qcs_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg} ({code})" if where else f"{msg} ({code})")
+        self.code = code
+
+
+_lib = None
+_vp, _sz = ctypes.c_void_p, ctypes.c_size_t
+_i32, _u32, _u64, _i64 = ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64
+
+
+def lib():
+    """The loaded libqcs.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = _build_mod.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libqcs.so is missing at {path}; build it with __graft_entry__.build() "
+                               "(the CUDA library is required, there is no CPU fallback)")
+        L = ctypes.CDLL(path)
+        sig = {
+            "qcs_default_params": (None, [ctypes.c_int, ctypes.POINTER(Params)]),
+            "qcs_create_problem": (ctypes.c_int, [ctypes.c_int, _vp, _i32, ctypes.c_int, ctypes.POINTER(Params),
+                                                  ctypes.POINTER(_vp)]),
+            "qcs_create_problem_channel": (ctypes.c_int, [ctypes.c_int, _vp, _i32, ctypes.c_int,
+                                                          ctypes.POINTER(Params), ctypes.POINTER(_vp)]),
+            "qcs_create_problem_circuit": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int,
+                                                          ctypes.POINTER(Params), ctypes.POINTER(_vp)]),
+            "qcs_run_walks": (ctypes.c_int, [_vp, _u64, _vp]),
+            "qcs_poll_collisions": (ctypes.c_int, [_vp, ctypes.POINTER(Result)]),
+            "qcs_wait": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(Result)]),
+            "qcs_cancel": (ctypes.c_int, [_vp]),
+            "qcs_get_clifford": (ctypes.c_int, [_vp, _vp, _vp]),
+            "qcs_verify_decomposition": (ctypes.c_int, [ctypes.c_int, _vp, _i32, _vp, ctypes.c_int]),
+            "qcs_walk_step": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u32, _vp, _vp, _vp, _sz, _vp]),
+            "qcs_rewalk": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u32, _vp, _vp, _vp, _vp, _sz, _vp,
+                                          _vp, _vp]),
+            "qcs_problem_sde": (ctypes.c_int, [_vp]),
+            "qcs_level_points": (_u64, [_vp, ctypes.c_int]),
+            "qcs_get_channel": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(_i32)]),
+            "qcs_destroy_problem": (None, [_vp]),
+            "qcs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "qcs_last_cuda_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().qcs_strerror(int(code)).decode()
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise QcsError(rc, where)
+
+
+def default_params(n: int, **overrides) -> Params:
+    p = Params()
+    lib().qcs_default_params(int(n), ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    """Device pointer of a CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+class Problem:
+    """One target; owns its device memory (freed by close())."""
+
+    def __init__(self, handle, n, k_max):
+        self._h = handle
+        self.n, self.k_max = n, k_max
+
+    # ---- construction -------------------------------------------------
+    @classmethod
+    def from_circuit(cls, n, gates, k_max, params: Params | None = None):
+        g = np.ascontiguousarray(np.asarray(gates, np.int32).reshape(-1, 3))
+        h = _vp()
+        rc = lib().qcs_create_problem_circuit(int(n), g.ctypes.data_as(_vp), len(g), int(k_max),
+                                              ctypes.byref(params) if params is not None else None, ctypes.byref(h))
+        _check(rc, "qcs_create_problem_circuit")
+        return cls(h, n, k_max)
+
+    @classmethod
+    def from_unitary(cls, n, target, exp, k_max, params: Params | None = None):
+        u = np.ascontiguousarray(np.asarray(target, np.int64))
+        h = _vp()
+        rc = lib().qcs_create_problem(int(n), u.ctypes.data_as(_vp), int(exp), int(k_max),
+                                      ctypes.byref(params) if params is not None else None, ctypes.byref(h))
+        _check(rc, "qcs_create_problem")
+        return cls(h, n, k_max)
+
+    @classmethod
+    def from_channel(cls, n, a, b, exp, k_max, params: Params | None = None):
+        ab = np.ascontiguousarray(np.stack([np.asarray(a, np.int64), np.asarray(b, np.int64)], axis=-1))
+        h = _vp()
+        rc = lib().qcs_create_problem_channel(int(n), ab.ctypes.data_as(_vp), int(exp), int(k_max),
+                                              ctypes.byref(params) if params is not None else None, ctypes.byref(h))
+        _check(rc, "qcs_create_problem_channel")
+        return cls(h, n, k_max)
+
+    # ---- facts -----------------------------------------------------------
+    @property
+    def sde(self) -> int:
+        return int(lib().qcs_problem_sde(self._h))
+
+    def level_points(self, k: int) -> int:
+        return int(lib().qcs_level_points(self._h, int(k)))
+
+    def channel(self):
+        D = 4 ** self.n
+        a = np.zeros((D, D), np.int64)
+        b = np.zeros((D, D), np.int64)
+        e = _i32(0)
+        _check(lib().qcs_get_channel(self._h, a.ctypes.data_as(_vp), b.ctypes.data_as(_vp), ctypes.byref(e)),
+               "qcs_get_channel")
+        return a, b, int(e.value)
+
+    # ---- device entry points --------------------------------------------
+    def walk_step(self, k, chunk, version, states, out, is_dp=None, stream=None):
+        """out = f(states) on the device; tensors are int64 (bit patterns of uint64)."""
+        rc = lib().qcs_walk_step(self._h, int(k), int(chunk), int(version), _ptr(states), _ptr(out),
+                                 _ptr(is_dp), states.numel(), _stream(stream))
+        _check(rc, "qcs_walk_step")
+
+    def rewalk(self, k, chunk, version, start_a, len_a, start_b, len_b, cls, ab, stream=None):
+        rc = lib().qcs_rewalk(self._h, int(k), int(chunk), int(version), _ptr(start_a), _ptr(len_a),
+                              _ptr(start_b), _ptr(len_b), start_a.numel(), _ptr(cls), _ptr(ab), _stream(stream))
+        _check(rc, "qcs_rewalk")
+
+    def run_walks(self, step_budget: int = 0, stream=None):
+        _check(lib().qcs_run_walks(self._h, int(step_budget), _stream(stream)), "qcs_run_walks")
+
+    def poll(self) -> dict:
+        r = Result()
+        _check(lib().qcs_poll_collisions(self._h, ctypes.byref(r)), "qcs_poll_collisions")
+        return r.as_dict()
+
+    def wait(self, timeout_ms: int = -1) -> dict:
+        r = Result()
+        rc = lib().qcs_wait(self._h, int(timeout_ms), ctypes.byref(r))
+        if rc not in (OK, ERR_TIMEOUT):
+            _check(rc, "qcs_wait")
+        d = r.as_dict()
+        d["timed_out"] = rc == ERR_TIMEOUT
+        return d
+
+    def cancel(self):
+        _check(lib().qcs_cancel(self._h), "qcs_cancel")
+
+    def clifford(self):
+        D = 4 ** self.n
+        perm = np.zeros(D, np.int32)
+        sign = np.zeros(D, np.int8)
+        _check(lib().qcs_get_clifford(self._h, perm.ctypes.data_as(_vp), sign.ctypes.data_as(_vp)),
+               "qcs_get_clifford")
+        return perm, sign
+
+    def close(self):
+        if self._h:
+            lib().qcs_destroy_problem(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def verify_decomposition(n, target, exp, paulis) -> bool:
+    """Exact host check of C = e^{i phi} R(P_t)..R(P_1) D (no GPU needed)."""
+    u = np.ascontiguousarray(np.asarray(target, np.int64))
+    p = np.ascontiguousarray(np.asarray(paulis, np.uint32))
+    rc = lib().qcs_verify_decomposition(int(n), u.ctypes.data_as(_vp), int(exp),
+                                        p.ctypes.data_as(_vp) if len(p) else None, len(p))
+    if rc == ERR_MISMATCH:
+        return False
+    _check(rc, "qcs_verify_decomposition")
+    return True

@@ -1,0 +1,127 @@
+// qcs_internal.h -- structures shared by the host library (qcs_api.cpp,
+// qcs_exact.cpp) and the CUDA kernels (qcs_walk.cu).  Not part of the ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace qcs {
+
+constexpr int kMaxH = 8;              // h = floor(k/2) <= 7 for k <= 15
+constexpr uint64_t kEmptyKey = ~0ull; // empty table slot / unwritten meta
+
+// Hash constants of the walk function (written specification, Sec. 2 "h"):
+// SplitMix64 output function (Steele, Lea & Flood 2014), its stream increment,
+// and two seeds taken from the fractional parts of sqrt2 and sqrt3.
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kSeedU = 0x6A09E667F3BCC908ull;
+constexpr uint64_t kSeedH = 0xBB67AE8584CAA73Bull;
+
+// Everything a warp needs to evaluate one step f of the walk at one level.
+struct LevelCtx {
+    const uint2 *C32;  // C^ numerators mod 2^32, (a, b), 4^n x 4^n row-major
+    const uint2 *U;    // fingerprint weights (Ua, Ub) per row, 4^n
+    uint64_t xi_h;     // xi^h, the number of rotation tuples per side
+    uint64_t maskL;    // low L bits
+    uint32_t xi;       // 4^n - 1
+    int32_t n, k, h, K;
+    int32_t ev;        // V side is raised from exponent h to K: ev = K - h
+    int32_t dshift;    // distinguished iff (x >> dshift) == 0, dshift = L - d_theta
+    uint32_t version;
+};
+
+// One distinguished point (Sec. 3: start, end, length).  32 bytes.
+struct Slot {
+    unsigned long long key;   // the distinguished state, kEmptyKey when free
+    unsigned long long start; // first state of the trail
+    unsigned long long meta;  // len | chunk << 32; kEmptyKey until published
+    unsigned long long pad;
+};
+
+// Two trails that reached one distinguished point with different starts.
+struct Pair {
+    unsigned long long start_a, start_b, dp;
+    uint32_t len_a, len_b, chunk, pad;
+};
+
+struct RewalkOut {
+    int32_t cls;    // QCS_MERGE_* (claw = candidate before the exact check)
+    uint32_t chunk; // chunk of the pair (odd k)
+    unsigned long long a, b;
+};
+
+// Per-walk state kept in device memory between launches.  32 bytes.
+struct WalkState {
+    unsigned long long start, cur;
+    uint32_t len, chunk, seq, pad;
+};
+
+enum Counter {
+    C_STEPS = 0,
+    C_WSTEPS,      // steps on the W side (these do the 4^n x 4^n contraction)
+    C_DPS,
+    C_ABANDONED,
+    C_DROPPED,
+    C_DUPLICATE,
+    C_PAIRS,       // collisions pushed (including overflowed ones)
+    C_WAIT_TIMEOUT,
+    C_NCOUNTERS = 16
+};
+
+struct WalkLaunch {
+    LevelCtx lv;
+    WalkState *walks;
+    int32_t n_walks;
+    int32_t n_chunks;   // xi for odd k, 0 for even k
+    uint32_t steps;     // steps per walk in this launch
+    uint32_t max_len;
+    uint64_t seed;
+    Slot *table;
+    uint64_t table_mask;
+    Pair *queue;
+    uint32_t *qhead;
+    uint32_t qcap;
+    unsigned long long *counters;
+};
+
+// ---- kernel launchers (qcs_walk.cu); all return cudaError_t of the launch ----
+cudaError_t launch_walk_step(const LevelCtx &lv, int chunk, const uint64_t *in, uint64_t *out,
+                             uint8_t *is_dp, size_t count, cudaStream_t s);
+cudaError_t launch_init_walks(const WalkLaunch &w, cudaStream_t s);
+cudaError_t launch_walks(const WalkLaunch &w, cudaStream_t s);
+cudaError_t launch_rewalk_pairs(const LevelCtx &lv, const Pair *pairs, const uint32_t *qhead,
+                                uint32_t qcap, RewalkOut *out, cudaStream_t s);
+cudaError_t launch_rewalk_arrays(const LevelCtx &lv, int chunk, const uint64_t *sa, const uint32_t *la,
+                                 const uint64_t *sb, const uint32_t *lb, size_t count, int32_t *cls,
+                                 uint64_t *ab, cudaStream_t s);
+// number of resident CTAs of the walk kernel per SM for n qubits (occupancy)
+int walk_blocks_per_sm(int n);
+int num_sms();
+
+// ---- exact host arithmetic (qcs_exact.cpp) ----
+// A matrix over Z[1/sqrt2]: (a + b sqrt2) / sqrt2^E, D x D row-major.
+struct PMat {
+    int D = 0, E = 0;
+    std::vector<int64_t> a, b;
+};
+
+// status codes mirror qcs.h; overflow is reported, never wraps
+int exact_channel_from_unitary(int n, const int64_t *u, int e, PMat *out);
+int exact_unitary_from_circuit(int n, const int32_t *gates, int n_gates, std::vector<int64_t> *u, int *e);
+int exact_check_channel(int n, const PMat &C);
+void exact_reduce(PMat *M);
+bool exact_is_clifford(const PMat &M);
+// left-multiply by R^(p) (transpose = false) or R^(p)^T (true); exponent + 1
+int exact_rhat_left(int n, uint32_t p, bool transpose, const PMat &M, PMat *out);
+// D^ = R^(P_1)^T .. R^(P_t)^T C^; QCS_OK if a signed permutation, else QCS_ERR_MISMATCH
+int exact_verify(int n, const PMat &C, const uint32_t *paulis, int t, PMat *Dout);
+// are V_qv and W_qw (level k, chunk) one Clifford coset?  (exact canonical forms)
+int exact_same_coset(int n, const PMat &C, int k, int chunk, const uint32_t *qv, const uint32_t *qw,
+                     bool *equal);
+int pauli_phase(int n, uint32_t p, uint32_t q); // P(p)P(q) = i^lambda P(p^q)
+
+} // namespace qcs

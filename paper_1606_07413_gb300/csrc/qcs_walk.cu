@@ -1,0 +1,630 @@
+// qcs_walk.cu -- the walk step, distinguished-point table and re-walk kernels
+// of the deterministic-walk T-count search (Di Matteo & Mosca, Sec. 2-3),
+// hand-written for sm_103a.
+//
+// One warp evaluates one step f = h o nu o mu of one walk (Sec. 2, Fig. 1):
+//   mu : decode the state into a side b and rotations q_1..q_h (Sec. 3, z_b);
+//   nu : the exact product V = R^(q_h)..R^(q_1) or W = R^(q_1)^T..R^(q_h)^T
+//        [R^(c)^T] C^ over Z[1/sqrt2] (Eq. mitm in channel form), taken modulo
+//        right multiplication by Cliffords (Eq. tcount_synthesis);
+//   h  : a coset-invariant hash back to an L-bit state.
+//
+// The hash is defined on the exact product M at exponent K: every column Q
+// gets the 32-bit linear fingerprint L_Q = sum_i Ua[i] a_iQ + Ub[i] b_iQ mod
+// 2^32, folded to phi_Q = min(L_Q, -L_Q) (so a column's sign does not matter),
+// and the sorted phi are hashed.  Because L is linear in M's integer
+// numerators and every factor acts linearly on them, L(M e_Q) =
+// ((adjoint network) U)^T (M's right factor) e_Q: the kernel pushes the weight
+// vector U through the transposed sparse R^ butterflies (4^n entries, h
+// stages) instead of pushing all 4^n - 1 columns through them.  The V side is
+// then read off directly (its right factor is the identity), and the W side is
+// one contraction of the transformed weights with C^, staged in shared memory.
+// The result is bit-identical to hashing the explicitly formed product.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "qcs_internal.h"
+
+namespace qcs {
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kMaxProbe = 16;
+constexpr int kSpinLimit = 1 << 14;
+constexpr uint32_t kMaxRewalkLen = 1u << 20; // longer trails are reported as no merge
+
+__device__ __forceinline__ uint64_t smix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <int NQ>
+struct Geo {
+    static constexpr int DIM = 1 << (2 * NQ);       // 4^n rows and columns
+    static constexpr int D = DIM - 1;               // non-identity Paulis
+    static constexpr int RPL = DIM >= 32 ? DIM / 32 : 1; // rows (and columns) per lane
+    static constexpr int SLOTS = RPL * 32;          // width of the fingerprint sort
+    static constexpr bool C_SMEM = NQ <= 3;         // C^ staged whole in shared memory
+    static constexpr size_t smem_bytes =
+        sizeof(uint2) * (DIM + (C_SMEM ? DIM * DIM : 0) + kWarps * DIM);
+};
+
+__device__ __forceinline__ uint32_t shl32(uint32_t v, int s) { return s >= 32 ? 0u : v << s; }
+
+// anticommutation of P(p), P(j) and the sign s(p, j) in
+// R(P_p) P_j R(P_p)^dag = (P_j + s P_{p^j}) / sqrt2  (Sec. 4.1)
+template <int NQ>
+__device__ __forceinline__ void rot_coef(uint32_t p, uint32_t j, bool &anti, bool &plus)
+{
+    constexpr uint32_t m = (1u << NQ) - 1;
+    const uint32_t px = p >> NQ, pz = p & m, jx = j >> NQ, jz = j & m;
+    anti = (__popc((px & jz) ^ (pz & jx)) & 1) != 0;
+    const uint32_t rx = px ^ jx, rz = pz ^ jz;
+    const int lam = (__popc(px & pz) + __popc(jx & jz) + 2 * __popc(pz & jx) - __popc(rx & rz)) & 3;
+    plus = (lam == 1);
+}
+
+// One adjoint butterfly stage on the weight vector held by the warp (row
+// j = lane + 32 t in registers ua/ub; su is the warp's exchange buffer).
+// The forward R^(p) maps a row that commutes with p to sqrt2 times itself,
+// (a, b) -> (2b, a), and an anticommuting row i to M_i + s(p, i^p) M_{i^p};
+// R^(p)^T uses s(p, i) instead, and s(p, i^p) = -s(p, i).  The adjoints are
+// (ua, ub) -> (ub, 2 ua) on commuting rows and u_j + s(p, j) u_{j^p}
+// (adjoint of R^) or u_j - s(p, j) u_{j^p} (adjoint of R^T) on the others.
+template <int NQ, bool ADJ_OF_TRANSPOSE>
+__device__ __forceinline__ void adj_stage(uint32_t p, uint32_t (&ua)[Geo<NQ>::RPL],
+                                          uint32_t (&ub)[Geo<NQ>::RPL], uint2 *su, int lane)
+{
+    using G = Geo<NQ>;
+#pragma unroll
+    for (int t = 0; t < G::RPL; t++) {
+        const int j = lane + 32 * t;
+        if (G::DIM >= 32 || j < G::DIM) su[j] = make_uint2(ua[t], ub[t]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < G::RPL; t++) {
+        const int j = lane + 32 * t;
+        if (G::DIM >= 32 || j < G::DIM) {
+            bool anti, plus;
+            rot_coef<NQ>(p, (uint32_t)j, anti, plus);
+            const uint2 v = su[j ^ (int)p];
+            const bool add = (plus != ADJ_OF_TRANSPOSE);
+            const uint32_t na = add ? ua[t] + v.x : ua[t] - v.x;
+            const uint32_t nb = add ? ub[t] + v.y : ub[t] - v.y;
+            const uint32_t ca = ub[t], cb = ua[t] << 1;
+            ua[t] = anti ? na : ca;
+            ub[t] = anti ? nb : cb;
+        }
+    }
+    __syncwarp();
+}
+
+struct Decoded {
+    int side;
+    uint64_t r;        // index of the rotation tuple, (x >> 1) mod xi^h
+    uint64_t qpack;    // q_1 .. q_h, 8 bits each (q <= 255)
+};
+
+__device__ __forceinline__ Decoded decode(uint64_t x, const LevelCtx &lv)
+{
+    Decoded d;
+    d.side = (int)(x & 1);
+    d.r = (x >> 1) % lv.xi_h;
+    uint64_t r = d.r;
+    d.qpack = 0;
+    for (int j = 0; j < lv.h; j++) {
+        d.qpack |= (uint64_t)((uint32_t)(r % lv.xi) + 1) << (8 * j);
+        r /= lv.xi;
+    }
+    return d;
+}
+
+// f(x): all 32 lanes call it with the same x; every lane gets the result.
+template <int NQ>
+__device__ uint64_t warp_step(uint64_t x, uint32_t chunk, const LevelCtx &lv, const uint2 *sU,
+                              const uint2 *Cm, uint2 *su, int lane)
+{
+    using G = Geo<NQ>;
+    const Decoded dx = decode(x, lv);
+
+    uint32_t ua[G::RPL], ub[G::RPL];
+#pragma unroll
+    for (int t = 0; t < G::RPL; t++) {
+        const int j = lane + 32 * t;
+        const uint2 u = (G::DIM >= 32 || j < G::DIM) ? sU[j] : make_uint2(0, 0);
+        ua[t] = u.x;
+        ub[t] = u.y;
+    }
+
+    uint32_t Lc[G::RPL];
+    if (dx.side == 0) {
+        // V side at exponent K: S R^(q_h)..R^(q_1) with S = multiply by
+        // sqrt2^ev.  Weights go through S^* first, then R^(q_h)^* .. R^(q_1)^*.
+        const int ev = lv.ev, sh = ev >> 1;
+#pragma unroll
+        for (int t = 0; t < G::RPL; t++) {
+            const uint32_t a = ua[t], b = ub[t];
+            ua[t] = (ev & 1) ? shl32(b, sh) : shl32(a, sh);
+            ub[t] = (ev & 1) ? shl32(a, sh + 1) : shl32(b, sh);
+        }
+        for (int j = lv.h - 1; j >= 0; j--)
+            adj_stage<NQ, false>((uint32_t)(dx.qpack >> (8 * j)) & 0xFFu, ua, ub, su, lane);
+#pragma unroll
+        for (int t = 0; t < G::RPL; t++) Lc[t] = ua[t]; // L(V e_Q) = (U~)_a[Q]
+    } else {
+        // W side: R^(q_1)^T .. R^(q_h)^T [R^(c)^T] C^; weights go through
+        // (R^(q_1)^T)^* first, ..., (R^(q_h)^T)^*, then (R^(c)^T)^*.
+        for (int j = 0; j < lv.h; j++)
+            adj_stage<NQ, true>((uint32_t)(dx.qpack >> (8 * j)) & 0xFFu, ua, ub, su, lane);
+        if (lv.k & 1) adj_stage<NQ, true>(chunk, ua, ub, su, lane);
+#pragma unroll
+        for (int t = 0; t < G::RPL; t++) {
+            const int j = lane + 32 * t;
+            if (G::DIM >= 32 || j < G::DIM) su[j] = make_uint2(ua[t], ub[t]);
+            Lc[t] = 0;
+        }
+        __syncwarp();
+        // L(W e_Q) = sum_i U~_a[i] C_a[i][Q] + U~_b[i] C_b[i][Q]   (rows 1..D)
+#pragma unroll 4
+        for (int i = 1; i < G::DIM; i++) {
+            const uint2 u = su[i];
+#pragma unroll
+            for (int t = 0; t < G::RPL; t++) {
+                const int Q = lane + 32 * t;
+                if (G::DIM >= 32 || Q < G::DIM) {
+                    const uint2 c = Cm[i * G::DIM + Q];
+                    Lc[t] += u.x * c.x + u.y * c.y;
+                }
+            }
+        }
+        __syncwarp();
+    }
+
+    // sign-invariant column fingerprints; column 0 (the identity) and padding
+    // lanes sort last as 0xFFFFFFFF (every phi is at most 2^31)
+    uint32_t key[G::RPL];
+#pragma unroll
+    for (int t = 0; t < G::RPL; t++) {
+        const int Q = lane + 32 * t;
+        const uint32_t l = Lc[t], nl = 0u - l;
+        key[t] = (Q >= 1 && Q <= G::D) ? min(l, nl) : 0xFFFFFFFFu;
+    }
+
+    // bitonic sort of SLOTS keys, element e = 32 t + lane, ascending
+#pragma unroll
+    for (int size = 2; size <= G::SLOTS; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int ts = stride >> 5;
+#pragma unroll
+                for (int t = 0; t < G::RPL; t++) {
+                    if ((t & ts) == 0) {
+                        const int e = 32 * t + lane;
+                        const bool up = (e & size) == 0;
+                        const uint32_t a = key[t], b = key[t | ts];
+                        const uint32_t lo = min(a, b), hi = max(a, b);
+                        key[t] = up ? lo : hi;
+                        key[t | ts] = up ? hi : lo;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < G::RPL; t++) {
+                    const int e = 32 * t + lane;
+                    const uint32_t o = __shfl_xor_sync(kFull, key[t], stride);
+                    const bool up = (e & size) == 0, lower = (e & stride) == 0;
+                    key[t] = (lower == up) ? min(key[t], o) : max(key[t], o);
+                }
+            }
+        }
+    }
+
+    // position-keyed hash of the sorted fingerprints
+    const uint64_t tag = (uint64_t)lv.n | ((uint64_t)lv.k << 8) | ((uint64_t)chunk << 16) |
+                         ((uint64_t)(uint32_t)lv.K << 32);
+    const uint64_t base = smix(smix(kSeedH ^ (uint64_t)lv.version) ^ tag);
+    uint64_t acc = 0;
+#pragma unroll
+    for (int t = 0; t < G::RPL; t++) {
+        const int e = 32 * t + lane;
+        if (e < G::D) acc += smix(base ^ (((uint64_t)e << 32) | key[t]));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+    return smix(acc) & lv.maskL;
+}
+
+// stage the fingerprint weights and (n <= 3) all of C^ into shared memory
+template <int NQ>
+__device__ __forceinline__ void stage(const LevelCtx &lv, uint2 *sU, uint2 *sC)
+{
+    using G = Geo<NQ>;
+    for (int i = threadIdx.x; i < G::DIM; i += blockDim.x) sU[i] = lv.U[i];
+    if (G::C_SMEM)
+        for (int i = threadIdx.x; i < G::DIM * G::DIM; i += blockDim.x) sC[i] = lv.C32[i];
+    __syncthreads();
+}
+
+template <int NQ>
+__global__ void __launch_bounds__(kThreads) k_walk_step(LevelCtx lv, uint32_t chunk, const uint64_t *__restrict__ in,
+                                                        uint64_t *__restrict__ out, uint8_t *__restrict__ is_dp,
+                                                        size_t count)
+{
+    using G = Geo<NQ>;
+    extern __shared__ uint2 smem[];
+    uint2 *sU = smem, *sC = smem + G::DIM, *sW = sC + (G::C_SMEM ? G::DIM * G::DIM : 0);
+    stage<NQ>(lv, sU, sC);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint2 *Cm = G::C_SMEM ? sC : lv.C32;
+    uint2 *su = sW + warp * G::DIM;
+    for (size_t i = (size_t)blockIdx.x * kWarps + warp; i < count; i += (size_t)gridDim.x * kWarps) {
+        const uint64_t y = warp_step<NQ>(in[i], chunk, lv, sU, Cm, su, lane);
+        if (lane == 0) {
+            out[i] = y;
+            if (is_dp) is_dp[i] = (uint8_t)((y >> lv.dshift) == 0);
+        }
+    }
+}
+
+__device__ __forceinline__ void new_trail(WalkState &st, uint32_t walk, const WalkLaunch &w)
+{
+    st.seq++;
+    st.start = smix(w.seed ^ smix(((uint64_t)walk << 32) | st.seq) ^ ((uint64_t)w.lv.version << 40)) & w.lv.maskL;
+    st.cur = st.start;
+    st.len = 0;
+    st.chunk = w.n_chunks ? 1u + (uint32_t)(smix(st.start ^ 0x5851F42D4C957F2Dull) % (uint64_t)w.n_chunks) : 0u;
+}
+
+struct LaneCounters {
+    unsigned long long dropped = 0, duplicate = 0, pairs = 0, timeout = 0;
+};
+
+// Insert (dp, start, len) for one chunk into the open-addressing table
+// (Sec. 3: store when absent; the same end with another start is a merge).
+// Called by one lane.  Every wait is bounded.
+__device__ void dp_insert(const WalkLaunch &w, uint64_t dp, uint32_t chunk, uint64_t start, uint32_t len,
+                          LaneCounters &c)
+{
+    const uint64_t h = smix(dp ^ ((uint64_t)chunk << 52));
+    for (int probe = 0; probe < kMaxProbe; probe++) {
+        Slot *s = &w.table[(h + (uint64_t)probe) & w.table_mask];
+        const unsigned long long old = atomicCAS(&s->key, kEmptyKey, (unsigned long long)dp);
+        if (old == kEmptyKey) {
+            s->start = start;
+            __threadfence();
+            atomicExch(&s->meta, (unsigned long long)len | ((unsigned long long)chunk << 32));
+            return;
+        }
+        if (old != dp) continue;
+        unsigned long long m = kEmptyKey;
+        for (int spin = 0; spin < kSpinLimit; spin++) {
+            m = *(volatile unsigned long long *)&s->meta;
+            if (m != kEmptyKey) break;
+            __nanosleep(64);
+        }
+        if (m == kEmptyKey) {
+            c.timeout++;
+            return;
+        }
+        __threadfence();
+        if ((uint32_t)(m >> 32) != chunk) continue;
+        const unsigned long long other = *(volatile unsigned long long *)&s->start;
+        if (other == start) {
+            c.duplicate++;
+            return;
+        }
+        c.pairs++;
+        const uint32_t idx = atomicAdd(w.qhead, 1u);
+        if (idx < w.qcap) {
+            Pair p;
+            p.start_a = other;
+            p.len_a = (uint32_t)m;
+            p.start_b = start;
+            p.len_b = len;
+            p.dp = dp;
+            p.chunk = chunk;
+            p.pad = 0;
+            w.queue[idx] = p;
+        }
+        return;
+    }
+    c.dropped++;
+}
+
+template <int NQ>
+__global__ void __launch_bounds__(kThreads) k_walks(WalkLaunch w)
+{
+    using G = Geo<NQ>;
+    extern __shared__ uint2 smem[];
+    uint2 *sU = smem, *sC = smem + G::DIM, *sW = sC + (G::C_SMEM ? G::DIM * G::DIM : 0);
+    stage<NQ>(w.lv, sU, sC);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint2 *Cm = G::C_SMEM ? sC : w.lv.C32;
+    uint2 *su = sW + warp * G::DIM;
+    unsigned long long n_steps = 0, n_w = 0, n_dp = 0, n_ab = 0;
+    LaneCounters c;
+    for (int walk = blockIdx.x * kWarps + warp; walk < w.n_walks; walk += gridDim.x * kWarps) {
+        WalkState st = w.walks[walk];
+        for (uint32_t s = 0; s < w.steps; s++) {
+            const uint64_t y = warp_step<NQ>(st.cur, st.chunk, w.lv, sU, Cm, su, lane);
+            n_steps++;
+            n_w += st.cur & 1;
+            st.len++;
+            if ((y >> w.lv.dshift) == 0) {
+                n_dp++;
+                if (lane == 0) dp_insert(w, y, st.chunk, st.start, st.len, c);
+                __syncwarp();
+                new_trail(st, (uint32_t)walk, w);
+            } else if (st.len >= w.max_len) {
+                n_ab++;
+                new_trail(st, (uint32_t)walk, w);
+            } else {
+                st.cur = y;
+            }
+        }
+        if (lane == 0) w.walks[walk] = st;
+    }
+    if (lane == 0) {
+        atomicAdd(&w.counters[C_STEPS], n_steps);
+        atomicAdd(&w.counters[C_WSTEPS], n_w);
+        atomicAdd(&w.counters[C_DPS], n_dp);
+        atomicAdd(&w.counters[C_ABANDONED], n_ab);
+        if (c.dropped) atomicAdd(&w.counters[C_DROPPED], c.dropped);
+        if (c.duplicate) atomicAdd(&w.counters[C_DUPLICATE], c.duplicate);
+        if (c.pairs) atomicAdd(&w.counters[C_PAIRS], c.pairs);
+        if (c.timeout) atomicAdd(&w.counters[C_WAIT_TIMEOUT], c.timeout);
+    }
+}
+
+__global__ void k_init_walks(WalkLaunch w)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.n_walks) return;
+    WalkState st;
+    st.seq = 0;
+    st.pad = 0;
+    new_trail(st, (uint32_t)i, w);
+    w.walks[i] = st;
+}
+
+// Sec. 3, Fig. 2: align the longer trail, step both until the images agree,
+// and classify the two distinct preimages.  Lengths are bounded by the
+// maximum trail length, so both loops end.
+template <int NQ>
+__device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa, uint32_t la, uint64_t sb,
+                                uint32_t lb, const uint2 *sU, const uint2 *Cm, uint2 *su, int lane)
+{
+    RewalkOut r;
+    r.chunk = chunk;
+    if (la > kMaxRewalkLen || lb > kMaxRewalkLen) {
+        r.cls = 5;
+        r.a = sa;
+        r.b = sb;
+        return r;
+    }
+    if (la < lb) {
+        uint64_t tx = sa; sa = sb; sb = tx;
+        uint32_t tl = la; la = lb; lb = tl;
+    }
+    uint64_t a = sa, b = sb;
+    for (uint32_t s = 0; s < la - lb; s++) a = warp_step<NQ>(a, chunk, lv, sU, Cm, su, lane);
+    if (a == b) {
+        r.cls = 0; // Robin Hood
+        r.a = r.b = a;
+        return r;
+    }
+    for (uint32_t s = 0; s < lb; s++) {
+        const uint64_t fa = warp_step<NQ>(a, chunk, lv, sU, Cm, su, lane);
+        const uint64_t fb = warp_step<NQ>(b, chunk, lv, sU, Cm, su, lane);
+        if (fa == fb) {
+            const Decoded da = decode(a, lv), db = decode(b, lv);
+            r.a = a;
+            r.b = b;
+            if (da.side == db.side) r.cls = (da.r == db.r) ? 1 : 2; // trivial / same side
+            else r.cls = 3;                                          // claw candidate
+            return r;
+        }
+        a = fa;
+        b = fb;
+    }
+    r.cls = 5; // no merge
+    r.a = a;
+    r.b = b;
+    return r;
+}
+
+template <int NQ>
+__global__ void __launch_bounds__(kThreads) k_rewalk_pairs(LevelCtx lv, const Pair *__restrict__ pairs,
+                                                           const uint32_t *__restrict__ qhead, uint32_t qcap,
+                                                           RewalkOut *__restrict__ out)
+{
+    using G = Geo<NQ>;
+    extern __shared__ uint2 smem[];
+    uint2 *sU = smem, *sC = smem + G::DIM, *sW = sC + (G::C_SMEM ? G::DIM * G::DIM : 0);
+    const uint32_t cnt = min(*qhead, qcap);
+    if (cnt == 0) return;
+    stage<NQ>(lv, sU, sC);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint2 *Cm = G::C_SMEM ? sC : lv.C32;
+    uint2 *su = sW + warp * G::DIM;
+    for (uint32_t p = blockIdx.x * kWarps + warp; p < cnt; p += gridDim.x * kWarps) {
+        const Pair P = pairs[p];
+        const RewalkOut r = rewalk_one<NQ>(lv, P.chunk, P.start_a, P.len_a, P.start_b, P.len_b, sU, Cm, su, lane);
+        if (lane == 0) out[p] = r;
+    }
+}
+
+template <int NQ>
+__global__ void __launch_bounds__(kThreads) k_rewalk_arrays(LevelCtx lv, uint32_t chunk, const uint64_t *sa,
+                                                            const uint32_t *la, const uint64_t *sb,
+                                                            const uint32_t *lb, size_t count, int32_t *cls,
+                                                            uint64_t *ab)
+{
+    using G = Geo<NQ>;
+    extern __shared__ uint2 smem[];
+    uint2 *sU = smem, *sC = smem + G::DIM, *sW = sC + (G::C_SMEM ? G::DIM * G::DIM : 0);
+    stage<NQ>(lv, sU, sC);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint2 *Cm = G::C_SMEM ? sC : lv.C32;
+    uint2 *su = sW + warp * G::DIM;
+    for (size_t p = (size_t)blockIdx.x * kWarps + warp; p < count; p += (size_t)gridDim.x * kWarps) {
+        const RewalkOut r = rewalk_one<NQ>(lv, chunk, sa[p], la[p], sb[p], lb[p], sU, Cm, su, lane);
+        if (lane == 0) {
+            cls[p] = r.cls;
+            ab[2 * p] = r.a;
+            ab[2 * p + 1] = r.b;
+        }
+    }
+}
+
+int g_num_sms = 0;
+
+template <int NQ>
+int blocks_per_sm()
+{
+    static int cached = 0;
+    if (!cached) {
+        cudaFuncSetAttribute(k_walks<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<NQ>::smem_bytes);
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walks<NQ>, kThreads, Geo<NQ>::smem_bytes);
+        cached = b > 0 ? b : 1;
+    }
+    return cached;
+}
+
+template <int NQ>
+unsigned grid_for(size_t warps_needed)
+{
+    const size_t cap = (size_t)num_sms() * (size_t)blocks_per_sm<NQ>();
+    size_t g = (warps_needed + kWarps - 1) / kWarps;
+    if (g > cap) g = cap;
+    if (g == 0) g = 1;
+    return (unsigned)g;
+}
+
+template <int NQ>
+cudaError_t walk_step_n(const LevelCtx &lv, int chunk, const uint64_t *in, uint64_t *out, uint8_t *is_dp,
+                        size_t count, cudaStream_t s)
+{
+    cudaFuncSetAttribute(k_walk_step<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<NQ>::smem_bytes);
+    k_walk_step<NQ><<<grid_for<NQ>(count), kThreads, Geo<NQ>::smem_bytes, s>>>(lv, (uint32_t)chunk, in, out, is_dp,
+                                                                               count);
+    return cudaGetLastError();
+}
+
+template <int NQ>
+cudaError_t walks_n(const WalkLaunch &w, cudaStream_t s)
+{
+    k_walks<NQ><<<grid_for<NQ>((size_t)w.n_walks), kThreads, Geo<NQ>::smem_bytes, s>>>(w);
+    return cudaGetLastError();
+}
+
+template <int NQ>
+cudaError_t rewalk_pairs_n(const LevelCtx &lv, const Pair *pairs, const uint32_t *qhead, uint32_t qcap,
+                           RewalkOut *out, cudaStream_t s)
+{
+    cudaFuncSetAttribute(k_rewalk_pairs<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)Geo<NQ>::smem_bytes);
+    k_rewalk_pairs<NQ><<<grid_for<NQ>(qcap), kThreads, Geo<NQ>::smem_bytes, s>>>(lv, pairs, qhead, qcap, out);
+    return cudaGetLastError();
+}
+
+template <int NQ>
+cudaError_t rewalk_arrays_n(const LevelCtx &lv, int chunk, const uint64_t *sa, const uint32_t *la,
+                            const uint64_t *sb, const uint32_t *lb, size_t count, int32_t *cls, uint64_t *ab,
+                            cudaStream_t s)
+{
+    cudaFuncSetAttribute(k_rewalk_arrays<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)Geo<NQ>::smem_bytes);
+    k_rewalk_arrays<NQ><<<grid_for<NQ>(count), kThreads, Geo<NQ>::smem_bytes, s>>>(lv, (uint32_t)chunk, sa, la,
+                                                                                   sb, lb, count, cls, ab);
+    return cudaGetLastError();
+}
+
+} // namespace
+
+int num_sms()
+{
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+int walk_blocks_per_sm(int n)
+{
+    switch (n) {
+    case 1: return blocks_per_sm<1>();
+    case 2: return blocks_per_sm<2>();
+    case 3: return blocks_per_sm<3>();
+    default: return blocks_per_sm<4>();
+    }
+}
+
+cudaError_t launch_walk_step(const LevelCtx &lv, int chunk, const uint64_t *in, uint64_t *out, uint8_t *is_dp,
+                             size_t count, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    switch (lv.n) {
+    case 1: return walk_step_n<1>(lv, chunk, in, out, is_dp, count, s);
+    case 2: return walk_step_n<2>(lv, chunk, in, out, is_dp, count, s);
+    case 3: return walk_step_n<3>(lv, chunk, in, out, is_dp, count, s);
+    case 4: return walk_step_n<4>(lv, chunk, in, out, is_dp, count, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_init_walks(const WalkLaunch &w, cudaStream_t s)
+{
+    k_init_walks<<<(w.n_walks + 255) / 256, 256, 0, s>>>(w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_walks(const WalkLaunch &w, cudaStream_t s)
+{
+    switch (w.lv.n) {
+    case 1: return walks_n<1>(w, s);
+    case 2: return walks_n<2>(w, s);
+    case 3: return walks_n<3>(w, s);
+    case 4: return walks_n<4>(w, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_rewalk_pairs(const LevelCtx &lv, const Pair *pairs, const uint32_t *qhead, uint32_t qcap,
+                                RewalkOut *out, cudaStream_t s)
+{
+    switch (lv.n) {
+    case 1: return rewalk_pairs_n<1>(lv, pairs, qhead, qcap, out, s);
+    case 2: return rewalk_pairs_n<2>(lv, pairs, qhead, qcap, out, s);
+    case 3: return rewalk_pairs_n<3>(lv, pairs, qhead, qcap, out, s);
+    case 4: return rewalk_pairs_n<4>(lv, pairs, qhead, qcap, out, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_rewalk_arrays(const LevelCtx &lv, int chunk, const uint64_t *sa, const uint32_t *la,
+                                 const uint64_t *sb, const uint32_t *lb, size_t count, int32_t *cls, uint64_t *ab,
+                                 cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    switch (lv.n) {
+    case 1: return rewalk_arrays_n<1>(lv, chunk, sa, la, sb, lb, count, cls, ab, s);
+    case 2: return rewalk_arrays_n<2>(lv, chunk, sa, la, sb, lb, count, cls, ab, s);
+    case 3: return rewalk_arrays_n<3>(lv, chunk, sa, la, sb, lb, count, cls, ab, s);
+    case 4: return rewalk_arrays_n<4>(lv, chunk, sa, la, sb, lb, count, cls, ab, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+} // namespace qcs

@@ -1,0 +1,113 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point include/qcs.h declares, and its exact host paths
+(verification, input validation) agree with the oracle."""
+import re
+
+import numpy as np
+import pytest
+
+import paper_1606_07413_gb300 as Q
+from paper_1606_07413_gb300 import workloads as W
+from paper_1606_07413_gb300 import build as B
+
+
+@pytest.fixture(scope="module")
+def qlib():
+    B.build()
+    return Q.lib()
+
+
+def declared_symbols():
+    hdr = open(B.os.path.join(B.INCLUDE, "qcs.h")).read()
+    return sorted(set(re.findall(r"QCS_API\s+[^;(]*?\b(qcs_[a-z_]+)\s*\(", hdr, flags=re.S)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ["qcs_create_problem", "qcs_create_problem_channel", "qcs_run_walks", "qcs_poll_collisions",
+                 "qcs_verify_decomposition", "qcs_walk_step", "qcs_destroy_problem", "qcs_strerror"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(qlib):
+    import subprocess
+
+    out = subprocess.check_output(["nm", "-D", "--defined-only", B.LIB]).decode()
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    for name in declared_symbols():
+        assert name in exported, name
+        assert hasattr(qlib, name)
+    # nothing but the ABI leaks out
+    assert all(s.startswith("qcs_") for s in exported if not s.startswith("_"))
+
+
+def test_strerror_and_defaults(qlib):
+    for code in range(0, -10, -1):
+        assert Q.strerror(code)
+    for n, L in ((2, 32), (3, 48), (4, 64)):
+        p = Q.default_params(n)
+        assert p.state_bits == L and p.walks >= 4096
+
+
+def test_verify_decomposition_host_exact(qlib, orc):
+    gates, _ = W.config_target(1)
+    u, e = orc.unitary_from_circuit(2, gates)
+    C = orc.channel_from_circuit(2, gates)
+    t, p = orc.mitm_tcount(C, 3)
+    assert Q.verify_decomposition(2, u, e, p)
+    bad = list(p)
+    bad[-1] = bad[-1] % 15 + 1
+    assert not Q.verify_decomposition(2, u, e, bad)
+    assert not Q.verify_decomposition(2, u, e, [])
+
+
+def test_verify_agrees_with_oracle_on_random_sequences(qlib, orc):
+    rng = np.random.default_rng(4)
+    for trial in range(20):
+        n = 2 if trial % 2 else 3
+        ps = [int(v) for v in rng.integers(1, 4 ** n, size=3)]
+        rows = [tuple(r) for r in W.clifford_word(rng, n, 20)] + [(W.OP_RP, p, 0) for p in ps]
+        u, e = orc.unitary_from_circuit(n, np.asarray(rows, np.int32))
+        C = orc.channel_from_circuit(n, np.asarray(rows, np.int32))
+        cand = ps if trial % 3 else [int(v) for v in rng.integers(1, 4 ** n, size=3)]
+        assert Q.verify_decomposition(n, u, e, cand) == orc.verify(C, cand)
+
+
+def test_create_problem_rejects_bad_input_before_any_device_work(qlib):
+    d = 4
+    u = np.zeros((d, d, 4), np.int64)
+    for i in range(d):
+        u[i, i, 0] = 1
+    u[0, 1, 0] = 1  # not unitary
+    with pytest.raises(Q.QcsError) as ei:
+        Q.Problem.from_unitary(2, u, 0, 3)
+    assert ei.value.code == Q.ERR_NOT_UNITARY
+    with pytest.raises(Q.QcsError) as ei:
+        Q.Problem.from_circuit(5, [(W.OP_H, 0, 0)], 3)
+    assert ei.value.code == Q.ERR_ARG
+    with pytest.raises(Q.QcsError) as ei:
+        Q.Problem.from_circuit(2, [(W.OP_CNOT, 0, 0)], 3)
+    assert ei.value.code == Q.ERR_ARG
+    with pytest.raises(Q.QcsError) as ei:
+        Q.Problem.from_circuit(2, [(W.OP_H, 0, 0)], 16)
+    assert ei.value.code == Q.ERR_ARG
+    p = Q.default_params(2, dp_bits=40)  # d_theta >= L
+    with pytest.raises(Q.QcsError) as ei:
+        Q.Problem.from_circuit(2, [(W.OP_H, 0, 0)], 3, p)
+    assert ei.value.code == Q.ERR_ARG
+    # a channel that is not orthogonal
+    D = 16
+    a = np.eye(D, dtype=np.int64)
+    a[3, 4] = 1
+    with pytest.raises(Q.QcsError) as ei:
+        Q.Problem.from_channel(2, a, np.zeros_like(a), 0, 3)
+    assert ei.value.code == Q.ERR_NOT_UNITARY
+
+
+def test_verify_rejects_bad_arguments(qlib):
+    u = np.zeros((4, 4, 4), np.int64)
+    for i in range(4):
+        u[i, i, 0] = 1
+    with pytest.raises(Q.QcsError):
+        Q.verify_decomposition(2, u, 0, [16])
+    assert Q.verify_decomposition(2, u, 0, [])
