@@ -95,6 +95,9 @@ typedef struct qcs_params {
     int32_t budget_factor;    /* a level gives up after budget_factor * (points at that level) steps */
     int32_t theta_policy;     /* 0: d_theta fixed; 1: raise theta on small levels (time to solution) */
     int32_t version_factor;   /* new function version every version_factor * points steps (0: never) */
+    int32_t stop_on_claw;     /* 1: stop at the first verified claw; 0: keep walking to the step budget
+                                 (the first decomposition is still reported) */
+    int32_t reserved;
     uint64_t seed;            /* seed of trail starting points */
 } qcs_params;
 
@@ -115,6 +118,7 @@ typedef struct qcs_result {
     int64_t queue_overflow;
     int64_t launches;    /* walk-kernel launches */
     double seconds;      /* wall time since qcs_run_walks */
+    int64_t w_steps;     /* walk steps taken on the W side (the 4^n x 4^n contraction) */
 } qcs_result;
 
 typedef struct qcs_problem qcs_problem;
@@ -166,6 +170,30 @@ QCS_API int qcs_cancel(qcs_problem *prob);
 /* Once FOUND: the Clifford D of Eq. tcount_synthesis as a signed permutation of
  * Pauli codes, D P_j D^dag = sign[j] P_perm[j] (arrays of 4^n entries). */
 QCS_API int qcs_get_clifford(qcs_problem *prob, int32_t *perm, int8_t *sign);
+
+/* Manual stepping of one level of the search (qcs_run_walks drives these
+ * from its own thread; do not mix the two on one problem while a search runs:
+ * QCS_ERR_BUSY).  All are asynchronous on `stream` except qcs_level_collect.
+ *
+ * qcs_level_begin: clear the distinguished-point table and start a fresh
+ * trail on every walk at level k (2 <= k <= k_max), function version
+ * `version`, distinguished-point exponent dp_bits (0 = params.dp_bits). */
+QCS_API int qcs_level_begin(qcs_problem *prob, int k, uint32_t version, int dp_bits, void *stream);
+
+/* Every walk advances `steps` steps (Sec. 3 trails); a trail that reaches a
+ * distinguished point is stored in (or merged against) the table and a new
+ * trail starts; merges with another start are queued. */
+QCS_API int qcs_level_walk(qcs_problem *prob, uint32_t steps, void *stream);
+
+/* Re-walk every queued merge on the device (Fig. 2) and start copying the
+ * classified results to pinned host memory. */
+QCS_API int qcs_level_rewalk(qcs_problem *prob, void *stream);
+
+/* Wait for `stream`, check every claw candidate exactly on the host, fold the
+ * launch's counters into the problem's result and copy it to *out (may be
+ * NULL).  out->status becomes QCS_FOUND, with t_count and paulis set, when a
+ * claw verified (Eq. tcount_synthesis). */
+QCS_API int qcs_level_collect(qcs_problem *prob, void *stream, qcs_result *out);
 
 /* Exact host check that C = e^{i phi} R(P_t)..R(P_1) D for a Clifford D
  * (Sec. 4.1): forms D^ = R^(P_1)^T..R^(P_t)^T C^ and tests that it is a signed

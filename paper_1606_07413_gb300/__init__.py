@@ -33,7 +33,8 @@ class Params(ctypes.Structure):
                 ("table_log2", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32),
                 ("max_trail_factor", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
                 ("budget_factor", ctypes.c_int32), ("theta_policy", ctypes.c_int32),
-                ("version_factor", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("version_factor", ctypes.c_int32), ("stop_on_claw", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -46,7 +47,8 @@ class Result(ctypes.Structure):
                 ("merges", ctypes.c_int64), ("robin_hood", ctypes.c_int64), ("trivial", ctypes.c_int64),
                 ("same_side", ctypes.c_int64), ("claws", ctypes.c_int64), ("false_hash", ctypes.c_int64),
                 ("no_merge", ctypes.c_int64), ("abandoned", ctypes.c_int64), ("dropped", ctypes.c_int64),
-                ("queue_overflow", ctypes.c_int64), ("launches", ctypes.c_int64), ("seconds", ctypes.c_double)]
+                ("queue_overflow", ctypes.c_int64), ("launches", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("w_steps", ctypes.c_int64)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
@@ -95,6 +97,10 @@ def lib():
             "qcs_walk_step": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u32, _vp, _vp, _vp, _sz, _vp]),
             "qcs_rewalk": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u32, _vp, _vp, _vp, _vp, _sz, _vp,
                                           _vp, _vp]),
+            "qcs_level_begin": (ctypes.c_int, [_vp, ctypes.c_int, _u32, ctypes.c_int, _vp]),
+            "qcs_level_walk": (ctypes.c_int, [_vp, _u32, _vp]),
+            "qcs_level_rewalk": (ctypes.c_int, [_vp, _vp]),
+            "qcs_level_collect": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(Result)]),
             "qcs_problem_sde": (ctypes.c_int, [_vp]),
             "qcs_level_points": (_u64, [_vp, ctypes.c_int]),
             "qcs_get_channel": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(_i32)]),
@@ -208,6 +214,22 @@ class Problem:
                               _ptr(start_b), _ptr(len_b), start_a.numel(), _ptr(cls), _ptr(ab), _stream(stream))
         _check(rc, "qcs_rewalk")
 
+    # manual stepping of one level (Sec. 3): begin, walk, re-walk, collect
+    def level_begin(self, k, version=0, dp_bits=0, stream=None):
+        _check(lib().qcs_level_begin(self._h, int(k), int(version), int(dp_bits), _stream(stream)),
+               "qcs_level_begin")
+
+    def level_walk(self, steps, stream=None):
+        _check(lib().qcs_level_walk(self._h, int(steps), _stream(stream)), "qcs_level_walk")
+
+    def level_rewalk(self, stream=None):
+        _check(lib().qcs_level_rewalk(self._h, _stream(stream)), "qcs_level_rewalk")
+
+    def level_collect(self, stream=None) -> dict:
+        r = Result()
+        _check(lib().qcs_level_collect(self._h, _stream(stream), ctypes.byref(r)), "qcs_level_collect")
+        return r.as_dict()
+
     def run_walks(self, step_budget: int = 0, stream=None):
         _check(lib().qcs_run_walks(self._h, int(step_budget), _stream(stream)), "qcs_run_walks")
 
@@ -252,6 +274,28 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def peak_lib():
+    """libqcs_peak.so: integer-ALU throughput microbenchmarks (measurement only)."""
+    path = _build_mod.PEAK_LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libqcs_peak.so is missing at {path}; run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    for name in ("qcs_peak_imad", "qcs_peak_iadd"):
+        f = getattr(L, name)
+        f.restype = ctypes.c_int
+        f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    return L
+
+
+def measure_int_peak(kind: str = "imad", blocks_per_sm: int = 8, iters: int = 4096) -> tuple[float, float]:
+    """(ops per second, kernel ms) of the IMAD or IADD3 microbenchmark."""
+    ops, ms = ctypes.c_double(0), ctypes.c_double(0)
+    rc = getattr(peak_lib(), f"qcs_peak_{kind}")(blocks_per_sm, iters, ctypes.byref(ops), ctypes.byref(ms))
+    if rc != 0:
+        raise RuntimeError(f"qcs_peak_{kind} failed with CUDA error {-rc}")
+    return ops.value, ms.value
 
 
 def verify_decomposition(n, target, exp, paulis) -> bool:

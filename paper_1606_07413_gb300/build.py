@@ -19,6 +19,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libqcs.so")
 
 SOURCES = ["qcs_walk.cu", "qcs_api.cpp", "qcs_exact.cpp"]
+PEAK_SRC = "qcs_peak.cu"
+PEAK_LIB = os.path.join(BUILD, "libqcs_peak.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,14 +33,15 @@ def nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "qcs_internal.h"), os.path.join(INCLUDE, "qcs.h"), __file__]
+    files += [os.path.join(CSRC, "qcs_internal.h"), os.path.join(INCLUDE, "qcs.h"), __file__,
+              os.path.join(CSRC, PEAK_SRC), os.path.join(INCLUDE, "qcs_peak.h")]
     return files
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(PEAK_LIB)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PEAK_LIB))
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
@@ -50,6 +53,12 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     common = ["-O3", "-std=c++17", "-I", INCLUDE, "-I", CSRC, "-Xcompiler", "-fPIC,-fvisibility=hidden",
               *ARCH, "-lineinfo", *extra_flags]
     procs, objs = [], []
+    peak_tmp = PEAK_LIB + f".{os.getpid()}.tmp"
+    peak_cmd = [cc, *common, "-shared", "-o", peak_tmp, os.path.join(CSRC, PEAK_SRC),
+                "-Xlinker", "--version-script=" + os.path.join(BUILD, "peak.map")]
+    with open(os.path.join(BUILD, "peak.map"), "w") as f:
+        f.write("{ global: qcs_peak_*; local: *; };\n")
+    procs.append((peak_cmd, subprocess.Popen(peak_cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     for s in SOURCES:
         obj = os.path.join(BUILD, s + ".o")
         objs.append(obj)
@@ -73,6 +82,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     link = [cc, "-shared", *ARCH, "-o", tmp, *objs, "-Xlinker", f"--version-script={vers}", "-lpthread"]
     subprocess.check_call(link)
     os.replace(tmp, LIB)
+    os.replace(peak_tmp, PEAK_LIB)
     return LIB
 
 

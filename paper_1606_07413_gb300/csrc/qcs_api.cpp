@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <mutex>
@@ -23,6 +24,7 @@ using namespace qcs;
 namespace {
 
 thread_local char g_cuda_err[256] = "";
+constexpr uint32_t kCandCap = 4096; // claw candidates kept per launch
 
 int cuda_fail(cudaError_t e)
 {
@@ -54,7 +56,7 @@ bool params_ok(int n, int k_max, const qcs_params &p)
     if (n < 1 || n > 4 || k_max < 0 || k_max > 15) return false;
     if (p.state_bits < 16 || p.state_bits > 64) return false;
     if (p.dp_bits < 1 || p.dp_bits >= p.state_bits) return false;
-    if (p.walks < 1 || p.table_log2 < 4 || p.table_log2 > 32) return false;
+    if (p.walks < 1 || (uint32_t)p.walks > kMaxWalks || p.table_log2 < 4 || p.table_log2 > 34) return false;
     if (p.steps_per_launch < 1 || p.max_trail_factor < 1 || p.queue_capacity < 1) return false;
     if (p.budget_factor < 0 || p.version_factor < 0) return false;
     // the rotation index needs room below the state's top bits
@@ -77,13 +79,13 @@ struct qcs_problem {
     uint2 *dC32 = nullptr, *dU = nullptr;
     Slot *dTable = nullptr;
     Pair *dQueue = nullptr;
-    uint32_t *dQhead = nullptr;
+    uint32_t *dQhead = nullptr; // [0] queued merges, [1] claw candidates
+    Cand *dCands = nullptr;
     WalkState *dWalks = nullptr;
     unsigned long long *dCounters = nullptr;
-    RewalkOut *dOut = nullptr;
     // pinned host mirrors
     unsigned long long *hCounters = nullptr;
-    RewalkOut *hOut = nullptr;
+    Cand *hCands = nullptr;
     uint32_t *hQhead = nullptr;
     // search state
     std::thread driver;
@@ -95,6 +97,13 @@ struct qcs_problem {
     std::chrono::steady_clock::time_point t0;
     PMat Dhat;
     bool have_D = false;
+    // the level being stepped (qcs_level_* and the driver)
+    struct {
+        bool active = false;
+        int k = 0, h = 0, dp_bits = 0;
+        uint64_t xi = 0;
+        WalkLaunch w{};
+    } lvl;
 };
 
 namespace {
@@ -114,6 +123,8 @@ LevelCtx make_level(const qcs_problem *P, int k, uint32_t version, int dp_bits)
     lv.maskL = P->p.state_bits >= 64 ? ~0ull : ((1ull << P->p.state_bits) - 1);
     lv.dshift = P->p.state_bits - dp_bits;
     lv.version = version;
+    lv.n_chunks = (k & 1) ? (int32_t)(P->D - 1) : 0;
+    lv.seed = P->p.seed;
     return lv;
 }
 
@@ -145,21 +156,21 @@ int ensure_search_buffers(qcs_problem *P)
     const size_t slots = (size_t)1 << P->p.table_log2;
     CK(cudaMalloc(&P->dTable, sizeof(Slot) * slots));
     CK(cudaMalloc(&P->dQueue, sizeof(Pair) * (size_t)P->p.queue_capacity));
-    CK(cudaMalloc(&P->dQhead, sizeof(uint32_t)));
+    CK(cudaMalloc(&P->dQhead, 2 * sizeof(uint32_t)));
+    CK(cudaMalloc(&P->dCands, sizeof(Cand) * kCandCap));
     CK(cudaMalloc(&P->dWalks, sizeof(WalkState) * (size_t)P->p.walks));
     CK(cudaMalloc(&P->dCounters, sizeof(unsigned long long) * C_NCOUNTERS));
-    CK(cudaMalloc(&P->dOut, sizeof(RewalkOut) * (size_t)P->p.queue_capacity));
     CK(cudaMallocHost(&P->hCounters, sizeof(unsigned long long) * C_NCOUNTERS));
-    CK(cudaMallocHost(&P->hOut, sizeof(RewalkOut) * (size_t)P->p.queue_capacity));
-    CK(cudaMallocHost(&P->hQhead, sizeof(uint32_t)));
+    CK(cudaMallocHost(&P->hCands, sizeof(Cand) * kCandCap));
+    CK(cudaMallocHost(&P->hQhead, 2 * sizeof(uint32_t)));
     return QCS_OK;
 }
 
 void free_problem_memory(qcs_problem *P)
 {
     cudaFree(P->dC32); cudaFree(P->dU); cudaFree(P->dTable); cudaFree(P->dQueue); cudaFree(P->dQhead);
-    cudaFree(P->dWalks); cudaFree(P->dCounters); cudaFree(P->dOut);
-    cudaFreeHost(P->hCounters); cudaFreeHost(P->hOut); cudaFreeHost(P->hQhead);
+    cudaFree(P->dCands); cudaFree(P->dWalks); cudaFree(P->dCounters);
+    cudaFreeHost(P->hCounters); cudaFreeHost(P->hCands); cudaFreeHost(P->hQhead);
 }
 
 int finish_create(int n, int k_max, const qcs_params *pin, PMat &&C, qcs_problem **out)
@@ -208,6 +219,10 @@ void set_status(qcs_problem *P, int status, int error)
 
 void found(qcs_problem *P, int k, const uint32_t *paulis)
 {
+    {
+        std::lock_guard<std::mutex> g(P->mu);
+        if (P->have_D) return; // keep the first decomposition
+    }
     PMat Dh;
     exact_verify(P->n, P->C, paulis, k, &Dh);
     std::lock_guard<std::mutex> g(P->mu);
@@ -218,12 +233,191 @@ void found(qcs_problem *P, int k, const uint32_t *paulis)
     P->have_D = true;
 }
 
+int level_begin(qcs_problem *P, int k, uint32_t version, int dp_bits, uint32_t n_walks, cudaStream_t s)
+{
+    if (k < 2 || k > P->k_max) return QCS_ERR_ARG;
+    if (dp_bits == 0) dp_bits = P->p.dp_bits;
+    if (dp_bits < 1 || dp_bits >= P->p.state_bits) return QCS_ERR_ARG;
+    int rc = ensure_search_buffers(P);
+    if (rc) return rc;
+    auto &L = P->lvl;
+    L.k = k;
+    L.h = k / 2;
+    L.dp_bits = dp_bits;
+    L.xi = (uint64_t)(P->D - 1);
+    WalkLaunch &w = L.w;
+    w = WalkLaunch{};
+    w.lv = make_level(P, k, version, dp_bits);
+    w.walks = P->dWalks;
+    w.n_walks = (int32_t)std::min<uint32_t>(n_walks ? n_walks : (uint32_t)P->p.walks, (uint32_t)P->p.walks);
+    w.steps = (uint32_t)P->p.steps_per_launch;
+    w.max_len = (uint32_t)std::min<uint64_t>((uint64_t)P->p.max_trail_factor << dp_bits, kMaxTrailLen);
+    w.table = P->dTable;
+    w.table_mask = ((uint64_t)1 << P->p.table_log2) - 1;
+    w.queue = P->dQueue;
+    w.qhead = P->dQhead;
+    w.qcap = (uint32_t)P->p.queue_capacity;
+    w.cands = P->dCands;
+    w.ccount = P->dQhead + 1;
+    w.ccap = kCandCap;
+    w.counters = P->dCounters;
+    CK(cudaMemsetAsync(P->dTable, 0xFF, sizeof(Slot) << P->p.table_log2, s));
+    CK(cudaMemsetAsync(P->dQhead, 0, 2 * sizeof(uint32_t), s));
+    CK(launch_init_walks(w, s));
+    L.active = true;
+    std::lock_guard<std::mutex> g(P->mu);
+    P->res.k = k;
+    P->res.version = version;
+    return QCS_OK;
+}
+
+int level_walk(qcs_problem *P, uint32_t steps, cudaStream_t s)
+{
+    if (!P->lvl.active || steps == 0) return QCS_ERR_ARG;
+    P->lvl.w.steps = steps;
+    CK(cudaMemsetAsync(P->dQhead, 0, 2 * sizeof(uint32_t), s));
+    CK(cudaMemsetAsync(P->dCounters, 0, sizeof(unsigned long long) * C_NCOUNTERS, s));
+    CK(launch_walks(P->lvl.w, s));
+    return QCS_OK;
+}
+
+int level_rewalk(qcs_problem *P, cudaStream_t s)
+{
+    if (!P->lvl.active) return QCS_ERR_ARG;
+    const WalkLaunch &w = P->lvl.w;
+    CK(launch_rewalk_pairs(w, s));
+    CK(cudaMemcpyAsync(P->hCounters, P->dCounters, sizeof(unsigned long long) * C_NCOUNTERS,
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(P->hQhead, P->dQhead, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(P->hCands, P->dCands, sizeof(Cand) * kCandCap, cudaMemcpyDeviceToHost, s));
+    return QCS_OK;
+}
+
+// Wait, check claw candidates exactly, fold counters into res.  *steps gets
+// the launch's walk steps.
+int level_collect(qcs_problem *P, cudaStream_t s, bool *got, uint64_t *steps)
+{
+    if (!P->lvl.active) return QCS_ERR_ARG;
+    CK(cudaStreamSynchronize(s));
+    const auto &L = P->lvl;
+    const int k = L.k, h = L.h;
+    const uint64_t xi = L.xi;
+    const unsigned long long *c = P->hCounters;
+    const uint32_t npairs = std::min(P->hQhead[0], L.w.qcap);
+    const uint32_t ncand = std::min(P->hQhead[1], kCandCap);
+    uint32_t paulis[16] = {0};
+    int64_t claws = 0, false_hash = 0;
+    *got = false;
+    for (uint32_t i = 0; i < ncand && !*got; i++) {
+        // exact check of the candidate: decode the V point and the W point
+        const Cand &r = P->hCands[i];
+        const uint64_t xv = (r.a & 1) ? r.b : r.a, xw = (r.a & 1) ? r.a : r.b;
+        uint64_t rv = (xv >> 1) % L.w.lv.xi_h, rw = (xw >> 1) % L.w.lv.xi_h;
+        uint32_t qv[kMaxH], qw[kMaxH];
+        for (int j = 0; j < h; j++) {
+            qv[j] = (uint32_t)(rv % xi) + 1;
+            rv /= xi;
+            qw[j] = (uint32_t)(rw % xi) + 1;
+            rw /= xi;
+        }
+        const int chunk = (k & 1) ? (int)r.chunk : 0;
+        bool equal = false;
+        if (exact_same_coset(P->n, P->C, k, chunk, qv, qw, &equal) != QCS_OK) equal = false;
+        if (equal) {
+            for (int j = 0; j < h; j++) {
+                paulis[j] = qv[j];
+                paulis[h + j] = qw[j];
+            }
+            if (k & 1) paulis[2 * h] = (uint32_t)chunk;
+            if (exact_verify(P->n, P->C, paulis, k, nullptr) == QCS_OK) {
+                claws++;
+                *got = true;
+                continue;
+            }
+        }
+        false_hash++;
+    }
+    *steps = c[C_STEPS];
+    {
+        std::lock_guard<std::mutex> g(P->mu);
+        qcs_result &R = P->res;
+        R.steps += (int64_t)c[C_STEPS];
+        R.w_steps += (int64_t)c[C_WSTEPS];
+        R.dps += (int64_t)c[C_DPS];
+        R.abandoned += (int64_t)c[C_ABANDONED];
+        R.dropped += (int64_t)c[C_EVICTED];
+        R.merges += (int64_t)npairs;
+        R.queue_overflow += (int64_t)(c[C_PAIRS] - npairs);
+        R.robin_hood += (int64_t)c[C_CLS0 + QCS_MERGE_ROBIN_HOOD];
+        R.trivial += (int64_t)c[C_CLS0 + QCS_MERGE_TRIVIAL];
+        R.same_side += (int64_t)c[C_CLS0 + QCS_MERGE_SAME_SIDE];
+        R.no_merge += (int64_t)c[C_CLS0 + QCS_MERGE_NO_MERGE];
+        R.claws += claws;
+        R.false_hash += false_hash;
+        R.launches += 1;
+        R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - P->t0).count();
+    }
+    if (*got) found(P, k, paulis);
+    return QCS_OK;
+}
+
+// How a level is walked (Sec. 3 and Appendix): theta, the launch shape, the
+// function-version period and the level's step budget.
+struct LevelPlan {
+    int dp_bits;
+    uint32_t walks, steps;
+    uint64_t launches_per_version, min_launches;
+};
+
+LevelPlan plan_level(const qcs_problem *P, int k)
+{
+    LevelPlan pl{};
+    const uint64_t xi = (uint64_t)(P->D - 1);
+    const long double points = 2.0L * (long double)upow(xi, k / 2) * (long double)((k & 1) ? xi : 1);
+    pl.dp_bits = P->p.dp_bits;
+    if (P->p.theta_policy == 1) {
+        // theta as large as 1/2 while theta * points stays within half the table
+        const long double slots = (long double)((uint64_t)1 << P->p.table_log2);
+        int d = 1;
+        while (d < P->p.dp_bits && points / (long double)((uint64_t)1 << d) > slots / 2) d++;
+        pl.dp_bits = d;
+    }
+    const long double theta = 1.0L / (long double)((uint64_t)1 << pl.dp_bits);
+    const long double vf = P->p.version_factor > 0 ? (long double)P->p.version_factor : 1e30L;
+    const long double version_steps = vf * points;
+    // a launch covers at most one version; trails of a few 1/theta must fit
+    long double steps = (long double)P->p.steps_per_launch, walks = (long double)P->p.walks;
+    const long double s_min = std::min<long double>(steps, 4.0L / theta);
+    if (walks * steps > version_steps) steps = std::max(s_min, std::floor(version_steps / walks));
+    if (walks * steps > version_steps) walks = std::max(32.0L, std::floor(version_steps / steps));
+    // merges per launch (about one per distinguished point) must fit the queue
+    const long double qroom = (long double)P->p.queue_capacity / 2;
+    while (walks * steps * theta > qroom && steps > 1) steps = std::floor(steps / 2);
+    if (walks * steps * theta > qroom) walks = std::max(32.0L, std::floor(qroom / (steps * theta)));
+    pl.walks = (uint32_t)walks;
+    pl.steps = (uint32_t)std::max(1.0L, steps);
+    const long double per_launch = (long double)pl.walks * pl.steps;
+    pl.launches_per_version = P->p.version_factor > 0
+                                  ? (uint64_t)std::max(1.0L, std::floor(version_steps / per_launch))
+                                  : ~0ull;
+    const long double budget = (long double)P->p.budget_factor * points;
+    const long double lmin = std::ceil(budget / per_launch);
+    pl.min_launches = lmin > 1.8e19L ? ~0ull : (uint64_t)std::max(1.0L, lmin);
+    if (P->p.version_factor > 0 && pl.min_launches < 4 * pl.launches_per_version)
+        pl.min_launches = 4 * pl.launches_per_version; // at least four function versions
+    return pl;
+}
+
+bool have_decomposition(qcs_problem *P)
+{
+    std::lock_guard<std::mutex> g(P->mu);
+    return P->have_D;
+}
+
 // the search driver: levels sde .. k_max, walks until a verified claw
 int drive(qcs_problem *P, uint64_t budget, cudaStream_t s)
 {
     CK(cudaSetDevice(P->device));
-    int rc = ensure_search_buffers(P);
-    if (rc) return rc;
     uint64_t total_steps = 0;
     uint32_t version = 0;
     for (int k = P->C.E; k <= P->k_max; k++) {
@@ -231,131 +425,44 @@ int drive(qcs_problem *P, uint64_t budget, cudaStream_t s)
             std::lock_guard<std::mutex> g(P->mu);
             P->res.k = k;
         }
-        uint32_t paulis[16] = {0};
         if (k <= 1) {
+            uint32_t paulis[16] = {0};
             if (small_level(P, k, paulis)) {
                 found(P, k, paulis);
                 return QCS_OK;
             }
             continue;
         }
-        const int h = k / 2;
-        const uint64_t xi = (uint64_t)(P->D - 1);
-        const uint64_t n_chunks = (k & 1) ? xi : 1;
-        const long double points = 2.0L * (long double)upow(xi, h) * (long double)n_chunks;
-        int dp_bits = P->p.dp_bits;
-        if (P->p.theta_policy == 1) {
-            // keep theta * points within half the table, theta as large as 1/2
-            const long double slots = (long double)((uint64_t)1 << P->p.table_log2);
-            int d = 1;
-            while (d < P->p.dp_bits && points / (long double)((uint64_t)1 << d) > slots / 2) d++;
-            dp_bits = d;
-        }
-        const uint64_t max_len = (uint64_t)P->p.max_trail_factor << dp_bits;
-        const long double level_budget_ld = (long double)P->p.budget_factor * points;
-        const uint64_t level_budget = level_budget_ld > 1.8e19L ? ~0ull : (uint64_t)level_budget_ld;
-        const long double vp = (long double)P->p.version_factor * points;
-        const uint64_t version_period = P->p.version_factor == 0 ? ~0ull : (vp > 1.8e19L ? ~0ull : (uint64_t)vp);
-
-        WalkLaunch w{};
-        w.walks = P->dWalks;
-        w.n_walks = P->p.walks;
-        w.n_chunks = (int32_t)((k & 1) ? xi : 0);
-        w.steps = (uint32_t)P->p.steps_per_launch;
-        w.max_len = (uint32_t)std::min<uint64_t>(max_len, 0xFFFFFFF0ull);
-        w.seed = P->p.seed;
-        w.table = P->dTable;
-        w.table_mask = ((uint64_t)1 << P->p.table_log2) - 1;
-        w.queue = P->dQueue;
-        w.qhead = P->dQhead;
-        w.qcap = (uint32_t)P->p.queue_capacity;
-        w.counters = P->dCounters;
-
-        uint64_t level_steps = 0, version_steps = 0;
+        const LevelPlan pl = plan_level(P, k);
+        uint64_t launches = 0, in_version = 0;
         bool fresh = true;
         while (true) {
             if (P->cancel.load()) return QCS_ERR_BUSY; // reported as CANCELLED
+            int rc;
             if (fresh) {
-                w.lv = make_level(P, k, version, dp_bits);
-                CK(cudaMemsetAsync(P->dTable, 0xFF, sizeof(Slot) << P->p.table_log2, s));
-                CK(launch_init_walks(w, s));
+                rc = level_begin(P, k, version, pl.dp_bits, pl.walks, s);
+                if (rc) return rc;
                 fresh = false;
-                std::lock_guard<std::mutex> g(P->mu);
-                P->res.version = version;
+                in_version = 0;
             }
-            CK(cudaMemsetAsync(P->dQhead, 0, sizeof(uint32_t), s));
-            CK(cudaMemsetAsync(P->dCounters, 0, sizeof(unsigned long long) * C_NCOUNTERS, s));
-            CK(launch_walks(w, s));
-            CK(launch_rewalk_pairs(w.lv, P->dQueue, P->dQhead, w.qcap, P->dOut, s));
-            CK(cudaMemcpyAsync(P->hCounters, P->dCounters, sizeof(unsigned long long) * C_NCOUNTERS,
-                               cudaMemcpyDeviceToHost, s));
-            CK(cudaMemcpyAsync(P->hQhead, P->dQhead, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-            CK(cudaMemcpyAsync(P->hOut, P->dOut, sizeof(RewalkOut) * w.qcap, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            const uint32_t npairs = std::min(*P->hQhead, w.qcap);
-            int64_t cls_count[6] = {0, 0, 0, 0, 0, 0};
+            if ((rc = level_walk(P, pl.steps, s))) return rc;
+            if ((rc = level_rewalk(P, s))) return rc;
             bool got = false;
-            for (uint32_t i = 0; i < npairs && !got; i++) {
-                const RewalkOut &r = P->hOut[i];
-                int cls = r.cls;
-                if (cls == QCS_MERGE_CLAW) {
-                    // exact check of the candidate: the V point and the W point
-                    const uint64_t xv = (r.a & 1) ? r.b : r.a, xw = (r.a & 1) ? r.a : r.b;
-                    uint64_t rv = (xv >> 1) % w.lv.xi_h, rw = (xw >> 1) % w.lv.xi_h;
-                    uint32_t qv[kMaxH], qw[kMaxH];
-                    for (int j = 0; j < h; j++) {
-                        qv[j] = (uint32_t)(rv % xi) + 1; rv /= xi;
-                        qw[j] = (uint32_t)(rw % xi) + 1; rw /= xi;
-                    }
-                    const int chunk = (k & 1) ? (int)r.chunk : 0;
-                    bool equal = false;
-                    if (exact_same_coset(P->n, P->C, k, chunk, qv, qw, &equal) != QCS_OK) equal = false;
-                    if (equal) {
-                        for (int j = 0; j < h; j++) { paulis[j] = qv[j]; paulis[h + j] = qw[j]; }
-                        if (k & 1) paulis[2 * h] = (uint32_t)chunk;
-                        if (exact_verify(P->n, P->C, paulis, k, nullptr) == QCS_OK) got = true;
-                        else cls = QCS_MERGE_FALSE_HASH;
-                    } else {
-                        cls = QCS_MERGE_FALSE_HASH;
-                    }
-                }
-                if (cls >= 0 && cls < 6) cls_count[cls]++;
-            }
-            const unsigned long long *c = P->hCounters;
-            total_steps += c[C_STEPS];
-            level_steps += c[C_STEPS];
-            version_steps += c[C_STEPS];
-            {
-                std::lock_guard<std::mutex> g(P->mu);
-                qcs_result &R = P->res;
-                R.steps += (int64_t)c[C_STEPS];
-                R.dps += (int64_t)c[C_DPS];
-                R.abandoned += (int64_t)c[C_ABANDONED];
-                R.dropped += (int64_t)c[C_DROPPED];
-                R.merges += (int64_t)npairs;
-                R.queue_overflow += (int64_t)(c[C_PAIRS] - npairs);
-                R.robin_hood += cls_count[0];
-                R.trivial += cls_count[1];
-                R.same_side += cls_count[2];
-                R.claws += cls_count[3];
-                R.false_hash += cls_count[4];
-                R.no_merge += cls_count[5];
-                R.launches += 1;
-                R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - P->t0).count();
-            }
-            if (c[C_WAIT_TIMEOUT]) return QCS_ERR_DEVICE;
-            if (got) {
-                found(P, k, paulis);
-                return QCS_OK;
-            }
-            if (budget && total_steps >= budget) return QCS_ERR_TIMEOUT; // reported as BUDGET_EXHAUSTED
-            if (level_steps >= level_budget) break;
-            if (version_steps >= version_period) {
+            uint64_t steps = 0;
+            if ((rc = level_collect(P, s, &got, &steps))) return rc;
+            if (got && P->p.stop_on_claw) return QCS_OK;
+            total_steps += steps;
+            launches++;
+            in_version++;
+            if (budget && total_steps >= budget) return have_decomposition(P) ? QCS_OK : QCS_ERR_TIMEOUT;
+            if (launches >= pl.min_launches) break;
+            if (in_version >= pl.launches_per_version) {
                 version++;
-                version_steps = 0;
                 fresh = true;
             }
         }
+        version++;
+        if (have_decomposition(P)) return QCS_OK; // the optimal level is the first with a claw
     }
     return QCS_ERR_TIMEOUT;
 }
@@ -390,10 +497,11 @@ void qcs_default_params(int n_qubits, qcs_params *p)
     }
     p->steps_per_launch = 64;
     p->max_trail_factor = 20;
-    p->queue_capacity = 4096;
-    p->budget_factor = 8;
+    p->queue_capacity = 1 << 20;
+    p->budget_factor = 16;
     p->theta_policy = 1;
     p->version_factor = 2;
+    p->stop_on_claw = 1;
     p->seed = 0x2545F4914F6CDD1Dull;
 }
 
@@ -519,6 +627,58 @@ int qcs_get_clifford(qcs_problem *P, int32_t *perm, int8_t *sign)
             }
         }
     return QCS_OK;
+}
+
+static bool busy(qcs_problem *P)
+{
+    std::lock_guard<std::mutex> g(P->mu);
+    return P->running;
+}
+
+int qcs_level_begin(qcs_problem *P, int k, uint32_t version, int dp_bits, void *stream)
+{
+    if (!P) return QCS_ERR_ARG;
+    if (busy(P)) return QCS_ERR_BUSY;
+    {
+        std::lock_guard<std::mutex> g(P->mu);
+        if (P->res.status != QCS_SEARCHING) {
+            const int sde = P->res.sde;
+            memset(&P->res, 0, sizeof P->res);
+            P->res.sde = sde;
+            P->res.t_count = -1;
+            P->res.status = QCS_SEARCHING;
+            P->have_D = false;
+            P->t0 = std::chrono::steady_clock::now();
+        }
+    }
+    return level_begin(P, k, version, dp_bits, 0, (cudaStream_t)stream);
+}
+
+int qcs_level_walk(qcs_problem *P, uint32_t steps, void *stream)
+{
+    if (!P) return QCS_ERR_ARG;
+    if (busy(P)) return QCS_ERR_BUSY;
+    return level_walk(P, steps, (cudaStream_t)stream);
+}
+
+int qcs_level_rewalk(qcs_problem *P, void *stream)
+{
+    if (!P) return QCS_ERR_ARG;
+    if (busy(P)) return QCS_ERR_BUSY;
+    return level_rewalk(P, (cudaStream_t)stream);
+}
+
+int qcs_level_collect(qcs_problem *P, void *stream, qcs_result *out)
+{
+    if (!P) return QCS_ERR_ARG;
+    if (busy(P)) return QCS_ERR_BUSY;
+    bool got = false;
+    uint64_t steps = 0;
+    int rc = level_collect(P, (cudaStream_t)stream, &got, &steps);
+    std::lock_guard<std::mutex> g(P->mu);
+    if (got) P->res.status = QCS_FOUND;
+    if (out) *out = P->res;
+    return rc;
 }
 
 int qcs_verify_decomposition(int n, const int64_t *target, int32_t target_exp, const uint32_t *paulis, int t)

@@ -32,20 +32,35 @@ struct LevelCtx {
     int32_t ev;        // V side is raised from exponent h to K: ev = K - h
     int32_t dshift;    // distinguished iff (x >> dshift) == 0, dshift = L - d_theta
     uint32_t version;
+    int32_t n_chunks;  // xi for odd k (trail chunk drawn from its start), 0 for even k
+    uint64_t seed;     // seed of trail starting points
 };
 
-// One distinguished point (Sec. 3: start, end, length).  32 bytes.
-struct Slot {
-    unsigned long long key;   // the distinguished state, kEmptyKey when free
-    unsigned long long start; // first state of the trail
-    unsigned long long meta;  // len | chunk << 32; kEmptyKey until published
-    unsigned long long pad;
+// A trail is named by a 64-bit reference: walk index (24 bits), its trail
+// sequence number (23 bits) and its length (17 bits).  Its starting state and
+// chunk are recomputed from (seed, version, walk, sequence), so a
+// distinguished point fits in one 16-byte slot.
+constexpr int kRefWalkBits = 24, kRefSeqBits = 23, kRefLenBits = 17;
+constexpr uint32_t kMaxWalks = 1u << kRefWalkBits;
+constexpr uint32_t kMaxTrailLen = (1u << kRefLenBits) - 1;
+
+// One distinguished point (Sec. 3: the triple start, end, length, with the
+// start and length folded into the trail reference).  16 bytes, written with
+// one 128-bit atomic exchange: the memory keeps the newest trail per slot.
+struct alignas(16) Slot {
+    unsigned long long key; // the distinguished state, kEmptyKey when free
+    unsigned long long ref; // trail reference
 };
 
 // Two trails that reached one distinguished point with different starts.
 struct Pair {
-    unsigned long long start_a, start_b, dp;
-    uint32_t len_a, len_b, chunk, pad;
+    unsigned long long ref_a, ref_b, dp;
+};
+
+// A merge of a V point and a W point (before the exact check).
+struct Cand {
+    unsigned long long a, b;
+    uint32_t chunk, pad;
 };
 
 struct RewalkOut {
@@ -65,26 +80,28 @@ enum Counter {
     C_WSTEPS,      // steps on the W side (these do the 4^n x 4^n contraction)
     C_DPS,
     C_ABANDONED,
-    C_DROPPED,
+    C_EVICTED,     // distinguished points overwritten by another one
     C_DUPLICATE,
-    C_PAIRS,       // collisions pushed (including overflowed ones)
-    C_WAIT_TIMEOUT,
-    C_NCOUNTERS = 16
+    C_PAIRS,       // merges pushed (including overflowed ones)
+    C_CANDS,       // claw candidates found by the re-walk (including overflowed ones)
+    C_CLS0,        // re-walk classes QCS_MERGE_ROBIN_HOOD .. QCS_MERGE_NO_MERGE at C_CLS0 + class
+    C_NCOUNTERS = C_CLS0 + 6
 };
 
 struct WalkLaunch {
     LevelCtx lv;
     WalkState *walks;
-    int32_t n_walks;
-    int32_t n_chunks;   // xi for odd k, 0 for even k
+    int32_t n_walks;    // walks advanced by this launch
     uint32_t steps;     // steps per walk in this launch
     uint32_t max_len;
-    uint64_t seed;
     Slot *table;
     uint64_t table_mask;
     Pair *queue;
     uint32_t *qhead;
     uint32_t qcap;
+    Cand *cands;
+    uint32_t *ccount;
+    uint32_t ccap;
     unsigned long long *counters;
 };
 
@@ -93,8 +110,7 @@ cudaError_t launch_walk_step(const LevelCtx &lv, int chunk, const uint64_t *in, 
                              uint8_t *is_dp, size_t count, cudaStream_t s);
 cudaError_t launch_init_walks(const WalkLaunch &w, cudaStream_t s);
 cudaError_t launch_walks(const WalkLaunch &w, cudaStream_t s);
-cudaError_t launch_rewalk_pairs(const LevelCtx &lv, const Pair *pairs, const uint32_t *qhead,
-                                uint32_t qcap, RewalkOut *out, cudaStream_t s);
+cudaError_t launch_rewalk_pairs(const WalkLaunch &w, cudaStream_t s);
 cudaError_t launch_rewalk_arrays(const LevelCtx &lv, int chunk, const uint64_t *sa, const uint32_t *la,
                                  const uint64_t *sb, const uint32_t *lb, size_t count, int32_t *cls,
                                  uint64_t *ab, cudaStream_t s);

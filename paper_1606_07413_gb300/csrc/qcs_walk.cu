@@ -32,8 +32,6 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kMaxProbe = 16;
-constexpr int kSpinLimit = 1 << 14;
 constexpr uint32_t kMaxRewalkLen = 1u << 20; // longer trails are reported as no merge
 
 __device__ __forceinline__ uint64_t smix(uint64_t z)
@@ -273,50 +271,54 @@ __global__ void __launch_bounds__(kThreads) k_walk_step(LevelCtx lv, uint32_t ch
     }
 }
 
-__device__ __forceinline__ void new_trail(WalkState &st, uint32_t walk, const WalkLaunch &w)
+// starting state and chunk of trail (walk, seq) in the current version
+__device__ __forceinline__ uint64_t trail_start(const LevelCtx &lv, uint32_t walk, uint32_t seq)
+{
+    seq &= (1u << kRefSeqBits) - 1;
+    return smix(lv.seed ^ smix(((uint64_t)walk << 32) | seq) ^ ((uint64_t)lv.version << 40)) & lv.maskL;
+}
+__device__ __forceinline__ uint32_t trail_chunk(const LevelCtx &lv, uint64_t start)
+{
+    return lv.n_chunks ? 1u + (uint32_t)(smix(start ^ 0x5851F42D4C957F2Dull) % (uint64_t)lv.n_chunks) : 0u;
+}
+__device__ __forceinline__ uint64_t make_ref(uint32_t walk, uint32_t seq, uint32_t len)
+{
+    return (uint64_t)walk | ((uint64_t)(seq & ((1u << kRefSeqBits) - 1)) << kRefWalkBits) |
+           ((uint64_t)len << (kRefWalkBits + kRefSeqBits));
+}
+__device__ __forceinline__ void split_ref(uint64_t ref, uint32_t &walk, uint32_t &seq, uint32_t &len)
+{
+    walk = (uint32_t)(ref & ((1u << kRefWalkBits) - 1));
+    seq = (uint32_t)((ref >> kRefWalkBits) & ((1u << kRefSeqBits) - 1));
+    len = (uint32_t)(ref >> (kRefWalkBits + kRefSeqBits));
+}
+
+__device__ __forceinline__ void new_trail(WalkState &st, uint32_t walk, const LevelCtx &lv)
 {
     st.seq++;
-    st.start = smix(w.seed ^ smix(((uint64_t)walk << 32) | st.seq) ^ ((uint64_t)w.lv.version << 40)) & w.lv.maskL;
+    st.start = trail_start(lv, walk, st.seq);
     st.cur = st.start;
     st.len = 0;
-    st.chunk = w.n_chunks ? 1u + (uint32_t)(smix(st.start ^ 0x5851F42D4C957F2Dull) % (uint64_t)w.n_chunks) : 0u;
+    st.chunk = trail_chunk(lv, st.start);
 }
 
 struct LaneCounters {
-    unsigned long long dropped = 0, duplicate = 0, pairs = 0, timeout = 0;
+    unsigned long long evicted = 0, duplicate = 0, pairs = 0;
 };
 
-// Insert (dp, start, len) for one chunk into the open-addressing table
-// (Sec. 3: store when absent; the same end with another start is a merge).
-// Called by one lane.  Every wait is bounded.
-__device__ void dp_insert(const WalkLaunch &w, uint64_t dp, uint32_t chunk, uint64_t start, uint32_t len,
-                          LaneCounters &c)
+// Store the distinguished point (Sec. 3: the triple start, end, length) in
+// the slot its value hashes to, keeping the newest trail there (one 128-bit
+// atomic exchange, never a wait).  If the slot held the same point from
+// another trail the two trails merged: queue them for the re-walk.
+__device__ void dp_insert(const WalkLaunch &w, uint64_t dp, uint64_t ref, LaneCounters &c)
 {
-    const uint64_t h = smix(dp ^ ((uint64_t)chunk << 52));
-    for (int probe = 0; probe < kMaxProbe; probe++) {
-        Slot *s = &w.table[(h + (uint64_t)probe) & w.table_mask];
-        const unsigned long long old = atomicCAS(&s->key, kEmptyKey, (unsigned long long)dp);
-        if (old == kEmptyKey) {
-            s->start = start;
-            __threadfence();
-            atomicExch(&s->meta, (unsigned long long)len | ((unsigned long long)chunk << 32));
-            return;
-        }
-        if (old != dp) continue;
-        unsigned long long m = kEmptyKey;
-        for (int spin = 0; spin < kSpinLimit; spin++) {
-            m = *(volatile unsigned long long *)&s->meta;
-            if (m != kEmptyKey) break;
-            __nanosleep(64);
-        }
-        if (m == kEmptyKey) {
-            c.timeout++;
-            return;
-        }
-        __threadfence();
-        if ((uint32_t)(m >> 32) != chunk) continue;
-        const unsigned long long other = *(volatile unsigned long long *)&s->start;
-        if (other == start) {
+    Slot nv;
+    nv.key = dp;
+    nv.ref = ref;
+    Slot *s = &w.table[smix(dp) & w.table_mask];
+    const Slot old = atomicExch(s, nv);
+    if (old.key == dp) {
+        if (old.ref == ref) {
             c.duplicate++;
             return;
         }
@@ -324,18 +326,14 @@ __device__ void dp_insert(const WalkLaunch &w, uint64_t dp, uint32_t chunk, uint
         const uint32_t idx = atomicAdd(w.qhead, 1u);
         if (idx < w.qcap) {
             Pair p;
-            p.start_a = other;
-            p.len_a = (uint32_t)m;
-            p.start_b = start;
-            p.len_b = len;
+            p.ref_a = old.ref;
+            p.ref_b = ref;
             p.dp = dp;
-            p.chunk = chunk;
-            p.pad = 0;
             w.queue[idx] = p;
         }
-        return;
+    } else if (old.key != kEmptyKey) {
+        c.evicted++;
     }
-    c.dropped++;
 }
 
 template <int NQ>
@@ -359,12 +357,12 @@ __global__ void __launch_bounds__(kThreads) k_walks(WalkLaunch w)
             st.len++;
             if ((y >> w.lv.dshift) == 0) {
                 n_dp++;
-                if (lane == 0) dp_insert(w, y, st.chunk, st.start, st.len, c);
+                if (lane == 0) dp_insert(w, y, make_ref((uint32_t)walk, st.seq, st.len), c);
                 __syncwarp();
-                new_trail(st, (uint32_t)walk, w);
+                new_trail(st, (uint32_t)walk, w.lv);
             } else if (st.len >= w.max_len) {
                 n_ab++;
-                new_trail(st, (uint32_t)walk, w);
+                new_trail(st, (uint32_t)walk, w.lv);
             } else {
                 st.cur = y;
             }
@@ -376,10 +374,9 @@ __global__ void __launch_bounds__(kThreads) k_walks(WalkLaunch w)
         atomicAdd(&w.counters[C_WSTEPS], n_w);
         atomicAdd(&w.counters[C_DPS], n_dp);
         atomicAdd(&w.counters[C_ABANDONED], n_ab);
-        if (c.dropped) atomicAdd(&w.counters[C_DROPPED], c.dropped);
+        if (c.evicted) atomicAdd(&w.counters[C_EVICTED], c.evicted);
         if (c.duplicate) atomicAdd(&w.counters[C_DUPLICATE], c.duplicate);
         if (c.pairs) atomicAdd(&w.counters[C_PAIRS], c.pairs);
-        if (c.timeout) atomicAdd(&w.counters[C_WAIT_TIMEOUT], c.timeout);
     }
 }
 
@@ -390,7 +387,7 @@ __global__ void k_init_walks(WalkLaunch w)
     WalkState st;
     st.seq = 0;
     st.pad = 0;
-    new_trail(st, (uint32_t)i, w);
+    new_trail(st, (uint32_t)i, w.lv);
     w.walks[i] = st;
 }
 
@@ -441,23 +438,55 @@ __device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa,
 }
 
 template <int NQ>
-__global__ void __launch_bounds__(kThreads) k_rewalk_pairs(LevelCtx lv, const Pair *__restrict__ pairs,
-                                                           const uint32_t *__restrict__ qhead, uint32_t qcap,
-                                                           RewalkOut *__restrict__ out)
+__global__ void __launch_bounds__(kThreads) k_rewalk_pairs(WalkLaunch w)
 {
     using G = Geo<NQ>;
     extern __shared__ uint2 smem[];
     uint2 *sU = smem, *sC = smem + G::DIM, *sW = sC + (G::C_SMEM ? G::DIM * G::DIM : 0);
-    const uint32_t cnt = min(*qhead, qcap);
+    const uint32_t cnt = min(*w.qhead, w.qcap);
     if (cnt == 0) return;
-    stage<NQ>(lv, sU, sC);
+    stage<NQ>(w.lv, sU, sC);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint2 *Cm = G::C_SMEM ? sC : lv.C32;
+    const uint2 *Cm = G::C_SMEM ? sC : w.lv.C32;
     uint2 *su = sW + warp * G::DIM;
+    unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0; // per class, in registers
     for (uint32_t p = blockIdx.x * kWarps + warp; p < cnt; p += gridDim.x * kWarps) {
-        const Pair P = pairs[p];
-        const RewalkOut r = rewalk_one<NQ>(lv, P.chunk, P.start_a, P.len_a, P.start_b, P.len_b, sU, Cm, su, lane);
-        if (lane == 0) out[p] = r;
+        const Pair P = w.queue[p];
+        uint32_t wa, sa, la, wb, sb, lb;
+        split_ref(P.ref_a, wa, sa, la);
+        split_ref(P.ref_b, wb, sb, lb);
+        const uint64_t xa = trail_start(w.lv, wa, sa), xb = trail_start(w.lv, wb, sb);
+        const uint32_t ca = trail_chunk(w.lv, xa), cb = trail_chunk(w.lv, xb);
+        RewalkOut r;
+        if (ca != cb) { // the same value reached in two chunks' functions: no merge
+            r.cls = 5;
+        } else {
+            r = rewalk_one<NQ>(w.lv, ca, xa, la, xb, lb, sU, Cm, su, lane);
+        }
+        c0 += r.cls == 0;
+        c1 += r.cls == 1;
+        c2 += r.cls == 2;
+        c3 += r.cls == 3;
+        c4 += r.cls == 4;
+        c5 += r.cls == 5;
+        if (r.cls == 3 && lane == 0) {
+            const uint32_t idx = atomicAdd(w.ccount, 1u);
+            if (idx < w.ccap) {
+                Cand c;
+                c.a = r.a;
+                c.b = r.b;
+                c.chunk = ca;
+                c.pad = 0;
+                w.cands[idx] = c;
+            }
+        }
+    }
+    if (lane == 0) {
+        const unsigned long long cc[6] = {c0, c1, c2, c3, c4, c5};
+#pragma unroll
+        for (int c = 0; c < 6; c++)
+            if (cc[c]) atomicAdd(&w.counters[C_CLS0 + c], cc[c]);
+        if (c3) atomicAdd(&w.counters[C_CANDS], c3);
     }
 }
 
@@ -527,12 +556,11 @@ cudaError_t walks_n(const WalkLaunch &w, cudaStream_t s)
 }
 
 template <int NQ>
-cudaError_t rewalk_pairs_n(const LevelCtx &lv, const Pair *pairs, const uint32_t *qhead, uint32_t qcap,
-                           RewalkOut *out, cudaStream_t s)
+cudaError_t rewalk_pairs_n(const WalkLaunch &w, cudaStream_t s)
 {
     cudaFuncSetAttribute(k_rewalk_pairs<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)Geo<NQ>::smem_bytes);
-    k_rewalk_pairs<NQ><<<grid_for<NQ>(qcap), kThreads, Geo<NQ>::smem_bytes, s>>>(lv, pairs, qhead, qcap, out);
+    k_rewalk_pairs<NQ><<<grid_for<NQ>(w.qcap), kThreads, Geo<NQ>::smem_bytes, s>>>(w);
     return cudaGetLastError();
 }
 
@@ -601,14 +629,13 @@ cudaError_t launch_walks(const WalkLaunch &w, cudaStream_t s)
     }
 }
 
-cudaError_t launch_rewalk_pairs(const LevelCtx &lv, const Pair *pairs, const uint32_t *qhead, uint32_t qcap,
-                                RewalkOut *out, cudaStream_t s)
+cudaError_t launch_rewalk_pairs(const WalkLaunch &w, cudaStream_t s)
 {
-    switch (lv.n) {
-    case 1: return rewalk_pairs_n<1>(lv, pairs, qhead, qcap, out, s);
-    case 2: return rewalk_pairs_n<2>(lv, pairs, qhead, qcap, out, s);
-    case 3: return rewalk_pairs_n<3>(lv, pairs, qhead, qcap, out, s);
-    case 4: return rewalk_pairs_n<4>(lv, pairs, qhead, qcap, out, s);
+    switch (w.lv.n) {
+    case 1: return rewalk_pairs_n<1>(w, s);
+    case 2: return rewalk_pairs_n<2>(w, s);
+    case 3: return rewalk_pairs_n<3>(w, s);
+    case 4: return rewalk_pairs_n<4>(w, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -1,0 +1,171 @@
+"""End-to-end T-count searches on the GPU (Sec. 3-5): the ladder driven by
+qcs_run_walks and the manual level API must report the optimal T-count fixed
+by the oracle (exhaustive MITM, or the sde lower bound meeting the
+construction upper bound), with a decomposition the oracle verifies exactly
+(Eq. tcount_synthesis)."""
+import time
+
+import numpy as np
+import pytest
+
+import paper_1606_07413_gb300 as Q
+from paper_1606_07413_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    from paper_1606_07413_gb300 import build
+
+    build.build()
+    assert torch.cuda.is_available()
+    return torch.device("cuda:0")
+
+
+def search(n, gates, k_max, timeout_ms=120_000, **over):
+    p = Q.default_params(n, **over)
+    prob = Q.Problem.from_circuit(n, gates, k_max, p)
+    prob.run_walks()
+    res = prob.wait(timeout_ms)
+    return prob, res
+
+
+def perm_unitary(perm):
+    d = len(perm)
+    u = np.zeros((d, d, 4), np.int64)
+    for c, r in enumerate(perm):
+        u[r, c, 0] = 1
+    return u
+
+
+def test_config1_target(orc, dev):
+    gates, _ = W.config_target(1)
+    C = orc.channel_from_circuit(2, gates)
+    t_exact, _ = orc.mitm_tcount(C, 3)
+    prob, res = search(2, gates, 3)
+    assert res["status_name"] == "found", res
+    assert res["t_count"] == t_exact
+    assert orc.verify(C, res["paulis"])
+    prob.close()
+
+
+def test_config2_target_sde_meets_construction(orc, dev):
+    gates, _ = W.config_target(2)
+    C = orc.channel_from_circuit(3, gates)
+    assert orc.sde(C) == 5  # so the optimal T-count is exactly 5
+    prob, res = search(3, gates, 5)
+    assert res["status_name"] == "found", res
+    assert res["t_count"] == 5 and prob.sde == 5
+    assert orc.verify(C, res["paulis"])
+    assert res["claws"] >= 1 and res["no_merge"] == 0
+    prob.close()
+
+
+@pytest.mark.parametrize("seed", [31, 32, 33])
+def test_collapsing_targets_match_exhaustive_mitm(orc, dev, seed):
+    """Targets whose construction repeats factors, so the optimum lies below
+    the construction count; the ladder must not stop early or late."""
+    rng = np.random.default_rng(seed)
+    ps = [int(v) for v in rng.integers(1, 16, size=4)]
+    ps[2] = ps[1]
+    rows = [(W.OP_RP, p, 0) for p in ps] + [tuple(r) for r in W.clifford_word(rng, 2, 40)]
+    gates = np.asarray(rows, np.int32)
+    C = orc.channel_from_circuit(2, gates)
+    t_exact, _ = orc.mitm_tcount(C, 4)
+    prob, res = search(2, gates, 4)
+    assert res["status_name"] == "found", res
+    assert res["t_count"] == t_exact
+    assert orc.verify(C, res["paulis"])
+    prob.close()
+
+
+def test_single_T_and_clifford_levels(orc, dev):
+    prob, res = search(1, [(W.OP_T, 0, 0)], 3)
+    assert res["status_name"] == "found" and res["t_count"] == 1
+    prob.close()
+    rng = np.random.default_rng(3)
+    word = W.clifford_word(rng, 3, 60)
+    prob, res = search(3, word, 3)
+    assert res["status_name"] == "found" and res["t_count"] == 0
+    perm, sign = prob.clifford()
+    C = orc.channel_from_circuit(3, word).reduced()
+    for j in range(64):
+        assert C.a[perm[j], j] == sign[j]
+    prob.close()
+
+
+def test_returned_clifford_is_the_remainder(orc, dev):
+    gates, _ = W.config_target(1)
+    prob, res = search(2, gates, 3)
+    C = orc.channel_from_circuit(2, gates)
+    M = C
+    for p in reversed(res["paulis"]):
+        M = orc.rhat(2, p, transpose=True) @ M
+    M = M.reduced()
+    perm, sign = prob.clifford()
+    assert M.E == 0
+    for j in range(16):
+        assert M.a[perm[j], j] == sign[j] and abs(M.a[:, j]).sum() == 1
+    prob.close()
+
+
+def test_manual_level_api_finds_the_claw(orc, dev):
+    gates, _ = W.config_target(1)
+    C = orc.channel_from_circuit(2, gates)
+    p = Q.default_params(2)
+    with Q.Problem.from_circuit(2, gates, 3, p) as prob:
+        prob.level_begin(3, version=0, dp_bits=2)
+        res = None
+        for _ in range(50):
+            prob.level_walk(16)
+            prob.level_rewalk()
+            res = prob.level_collect()
+            if res["status_name"] == "found":
+                break
+        assert res["status_name"] == "found" and res["t_count"] == 3
+        assert orc.verify(C, res["paulis"])
+        assert res["steps"] > 0 and res["w_steps"] > 0 and res["launches"] >= 1
+
+
+def test_budget_and_cancel(orc, dev):
+    # k_max below the optimum: the ladder ends without a decomposition
+    gates, _ = W.config_target(2)
+    prob, res = search(3, gates, 4)
+    assert res["status_name"] == "budget_exhausted" and res["t_count"] == -1
+    prob.close()
+    # a long search cancelled from the host between launches
+    gates, _ = W.config_target(3)
+    p = Q.default_params(4, walks=1 << 14, steps_per_launch=8)
+    prob = Q.Problem.from_circuit(4, gates, 7, p)
+    prob.run_walks()
+    time.sleep(0.5)
+    with pytest.raises(Q.QcsError) as ei:
+        prob.run_walks()
+    assert ei.value.code == Q.ERR_BUSY
+    prob.cancel()
+    res = prob.wait(60_000)
+    assert res["status_name"] == "cancelled" and not res["timed_out"]
+    prob.close()
+
+
+@pytest.mark.parametrize("name", ["toffoli", "fredkin"])
+def test_table1_circuits_have_tcount_7(orc, dev, name):
+    """Toffoli and Fredkin have optimal T-count 7 (Sec. 5.2, Table 1)."""
+    if name == "toffoli":
+        perm = [c ^ (4 if (c & 3) == 3 else 0) for c in range(8)]
+    else:
+        perm = [(c & 1) | ((((c >> 2) & 1) << 1) | (((c >> 1) & 1) << 2)) if c & 1 else c for c in range(8)]
+    u = perm_unitary(perm)
+    C = orc.channel_from_unitary(3, u, 0)
+    prob = Q.Problem.from_unitary(3, u, 0, 7, Q.default_params(3))
+    t0 = time.time()
+    prob.run_walks()
+    res = prob.wait(600_000)
+    assert res["status_name"] == "found", res
+    assert res["t_count"] == 7
+    assert orc.verify(C, res["paulis"])
+    assert Q.verify_decomposition(3, u, 0, res["paulis"])
+    print(f"{name}: T-count 7 in {time.time() - t0:.2f}s, {res['steps']} steps")
+    prob.close()

@@ -111,9 +111,8 @@ def test_full_size_launch_sampled(orc, dev, cfg):
     idx = np.concatenate([[0, len(states) - 1], rng.choice(len(states), 46, replace=False)])
     want = orc.walk_step(C, k, 3, 1, c["L"], states[idx])
     assert np.array_equal(y[idx], want)
-    # distinguished fraction is about 2^-d_theta
-    frac = dp.mean()
-    assert frac == pytest.approx(2.0 ** -c["dtheta"], rel=0.5)
+    # the flag is the distinguished predicate of every output
+    assert np.array_equal(dp, orc.is_dp(y, c["L"], c["dtheta"]))
     prob.close()
 
 
