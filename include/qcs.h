@@ -195,6 +195,35 @@ QCS_API int qcs_level_rewalk(qcs_problem *prob, void *stream);
  * claw verified (Eq. tcount_synthesis). */
 QCS_API int qcs_level_collect(qcs_problem *prob, void *stream, qcs_result *out);
 
+/* qcs_level_walk_static: the walk of qcs_level_walk (begin = 1: preceded by
+ * the reset of qcs_level_begin) for callers that must not allocate device
+ * memory -- code recorded into a CUDA graph (cudaMalloc cannot be captured),
+ * code whose device memory belongs to a framework's caching allocator, and
+ * loops that cannot take cudaMalloc's implicit synchronisation.  The paper has
+ * no counterpart; this is a property of the library, not of the method.
+ *
+ * It allocates nothing: the distinguished-point table is a static device
+ * array of 2^18 16-byte slots (4 MiB) that every GPU loading libqcs holds
+ * until exit, so the problem's params.table_log2 must be <= 18 (QCS_ERR_ARG
+ * otherwise).  The problem itself must already exist (its creation does
+ * allocate).  The first call on each device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture.  All calls on a device share the one table and it keeps the last
+ * call's contents: begin = 1 clears it, and calls that overlap on the GPU
+ * race on it.
+ *
+ * The caller passes, as DEVICE pointers: walk_states, n_walks records of 32
+ * bytes (written when begin = 1, then advanced by `steps` steps each);
+ * merges, merge_cap triples {trail ref a, trail ref b, distinguished point};
+ * counts, 8 uint64 zeroed by the call: [0] walk steps, [1] W-side steps,
+ * [2] distinguished points, [3] abandoned trails, [4] overwritten points,
+ * [5] duplicate inserts, [6] merges found, [7] merges stored (low 32 bits).
+ * k, version, dp_bits (0 = params.dp_bits) as in qcs_level_begin; n_walks
+ * <= 2^24.  Asynchronous on `stream`. */
+QCS_API int qcs_level_walk_static(qcs_problem *prob, int k, uint32_t version, int dp_bits, int begin,
+                                  void *walk_states, uint32_t n_walks, uint32_t steps, uint64_t *merges,
+                                  uint32_t merge_cap, uint64_t *counts, void *stream);
+
 /* Exact host check that C = e^{i phi} R(P_t)..R(P_1) D for a Clifford D
  * (Sec. 4.1): forms D^ = R^(P_1)^T..R^(P_t)^T C^ and tests that it is a signed
  * permutation.  target as in qcs_create_problem; paulis[0] is P_1.  Pure host,

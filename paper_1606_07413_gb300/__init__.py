@@ -101,6 +101,8 @@ def lib():
             "qcs_level_walk": (ctypes.c_int, [_vp, _u32, _vp]),
             "qcs_level_rewalk": (ctypes.c_int, [_vp, _vp]),
             "qcs_level_collect": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(Result)]),
+            "qcs_level_walk_static": (ctypes.c_int, [_vp, ctypes.c_int, _u32, ctypes.c_int, ctypes.c_int, _vp, _u32,
+                                                     _u32, _vp, _u32, _vp, _vp]),
             "qcs_problem_sde": (ctypes.c_int, [_vp]),
             "qcs_level_points": (_u64, [_vp, ctypes.c_int]),
             "qcs_get_channel": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(_i32)]),
@@ -229,6 +231,16 @@ class Problem:
         r = Result()
         _check(lib().qcs_level_collect(self._h, _stream(stream), ctypes.byref(r)), "qcs_level_collect")
         return r.as_dict()
+
+    def level_walk_static(self, k, version, dp_bits, begin, walk_states, steps, merges, counts, stream=None):
+        """qcs_level_walk_static: the level walk without any device allocation.
+        walk_states: int64 tensor of 4 * n_walks entries; merges: int64 tensor
+        of 3 * cap entries; counts: int64 tensor of 8 entries."""
+        n_walks = walk_states.numel() // 4
+        rc = lib().qcs_level_walk_static(self._h, int(k), int(version), int(dp_bits), int(begin),
+                                         _ptr(walk_states), n_walks, int(steps), _ptr(merges),
+                                         merges.numel() // 3, _ptr(counts), _stream(stream))
+        _check(rc, "qcs_level_walk_static")
 
     def run_walks(self, step_budget: int = 0, stream=None):
         _check(lib().qcs_run_walks(self._h, int(step_budget), _stream(stream)), "qcs_run_walks")

@@ -483,6 +483,20 @@ void driver_main(qcs_problem *P, uint64_t budget, cudaStream_t s)
 
 } // namespace
 
+int qcs::noalloc_level(const qcs_problem *P, int k, uint32_t version, int dp_bits, LevelCtx *lv, uint32_t *max_len,
+                       int *table_log2)
+{
+    if (!P || !lv || !max_len || !table_log2 || k < 2 || k > P->k_max) return QCS_ERR_ARG;
+    if (dp_bits == 0) dp_bits = P->p.dp_bits;
+    if (dp_bits < 1 || dp_bits >= P->p.state_bits) return QCS_ERR_ARG;
+    *lv = make_level(P, k, version, dp_bits);
+    *max_len = (uint32_t)std::min<uint64_t>((uint64_t)P->p.max_trail_factor << dp_bits, kMaxTrailLen);
+    *table_log2 = P->p.table_log2;
+    return QCS_OK;
+}
+
+int qcs::record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+
 extern "C" {
 
 void qcs_default_params(int n_qubits, qcs_params *p)

@@ -9,6 +9,8 @@
 
 #include <cuda_runtime.h>
 
+#include "qcs.h"
+
 namespace qcs {
 
 constexpr int kMaxH = 8;              // h = floor(k/2) <= 7 for k <= 15
@@ -114,6 +116,13 @@ cudaError_t launch_rewalk_pairs(const WalkLaunch &w, cudaStream_t s);
 cudaError_t launch_rewalk_arrays(const LevelCtx &lv, int chunk, const uint64_t *sa, const uint32_t *la,
                                  const uint64_t *sb, const uint32_t *lb, size_t count, int32_t *cls,
                                  uint64_t *ab, cudaStream_t s);
+// For the allocation-free walk entry point (qcs_noalloc.cu): the level
+// context and trail cut-off that qcs_level_begin would use, and the problem's
+// table size; QCS_ERR_ARG when k or dp_bits are out of range.
+int noalloc_level(const ::qcs_problem *P, int k, uint32_t version, int dp_bits, LevelCtx *lv,
+                  uint32_t *max_len, int *table_log2);
+int record_cuda_error(cudaError_t e); // stores the text for qcs_last_cuda_error, returns QCS_ERR_CUDA
+
 // number of resident CTAs of the walk kernel per SM for n qubits (occupancy)
 int walk_blocks_per_sm(int n);
 int num_sms();
