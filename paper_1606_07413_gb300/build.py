@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         f.write("{ global: qcs_peak_*; local: *; };\n")
     procs.append((peak_cmd, subprocess.Popen(peak_cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     for s in SOURCES:
-        obj = os.path.join(BUILD, s + ".o")
+        obj = os.path.join(BUILD, os.path.basename(s) + ".o")
         objs.append(obj)
         cmd = [cc, *common, "-c", os.path.join(CSRC, s), "-o", obj]
         if s.endswith(".cu"):

@@ -77,6 +77,7 @@ struct qcs_problem {
     PMat C; // reduced, exponent = sde
     // device data
     uint2 *dC32 = nullptr, *dU = nullptr;
+    uint32_t *dCoef = nullptr;
     Slot *dTable = nullptr;
     Pair *dQueue = nullptr;
     uint32_t *dQhead = nullptr; // [0] queued merges, [1] claw candidates
@@ -113,11 +114,15 @@ LevelCtx make_level(const qcs_problem *P, int k, uint32_t version, int dp_bits)
     LevelCtx lv{};
     lv.C32 = P->dC32;
     lv.U = P->dU;
+    lv.coef = P->dCoef;
     lv.n = P->n;
     lv.k = k;
     lv.h = k / 2;
     lv.xi = (uint32_t)(P->D - 1);
     lv.xi_h = upow(lv.xi, lv.h);
+    lv.mu_xi_h = ~0ull / lv.xi_h;
+    lv.mu_xi = ~0ull / lv.xi;
+    lv.mu32_xi = 0xFFFFFFFFu / lv.xi;
     lv.K = P->C.E + (k & 1) + lv.h;
     lv.ev = lv.K - lv.h;
     lv.maskL = P->p.state_bits >= 64 ? ~0ull : ((1ull << P->p.state_bits) - 1);
@@ -130,10 +135,17 @@ LevelCtx make_level(const qcs_problem *P, int k, uint32_t version, int dp_bits)
 
 int upload_problem(qcs_problem *P)
 {
-    const int D = P->D;
+    const int D = P->D, n = P->n;
+    const int R = D >= 32 ? D / 32 : 1; // columns per lane in the walk kernel
+    // C^ low words; for D >= 32 row i keeps lane l's columns l + 32 t (t < R)
+    // next to each other at i * D + l * R + t
     std::vector<uint2> c32((size_t)D * D), u(D);
-    for (size_t i = 0; i < c32.size(); i++)
-        c32[i] = make_uint2((uint32_t)(uint64_t)P->C.a[i], (uint32_t)(uint64_t)P->C.b[i]);
+    for (int i = 0; i < D; i++)
+        for (int Q = 0; Q < D; Q++) {
+            const size_t src = (size_t)i * D + Q;
+            const size_t dst = D >= 32 ? (size_t)i * D + (size_t)(Q % 32) * R + (size_t)(Q / 32) : src;
+            c32[dst] = make_uint2((uint32_t)(uint64_t)P->C.a[src], (uint32_t)(uint64_t)P->C.b[src]);
+        }
     // fingerprint weights: the SplitMix64 stream seeded with kSeedU, outputs
     // 2i and 2i+1 give (Ua[i], Ub[i]); row 0 (the identity) gets zero weight
     u[0] = make_uint2(0, 0);
@@ -142,11 +154,25 @@ int upload_problem(qcs_problem *P)
         uint64_t wb = smix_host(kSeedU + (2ull * i + 2) * kGamma);
         u[i] = make_uint2((uint32_t)wa, (uint32_t)wb);
     }
+    // rotation coefficients per Pauli p: word t, bit l: row l + 32 t
+    // anticommutes with p; word R + t, bit l: s(p, row) = +1 (lambda = 1)
+    std::vector<uint32_t> coef((size_t)D * 2 * R, 0);
+    const uint32_t m = (1u << n) - 1;
+    for (uint32_t p = 0; p < (uint32_t)D; p++)
+        for (uint32_t j = 0; j < (uint32_t)D; j++) {
+            const uint32_t t = j / 32, l = j % 32;
+            const bool anti = (__builtin_popcount(((p >> n) & (j & m)) ^ ((p & m) & (j >> n))) & 1) != 0;
+            const bool plus = pauli_phase(n, p, j) == 1;
+            if (anti) coef[(size_t)p * 2 * R + t] |= 1u << l;
+            if (plus) coef[(size_t)p * 2 * R + R + t] |= 1u << l;
+        }
     CK(cudaGetDevice(&P->device));
     CK(cudaMalloc(&P->dC32, sizeof(uint2) * c32.size()));
     CK(cudaMalloc(&P->dU, sizeof(uint2) * D));
+    CK(cudaMalloc(&P->dCoef, sizeof(uint32_t) * coef.size()));
     CK(cudaMemcpy(P->dC32, c32.data(), sizeof(uint2) * c32.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->dU, u.data(), sizeof(uint2) * D, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->dCoef, coef.data(), sizeof(uint32_t) * coef.size(), cudaMemcpyHostToDevice));
     return QCS_OK;
 }
 
@@ -168,7 +194,7 @@ int ensure_search_buffers(qcs_problem *P)
 
 void free_problem_memory(qcs_problem *P)
 {
-    cudaFree(P->dC32); cudaFree(P->dU); cudaFree(P->dTable); cudaFree(P->dQueue); cudaFree(P->dQhead);
+    cudaFree(P->dC32); cudaFree(P->dU); cudaFree(P->dCoef); cudaFree(P->dTable); cudaFree(P->dQueue); cudaFree(P->dQhead);
     cudaFree(P->dCands); cudaFree(P->dWalks); cudaFree(P->dCounters);
     cudaFreeHost(P->hCounters); cudaFreeHost(P->hCands); cudaFreeHost(P->hQhead);
 }

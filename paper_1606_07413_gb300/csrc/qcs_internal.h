@@ -25,9 +25,19 @@ constexpr uint64_t kSeedH = 0xBB67AE8584CAA73Bull;
 
 // Everything a warp needs to evaluate one step f of the walk at one level.
 struct LevelCtx {
-    const uint2 *C32;  // C^ numerators mod 2^32, (a, b), 4^n x 4^n row-major
+    // C^ numerators mod 2^32 as (a, b), 4^n x 4^n.  Row i, column Q = lane +
+    // 32 t (t < R = max(1, 4^n / 32)) sits at i * 4^n + lane * R + t, so one
+    // lane's R columns of a row are contiguous.
+    const uint2 *C32;
     const uint2 *U;    // fingerprint weights (Ua, Ub) per row, 4^n
+    // rotation coefficients: for Pauli p, 2R words; word t (t < R) has bit
+    // lane set when row lane + 32 t anticommutes with p, word R + t when the
+    // sign s(p, row) is +1.  4^n x 2R uint32.
+    const uint32_t *coef;
     uint64_t xi_h;     // xi^h, the number of rotation tuples per side
+    uint64_t mu_xi_h;  // floor((2^64 - 1) / xi_h), for division by xi_h
+    uint64_t mu_xi;    // floor((2^64 - 1) / xi)
+    uint32_t mu32_xi;  // floor((2^32 - 1) / xi)
     uint64_t maskL;    // low L bits
     uint32_t xi;       // 4^n - 1
     int32_t n, k, h, K;

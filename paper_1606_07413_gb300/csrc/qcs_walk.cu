@@ -29,7 +29,18 @@
 namespace qcs {
 namespace {
 
-constexpr int kWarps = 8;
+// launch shape of the walk kernels (tuned on GB300; see the sweep notes)
+#ifndef QCS_WARPS
+#define QCS_WARPS 8
+#endif
+#ifndef QCS_MIN_BLOCKS
+#define QCS_MIN_BLOCKS 1
+#endif
+#ifndef QCS_GEMV_UNROLL
+#define QCS_GEMV_UNROLL 2
+#endif
+constexpr int kWarps = QCS_WARPS;
+constexpr int kGemvUnroll = QCS_GEMV_UNROLL;
 constexpr int kThreads = kWarps * 32;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr uint32_t kMaxRewalkLen = 1u << 20; // longer trails are reported as no merge
@@ -43,54 +54,80 @@ __device__ __forceinline__ uint64_t smix(uint64_t z)
 
 template <int NQ>
 struct Geo {
-    static constexpr int DIM = 1 << (2 * NQ);       // 4^n rows and columns
-    static constexpr int D = DIM - 1;               // non-identity Paulis
+    static constexpr int DIM = 1 << (2 * NQ);            // 4^n rows and columns
+    static constexpr int D = DIM - 1;                    // non-identity Paulis
     static constexpr int RPL = DIM >= 32 ? DIM / 32 : 1; // rows (and columns) per lane
-    static constexpr int SLOTS = RPL * 32;          // width of the fingerprint sort
-    static constexpr bool C_SMEM = NQ <= 3;         // C^ staged whole in shared memory
-    static constexpr size_t smem_bytes =
-        sizeof(uint2) * (DIM + (C_SMEM ? DIM * DIM : 0) + kWarps * DIM);
+    static constexpr int SLOTS = RPL * 32;               // width of the fingerprint sort
+    static constexpr bool C_SMEM = NQ <= 3;              // C^ staged whole in shared memory
+    static constexpr int COEF_WORDS = DIM * 2 * RPL;     // rotation coefficient bits
+    static constexpr int MAX_CHUNKS = 256;               // hash bases, one per chunk
+    // shared memory: weights | C^ (n <= 3) | coefficients | chunk bases | exchange buffers
+    static constexpr size_t off_C = sizeof(uint2) * DIM;
+    static constexpr size_t off_coef = off_C + (C_SMEM ? sizeof(uint2) * DIM * DIM : 0);
+    static constexpr size_t off_base = off_coef + sizeof(uint32_t) * COEF_WORDS;
+    static constexpr size_t off_xchg = off_base + sizeof(uint64_t) * MAX_CHUNKS;
+    static constexpr size_t smem_bytes = off_xchg + sizeof(uint2) * kWarps * DIM;
+};
+
+// Shared-memory views of one CTA (C may point to global memory for n = 4).
+template <int NQ>
+struct Smem {
+    uint2 *U;
+    const uint2 *C;
+    uint32_t *coef;
+    uint64_t *base;
+    uint2 *xchg; // this warp's exchange buffer
 };
 
 __device__ __forceinline__ uint32_t shl32(uint32_t v, int s) { return s >= 32 ? 0u : v << s; }
 
-// anticommutation of P(p), P(j) and the sign s(p, j) in
-// R(P_p) P_j R(P_p)^dag = (P_j + s P_{p^j}) / sqrt2  (Sec. 4.1)
-template <int NQ>
-__device__ __forceinline__ void rot_coef(uint32_t p, uint32_t j, bool &anti, bool &plus)
+// y mod M and q = y / M given mu = floor((2^64 - 1) / M): the estimate
+// umulhi(y, mu) is at most two below the true quotient (Barrett reduction)
+__device__ __forceinline__ uint64_t divmod(uint64_t y, uint64_t M, uint64_t mu, uint64_t &q)
 {
-    constexpr uint32_t m = (1u << NQ) - 1;
-    const uint32_t px = p >> NQ, pz = p & m, jx = j >> NQ, jz = j & m;
-    anti = (__popc((px & jz) ^ (pz & jx)) & 1) != 0;
-    const uint32_t rx = px ^ jx, rz = pz ^ jz;
-    const int lam = (__popc(px & pz) + __popc(jx & jz) + 2 * __popc(pz & jx) - __popc(rx & rz)) & 3;
-    plus = (lam == 1);
+    q = __umul64hi(y, mu);
+    uint64_t r = y - q * M;
+    if (r >= M) { r -= M; q++; }
+    if (r >= M) { r -= M; q++; }
+    return r;
 }
 
 // One adjoint butterfly stage on the weight vector held by the warp (row
-// j = lane + 32 t in registers ua/ub; su is the warp's exchange buffer).
-// The forward R^(p) maps a row that commutes with p to sqrt2 times itself,
-// (a, b) -> (2b, a), and an anticommuting row i to M_i + s(p, i^p) M_{i^p};
-// R^(p)^T uses s(p, i) instead, and s(p, i^p) = -s(p, i).  The adjoints are
-// (ua, ub) -> (ub, 2 ua) on commuting rows and u_j + s(p, j) u_{j^p}
-// (adjoint of R^) or u_j - s(p, j) u_{j^p} (adjoint of R^T) on the others.
+// j = lane + 32 t in registers ua/ub; the warp's exchange buffer carries the
+// partner rows).  The forward R^(p) maps a row that commutes with p to sqrt2
+// times itself, (a, b) -> (2b, a), and an anticommuting row i to
+// M_i + s(p, i^p) M_{i^p}; R^(p)^T uses s(p, i) instead, and
+// s(p, i^p) = -s(p, i).  The adjoints are (ua, ub) -> (ub, 2 ua) on commuting
+// rows and u_j + s(p, j) u_{j^p} (adjoint of R^) or u_j - s(p, j) u_{j^p}
+// (adjoint of R^T) on the others.  Commutation and sign come from the
+// per-Pauli bit masks staged in shared memory.
 template <int NQ, bool ADJ_OF_TRANSPOSE>
 __device__ __forceinline__ void adj_stage(uint32_t p, uint32_t (&ua)[Geo<NQ>::RPL],
-                                          uint32_t (&ub)[Geo<NQ>::RPL], uint2 *su, int lane)
+                                          uint32_t (&ub)[Geo<NQ>::RPL], const Smem<NQ> &sm, int lane)
 {
     using G = Geo<NQ>;
+    uint2 *su = sm.xchg;
 #pragma unroll
     for (int t = 0; t < G::RPL; t++) {
         const int j = lane + 32 * t;
         if (G::DIM >= 32 || j < G::DIM) su[j] = make_uint2(ua[t], ub[t]);
     }
     __syncwarp();
+    const uint32_t *cwp = sm.coef + p * (2 * G::RPL);
+    uint32_t cw[2 * G::RPL];
+    if (G::RPL == 2) {
+        const uint4 v4 = *reinterpret_cast<const uint4 *>(cwp);
+        cw[0] = v4.x; cw[1] = v4.y; cw[2] = v4.z; cw[3 % (2 * G::RPL)] = v4.w;
+    } else {
+#pragma unroll
+        for (int t = 0; t < 2 * G::RPL; t++) cw[t] = cwp[t];
+    }
 #pragma unroll
     for (int t = 0; t < G::RPL; t++) {
         const int j = lane + 32 * t;
         if (G::DIM >= 32 || j < G::DIM) {
-            bool anti, plus;
-            rot_coef<NQ>(p, (uint32_t)j, anti, plus);
+            const bool anti = (cw[t] >> lane) & 1u;
+            const bool plus = (cw[G::RPL + t] >> lane) & 1u;
             const uint2 v = su[j ^ (int)p];
             const bool add = (plus != ADJ_OF_TRANSPOSE);
             const uint32_t na = add ? ua[t] + v.x : ua[t] - v.x;
@@ -105,28 +142,43 @@ __device__ __forceinline__ void adj_stage(uint32_t p, uint32_t (&ua)[Geo<NQ>::RP
 
 struct Decoded {
     int side;
-    uint64_t r;        // index of the rotation tuple, (x >> 1) mod xi^h
-    uint64_t qpack;    // q_1 .. q_h, 8 bits each (q <= 255)
+    uint64_t r;     // index of the rotation tuple, (x >> 1) mod xi^h
+    uint64_t qpack; // q_1 .. q_h, 8 bits each (q <= 255)
 };
 
 __device__ __forceinline__ Decoded decode(uint64_t x, const LevelCtx &lv)
 {
     Decoded d;
     d.side = (int)(x & 1);
-    d.r = (x >> 1) % lv.xi_h;
-    uint64_t r = d.r;
+    uint64_t q;
+    d.r = divmod(x >> 1, lv.xi_h, lv.mu_xi_h, q);
     d.qpack = 0;
-    for (int j = 0; j < lv.h; j++) {
-        d.qpack |= (uint64_t)((uint32_t)(r % lv.xi) + 1) << (8 * j);
-        r /= lv.xi;
+    if (lv.h == 0) return d;
+    // base-xi digits of r < xi^h: h - 1 divisions, the last quotient is the
+    // last digit; 32-bit Barrett steps once the remainder fits 32 bits
+    uint64_t r = d.r;
+    int j = 0;
+    for (; j < lv.h - 1 && r > 0xFFFFFFFFull; j++) {
+        const uint64_t digit = divmod(r, lv.xi, lv.mu_xi, q);
+        d.qpack |= (digit + 1) << (8 * j);
+        r = q;
     }
+    uint32_t r32 = (uint32_t)r;
+    for (; j < lv.h - 1; j++) {
+        uint32_t q32 = __umulhi(r32, lv.mu32_xi);
+        uint32_t digit = r32 - q32 * lv.xi;
+        if (digit >= lv.xi) { digit -= lv.xi; q32++; }
+        if (digit >= lv.xi) { digit -= lv.xi; q32++; }
+        d.qpack |= (uint64_t)(digit + 1) << (8 * j);
+        r32 = q32;
+    }
+    d.qpack |= (uint64_t)(r32 + 1) << (8 * j);
     return d;
 }
 
 // f(x): all 32 lanes call it with the same x; every lane gets the result.
 template <int NQ>
-__device__ uint64_t warp_step(uint64_t x, uint32_t chunk, const LevelCtx &lv, const uint2 *sU,
-                              const uint2 *Cm, uint2 *su, int lane)
+__device__ uint64_t warp_step(uint64_t x, uint32_t chunk, const LevelCtx &lv, const Smem<NQ> &sm, int lane)
 {
     using G = Geo<NQ>;
     const Decoded dx = decode(x, lv);
@@ -135,7 +187,7 @@ __device__ uint64_t warp_step(uint64_t x, uint32_t chunk, const LevelCtx &lv, co
 #pragma unroll
     for (int t = 0; t < G::RPL; t++) {
         const int j = lane + 32 * t;
-        const uint2 u = (G::DIM >= 32 || j < G::DIM) ? sU[j] : make_uint2(0, 0);
+        const uint2 u = (G::DIM >= 32 || j < G::DIM) ? sm.U[j] : make_uint2(0, 0);
         ua[t] = u.x;
         ub[t] = u.y;
     }
@@ -152,15 +204,16 @@ __device__ uint64_t warp_step(uint64_t x, uint32_t chunk, const LevelCtx &lv, co
             ub[t] = (ev & 1) ? shl32(a, sh + 1) : shl32(b, sh);
         }
         for (int j = lv.h - 1; j >= 0; j--)
-            adj_stage<NQ, false>((uint32_t)(dx.qpack >> (8 * j)) & 0xFFu, ua, ub, su, lane);
+            adj_stage<NQ, false>((uint32_t)(dx.qpack >> (8 * j)) & 0xFFu, ua, ub, sm, lane);
 #pragma unroll
         for (int t = 0; t < G::RPL; t++) Lc[t] = ua[t]; // L(V e_Q) = (U~)_a[Q]
     } else {
         // W side: R^(q_1)^T .. R^(q_h)^T [R^(c)^T] C^; weights go through
         // (R^(q_1)^T)^* first, ..., (R^(q_h)^T)^*, then (R^(c)^T)^*.
         for (int j = 0; j < lv.h; j++)
-            adj_stage<NQ, true>((uint32_t)(dx.qpack >> (8 * j)) & 0xFFu, ua, ub, su, lane);
-        if (lv.k & 1) adj_stage<NQ, true>(chunk, ua, ub, su, lane);
+            adj_stage<NQ, true>((uint32_t)(dx.qpack >> (8 * j)) & 0xFFu, ua, ub, sm, lane);
+        if (lv.k & 1) adj_stage<NQ, true>(chunk, ua, ub, sm, lane);
+        uint2 *su = sm.xchg;
 #pragma unroll
         for (int t = 0; t < G::RPL; t++) {
             const int j = lane + 32 * t;
@@ -168,24 +221,36 @@ __device__ uint64_t warp_step(uint64_t x, uint32_t chunk, const LevelCtx &lv, co
             Lc[t] = 0;
         }
         __syncwarp();
-        // L(W e_Q) = sum_i U~_a[i] C_a[i][Q] + U~_b[i] C_b[i][Q]   (rows 1..D)
-#pragma unroll 4
-        for (int i = 1; i < G::DIM; i++) {
-            const uint2 u = su[i];
+        // L(W e_Q) = sum_i U~_a[i] C_a[i][Q] + U~_b[i] C_b[i][Q]; row 0 has
+        // zero weight and C[0][Q] = 0 for Q >= 1, so all rows may be summed.
+        if (G::DIM >= 32) {
+            const uint4 *su4 = reinterpret_cast<const uint4 *>(su);
+#pragma unroll kGemvUnroll
+            for (int i = 0; i < G::DIM; i += 2) {
+                const uint4 uu = su4[i >> 1]; // rows i and i + 1
+                const uint2 *c0 = sm.C + i * G::DIM + lane * G::RPL;
+                const uint2 *c1 = c0 + G::DIM;
 #pragma unroll
-            for (int t = 0; t < G::RPL; t++) {
-                const int Q = lane + 32 * t;
-                if (G::DIM >= 32 || Q < G::DIM) {
-                    const uint2 c = Cm[i * G::DIM + Q];
-                    Lc[t] += u.x * c.x + u.y * c.y;
+                for (int t = 0; t < G::RPL; t += 2) {
+                    const uint4 a = *reinterpret_cast<const uint4 *>(c0 + t);
+                    const uint4 b = *reinterpret_cast<const uint4 *>(c1 + t);
+                    Lc[t] += uu.x * a.x + uu.y * a.y + uu.z * b.x + uu.w * b.y;
+                    Lc[t + 1] += uu.x * a.z + uu.y * a.w + uu.z * b.z + uu.w * b.w;
                 }
+            }
+        } else if (lane < G::DIM) {
+            for (int i = 0; i < G::DIM; i++) {
+                const uint2 u = su[i], c = sm.C[i * G::DIM + lane];
+                Lc[0] += u.x * c.x + u.y * c.y;
             }
         }
         __syncwarp();
     }
 
     // sign-invariant column fingerprints; column 0 (the identity) and padding
-    // lanes sort last as 0xFFFFFFFF (every phi is at most 2^31)
+    // lanes sort last as 0xFFFFFFFF (every phi is at most 2^31).  Sort element
+    // e = RPL lane + t starts with this lane's column lane + 32 t (where the
+    // keys start does not matter to a sort).
     uint32_t key[G::RPL];
 #pragma unroll
     for (int t = 0; t < G::RPL; t++) {
@@ -193,61 +258,86 @@ __device__ uint64_t warp_step(uint64_t x, uint32_t chunk, const LevelCtx &lv, co
         const uint32_t l = Lc[t], nl = 0u - l;
         key[t] = (Q >= 1 && Q <= G::D) ? min(l, nl) : 0xFFFFFFFFu;
     }
-
-    // bitonic sort of SLOTS keys, element e = 32 t + lane, ascending
+    // bitonic sort of SLOTS keys, ascending in e; strides below RPL stay in
+    // registers, larger ones go through shuffles (there a lane's keys share
+    // the direction bits, which come from the lane part of e)
 #pragma unroll
     for (int size = 2; size <= G::SLOTS; size <<= 1) {
 #pragma unroll
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            if (stride >= 32) {
-                const int ts = stride >> 5;
+            if (stride < G::RPL) {
 #pragma unroll
                 for (int t = 0; t < G::RPL; t++) {
-                    if ((t & ts) == 0) {
-                        const int e = 32 * t + lane;
+                    if ((t & stride) == 0) {
+                        const int e = G::RPL * lane + t;
                         const bool up = (e & size) == 0;
-                        const uint32_t a = key[t], b = key[t | ts];
-                        const uint32_t lo = min(a, b), hi = max(a, b);
-                        key[t] = up ? lo : hi;
-                        key[t | ts] = up ? hi : lo;
+                        const uint32_t a = key[t], b = key[t | stride];
+                        const bool swap = (a > b) == up;
+                        key[t] = swap ? b : a;
+                        key[t | stride] = swap ? a : b;
                     }
                 }
             } else {
+                const int lstride = stride / G::RPL, eb = G::RPL * lane;
+                const bool keep_min = ((eb & stride) == 0) == ((eb & size) == 0);
 #pragma unroll
                 for (int t = 0; t < G::RPL; t++) {
-                    const int e = 32 * t + lane;
-                    const uint32_t o = __shfl_xor_sync(kFull, key[t], stride);
-                    const bool up = (e & size) == 0, lower = (e & stride) == 0;
-                    key[t] = (lower == up) ? min(key[t], o) : max(key[t], o);
+                    const uint32_t o = __shfl_xor_sync(kFull, key[t], lstride);
+                    key[t] = ((key[t] < o) == keep_min) ? key[t] : o;
                 }
             }
         }
     }
 
     // position-keyed hash of the sorted fingerprints
-    const uint64_t tag = (uint64_t)lv.n | ((uint64_t)lv.k << 8) | ((uint64_t)chunk << 16) |
-                         ((uint64_t)(uint32_t)lv.K << 32);
-    const uint64_t base = smix(smix(kSeedH ^ (uint64_t)lv.version) ^ tag);
+    const uint64_t base = sm.base[chunk];
     uint64_t acc = 0;
 #pragma unroll
     for (int t = 0; t < G::RPL; t++) {
-        const int e = 32 * t + lane;
+        const int e = G::RPL * lane + t;
         if (e < G::D) acc += smix(base ^ (((uint64_t)e << 32) | key[t]));
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+    // warp sum mod 2^64 from three 32-bit reductions: the high words (mod
+    // 2^32) and the two 16-bit halves of the low words (no overflow: 32 terms)
+    const uint32_t lo = (uint32_t)acc, hi = (uint32_t)(acc >> 32);
+    const uint32_t s_hi = __reduce_add_sync(kFull, hi);
+    const uint32_t s_l0 = __reduce_add_sync(kFull, lo & 0xFFFFu);
+    const uint32_t s_l1 = __reduce_add_sync(kFull, lo >> 16);
+    acc = ((uint64_t)s_hi << 32) + ((uint64_t)s_l1 << 16) + (uint64_t)s_l0;
     return smix(acc) & lv.maskL;
 }
 
-// stage the fingerprint weights and (n <= 3) all of C^ into shared memory
+// Stage the weights, the rotation coefficients, the per-chunk hash bases and
+// (n <= 3) all of C^ into shared memory; returns this warp's views.
 template <int NQ>
-__device__ __forceinline__ void stage(const LevelCtx &lv, uint2 *sU, uint2 *sC)
+__device__ __forceinline__ Smem<NQ> stage(const LevelCtx &lv, unsigned char *raw)
 {
     using G = Geo<NQ>;
-    for (int i = threadIdx.x; i < G::DIM; i += blockDim.x) sU[i] = lv.U[i];
-    if (G::C_SMEM)
-        for (int i = threadIdx.x; i < G::DIM * G::DIM; i += blockDim.x) sC[i] = lv.C32[i];
+    Smem<NQ> sm;
+    sm.U = reinterpret_cast<uint2 *>(raw);
+    uint2 *sC = reinterpret_cast<uint2 *>(raw + G::off_C);
+    sm.coef = reinterpret_cast<uint32_t *>(raw + G::off_coef);
+    sm.base = reinterpret_cast<uint64_t *>(raw + G::off_base);
+    sm.xchg = reinterpret_cast<uint2 *>(raw + G::off_xchg) + (threadIdx.x >> 5) * G::DIM;
+    for (int i = threadIdx.x; i < G::DIM; i += blockDim.x) sm.U[i] = lv.U[i];
+    for (int i = threadIdx.x; i < G::COEF_WORDS; i += blockDim.x) sm.coef[i] = lv.coef[i];
+    // base(chunk) = smix(smix(seed_H ^ version) ^ (n | k << 8 | chunk << 16 | K << 32))
+    const uint64_t vmix = smix(kSeedH ^ (uint64_t)lv.version);
+    for (int c = threadIdx.x; c < G::MAX_CHUNKS; c += blockDim.x) {
+        const uint64_t tag = (uint64_t)lv.n | ((uint64_t)lv.k << 8) | ((uint64_t)c << 16) |
+                             ((uint64_t)(uint32_t)lv.K << 32);
+        sm.base[c] = smix(vmix ^ tag);
+    }
+    if (G::C_SMEM) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(lv.C32);
+        uint4 *dst = reinterpret_cast<uint4 *>(sC);
+        for (int i = threadIdx.x; i < G::DIM * G::DIM / 2; i += blockDim.x) dst[i] = src[i];
+        sm.C = sC;
+    } else {
+        sm.C = lv.C32;
+    }
     __syncthreads();
+    return sm;
 }
 
 template <int NQ>
@@ -255,15 +345,11 @@ __global__ void __launch_bounds__(kThreads) k_walk_step(LevelCtx lv, uint32_t ch
                                                         uint64_t *__restrict__ out, uint8_t *__restrict__ is_dp,
                                                         size_t count)
 {
-    using G = Geo<NQ>;
-    extern __shared__ uint2 smem[];
-    uint2 *sU = smem, *sC = smem + G::DIM, *sW = sC + (G::C_SMEM ? G::DIM * G::DIM : 0);
-    stage<NQ>(lv, sU, sC);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Smem<NQ> sm = stage<NQ>(lv, smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint2 *Cm = G::C_SMEM ? sC : lv.C32;
-    uint2 *su = sW + warp * G::DIM;
     for (size_t i = (size_t)blockIdx.x * kWarps + warp; i < count; i += (size_t)gridDim.x * kWarps) {
-        const uint64_t y = warp_step<NQ>(in[i], chunk, lv, sU, Cm, su, lane);
+        const uint64_t y = warp_step<NQ>(in[i], chunk, lv, sm, lane);
         if (lane == 0) {
             out[i] = y;
             if (is_dp) is_dp[i] = (uint8_t)((y >> lv.dshift) == 0);
@@ -337,21 +423,17 @@ __device__ void dp_insert(const WalkLaunch &w, uint64_t dp, uint64_t ref, LaneCo
 }
 
 template <int NQ>
-__global__ void __launch_bounds__(kThreads) k_walks(WalkLaunch w)
+__global__ void __launch_bounds__(kThreads, QCS_MIN_BLOCKS) k_walks(WalkLaunch w)
 {
-    using G = Geo<NQ>;
-    extern __shared__ uint2 smem[];
-    uint2 *sU = smem, *sC = smem + G::DIM, *sW = sC + (G::C_SMEM ? G::DIM * G::DIM : 0);
-    stage<NQ>(w.lv, sU, sC);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Smem<NQ> sm = stage<NQ>(w.lv, smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint2 *Cm = G::C_SMEM ? sC : w.lv.C32;
-    uint2 *su = sW + warp * G::DIM;
     unsigned long long n_steps = 0, n_w = 0, n_dp = 0, n_ab = 0;
     LaneCounters c;
     for (int walk = blockIdx.x * kWarps + warp; walk < w.n_walks; walk += gridDim.x * kWarps) {
         WalkState st = w.walks[walk];
         for (uint32_t s = 0; s < w.steps; s++) {
-            const uint64_t y = warp_step<NQ>(st.cur, st.chunk, w.lv, sU, Cm, su, lane);
+            const uint64_t y = warp_step<NQ>(st.cur, st.chunk, w.lv, sm, lane);
             n_steps++;
             n_w += st.cur & 1;
             st.len++;
@@ -396,7 +478,7 @@ __global__ void k_init_walks(WalkLaunch w)
 // maximum trail length, so both loops end.
 template <int NQ>
 __device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa, uint32_t la, uint64_t sb,
-                                uint32_t lb, const uint2 *sU, const uint2 *Cm, uint2 *su, int lane)
+                                uint32_t lb, const Smem<NQ> &sm, int lane)
 {
     RewalkOut r;
     r.chunk = chunk;
@@ -411,15 +493,15 @@ __device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa,
         uint32_t tl = la; la = lb; lb = tl;
     }
     uint64_t a = sa, b = sb;
-    for (uint32_t s = 0; s < la - lb; s++) a = warp_step<NQ>(a, chunk, lv, sU, Cm, su, lane);
+    for (uint32_t s = 0; s < la - lb; s++) a = warp_step<NQ>(a, chunk, lv, sm, lane);
     if (a == b) {
         r.cls = 0; // Robin Hood
         r.a = r.b = a;
         return r;
     }
     for (uint32_t s = 0; s < lb; s++) {
-        const uint64_t fa = warp_step<NQ>(a, chunk, lv, sU, Cm, su, lane);
-        const uint64_t fb = warp_step<NQ>(b, chunk, lv, sU, Cm, su, lane);
+        const uint64_t fa = warp_step<NQ>(a, chunk, lv, sm, lane);
+        const uint64_t fb = warp_step<NQ>(b, chunk, lv, sm, lane);
         if (fa == fb) {
             const Decoded da = decode(a, lv), db = decode(b, lv);
             r.a = a;
@@ -440,15 +522,11 @@ __device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa,
 template <int NQ>
 __global__ void __launch_bounds__(kThreads) k_rewalk_pairs(WalkLaunch w)
 {
-    using G = Geo<NQ>;
-    extern __shared__ uint2 smem[];
-    uint2 *sU = smem, *sC = smem + G::DIM, *sW = sC + (G::C_SMEM ? G::DIM * G::DIM : 0);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t cnt = min(*w.qhead, w.qcap);
     if (cnt == 0) return;
-    stage<NQ>(w.lv, sU, sC);
+    const Smem<NQ> sm = stage<NQ>(w.lv, smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint2 *Cm = G::C_SMEM ? sC : w.lv.C32;
-    uint2 *su = sW + warp * G::DIM;
     unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0; // per class, in registers
     for (uint32_t p = blockIdx.x * kWarps + warp; p < cnt; p += gridDim.x * kWarps) {
         const Pair P = w.queue[p];
@@ -461,7 +539,7 @@ __global__ void __launch_bounds__(kThreads) k_rewalk_pairs(WalkLaunch w)
         if (ca != cb) { // the same value reached in two chunks' functions: no merge
             r.cls = 5;
         } else {
-            r = rewalk_one<NQ>(w.lv, ca, xa, la, xb, lb, sU, Cm, su, lane);
+            r = rewalk_one<NQ>(w.lv, ca, xa, la, xb, lb, sm, lane);
         }
         c0 += r.cls == 0;
         c1 += r.cls == 1;
@@ -496,15 +574,11 @@ __global__ void __launch_bounds__(kThreads) k_rewalk_arrays(LevelCtx lv, uint32_
                                                             const uint32_t *lb, size_t count, int32_t *cls,
                                                             uint64_t *ab)
 {
-    using G = Geo<NQ>;
-    extern __shared__ uint2 smem[];
-    uint2 *sU = smem, *sC = smem + G::DIM, *sW = sC + (G::C_SMEM ? G::DIM * G::DIM : 0);
-    stage<NQ>(lv, sU, sC);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Smem<NQ> sm = stage<NQ>(lv, smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint2 *Cm = G::C_SMEM ? sC : lv.C32;
-    uint2 *su = sW + warp * G::DIM;
     for (size_t p = (size_t)blockIdx.x * kWarps + warp; p < count; p += (size_t)gridDim.x * kWarps) {
-        const RewalkOut r = rewalk_one<NQ>(lv, chunk, sa[p], la[p], sb[p], lb[p], sU, Cm, su, lane);
+        const RewalkOut r = rewalk_one<NQ>(lv, chunk, sa[p], la[p], sb[p], lb[p], sm, lane);
         if (lane == 0) {
             cls[p] = r.cls;
             ab[2 * p] = r.a;
