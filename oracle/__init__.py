@@ -69,7 +69,8 @@ def _declare(L):
         "or_half_product": (_ci, [_ci, _i64p, _i64p, _ci, _ci, _ci, _ci, _i32p, _i64p, _i64p, _intp]),
         "or_fp_weights": (None, [_ci, _u32p, _u32p]),
         "or_matrix_hash": (_cu64, [_ci, _i64p, _i64p, _ci, _ci, _ci, _cu32, _ci]),
-        "or_decode": (_ci, [_ci, _ci, _cu64, _i32p]),
+        "or_decode": (_ci, [_ci, _ci, _ci, _cu64, _i32p]),
+        "or_field_bits": (_ci, [_ci, _ci, _ci]),
         "or_walk_step": (_ci, [_ci, _i64p, _i64p, _ci, _ci, _ci, _cu32, _ci, _u64p, _u64p, _ci]),
         "or_canon": (_ci, [_ci, _i64p, _i64p, _ci, _i64p, _intp]),
         "or_is_clifford": (_ci, [_ci, _i64p, _i64p, _ci]),
@@ -79,7 +80,7 @@ def _declare(L):
         "or_mitm_level": (_ci, [_ci, _i64p, _i64p, _ci, _ci, _i32p]),
         "or_rewalk": (_ci, [_ci, _i64p, _i64p, _ci, _ci, _ci, _cu32, _ci, _cu64, _ci64, _cu64, _ci64,
                             _u64p, _i32p]),
-        "or_classify": (_ci, [_ci, _i64p, _i64p, _ci, _ci, _ci, _cu64, _cu64, _i32p]),
+        "or_classify": (_ci, [_ci, _i64p, _i64p, _ci, _ci, _ci, _ci, _cu64, _cu64, _i32p]),
         "or_vow_search": (_ci, [_ci, _i64p, _i64p, _ci, _ci, _i64p, _i32p, _i64p]),
     }
     for name, (res, args) in sig.items():
@@ -202,10 +203,25 @@ def matrix_hash(M: Chan, k: int, chunk: int, version: int, L: int) -> int:
     return int(lib().or_matrix_hash(M.n, M.a, M.b, M.E, k, chunk, version, L))
 
 
-def decode(n: int, k: int, x: int) -> tuple[int, list[int]]:
+def decode(n: int, k: int, L: int, x: int) -> tuple[int, list[int]]:
     q = np.zeros(16, np.int32)
-    side = lib().or_decode(n, k, int(x), q)
+    side = lib().or_decode(n, k, L, int(x), q)
     return int(side), [int(v) for v in q[: k // 2]]
+
+
+def field_bits(n: int, k: int, L: int) -> int:
+    return int(lib().or_field_bits(n, k, L))
+
+
+def encode(n: int, k: int, L: int, side: int, q) -> int:
+    """A state that decodes to (side, q): the smallest field value per rotation."""
+    xi = 4 ** n - 1
+    ell = field_bits(n, k, L)
+    x = side & 1
+    for j, qj in enumerate(q):
+        v = -(-(qj - 1) * (1 << ell) // xi)  # ceil((q_j - 1) 2^l / xi)
+        x |= v << (1 + ell * j)
+    return x
 
 
 def walk_step(C: Chan, k: int, chunk: int, version: int, L: int, states) -> np.ndarray:
@@ -279,9 +295,9 @@ def rewalk(C: Chan, k, chunk, version, L, x0a, la, x0b, lb):
     return int(cls), int(ab[0]), int(ab[1]), [int(v) for v in p[:k]]
 
 
-def classify(C: Chan, k, chunk, a, b):
+def classify(C: Chan, k, chunk, L, a, b):
     p = np.zeros(16, np.int32)
-    cls = lib().or_classify(C.n, C.a, C.b, C.E, k, chunk, int(a), int(b), p)
+    cls = lib().or_classify(C.n, C.a, C.b, C.E, k, chunk, L, int(a), int(b), p)
     return int(cls), [int(v) for v in p[:k]]
 
 

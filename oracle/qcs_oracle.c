@@ -18,8 +18,9 @@
  *    P(j) = i^{|x & z|} X^x Z^z (Hermitian).  X^x Z^z |c> = (-1)^{|z & c|} |c ^ x>.
  *  - Exact reals in Z[1/sqrt2] are pairs (a, b) meaning (a + b sqrt2) / sqrt2^E
  *    with one exponent E shared by a whole matrix.
- *  - Walk state x (L bits): side = x & 1 (0: V side, 1: W side),
- *    r = (x >> 1) mod xi^h, digits of r little-endian in base xi, q_j = digit_j + 1.
+ *  - Walk state x (L bits): side = x & 1 (0: V side, 1: W side); rotation j
+ *    (0-based) reads the l-bit field at bit 1 + l j, l = min(16, (L-1)/h), and
+ *    maps its value v to q_j = floor(v xi / 2^l) + 1.
  *  - V_q = R(q_h) ... R(q_1);  W_q' = R(q'_1)^T ... R(q'_h)^T [R(c)^T] C  (Eq. mitm
  *    in channel form; the bracket is present for odd k, chunk c in 1..xi).
  *    Both are represented at K = sde(C) + (k & 1) + h.
@@ -652,17 +653,28 @@ OR_API uint64_t or_matrix_hash(int n, const int64_t *a, const int64_t *b, int K,
     return r;
 }
 
-/* mu: state -> (side, q_1..q_h) */
-OR_API int or_decode(int n, int k, uint64_t x, int32_t *q)
+/* mu (Sec. 2: the string is the concatenation of one l-bit code per
+ * rotation): bit 0 is the side; rotation j (0-based) reads its own field of
+ * l = min(16, (L - 1) / h) bits starting at bit 1 + l j, and the field value v
+ * names the Pauli code q_j = floor(v xi / 2^l) + 1 (multiply-shift reduction
+ * of the l-bit code onto the xi = 4^n - 1 non-identity Paulis). */
+OR_API int or_field_bits(int n, int k, int L)
+{
+    (void)n;
+    int h = k / 2;
+    if (h == 0) return 0;
+    int l = (L - 1) / h;
+    return l > 16 ? 16 : l;
+}
+
+OR_API int or_decode(int n, int k, int L, uint64_t x, int32_t *q)
 {
     int h = k / 2;
     uint64_t xi = (uint64_t)((1 << (2 * n)) - 1);
-    uint64_t span = 1;
-    for (int j = 0; j < h; j++) span *= xi;
-    uint64_t r = (x >> 1) % span;
+    int l = or_field_bits(n, k, L);
     for (int j = 0; j < h; j++) {
-        q[j] = (int32_t)(r % xi) + 1;
-        r /= xi;
+        uint64_t v = (x >> (1 + l * j)) & ((1ull << l) - 1);
+        q[j] = (int32_t)((v * xi) >> l) + 1;
     }
     return (int)(x & 1);
 }
@@ -670,7 +682,7 @@ OR_API int or_decode(int n, int k, uint64_t x, int32_t *q)
 static uint64_t walk_f(int n, const pmat *C, int k, int chunk, uint32_t version, int L, uint64_t x)
 {
     int32_t q[16];
-    int side = or_decode(n, k, x, q);
+    int side = or_decode(n, k, L, x, q);
     int K;
     pmat M = half_product(n, C, k, chunk, side, q, &K);
     uint64_t y = coset_hash(n, &M, k, chunk, version, L);
@@ -932,12 +944,12 @@ OR_API int or_mitm_level(int n, const int64_t *Ca, const int64_t *Cb, int e, int
 enum { M_ROBIN_HOOD = 0, M_TRIVIAL = 1, M_SAME_SIDE = 2, M_CLAW = 3, M_FALSE_HASH = 4, M_NO_MERGE = 5 };
 
 /* decide what kind of merge f(a) = f(b) with a != b is */
-static int classify_merge(int n, const pmat *C, int k, int chunk, uint64_t a, uint64_t b,
+static int classify_merge(int n, const pmat *C, int k, int chunk, int L, uint64_t a, uint64_t b,
                           int32_t *paulis)
 {
     int32_t qa[16], qb[16];
     int h = k / 2;
-    int sa = or_decode(n, k, a, qa), sb = or_decode(n, k, b, qb);
+    int sa = or_decode(n, k, L, a, qa), sb = or_decode(n, k, L, b, qb);
     if (sa == sb) {
         int same = 1;
         for (int j = 0; j < h; j++) same &= (qa[j] == qb[j]);
@@ -974,7 +986,7 @@ static int rewalk(int n, const pmat *C, int k, int chunk, uint32_t version, int 
         uint64_t fb = walk_f(n, C, k, chunk, version, L, b);
         if (fa == fb) {
             ab[0] = a; ab[1] = b;
-            return classify_merge(n, C, k, chunk, a, b, paulis);
+            return classify_merge(n, C, k, chunk, L, a, b, paulis);
         }
         a = fa; b = fb;
     }
@@ -993,12 +1005,12 @@ OR_API int or_rewalk(int n, const int64_t *Ca, const int64_t *Cb, int e, int k, 
     return r;
 }
 
-OR_API int or_classify(int n, const int64_t *Ca, const int64_t *Cb, int e, int k, int chunk,
+OR_API int or_classify(int n, const int64_t *Ca, const int64_t *Cb, int e, int k, int chunk, int L,
                        uint64_t a, uint64_t b, int32_t *paulis)
 {
     int D = 1 << (2 * n);
     pmat C = pm_wrap(D, Ca, Cb, e);
-    int r = classify_merge(n, &C, k, chunk, a, b, paulis);
+    int r = classify_merge(n, &C, k, chunk, L, a, b, paulis);
     pm_free(&C);
     return r;
 }

@@ -51,6 +51,25 @@ uint64_t upow(uint64_t b, int e)
     return r;
 }
 
+// bits of one rotation's field in an L-bit state at h rotations per side
+int field_bits(int L, int h)
+{
+    if (h == 0) return 0;
+    const int l = (L - 1) / h;
+    return l > 16 ? 16 : l;
+}
+
+// the rotations of state x at h rotations per side (see decode in qcs_walk.cu)
+void decode_state(uint64_t x, int n, int L, int h, uint32_t *q)
+{
+    const int l = field_bits(L, h);
+    const uint64_t xi = (1u << (2 * n)) - 1;
+    for (int j = 0; j < h; j++) {
+        const uint64_t v = (x >> (1 + l * j)) & ((1ull << l) - 1);
+        q[j] = (uint32_t)((v * xi) >> l) + 1;
+    }
+}
+
 bool params_ok(int n, int k_max, const qcs_params &p)
 {
     if (n < 1 || n > 4 || k_max < 0 || k_max > 15) return false;
@@ -59,14 +78,9 @@ bool params_ok(int n, int k_max, const qcs_params &p)
     if (p.walks < 1 || (uint32_t)p.walks > kMaxWalks || p.table_log2 < 4 || p.table_log2 > 34) return false;
     if (p.steps_per_launch < 1 || p.max_trail_factor < 1 || p.queue_capacity < 1) return false;
     if (p.budget_factor < 0 || p.version_factor < 0) return false;
-    // the rotation index needs room below the state's top bits
-    const uint64_t xi = (1u << (2 * n)) - 1;
+    // every rotation field must reach all 4^n - 1 Paulis: 2^ell > xi
     const int h = k_max / 2;
-    long double span = 1;
-    for (int j = 0; j < h; j++) span *= (long double)xi;
-    long double room = 1;
-    for (int j = 0; j < p.state_bits - 1; j++) room *= 2;
-    return span * 16 <= room;
+    return h == 0 || field_bits(p.state_bits, h) >= 2 * n;
 }
 
 } // namespace
@@ -120,9 +134,8 @@ LevelCtx make_level(const qcs_problem *P, int k, uint32_t version, int dp_bits)
     lv.h = k / 2;
     lv.xi = (uint32_t)(P->D - 1);
     lv.xi_h = upow(lv.xi, lv.h);
-    lv.mu_xi_h = ~0ull / lv.xi_h;
-    lv.mu_xi = ~0ull / lv.xi;
-    lv.mu32_xi = 0xFFFFFFFFu / lv.xi;
+    lv.ell = field_bits(P->p.state_bits, lv.h);
+    lv.fmask = lv.ell ? (uint32_t)((1ull << lv.ell) - 1) : 0u;
     lv.K = P->C.E + (k & 1) + lv.h;
     lv.ev = lv.K - lv.h;
     lv.maskL = P->p.state_bits >= 64 ? ~0ull : ((1ull << P->p.state_bits) - 1);
@@ -338,14 +351,9 @@ int level_collect(qcs_problem *P, cudaStream_t s, bool *got, uint64_t *steps)
         // exact check of the candidate: decode the V point and the W point
         const Cand &r = P->hCands[i];
         const uint64_t xv = (r.a & 1) ? r.b : r.a, xw = (r.a & 1) ? r.a : r.b;
-        uint64_t rv = (xv >> 1) % L.w.lv.xi_h, rw = (xw >> 1) % L.w.lv.xi_h;
         uint32_t qv[kMaxH], qw[kMaxH];
-        for (int j = 0; j < h; j++) {
-            qv[j] = (uint32_t)(rv % xi) + 1;
-            rv /= xi;
-            qw[j] = (uint32_t)(rw % xi) + 1;
-            rw /= xi;
-        }
+        decode_state(xv, P->n, P->p.state_bits, h, qv);
+        decode_state(xw, P->n, P->p.state_bits, h, qw);
         const int chunk = (k & 1) ? (int)r.chunk : 0;
         bool equal = false;
         if (exact_same_coset(P->n, P->C, k, chunk, qv, qw, &equal) != QCS_OK) equal = false;

@@ -35,9 +35,8 @@ struct LevelCtx {
     // sign s(p, row) is +1.  4^n x 2R uint32.
     const uint32_t *coef;
     uint64_t xi_h;     // xi^h, the number of rotation tuples per side
-    uint64_t mu_xi_h;  // floor((2^64 - 1) / xi_h), for division by xi_h
-    uint64_t mu_xi;    // floor((2^64 - 1) / xi)
-    uint32_t mu32_xi;  // floor((2^32 - 1) / xi)
+    int32_t ell;       // bits of one rotation's field in the state: min(16, (L - 1) / h)
+    uint32_t fmask;    // 2^ell - 1
     uint64_t maskL;    // low L bits
     uint32_t xi;       // 4^n - 1
     int32_t n, k, h, K;

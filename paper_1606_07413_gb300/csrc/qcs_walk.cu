@@ -81,17 +81,6 @@ struct Smem {
 
 __device__ __forceinline__ uint32_t shl32(uint32_t v, int s) { return s >= 32 ? 0u : v << s; }
 
-// y mod M and q = y / M given mu = floor((2^64 - 1) / M): the estimate
-// umulhi(y, mu) is at most two below the true quotient (Barrett reduction)
-__device__ __forceinline__ uint64_t divmod(uint64_t y, uint64_t M, uint64_t mu, uint64_t &q)
-{
-    q = __umul64hi(y, mu);
-    uint64_t r = y - q * M;
-    if (r >= M) { r -= M; q++; }
-    if (r >= M) { r -= M; q++; }
-    return r;
-}
-
 // One adjoint butterfly stage on the weight vector held by the warp (row
 // j = lane + 32 t in registers ua/ub; the warp's exchange buffer carries the
 // partner rows).  The forward R^(p) maps a row that commutes with p to sqrt2
@@ -142,37 +131,23 @@ __device__ __forceinline__ void adj_stage(uint32_t p, uint32_t (&ua)[Geo<NQ>::RP
 
 struct Decoded {
     int side;
-    uint64_t r;     // index of the rotation tuple, (x >> 1) mod xi^h
     uint64_t qpack; // q_1 .. q_h, 8 bits each (q <= 255)
 };
 
+// mu (Sec. 2, the state is a concatenation of per-rotation codes): bit 0 is
+// the side; rotation j reads the ell-bit field at bit 1 + ell j and maps its
+// value v onto the xi non-identity Paulis as q_j = floor(v xi / 2^ell) + 1.
 __device__ __forceinline__ Decoded decode(uint64_t x, const LevelCtx &lv)
 {
     Decoded d;
     d.side = (int)(x & 1);
-    uint64_t q;
-    d.r = divmod(x >> 1, lv.xi_h, lv.mu_xi_h, q);
     d.qpack = 0;
-    if (lv.h == 0) return d;
-    // base-xi digits of r < xi^h: h - 1 divisions, the last quotient is the
-    // last digit; 32-bit Barrett steps once the remainder fits 32 bits
-    uint64_t r = d.r;
-    int j = 0;
-    for (; j < lv.h - 1 && r > 0xFFFFFFFFull; j++) {
-        const uint64_t digit = divmod(r, lv.xi, lv.mu_xi, q);
-        d.qpack |= (digit + 1) << (8 * j);
-        r = q;
+    uint64_t f = x >> 1;
+    for (int j = 0; j < lv.h; j++) {
+        const uint32_t v = (uint32_t)f & lv.fmask;
+        d.qpack |= (uint64_t)(((v * lv.xi) >> lv.ell) + 1) << (8 * j);
+        f >>= lv.ell;
     }
-    uint32_t r32 = (uint32_t)r;
-    for (; j < lv.h - 1; j++) {
-        uint32_t q32 = __umulhi(r32, lv.mu32_xi);
-        uint32_t digit = r32 - q32 * lv.xi;
-        if (digit >= lv.xi) { digit -= lv.xi; q32++; }
-        if (digit >= lv.xi) { digit -= lv.xi; q32++; }
-        d.qpack |= (uint64_t)(digit + 1) << (8 * j);
-        r32 = q32;
-    }
-    d.qpack |= (uint64_t)(r32 + 1) << (8 * j);
     return d;
 }
 
@@ -506,7 +481,7 @@ __device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa,
             const Decoded da = decode(a, lv), db = decode(b, lv);
             r.a = a;
             r.b = b;
-            if (da.side == db.side) r.cls = (da.r == db.r) ? 1 : 2; // trivial / same side
+            if (da.side == db.side) r.cls = (da.qpack == db.qpack) ? 1 : 2; // trivial / same side
             else r.cls = 3;                                          // claw candidate
             return r;
         }

@@ -188,9 +188,8 @@ def test_claw_states_step_together_on_gpu(orc, dev):
     gates = np.asarray(rows, np.int32)
     prob, C, p = make(orc, n, gates, t)
     h = t // 2
-    xi = 63
-    xv = sum((q - 1) * xi ** j for j, q in enumerate(ps[:h])) << 1
-    xw = (sum((q - 1) * xi ** j for j, q in enumerate(ps[h:2 * h])) << 1) | 1
+    xv = orc.encode(n, t, p.state_bits, 0, ps[:h])
+    xw = orc.encode(n, t, p.state_bits, 1, ps[h:2 * h])
     y, _ = gpu_step(prob, dev, t, ps[2 * h], 12, [xv, xw])
     assert y[0] == y[1]
     prob.close()

@@ -319,11 +319,10 @@ def test_claw_halves_hash_equal(orc):
         assert orc.same_coset(V, Wm)
         assert orc.matrix_hash(V, t, chunk, 3, c["L"]) == orc.matrix_hash(Wm, t, chunk, 3, c["L"])
         # the states that decode to these halves step to the same point
-        xi = 4 ** c["n"] - 1
-        r_v = sum((q - 1) * xi ** j for j, q in enumerate(p[:h]))
-        r_w = sum((q - 1) * xi ** j for j, q in enumerate(p[h:2 * h]))
-        xv, xw = (r_v << 1) | 0, (r_w << 1) | 1
-        assert orc.decode(c["n"], t, xv) == (0, p[:h])
+        xv = orc.encode(c["n"], t, c["L"], 0, p[:h])
+        xw = orc.encode(c["n"], t, c["L"], 1, p[h:2 * h])
+        assert orc.decode(c["n"], t, c["L"], xv) == (0, p[:h])
+        assert orc.decode(c["n"], t, c["L"], xw) == (1, p[h:2 * h])
         y = orc.walk_step(C, t, chunk, 3, c["L"], [xv, xw])
         assert y[0] == y[1]
         cls, a, b, paulis = orc.rewalk(C, t, chunk, 3, c["L"], xv, 1, xw, 1)
@@ -333,13 +332,34 @@ def test_claw_halves_hash_equal(orc):
 def test_walk_step_is_a_function_of_the_decoded_point(orc):
     gates, _ = W.config_target(1)
     C = orc.channel_from_circuit(2, gates)
-    xi_h = 15
-    x = np.asarray([7, 7 + 2 * xi_h, 7 + 2 * xi_h * 1000], np.uint64)
+    ell = orc.field_bits(2, 2, 32)
+    assert ell == 16
+    # bits above the side bit and the rotation field do not matter
+    x = np.asarray([7, 7 + (1 << (1 + ell)), 7 + (12345 << (1 + ell))], np.uint64)
     y = orc.walk_step(C, 2, 0, 1, 32, x)
     assert y[0] == y[1] == y[2]
-    assert orc.classify(C, 2, 0, int(x[0]), int(x[1]))[0] == orc.TRIVIAL
+    assert orc.classify(C, 2, 0, 32, int(x[0]), int(x[1]))[0] == orc.TRIVIAL
     y = orc.walk_step(C, 2, 0, 1, 32, np.asarray([6, 7], np.uint64))
     assert y[0] != y[1]
+
+
+@pytest.mark.parametrize("n,k,L", [(1, 15, 32), (2, 2, 32), (2, 7, 32), (3, 5, 48), (3, 15, 48), (4, 7, 64),
+                                   (4, 15, 64)])
+def test_decode_fields_cover_every_rotation_evenly(orc, n, k, L):
+    """Each rotation reads its own l-bit field (Sec. 2 concatenation of
+    codes); the multiply-shift map of a field onto the 4^n - 1 Paulis is onto,
+    and every Pauli gets floor or ceil of 2^l / xi field values."""
+    xi, h = 4 ** n - 1, k // 2
+    ell = orc.field_bits(n, k, L)
+    assert 1 + ell * h <= L and (1 << ell) >= xi
+    counts = np.bincount([(v * xi) >> ell for v in range(1 << ell)], minlength=xi)
+    assert counts.min() >= (1 << ell) // xi and counts.max() <= -(-(1 << ell) // xi)
+    rng = np.random.default_rng(n * 100 + k)
+    for _ in range(50):
+        q = [int(v) for v in rng.integers(1, xi + 1, size=h)]
+        side = int(rng.integers(2))
+        x = orc.encode(n, k, L, side, q)
+        assert x < (1 << L) and orc.decode(n, k, L, x) == (side, q)
 
 
 def test_serial_walk_search_finds_the_optimal_tcount(orc):
@@ -398,11 +418,10 @@ def test_known_normal_form_is_a_claw(orc, n, t):
     # swapping the two W-side factors breaks the claw (they do not commute)
     Wswap = orc.half_product(C, t, chunk, 1, ps[h:2 * h][::-1])
     assert not orc.same_coset(V, Wswap)
-    xi = 4 ** n - 1
-    xv = sum((q - 1) * xi ** j for j, q in enumerate(ps[:h])) << 1
-    xw = (sum((q - 1) * xi ** j for j, q in enumerate(ps[h:2 * h])) << 1) | 1
     L = {2: 32, 3: 48}[n]
+    xv = orc.encode(n, t, L, 0, ps[:h])
+    xw = orc.encode(n, t, L, 1, ps[h:2 * h])
     y = orc.walk_step(C, t, chunk, 9, L, [xv, xw])
     assert y[0] == y[1]
-    cls, paulis = orc.classify(C, t, chunk, xv, xw)
+    cls, paulis = orc.classify(C, t, chunk, L, xv, xw)
     assert cls == orc.CLAW and paulis == ps
