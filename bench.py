@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-T-count run")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and other-size runs")
     return ap.parse_args()
 
 
@@ -139,6 +140,96 @@ class ClockSampler:
         loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
         return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ other workloads
+def level_throughput(Q, W, torch, cfg, k, steps, stream, launches=3, imad_per_s=None):
+    """Walk steps/s of one single-target level launch at a configured size."""
+    c = W.CONFIGS[cfg]
+    gates, _ = W.config_target(cfg)
+    p = Q.default_params(c["n"], walks=c["walks"], state_bits=c["L"], dp_bits=c["dtheta"],
+                         table_log2=min(c["table_log2"], 24))
+    prob = Q.Problem.from_circuit(c["n"], gates, c["k_max"], p)
+    prob.level_begin(k, 0, c["dtheta"], stream=stream)
+    prob.level_walk(steps, stream); prob.level_rewalk(stream); prob.level_collect(stream)
+    r0 = prob.poll()
+    ms = []
+    for _ in range(launches):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        prob.level_walk(steps, stream)
+        e1.record(stream)
+        prob.level_rewalk(stream)
+        prob.level_collect(stream)
+        ms.append(e0.elapsed_time(e1))
+    r1 = prob.poll()
+    prob.close()
+    d = 4 ** c["n"] - 1
+    walk_s = sum(ms) / 1e3
+    out = {"workload": f"n{c['n']}_level{k}_walks{c['walks']}_L{c['L']}_theta2^-{c['dtheta']}",
+           "walk_steps_per_s": (r1["steps"] - r0["steps"]) / walk_s}
+    if imad_per_s:
+        out["imad_frac"] = (r1["w_steps"] - r0["w_steps"]) * 2 * d * d / walk_s / imad_per_s
+    return out
+
+
+def run_batched(Q, W, torch, stream, n_targets=256, rounds=12):
+    """Config 4: many seeded targets in one persistent launch per qubit count
+    (one CUDA-graph replay per round) against the same jobs launched one
+    target at a time, on identical work (the trajectories are deterministic)."""
+    from paper_1606_07413_gb300 import autotune
+
+    targets = W.batched_targets(n_targets)
+    t0 = time.perf_counter()
+    best, trials = autotune.tune_batch(targets[:48], rounds=8, stream=stream)
+    tune_s = time.perf_counter() - t0
+
+    def mk(i, t):
+        return Q.Problem.from_circuit(t["n"], t["gates"], t["t"],
+                                      Q.default_params(t["n"], theta_min_bits=best["theta_min_bits"], seed=1000 + i))
+
+    def bp(J):
+        return Q.default_batch_params(max_jobs=J, walks_per_job=best["walks_per_job"],
+                                      steps_per_round=best["steps_per_round"], table_log2=18,
+                                      queue_capacity=best["queue_capacity"])
+
+    probs = [mk(i, t) for i, t in enumerate(targets)]
+    with Q.Batch(bp(len(targets)), stream) as b:
+        ids = [b.add(p) for p in probs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(rounds):
+            b.round()
+        batched_s = time.perf_counter() - t0
+        res = [b.poll(j) for j in ids]
+    for p in probs:
+        p.close()
+    one_s = 0.0
+    for i, t in enumerate(targets):
+        p = mk(i, t)
+        with Q.Batch(bp(1), stream) as b:
+            j = b.add(p)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(rounds):
+                b.round()
+            one_s += time.perf_counter() - t0
+        p.close()
+    fev = sum(r["steps"] + r["rewalk_steps"] for r in res)
+    walk = sum(r["steps"] for r in res)
+    imad = sum(r["w_steps"] * 2 * (4 ** t["n"] - 1) ** 2 for r, t in zip(res, targets))
+    tts = sorted(r["seconds"] for r in res if r["status_name"] == "found")
+    q = lambda f: tts[min(len(tts) - 1, int(f * len(tts)))] if tts else None
+    return {
+        "workload": f"{n_targets} seeded targets, n~U{{2,3,4}}, T-count~U{{3..7}}, {rounds} rounds",
+        "autotuned": best, "autotune_seconds": tune_s, "autotune_trials": len(trials),
+        "batched_fevals_per_s": fev / batched_s, "one_target_fevals_per_s": fev / one_s,
+        "batched_walk_steps_per_s": walk / batched_s, "one_target_walk_steps_per_s": walk / one_s,
+        "speedup": one_s / batched_s, "batched_s": batched_s, "one_target_s": one_s,
+        "imad_per_s_batched": imad / batched_s,
+        "found": len(tts), "time_to_tcount_p50_s": q(0.5), "time_to_tcount_p99_s": q(0.99),
+        "graph": "each batched round is one CUDA-graph replay",
+    }
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -238,6 +329,7 @@ def run_ours(args):
     # launches with per-launch host reads, same throughput setting
     e2e = None
     tts = None
+    extra = None
     if rank == 0:
         budget = args.steps * c["walks"] * STEPS_PER_LAUNCH
         pe = Q.default_params(c["n"], walks=c["walks"], state_bits=c["L"], dp_bits=c["dtheta"],
@@ -268,6 +360,12 @@ def run_ours(args):
                    "note": "full ladder from the sde bound, theta policy 1; the library reports FOUND "
                            "only after its exact host verification of the decomposition"}
             pt.close()
+        if not args.no_extra:
+            extra = {
+                "batched": run_batched(Q, W, torch, stream),
+                "n2_level3": level_throughput(Q, W, torch, 1, 3, 512, stream, imad_per_s=imad_per_s),
+                "n4_level7": level_throughput(Q, W, torch, 3, 7, 16, stream, imad_per_s=imad_per_s),
+            }
     prob.close()
 
     if rank == 0:
@@ -280,6 +378,8 @@ def run_ours(args):
             "gpu_launches": 2 * args.steps, "time_to_optimal_t_count": tts,
             "wall_s": wall,
         }
+        if extra:
+            line.update(extra)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -97,7 +97,7 @@ typedef struct qcs_params {
     int32_t version_factor;   /* new function version every version_factor * points steps (0: never) */
     int32_t stop_on_claw;     /* 1: stop at the first verified claw; 0: keep walking to the step budget
                                  (the first decomposition is still reported) */
-    int32_t reserved;
+    int32_t theta_min_bits;   /* theta_policy 1 never raises theta above 2^-theta_min_bits (>= 1) */
     uint64_t seed;            /* seed of trail starting points */
 } qcs_params;
 
@@ -119,6 +119,7 @@ typedef struct qcs_result {
     int64_t launches;    /* walk-kernel launches */
     double seconds;      /* wall time since qcs_run_walks */
     int64_t w_steps;     /* walk steps taken on the W side (the 4^n x 4^n contraction) */
+    int64_t rewalk_steps; /* evaluations of f made by the re-walk (Fig. 2 trace-back) */
 } qcs_result;
 
 typedef struct qcs_problem qcs_problem;
@@ -223,6 +224,56 @@ QCS_API int qcs_level_collect(qcs_problem *prob, void *stream, qcs_result *out);
 QCS_API int qcs_level_walk_static(qcs_problem *prob, int k, uint32_t version, int dp_bits, int begin,
                                   void *walk_states, uint32_t n_walks, uint32_t steps, uint64_t *merges,
                                   uint32_t merge_cap, uint64_t *counts, void *stream);
+
+/* ---- many targets at once (the batched search) -------------------------
+ * A batch runs many problems together: each job is one target on its own
+ * T-count ladder with its own walks, distinguished-point table and merge
+ * queue (Sec. 3); one round advances every active job by one launch of its
+ * level (walk, re-walk, exact claw checks), with all jobs of one qubit count
+ * in one persistent walk kernel and one persistent re-walk kernel.  With
+ * use_graph = 1 a round is one replay of a CUDA graph captured at the first
+ * round.  Jobs may be added and removed between rounds. */
+typedef struct qcs_batch qcs_batch;
+
+typedef struct qcs_batch_params {
+    int32_t max_jobs;        /* job slots, 1..65536 */
+    int32_t walks_per_job;   /* concurrent walks of each job (multiple of 8) */
+    int32_t steps_per_round; /* walk steps per walk per round (upper bound) */
+    int32_t table_log2;      /* distinguished-point table of each job: 2^table_log2 slots */
+    int32_t queue_capacity;  /* merges kept per job per round */
+    int32_t use_graph;       /* 1: each round is one CUDA-graph replay */
+    int32_t reserved[2];
+} qcs_batch_params;
+
+QCS_API void qcs_batch_default_params(qcs_batch_params *p);
+
+/* Allocates the pooled per-job arrays for max_jobs jobs.  stream: the CUDA
+ * stream of every round (a non-default stream is needed for graph capture;
+ * NULL makes the batch create its own). */
+QCS_API int qcs_batch_create(const qcs_batch_params *p, void *stream, qcs_batch **out);
+
+/* Device bytes one job of this problem's size needs in this batch (its walks,
+ * table and queue plus the problem's matrices): the basis of admission. */
+QCS_API uint64_t qcs_batch_job_bytes(const qcs_batch *batch, const qcs_problem *prob);
+
+/* Add a created problem as a job (its ladder starts at sde(C^)); the batch
+ * borrows prob until the job is removed or the batch destroyed.  Allocates the
+ * job's walks, table and queue.  *job gets the job's slot.  QCS_ERR_BUSY when
+ * every slot is used or the problem is running qcs_run_walks. */
+QCS_API int qcs_batch_add(qcs_batch *batch, qcs_problem *prob, int *job);
+
+/* Remove a job (finished or not) and free its buffers. */
+QCS_API int qcs_batch_remove(qcs_batch *batch, int job);
+
+/* One round for every active job; blocks until the round's results are in.
+ * *n_active (may be NULL) gets the number of jobs still searching. */
+QCS_API int qcs_batch_round(qcs_batch *batch, int *n_active);
+
+/* A job's result (as qcs_poll_collisions reports it for the problem). */
+QCS_API int qcs_batch_poll(qcs_batch *batch, int job, qcs_result *out);
+
+/* Frees the batch and every job's buffers (not the problems). */
+QCS_API void qcs_batch_destroy(qcs_batch *batch);
 
 /* Exact host check that C = e^{i phi} R(P_t)..R(P_1) D for a Clifford D
  * (Sec. 4.1): forms D^ = R^(P_1)^T..R^(P_t)^T C^ and tests that it is a signed

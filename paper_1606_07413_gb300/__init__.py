@@ -16,8 +16,8 @@ import numpy as np
 
 from . import build as _build_mod
 
-__all__ = ["lib", "Params", "Result", "Problem", "default_params", "verify_decomposition",
-           "strerror", "QcsError"]
+__all__ = ["lib", "Params", "Result", "Problem", "Batch", "BatchParams", "default_params",
+           "default_batch_params", "verify_decomposition", "strerror", "QcsError"]
 
 OK = 0
 ERR_ARG, ERR_NOT_UNITARY, ERR_NOMEM, ERR_CUDA, ERR_MISMATCH, ERR_OVERFLOW, ERR_BUSY, ERR_TIMEOUT, ERR_DEVICE = \
@@ -33,7 +33,7 @@ class Params(ctypes.Structure):
                 ("table_log2", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32),
                 ("max_trail_factor", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
                 ("budget_factor", ctypes.c_int32), ("theta_policy", ctypes.c_int32),
-                ("version_factor", ctypes.c_int32), ("stop_on_claw", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("version_factor", ctypes.c_int32), ("stop_on_claw", ctypes.c_int32), ("theta_min_bits", ctypes.c_int32),
                 ("seed", ctypes.c_uint64)]
 
     def as_dict(self):
@@ -48,13 +48,23 @@ class Result(ctypes.Structure):
                 ("same_side", ctypes.c_int64), ("claws", ctypes.c_int64), ("false_hash", ctypes.c_int64),
                 ("no_merge", ctypes.c_int64), ("abandoned", ctypes.c_int64), ("dropped", ctypes.c_int64),
                 ("queue_overflow", ctypes.c_int64), ("launches", ctypes.c_int64), ("seconds", ctypes.c_double),
-                ("w_steps", ctypes.c_int64)]
+                ("w_steps", ctypes.c_int64), ("rewalk_steps", ctypes.c_int64)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
         d["paulis"] = [int(v) for v in self.paulis[: max(self.t_count, 0)]]
         d["status_name"] = STATUS_NAMES.get(self.status, "?")
         return d
+
+
+class BatchParams(ctypes.Structure):
+    _fields_ = [("max_jobs", ctypes.c_int32), ("walks_per_job", ctypes.c_int32),
+                ("steps_per_round", ctypes.c_int32), ("table_log2", ctypes.c_int32),
+                ("queue_capacity", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
 
 
 class QcsError(RuntimeError):
@@ -103,6 +113,14 @@ def lib():
             "qcs_level_collect": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(Result)]),
             "qcs_level_walk_static": (ctypes.c_int, [_vp, ctypes.c_int, _u32, ctypes.c_int, ctypes.c_int, _vp, _u32,
                                                      _u32, _vp, _u32, _vp, _vp]),
+            "qcs_batch_default_params": (None, [ctypes.POINTER(BatchParams)]),
+            "qcs_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchParams), _vp, ctypes.POINTER(_vp)]),
+            "qcs_batch_job_bytes": (_u64, [_vp, _vp]),
+            "qcs_batch_add": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_int)]),
+            "qcs_batch_remove": (ctypes.c_int, [_vp, ctypes.c_int]),
+            "qcs_batch_round": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+            "qcs_batch_poll": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(Result)]),
+            "qcs_batch_destroy": (None, [_vp]),
             "qcs_problem_sde": (ctypes.c_int, [_vp]),
             "qcs_level_points": (_u64, [_vp, ctypes.c_int]),
             "qcs_get_channel": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(_i32)]),
@@ -273,6 +291,66 @@ class Problem:
     def close(self):
         if self._h:
             lib().qcs_destroy_problem(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def default_batch_params(**overrides) -> BatchParams:
+    p = BatchParams()
+    lib().qcs_batch_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+class Batch:
+    """Many problems searched together (qcs_batch_*): one round advances every
+    active job; jobs join and leave between rounds."""
+
+    def __init__(self, params: BatchParams | None = None, stream=None):
+        self._h = _vp()
+        s = None if stream is None else ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        _check(lib().qcs_batch_create(ctypes.byref(params) if params is not None else None, s,
+                                      ctypes.byref(self._h)), "qcs_batch_create")
+        self._problems = {}
+
+    def job_bytes(self, prob: "Problem") -> int:
+        return int(lib().qcs_batch_job_bytes(self._h, prob._h))
+
+    def add(self, prob: "Problem") -> int:
+        j = ctypes.c_int(-1)
+        _check(lib().qcs_batch_add(self._h, prob._h, ctypes.byref(j)), "qcs_batch_add")
+        self._problems[j.value] = prob
+        return j.value
+
+    def remove(self, job: int):
+        _check(lib().qcs_batch_remove(self._h, int(job)), "qcs_batch_remove")
+        self._problems.pop(job, None)
+
+    def round(self) -> int:
+        n = ctypes.c_int(0)
+        _check(lib().qcs_batch_round(self._h, ctypes.byref(n)), "qcs_batch_round")
+        return n.value
+
+    def poll(self, job: int) -> dict:
+        r = Result()
+        _check(lib().qcs_batch_poll(self._h, int(job), ctypes.byref(r)), "qcs_batch_poll")
+        return r.as_dict()
+
+    def close(self):
+        if self._h:
+            lib().qcs_batch_destroy(self._h)
             self._h = None
 
     def __enter__(self):

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libqcs.so")
 
-SOURCES = ["qcs_walk.cu", "qcs_api.cpp", "qcs_exact.cpp", "qcs_noalloc.cu"]
+SOURCES = ["qcs_walk.cu", "qcs_api.cpp", "qcs_exact.cpp", "qcs_noalloc.cu", "qcs_batch.cpp"]
 PEAK_SRC = "qcs_peak.cu"
 PEAK_LIB = os.path.join(BUILD, "libqcs_peak.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -44,7 +44,9 @@ uint64_t smix_host(uint64_t z)
     return z ^ (z >> 31);
 }
 
-uint64_t upow(uint64_t b, int e)
+} // namespace
+
+uint64_t qcs::upow(uint64_t b, int e)
 {
     uint64_t r = 1;
     while (e-- > 0) r *= b;
@@ -52,7 +54,7 @@ uint64_t upow(uint64_t b, int e)
 }
 
 // bits of one rotation's field in an L-bit state at h rotations per side
-int field_bits(int L, int h)
+int qcs::field_bits(int L, int h)
 {
     if (h == 0) return 0;
     const int l = (L - 1) / h;
@@ -60,7 +62,7 @@ int field_bits(int L, int h)
 }
 
 // the rotations of state x at h rotations per side (see decode in qcs_walk.cu)
-void decode_state(uint64_t x, int n, int L, int h, uint32_t *q)
+void qcs::decode_state(uint64_t x, int n, int L, int h, uint32_t *q)
 {
     const int l = field_bits(L, h);
     const uint64_t xi = (1u << (2 * n)) - 1;
@@ -70,6 +72,8 @@ void decode_state(uint64_t x, int n, int L, int h, uint32_t *q)
     }
 }
 
+namespace {
+
 bool params_ok(int n, int k_max, const qcs_params &p)
 {
     if (n < 1 || n > 4 || k_max < 0 || k_max > 15) return false;
@@ -77,7 +81,7 @@ bool params_ok(int n, int k_max, const qcs_params &p)
     if (p.dp_bits < 1 || p.dp_bits >= p.state_bits) return false;
     if (p.walks < 1 || (uint32_t)p.walks > kMaxWalks || p.table_log2 < 4 || p.table_log2 > 34) return false;
     if (p.steps_per_launch < 1 || p.max_trail_factor < 1 || p.queue_capacity < 1) return false;
-    if (p.budget_factor < 0 || p.version_factor < 0) return false;
+    if (p.budget_factor < 0 || p.version_factor < 0 || p.theta_min_bits < 0) return false;
     // every rotation field must reach all 4^n - 1 Paulis: 2^ell > xi
     const int h = k_max / 2;
     return h == 0 || field_bits(p.state_bits, h) >= 2 * n;
@@ -85,48 +89,12 @@ bool params_ok(int n, int k_max, const qcs_params &p)
 
 } // namespace
 
-struct qcs_problem {
-    int n = 0, D = 0, k_max = 0, device = 0;
-    qcs_params p{};
-    PMat C; // reduced, exponent = sde
-    // device data
-    uint2 *dC32 = nullptr, *dU = nullptr;
-    uint32_t *dCoef = nullptr;
-    Slot *dTable = nullptr;
-    Pair *dQueue = nullptr;
-    uint32_t *dQhead = nullptr; // [0] queued merges, [1] claw candidates
-    Cand *dCands = nullptr;
-    WalkState *dWalks = nullptr;
-    unsigned long long *dCounters = nullptr;
-    // pinned host mirrors
-    unsigned long long *hCounters = nullptr;
-    Cand *hCands = nullptr;
-    uint32_t *hQhead = nullptr;
-    // search state
-    std::thread driver;
-    std::mutex mu;
-    std::condition_variable cv;
-    std::atomic<bool> cancel{false};
-    bool running = false;
-    qcs_result res{};
-    std::chrono::steady_clock::time_point t0;
-    PMat Dhat;
-    bool have_D = false;
-    // the level being stepped (qcs_level_* and the driver)
-    struct {
-        bool active = false;
-        int k = 0, h = 0, dp_bits = 0;
-        uint64_t xi = 0;
-        WalkLaunch w{};
-    } lvl;
-};
 
-namespace {
-
-LevelCtx make_level(const qcs_problem *P, int k, uint32_t version, int dp_bits)
+LevelCtx qcs::make_level(const qcs_problem *P, int k, uint32_t version, int dp_bits)
 {
     LevelCtx lv{};
     lv.C32 = P->dC32;
+    lv.C8 = reinterpret_cast<const uint4 *>(P->dC8);
     lv.U = P->dU;
     lv.coef = P->dCoef;
     lv.n = P->n;
@@ -145,6 +113,8 @@ LevelCtx make_level(const qcs_problem *P, int k, uint32_t version, int dp_bits)
     lv.seed = P->p.seed;
     return lv;
 }
+
+namespace {
 
 int upload_problem(qcs_problem *P)
 {
@@ -179,7 +149,28 @@ int upload_problem(qcs_problem *P)
             if (anti) coef[(size_t)p * 2 * R + t] |= 1u << l;
             if (plus) coef[(size_t)p * 2 * R + R + t] |= 1u << l;
         }
+    // n = 4: also C^ as int8 pairs when every entry fits; row i, lane l holds
+    // columns l + 32 t (t < 8) as bytes 2t (a) and 2t + 1 (b) of 16 bytes
+    std::vector<int8_t> c8;
+    if (n == 4) {
+        bool fits = true;
+        for (size_t i = 0; i < P->C.a.size() && fits; i++)
+            fits = P->C.a[i] >= -127 && P->C.a[i] <= 127 && P->C.b[i] >= -127 && P->C.b[i] <= 127;
+        if (fits) {
+            c8.resize((size_t)D * D * 2);
+            for (int i = 0; i < D; i++)
+                for (int Q = 0; Q < D; Q++) {
+                    const size_t o = ((size_t)i * 32 + (size_t)(Q % 32)) * 16 + 2 * (size_t)(Q / 32);
+                    c8[o] = (int8_t)P->C.a[(size_t)i * D + Q];
+                    c8[o + 1] = (int8_t)P->C.b[(size_t)i * D + Q];
+                }
+        }
+    }
     CK(cudaGetDevice(&P->device));
+    if (!c8.empty()) {
+        CK(cudaMalloc(&P->dC8, c8.size()));
+        CK(cudaMemcpy(P->dC8, c8.data(), c8.size(), cudaMemcpyHostToDevice));
+    }
     CK(cudaMalloc(&P->dC32, sizeof(uint2) * c32.size()));
     CK(cudaMalloc(&P->dU, sizeof(uint2) * D));
     CK(cudaMalloc(&P->dCoef, sizeof(uint32_t) * coef.size()));
@@ -207,7 +198,7 @@ int ensure_search_buffers(qcs_problem *P)
 
 void free_problem_memory(qcs_problem *P)
 {
-    cudaFree(P->dC32); cudaFree(P->dU); cudaFree(P->dCoef); cudaFree(P->dTable); cudaFree(P->dQueue); cudaFree(P->dQhead);
+    cudaFree(P->dC32); cudaFree(P->dC8); cudaFree(P->dU); cudaFree(P->dCoef); cudaFree(P->dTable); cudaFree(P->dQueue); cudaFree(P->dQhead);
     cudaFree(P->dCands); cudaFree(P->dWalks); cudaFree(P->dCounters);
     cudaFreeHost(P->hCounters); cudaFreeHost(P->hCands); cudaFreeHost(P->hQhead);
 }
@@ -256,7 +247,9 @@ void set_status(qcs_problem *P, int status, int error)
     P->res.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - P->t0).count();
 }
 
-void found(qcs_problem *P, int k, const uint32_t *paulis)
+} // namespace
+
+void qcs::found(qcs_problem *P, int k, const uint32_t *paulis)
 {
     {
         std::lock_guard<std::mutex> g(P->mu);
@@ -271,6 +264,8 @@ void found(qcs_problem *P, int k, const uint32_t *paulis)
     P->Dhat = std::move(Dh);
     P->have_D = true;
 }
+
+namespace {
 
 int level_begin(qcs_problem *P, int k, uint32_t version, int dp_bits, uint32_t n_walks, cudaStream_t s)
 {
@@ -377,6 +372,7 @@ int level_collect(qcs_problem *P, cudaStream_t s, bool *got, uint64_t *steps)
         qcs_result &R = P->res;
         R.steps += (int64_t)c[C_STEPS];
         R.w_steps += (int64_t)c[C_WSTEPS];
+        R.rewalk_steps += (int64_t)c[C_RSTEPS];
         R.dps += (int64_t)c[C_DPS];
         R.abandoned += (int64_t)c[C_ABANDONED];
         R.dropped += (int64_t)c[C_EVICTED];
@@ -395,52 +391,50 @@ int level_collect(qcs_problem *P, cudaStream_t s, bool *got, uint64_t *steps)
     return QCS_OK;
 }
 
-// How a level is walked (Sec. 3 and Appendix): theta, the launch shape, the
-// function-version period and the level's step budget.
-struct LevelPlan {
-    int dp_bits;
-    uint32_t walks, steps;
-    uint64_t launches_per_version, min_launches;
-};
 
-LevelPlan plan_level(const qcs_problem *P, int k)
+
+} // namespace
+
+LevelPlan qcs::plan_level(const qcs_problem *P, int k, const qcs_params &p)
 {
     LevelPlan pl{};
     const uint64_t xi = (uint64_t)(P->D - 1);
     const long double points = 2.0L * (long double)upow(xi, k / 2) * (long double)((k & 1) ? xi : 1);
-    pl.dp_bits = P->p.dp_bits;
-    if (P->p.theta_policy == 1) {
+    pl.dp_bits = p.dp_bits;
+    if (p.theta_policy == 1) {
         // theta as large as 1/2 while theta * points stays within half the table
-        const long double slots = (long double)((uint64_t)1 << P->p.table_log2);
-        int d = 1;
-        while (d < P->p.dp_bits && points / (long double)((uint64_t)1 << d) > slots / 2) d++;
+        const long double slots = (long double)((uint64_t)1 << p.table_log2);
+        int d = std::max(1, std::min(p.theta_min_bits, p.dp_bits));
+        while (d < p.dp_bits && points / (long double)((uint64_t)1 << d) > slots / 2) d++;
         pl.dp_bits = d;
     }
     const long double theta = 1.0L / (long double)((uint64_t)1 << pl.dp_bits);
-    const long double vf = P->p.version_factor > 0 ? (long double)P->p.version_factor : 1e30L;
+    const long double vf = p.version_factor > 0 ? (long double)p.version_factor : 1e30L;
     const long double version_steps = vf * points;
     // a launch covers at most one version; trails of a few 1/theta must fit
-    long double steps = (long double)P->p.steps_per_launch, walks = (long double)P->p.walks;
+    long double steps = (long double)p.steps_per_launch, walks = (long double)p.walks;
     const long double s_min = std::min<long double>(steps, 4.0L / theta);
     if (walks * steps > version_steps) steps = std::max(s_min, std::floor(version_steps / walks));
     if (walks * steps > version_steps) walks = std::max(32.0L, std::floor(version_steps / steps));
     // merges per launch (about one per distinguished point) must fit the queue
-    const long double qroom = (long double)P->p.queue_capacity / 2;
+    const long double qroom = (long double)p.queue_capacity / 2;
     while (walks * steps * theta > qroom && steps > 1) steps = std::floor(steps / 2);
     if (walks * steps * theta > qroom) walks = std::max(32.0L, std::floor(qroom / (steps * theta)));
     pl.walks = (uint32_t)walks;
     pl.steps = (uint32_t)std::max(1.0L, steps);
     const long double per_launch = (long double)pl.walks * pl.steps;
-    pl.launches_per_version = P->p.version_factor > 0
+    pl.launches_per_version = p.version_factor > 0
                                   ? (uint64_t)std::max(1.0L, std::floor(version_steps / per_launch))
                                   : ~0ull;
-    const long double budget = (long double)P->p.budget_factor * points;
+    const long double budget = (long double)p.budget_factor * points;
     const long double lmin = std::ceil(budget / per_launch);
     pl.min_launches = lmin > 1.8e19L ? ~0ull : (uint64_t)std::max(1.0L, lmin);
-    if (P->p.version_factor > 0 && pl.min_launches < 4 * pl.launches_per_version)
+    if (p.version_factor > 0 && pl.min_launches < 4 * pl.launches_per_version)
         pl.min_launches = 4 * pl.launches_per_version; // at least four function versions
     return pl;
 }
+
+namespace {
 
 bool have_decomposition(qcs_problem *P)
 {
@@ -467,7 +461,7 @@ int drive(qcs_problem *P, uint64_t budget, cudaStream_t s)
             }
             continue;
         }
-        const LevelPlan pl = plan_level(P, k);
+        const LevelPlan pl = plan_level(P, k, P->p);
         uint64_t launches = 0, in_version = 0;
         bool fresh = true;
         while (true) {
@@ -550,6 +544,7 @@ void qcs_default_params(int n_qubits, qcs_params *p)
     p->theta_policy = 1;
     p->version_factor = 2;
     p->stop_on_claw = 1;
+    p->theta_min_bits = 1;
     p->seed = 0x2545F4914F6CDD1Dull;
 }
 

@@ -2,9 +2,14 @@
 // qcs_exact.cpp) and the CUDA kernels (qcs_walk.cu).  Not part of the ABI.
 #pragma once
 
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -29,6 +34,9 @@ struct LevelCtx {
     // 32 t (t < R = max(1, 4^n / 32)) sits at i * 4^n + lane * R + t, so one
     // lane's R columns of a row are contiguous.
     const uint2 *C32;
+    // n = 4: C^ as int8 pairs when every entry fits in [-127, 127], else null;
+    // row i, lane l holds columns l + 32 t (t < 8) as 16 bytes (a_t, b_t)
+    const uint4 *C8;
     const uint2 *U;    // fingerprint weights (Ua, Ub) per row, 4^n
     // rotation coefficients: for Pauli p, 2R words; word t (t < R) has bit
     // lane set when row lane + 32 t anticommutes with p, word R + t when the
@@ -95,6 +103,7 @@ enum Counter {
     C_DUPLICATE,
     C_PAIRS,       // merges pushed (including overflowed ones)
     C_CANDS,       // claw candidates found by the re-walk (including overflowed ones)
+    C_RSTEPS,      // walk steps taken by the re-walk (evaluations of f)
     C_CLS0,        // re-walk classes QCS_MERGE_ROBIN_HOOD .. QCS_MERGE_NO_MERGE at C_CLS0 + class
     C_NCOUNTERS = C_CLS0 + 6
 };
@@ -116,7 +125,20 @@ struct WalkLaunch {
     unsigned long long *counters;
 };
 
+// Many jobs in one launch: per qubit count, the device list of tasks
+// (job index, first walk) with kWarps walks each, and of job indices.
+struct BatchArgs {
+    const WalkLaunch *jobs;   // device array indexed by job
+    const uint32_t *tasks;    // 2 * n_tasks entries
+    const uint32_t *n_tasks;  // device scalar
+    const uint32_t *job_ids;  // jobs of this qubit count
+    const uint32_t *n_jobs;   // device scalar
+};
+int walks_per_task(int n); // walks (warps) per CTA of the walk kernels for n qubits
+
 // ---- kernel launchers (qcs_walk.cu); all return cudaError_t of the launch ----
+cudaError_t launch_walks_batch(int n, const BatchArgs &a, cudaStream_t s);
+cudaError_t launch_rewalk_batch(int n, const BatchArgs &a, cudaStream_t s);
 cudaError_t launch_walk_step(const LevelCtx &lv, int chunk, const uint64_t *in, uint64_t *out,
                              uint8_t *is_dp, size_t count, cudaStream_t s);
 cudaError_t launch_init_walks(const WalkLaunch &w, cudaStream_t s);
@@ -158,4 +180,58 @@ int exact_same_coset(int n, const PMat &C, int k, int chunk, const uint32_t *qv,
                      bool *equal);
 int pauli_phase(int n, uint32_t p, uint32_t q); // P(p)P(q) = i^lambda P(p^q)
 
+// How a level is walked (Sec. 3 and Appendix): theta, the launch shape, the
+// function-version period and the level's step budget.
+struct LevelPlan {
+    int dp_bits;
+    uint32_t walks, steps;
+    uint64_t launches_per_version, min_launches;
+};
+
+// helpers of the host library shared by qcs_api.cpp and qcs_batch.cpp
+uint64_t upow(uint64_t b, int e);
+int field_bits(int L, int h);
+void decode_state(uint64_t x, int n, int L, int h, uint32_t *q);
+LevelCtx make_level(const ::qcs_problem *P, int k, uint32_t version, int dp_bits);
+LevelPlan plan_level(const ::qcs_problem *P, int k, const qcs_params &p);
+void found(::qcs_problem *P, int k, const uint32_t *paulis);
+
 } // namespace qcs
+
+// A search problem (include/qcs.h): the exact target and its device copies.
+struct qcs_problem {
+    int n = 0, D = 0, k_max = 0, device = 0;
+    qcs_params p{};
+    qcs::PMat C; // reduced, exponent = sde
+    // device data
+    uint2 *dC32 = nullptr, *dU = nullptr;
+    int8_t *dC8 = nullptr; // n = 4 only, when every entry of C^ fits in int8
+    uint32_t *dCoef = nullptr;
+    qcs::Slot *dTable = nullptr;
+    qcs::Pair *dQueue = nullptr;
+    uint32_t *dQhead = nullptr; // [0] queued merges, [1] claw candidates
+    qcs::Cand *dCands = nullptr;
+    qcs::WalkState *dWalks = nullptr;
+    unsigned long long *dCounters = nullptr;
+    // pinned host mirrors
+    unsigned long long *hCounters = nullptr;
+    qcs::Cand *hCands = nullptr;
+    uint32_t *hQhead = nullptr;
+    // search state
+    std::thread driver;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::atomic<bool> cancel{false};
+    bool running = false;
+    qcs_result res{};
+    std::chrono::steady_clock::time_point t0;
+    qcs::PMat Dhat;
+    bool have_D = false;
+    // the level being stepped (qcs_level_* and the driver)
+    struct {
+        bool active = false;
+        int k = 0, h = 0, dp_bits = 0;
+        uint64_t xi = 0;
+        qcs::WalkLaunch w{};
+    } lvl;
+};

@@ -58,15 +58,21 @@ struct Geo {
     static constexpr int D = DIM - 1;                    // non-identity Paulis
     static constexpr int RPL = DIM >= 32 ? DIM / 32 : 1; // rows (and columns) per lane
     static constexpr int SLOTS = RPL * 32;               // width of the fingerprint sort
-    static constexpr bool C_SMEM = NQ <= 3;              // C^ staged whole in shared memory
+    // n <= 3: C^ low words staged whole (32 KB at n = 3); n = 4: C^ as int8
+    // pairs (128 KB) when every entry fits, else read through L2
+    static constexpr bool C_SMEM = NQ <= 3;
+    static constexpr bool C8_SMEM = NQ == 4;
+    static constexpr int WARPS = NQ == 4 ? 16 : kWarps;  // walks (warps) per CTA
+    static constexpr int THREADS = WARPS * 32;
     static constexpr int COEF_WORDS = DIM * 2 * RPL;     // rotation coefficient bits
     static constexpr int MAX_CHUNKS = 256;               // hash bases, one per chunk
-    // shared memory: weights | C^ (n <= 3) | coefficients | chunk bases | exchange buffers
+    // shared memory: weights | C^ | coefficients | chunk bases | exchange buffers
     static constexpr size_t off_C = sizeof(uint2) * DIM;
-    static constexpr size_t off_coef = off_C + (C_SMEM ? sizeof(uint2) * DIM * DIM : 0);
+    static constexpr size_t off_coef =
+        off_C + (C_SMEM ? sizeof(uint2) * DIM * DIM : 0) + (C8_SMEM ? 2 * DIM * DIM : 0);
     static constexpr size_t off_base = off_coef + sizeof(uint32_t) * COEF_WORDS;
     static constexpr size_t off_xchg = off_base + sizeof(uint64_t) * MAX_CHUNKS;
-    static constexpr size_t smem_bytes = off_xchg + sizeof(uint2) * kWarps * DIM;
+    static constexpr size_t smem_bytes = off_xchg + sizeof(uint2) * WARPS * DIM;
 };
 
 // Shared-memory views of one CTA (C may point to global memory for n = 4).
@@ -74,6 +80,7 @@ template <int NQ>
 struct Smem {
     uint2 *U;
     const uint2 *C;
+    const uint4 *C8;  // n = 4: int8 pairs, row i lane l at [32 i + l] (8 columns), or null
     uint32_t *coef;
     uint64_t *base;
     uint2 *xchg; // this warp's exchange buffer
@@ -198,7 +205,25 @@ __device__ uint64_t warp_step(uint64_t x, uint32_t chunk, const LevelCtx &lv, co
         __syncwarp();
         // L(W e_Q) = sum_i U~_a[i] C_a[i][Q] + U~_b[i] C_b[i][Q]; row 0 has
         // zero weight and C[0][Q] = 0 for Q >= 1, so all rows may be summed.
-        if (G::DIM >= 32) {
+        if (G::C8_SMEM && sm.C8) {
+            // int8 pairs: byte 2t / 2t + 1 of a lane's 16 bytes are a / b of column lane + 32 t
+            const uint4 *su4 = reinterpret_cast<const uint4 *>(su);
+#pragma unroll 2
+            for (int i = 0; i < G::DIM; i += 2) {
+                const uint4 uu = su4[i >> 1];
+                const uint4 r0 = sm.C8[32 * i + lane], r1 = sm.C8[32 * (i + 1) + lane];
+                const uint32_t w0[4] = {r0.x, r0.y, r0.z, r0.w}, w1[4] = {r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+                for (int t = 0; t < G::RPL; t++) {
+                    const int sh = 16 * (t & 1);
+                    const int32_t a0 = (int32_t)(int8_t)(w0[t >> 1] >> sh);
+                    const int32_t b0 = (int32_t)(int8_t)(w0[t >> 1] >> (sh + 8));
+                    const int32_t a1 = (int32_t)(int8_t)(w1[t >> 1] >> sh);
+                    const int32_t b1 = (int32_t)(int8_t)(w1[t >> 1] >> (sh + 8));
+                    Lc[t] += uu.x * (uint32_t)a0 + uu.y * (uint32_t)b0 + uu.z * (uint32_t)a1 + uu.w * (uint32_t)b1;
+                }
+            }
+        } else if (G::DIM >= 32) {
             const uint4 *su4 = reinterpret_cast<const uint4 *>(su);
 #pragma unroll kGemvUnroll
             for (int i = 0; i < G::DIM; i += 2) {
@@ -303,6 +328,7 @@ __device__ __forceinline__ Smem<NQ> stage(const LevelCtx &lv, unsigned char *raw
                              ((uint64_t)(uint32_t)lv.K << 32);
         sm.base[c] = smix(vmix ^ tag);
     }
+    sm.C8 = nullptr;
     if (G::C_SMEM) {
         const uint4 *src = reinterpret_cast<const uint4 *>(lv.C32);
         uint4 *dst = reinterpret_cast<uint4 *>(sC);
@@ -310,20 +336,25 @@ __device__ __forceinline__ Smem<NQ> stage(const LevelCtx &lv, unsigned char *raw
         sm.C = sC;
     } else {
         sm.C = lv.C32;
+        if (G::C8_SMEM && lv.C8) {
+            uint4 *dst = reinterpret_cast<uint4 *>(sC);
+            for (int i = threadIdx.x; i < G::DIM * G::DIM * 2 / 16; i += blockDim.x) dst[i] = lv.C8[i];
+            sm.C8 = dst;
+        }
     }
     __syncthreads();
     return sm;
 }
 
 template <int NQ>
-__global__ void __launch_bounds__(kThreads) k_walk_step(LevelCtx lv, uint32_t chunk, const uint64_t *__restrict__ in,
+__global__ void __launch_bounds__(Geo<NQ>::THREADS) k_walk_step(LevelCtx lv, uint32_t chunk, const uint64_t *__restrict__ in,
                                                         uint64_t *__restrict__ out, uint8_t *__restrict__ is_dp,
                                                         size_t count)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Smem<NQ> sm = stage<NQ>(lv, smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (size_t i = (size_t)blockIdx.x * kWarps + warp; i < count; i += (size_t)gridDim.x * kWarps) {
+    for (size_t i = (size_t)blockIdx.x * Geo<NQ>::WARPS + warp; i < count; i += (size_t)gridDim.x * Geo<NQ>::WARPS) {
         const uint64_t y = warp_step<NQ>(in[i], chunk, lv, sm, lane);
         if (lane == 0) {
             out[i] = y;
@@ -363,15 +394,31 @@ __device__ __forceinline__ void new_trail(WalkState &st, uint32_t walk, const Le
     st.chunk = trail_chunk(lv, st.start);
 }
 
-struct LaneCounters {
-    unsigned long long evicted = 0, duplicate = 0, pairs = 0;
+// per-warp tallies, added to the job's counters by lane 0 (flush_tally)
+struct Tally {
+    unsigned long long steps = 0, w = 0, dp = 0, ab = 0, evicted = 0, duplicate = 0, pairs = 0;
 };
+
+__device__ __forceinline__ void flush_tally(unsigned long long *counters, Tally &t, int lane)
+{
+    if (lane == 0) {
+        if (t.steps) atomicAdd(&counters[C_STEPS], t.steps);
+        if (t.w) atomicAdd(&counters[C_WSTEPS], t.w);
+        if (t.dp) atomicAdd(&counters[C_DPS], t.dp);
+        if (t.ab) atomicAdd(&counters[C_ABANDONED], t.ab);
+        if (t.evicted) atomicAdd(&counters[C_EVICTED], t.evicted);
+        if (t.duplicate) atomicAdd(&counters[C_DUPLICATE], t.duplicate);
+        if (t.pairs) atomicAdd(&counters[C_PAIRS], t.pairs);
+    }
+    t = Tally();
+}
 
 // Store the distinguished point (Sec. 3: the triple start, end, length) in
 // the slot its value hashes to, keeping the newest trail there (one 128-bit
 // atomic exchange, never a wait).  If the slot held the same point from
 // another trail the two trails merged: queue them for the re-walk.
-__device__ void dp_insert(const WalkLaunch &w, uint64_t dp, uint64_t ref, LaneCounters &c)
+template <typename WL>
+__device__ void dp_insert(const WL &w, uint64_t dp, uint64_t ref, Tally &c)
 {
     Slot nv;
     nv.key = dp;
@@ -397,44 +444,80 @@ __device__ void dp_insert(const WalkLaunch &w, uint64_t dp, uint64_t ref, LaneCo
     }
 }
 
+// Advance one walk by w.steps steps (Sec. 3 trails): a trail that reaches a
+// distinguished point is stored and a new one starts; a trail longer than
+// the cut-off is abandoned.  All lanes of the warp call it.
+template <int NQ, typename WL>
+__device__ __forceinline__ void walk_one(const WL &w, const Smem<NQ> &sm, int walk, int lane, Tally &t)
+{
+    WalkState st = w.walks[walk];
+    const uint32_t steps = w.steps, max_len = w.max_len;
+    const int dshift = w.lv.dshift;
+    for (uint32_t s = 0; s < steps; s++) {
+        const uint64_t y = warp_step<NQ>(st.cur, st.chunk, w.lv, sm, lane);
+        t.steps++;
+        t.w += st.cur & 1;
+        st.len++;
+        if ((y >> dshift) == 0) {
+            t.dp++;
+            if (lane == 0) dp_insert(w, y, make_ref((uint32_t)walk, st.seq, st.len), t);
+            __syncwarp();
+            new_trail(st, (uint32_t)walk, w.lv);
+        } else if (st.len >= max_len) {
+            t.ab++;
+            new_trail(st, (uint32_t)walk, w.lv);
+        } else {
+            st.cur = y;
+        }
+    }
+    if (lane == 0) w.walks[walk] = st;
+}
+
 template <int NQ>
-__global__ void __launch_bounds__(kThreads, QCS_MIN_BLOCKS) k_walks(WalkLaunch w)
+__global__ void __launch_bounds__(Geo<NQ>::THREADS, QCS_MIN_BLOCKS) k_walks(WalkLaunch w)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Smem<NQ> sm = stage<NQ>(w.lv, smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned long long n_steps = 0, n_w = 0, n_dp = 0, n_ab = 0;
-    LaneCounters c;
-    for (int walk = blockIdx.x * kWarps + warp; walk < w.n_walks; walk += gridDim.x * kWarps) {
-        WalkState st = w.walks[walk];
-        for (uint32_t s = 0; s < w.steps; s++) {
-            const uint64_t y = warp_step<NQ>(st.cur, st.chunk, w.lv, sm, lane);
-            n_steps++;
-            n_w += st.cur & 1;
-            st.len++;
-            if ((y >> w.lv.dshift) == 0) {
-                n_dp++;
-                if (lane == 0) dp_insert(w, y, make_ref((uint32_t)walk, st.seq, st.len), c);
-                __syncwarp();
-                new_trail(st, (uint32_t)walk, w.lv);
-            } else if (st.len >= w.max_len) {
-                n_ab++;
-                new_trail(st, (uint32_t)walk, w.lv);
-            } else {
-                st.cur = y;
-            }
+    Tally t;
+    for (int walk = blockIdx.x * Geo<NQ>::WARPS + warp; walk < w.n_walks; walk += gridDim.x * Geo<NQ>::WARPS)
+        walk_one<NQ>(w, sm, walk, lane, t);
+    flush_tally(w.counters, t, lane);
+}
+
+// Many jobs (targets, each at its own level) in one persistent launch: the
+// CTA takes a contiguous range of tasks (job, first walk) of this qubit
+// count, restages the job's data when the job changes, and each warp walks
+// one of the task's WARPS walks.  The job's launch record is copied to
+// shared memory.
+template <int NQ>
+__global__ void __launch_bounds__(Geo<NQ>::THREADS, QCS_MIN_BLOCKS) k_walks_batch(BatchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ WalkLaunch sw;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t nt = *a.n_tasks;
+    int cur = -1;
+    Smem<NQ> sm;
+    Tally t;
+    // a contiguous range of tasks per CTA, so that job changes (restaging) are rare
+    const uint32_t t_begin = (uint32_t)(((uint64_t)nt * blockIdx.x) / gridDim.x);
+    const uint32_t t_end = (uint32_t)(((uint64_t)nt * (blockIdx.x + 1)) / gridDim.x);
+    for (uint32_t task = t_begin; task < t_end; task++) {
+        const int job = (int)a.tasks[2 * task];
+        const int first = (int)a.tasks[2 * task + 1];
+        if (job != cur) {
+            if (cur >= 0) flush_tally(sw.counters, t, lane);
+            __syncthreads(); // every warp is done with the previous job's data
+            if (threadIdx.x == 0) sw = a.jobs[job];
+            __syncthreads();
+            sm = stage<NQ>(sw.lv, smem_raw);
+            cur = job;
         }
-        if (lane == 0) w.walks[walk] = st;
+        const int walk = first + warp;
+        if (walk < sw.n_walks) walk_one<NQ>(sw, sm, walk, lane, t);
     }
-    if (lane == 0) {
-        atomicAdd(&w.counters[C_STEPS], n_steps);
-        atomicAdd(&w.counters[C_WSTEPS], n_w);
-        atomicAdd(&w.counters[C_DPS], n_dp);
-        atomicAdd(&w.counters[C_ABANDONED], n_ab);
-        if (c.evicted) atomicAdd(&w.counters[C_EVICTED], c.evicted);
-        if (c.duplicate) atomicAdd(&w.counters[C_DUPLICATE], c.duplicate);
-        if (c.pairs) atomicAdd(&w.counters[C_PAIRS], c.pairs);
-    }
+    if (cur >= 0) flush_tally(sw.counters, t, lane);
 }
 
 __global__ void k_init_walks(WalkLaunch w)
@@ -453,9 +536,10 @@ __global__ void k_init_walks(WalkLaunch w)
 // maximum trail length, so both loops end.
 template <int NQ>
 __device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa, uint32_t la, uint64_t sb,
-                                uint32_t lb, const Smem<NQ> &sm, int lane)
+                                uint32_t lb, const Smem<NQ> &sm, int lane, unsigned long long *fevals = nullptr)
 {
     RewalkOut r;
+    unsigned long long nf = 0;
     r.chunk = chunk;
     if (la > kMaxRewalkLen || lb > kMaxRewalkLen) {
         r.cls = 5;
@@ -469,6 +553,8 @@ __device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa,
     }
     uint64_t a = sa, b = sb;
     for (uint32_t s = 0; s < la - lb; s++) a = warp_step<NQ>(a, chunk, lv, sm, lane);
+    nf += la - lb;
+    if (fevals) *fevals += nf;
     if (a == b) {
         r.cls = 0; // Robin Hood
         r.a = r.b = a;
@@ -477,6 +563,7 @@ __device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa,
     for (uint32_t s = 0; s < lb; s++) {
         const uint64_t fa = warp_step<NQ>(a, chunk, lv, sm, lane);
         const uint64_t fb = warp_step<NQ>(b, chunk, lv, sm, lane);
+        if (fevals) *fevals += 2;
         if (fa == fb) {
             const Decoded da = decode(a, lv), db = decode(b, lv);
             r.a = a;
@@ -494,16 +581,15 @@ __device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa,
     return r;
 }
 
-template <int NQ>
-__global__ void __launch_bounds__(kThreads) k_rewalk_pairs(WalkLaunch w)
+// Re-walk this CTA's share of one job's queued merges; classes are counted
+// per warp and claw candidates appended to the job's candidate list.
+template <int NQ, typename WL>
+__device__ __forceinline__ void rewalk_job(const WL &w, const Smem<NQ> &sm, uint32_t p_begin, uint32_t p_end,
+                                           uint32_t p_stride, int lane)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const uint32_t cnt = min(*w.qhead, w.qcap);
-    if (cnt == 0) return;
-    const Smem<NQ> sm = stage<NQ>(w.lv, smem_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0; // per class, in registers
-    for (uint32_t p = blockIdx.x * kWarps + warp; p < cnt; p += gridDim.x * kWarps) {
+    unsigned long long fev = 0;
+    for (uint32_t p = p_begin; p < p_end; p += p_stride) {
         const Pair P = w.queue[p];
         uint32_t wa, sa, la, wb, sb, lb;
         split_ref(P.ref_a, wa, sa, la);
@@ -514,7 +600,7 @@ __global__ void __launch_bounds__(kThreads) k_rewalk_pairs(WalkLaunch w)
         if (ca != cb) { // the same value reached in two chunks' functions: no merge
             r.cls = 5;
         } else {
-            r = rewalk_one<NQ>(w.lv, ca, xa, la, xb, lb, sm, lane);
+            r = rewalk_one<NQ>(w.lv, ca, xa, la, xb, lb, sm, lane, &fev);
         }
         c0 += r.cls == 0;
         c1 += r.cls == 1;
@@ -540,11 +626,57 @@ __global__ void __launch_bounds__(kThreads) k_rewalk_pairs(WalkLaunch w)
         for (int c = 0; c < 6; c++)
             if (cc[c]) atomicAdd(&w.counters[C_CLS0 + c], cc[c]);
         if (c3) atomicAdd(&w.counters[C_CANDS], c3);
+        if (fev) atomicAdd(&w.counters[C_RSTEPS], fev);
     }
 }
 
 template <int NQ>
-__global__ void __launch_bounds__(kThreads) k_rewalk_arrays(LevelCtx lv, uint32_t chunk, const uint64_t *sa,
+__global__ void __launch_bounds__(Geo<NQ>::THREADS) k_rewalk_pairs(WalkLaunch w)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t cnt = min(*w.qhead, w.qcap);
+    if (cnt <= blockIdx.x * Geo<NQ>::WARPS) return; // no pair for this CTA (uniform)
+    const Smem<NQ> sm = stage<NQ>(w.lv, smem_raw);
+    rewalk_job<NQ>(w, sm, blockIdx.x * Geo<NQ>::WARPS + (threadIdx.x >> 5), cnt, gridDim.x * Geo<NQ>::WARPS,
+                   threadIdx.x & 31);
+}
+
+// The batched re-walk: the queued merges of all jobs of this qubit count
+// form one index space; each CTA takes a contiguous range of it, so it
+// restages a job's data only where its range enters that job.
+template <int NQ>
+__global__ void __launch_bounds__(Geo<NQ>::THREADS) k_rewalk_batch(BatchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ WalkLaunch sw;
+    const uint32_t nj = *a.n_jobs;
+    uint64_t total = 0;
+    for (uint32_t j = 0; j < nj; j++) {
+        const WalkLaunch &w = a.jobs[a.job_ids[j]];
+        total += min(*w.qhead, w.qcap);
+    }
+    const uint64_t lo = total * blockIdx.x / gridDim.x, hi = total * (blockIdx.x + 1) / gridDim.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t base = 0;
+    for (uint32_t j = 0; j < nj && base < hi; j++) {
+        const int job = (int)a.job_ids[j];
+        const uint32_t cnt = min(*a.jobs[job].qhead, a.jobs[job].qcap);
+        if (base + cnt <= lo) {
+            base += cnt;
+            continue;
+        }
+        const uint32_t p_begin = (uint32_t)(max(lo, base) - base), p_end = (uint32_t)(min(hi, base + cnt) - base);
+        base += cnt;
+        __syncthreads();
+        if (threadIdx.x == 0) sw = a.jobs[job];
+        __syncthreads();
+        const Smem<NQ> sm = stage<NQ>(sw.lv, smem_raw);
+        rewalk_job<NQ>(sw, sm, p_begin + warp, p_end, Geo<NQ>::WARPS, lane);
+    }
+}
+
+template <int NQ>
+__global__ void __launch_bounds__(Geo<NQ>::THREADS) k_rewalk_arrays(LevelCtx lv, uint32_t chunk, const uint64_t *sa,
                                                             const uint32_t *la, const uint64_t *sb,
                                                             const uint32_t *lb, size_t count, int32_t *cls,
                                                             uint64_t *ab)
@@ -552,7 +684,7 @@ __global__ void __launch_bounds__(kThreads) k_rewalk_arrays(LevelCtx lv, uint32_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Smem<NQ> sm = stage<NQ>(lv, smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (size_t p = (size_t)blockIdx.x * kWarps + warp; p < count; p += (size_t)gridDim.x * kWarps) {
+    for (size_t p = (size_t)blockIdx.x * Geo<NQ>::WARPS + warp; p < count; p += (size_t)gridDim.x * Geo<NQ>::WARPS) {
         const RewalkOut r = rewalk_one<NQ>(lv, chunk, sa[p], la[p], sb[p], lb[p], sm, lane);
         if (lane == 0) {
             cls[p] = r.cls;
@@ -571,7 +703,7 @@ int blocks_per_sm()
     if (!cached) {
         cudaFuncSetAttribute(k_walks<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<NQ>::smem_bytes);
         int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walks<NQ>, kThreads, Geo<NQ>::smem_bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walks<NQ>, Geo<NQ>::THREADS, Geo<NQ>::smem_bytes);
         cached = b > 0 ? b : 1;
     }
     return cached;
@@ -581,7 +713,7 @@ template <int NQ>
 unsigned grid_for(size_t warps_needed)
 {
     const size_t cap = (size_t)num_sms() * (size_t)blocks_per_sm<NQ>();
-    size_t g = (warps_needed + kWarps - 1) / kWarps;
+    size_t g = (warps_needed + Geo<NQ>::WARPS - 1) / Geo<NQ>::WARPS;
     if (g > cap) g = cap;
     if (g == 0) g = 1;
     return (unsigned)g;
@@ -592,7 +724,7 @@ cudaError_t walk_step_n(const LevelCtx &lv, int chunk, const uint64_t *in, uint6
                         size_t count, cudaStream_t s)
 {
     cudaFuncSetAttribute(k_walk_step<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<NQ>::smem_bytes);
-    k_walk_step<NQ><<<grid_for<NQ>(count), kThreads, Geo<NQ>::smem_bytes, s>>>(lv, (uint32_t)chunk, in, out, is_dp,
+    k_walk_step<NQ><<<grid_for<NQ>(count), Geo<NQ>::THREADS, Geo<NQ>::smem_bytes, s>>>(lv, (uint32_t)chunk, in, out, is_dp,
                                                                                count);
     return cudaGetLastError();
 }
@@ -605,11 +737,40 @@ cudaError_t walks_n(const WalkLaunch &w, cudaStream_t s)
 }
 
 template <int NQ>
+int batch_grid()
+{
+    static int g = 0;
+    if (!g) {
+        cudaFuncSetAttribute(k_walks_batch<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<NQ>::smem_bytes);
+        cudaFuncSetAttribute(k_rewalk_batch<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Geo<NQ>::smem_bytes);
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walks_batch<NQ>, Geo<NQ>::THREADS, Geo<NQ>::smem_bytes);
+        g = num_sms() * (b > 0 ? b : 1);
+    }
+    return g;
+}
+
+template <int NQ>
+cudaError_t walks_batch_n(const BatchArgs &a, cudaStream_t s)
+{
+    k_walks_batch<NQ><<<batch_grid<NQ>(), Geo<NQ>::THREADS, Geo<NQ>::smem_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NQ>
+cudaError_t rewalk_batch_n(const BatchArgs &a, cudaStream_t s)
+{
+    k_rewalk_batch<NQ><<<batch_grid<NQ>(), Geo<NQ>::THREADS, Geo<NQ>::smem_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NQ>
 cudaError_t rewalk_pairs_n(const WalkLaunch &w, cudaStream_t s)
 {
     cudaFuncSetAttribute(k_rewalk_pairs<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)Geo<NQ>::smem_bytes);
-    k_rewalk_pairs<NQ><<<grid_for<NQ>(w.qcap), kThreads, Geo<NQ>::smem_bytes, s>>>(w);
+    k_rewalk_pairs<NQ><<<grid_for<NQ>(w.qcap), Geo<NQ>::THREADS, Geo<NQ>::smem_bytes, s>>>(w);
     return cudaGetLastError();
 }
 
@@ -620,7 +781,7 @@ cudaError_t rewalk_arrays_n(const LevelCtx &lv, int chunk, const uint64_t *sa, c
 {
     cudaFuncSetAttribute(k_rewalk_arrays<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)Geo<NQ>::smem_bytes);
-    k_rewalk_arrays<NQ><<<grid_for<NQ>(count), kThreads, Geo<NQ>::smem_bytes, s>>>(lv, (uint32_t)chunk, sa, la,
+    k_rewalk_arrays<NQ><<<grid_for<NQ>(count), Geo<NQ>::THREADS, Geo<NQ>::smem_bytes, s>>>(lv, (uint32_t)chunk, sa, la,
                                                                                    sb, lb, count, cls, ab);
     return cudaGetLastError();
 }
@@ -637,6 +798,8 @@ int num_sms()
     }
     return g_num_sms;
 }
+
+int walks_per_task(int n) { return n == 4 ? Geo<4>::WARPS : n == 3 ? Geo<3>::WARPS : n == 2 ? Geo<2>::WARPS : Geo<1>::WARPS; }
 
 int walk_blocks_per_sm(int n)
 {
@@ -663,7 +826,7 @@ cudaError_t launch_walk_step(const LevelCtx &lv, int chunk, const uint64_t *in, 
 
 cudaError_t launch_init_walks(const WalkLaunch &w, cudaStream_t s)
 {
-    k_init_walks<<<(w.n_walks + 255) / 256, 256, 0, s>>>(w);
+    if (w.n_walks > 0) k_init_walks<<<(w.n_walks + 255) / 256, 256, 0, s>>>(w);
     return cudaGetLastError();
 }
 
@@ -685,6 +848,28 @@ cudaError_t launch_rewalk_pairs(const WalkLaunch &w, cudaStream_t s)
     case 2: return rewalk_pairs_n<2>(w, s);
     case 3: return rewalk_pairs_n<3>(w, s);
     case 4: return rewalk_pairs_n<4>(w, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_walks_batch(int n, const BatchArgs &a, cudaStream_t s)
+{
+    switch (n) {
+    case 1: return walks_batch_n<1>(a, s);
+    case 2: return walks_batch_n<2>(a, s);
+    case 3: return walks_batch_n<3>(a, s);
+    case 4: return walks_batch_n<4>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_rewalk_batch(int n, const BatchArgs &a, cudaStream_t s)
+{
+    switch (n) {
+    case 1: return rewalk_batch_n<1>(a, s);
+    case 2: return rewalk_batch_n<2>(a, s);
+    case 3: return rewalk_batch_n<3>(a, s);
+    case 4: return rewalk_batch_n<4>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }
