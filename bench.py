@@ -232,6 +232,33 @@ def run_batched(Q, W, torch, stream, n_targets=256, rounds=12):
     }
 
 
+def run_serving(Q, W, torch, stream, tuned, n_requests=2000, rate=50.0, budget_bytes=2 << 30,
+                deadline_s=10.0, drain_s=15.0):
+    """Config 5: a Poisson stream of seeded targets replayed in real time into
+    the continuous-batching server; latency is arrival to answer."""
+    from paper_1606_07413_gb300 import serve
+
+    times, targets = W.poisson_arrivals(n_requests, rate)
+    bp = Q.default_batch_params(max_jobs=512, walks_per_job=tuned["walks_per_job"],
+                                steps_per_round=tuned["steps_per_round"], table_log2=18,
+                                queue_capacity=tuned["queue_capacity"])
+    with serve.Server(bp, budget_bytes, stream=stream, deadline_s=deadline_s) as srv:
+        rids, wall = serve.replay_stream(srv, times, targets, time_limit_s=float(times[-1]) + drain_s)
+        polls = [srv.poll(r) for r in rids]
+        fevals, rounds, peak = srv.fevals, srv.rounds, srv.peak_used
+    lat = sorted(p["latency"] for p in polls if p["status"] == "found")
+    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None
+    status = {}
+    for p in polls:
+        status[p["status"]] = status.get(p["status"], 0) + 1
+    return {
+        "workload": f"{n_requests} seeded targets, Poisson arrivals at {rate}/s, n~U{{2,3,4}}, T-count~U{{3..7}}",
+        "answered_p50_s": q(0.5), "answered_p99_s": q(0.99), "status_counts": status,
+        "fevals_per_s": fevals / wall, "wall_s": wall, "rounds": rounds, "memory_budget_bytes": budget_bytes,
+        "peak_admitted_bytes": peak, "deadline_s": deadline_s,
+    }
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import torch
@@ -361,8 +388,10 @@ def run_ours(args):
                            "only after its exact host verification of the decomposition"}
             pt.close()
         if not args.no_extra:
+            batched = run_batched(Q, W, torch, stream)
             extra = {
-                "batched": run_batched(Q, W, torch, stream),
+                "batched": batched,
+                "serving": run_serving(Q, W, torch, stream, batched["autotuned"]),
                 "n2_level3": level_throughput(Q, W, torch, 1, 3, 512, stream, imad_per_s=imad_per_s),
                 "n4_level7": level_throughput(Q, W, torch, 3, 7, 16, stream, imad_per_s=imad_per_s),
             }
