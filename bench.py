@@ -64,6 +64,27 @@ def workload_config(c):
     }
 
 
+# ------------------------------------------------------------------ ranks
+def rank_seed(rank: int) -> int:
+    """Walk seed of one rank.  Ranks are independent replicas of the level
+    walk with disjoint pseudo-random walk families, so their steps add up and
+    they never talk except to combine their timings."""
+    return 0x5EED0000 + rank
+
+
+def combine_ranks(t_local: float, units_local: float, world: int, dist=None, device="cpu"):
+    """Whole-job timing over ranks: the slowest rank's time and all ranks' units."""
+    import torch
+
+    if world <= 1 or dist is None:
+        return t_local, units_local
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ------------------------------------------------------------------ CPU oracle
 def _oracle_worker(args):
     n, gates, k, chunk, L, states = args
@@ -232,6 +253,39 @@ def run_batched(Q, W, torch, stream, n_targets=256, rounds=12):
     }
 
 
+def table1_circuits(Q, stream, trials=10):
+    """Time to the optimal T-count of the Toffoli and Fredkin gates (textbook
+    permutation matrices), the paper's Table 1 circuits with published means
+    25.9870 s and 25.0031 s on 4096 Blue Gene/Q cores (context, not a target:
+    other hardware).  Each trial is a full ladder from sde = 2 through the
+    public API with its own walk seed."""
+    def perm_unitary(perm):
+        u = np.zeros((8, 8, 4), np.int64)
+        for c, r in enumerate(perm):
+            u[r, c, 0] = 1
+        return u
+
+    circuits = {
+        "toffoli": [c ^ (4 if (c & 3) == 3 else 0) for c in range(8)],
+        "fredkin": [(c & 1) | ((((c >> 2) & 1) << 1) | (((c >> 1) & 1) << 2)) if c & 1 else c for c in range(8)],
+    }
+    paper = {"toffoli": 25.9870, "fredkin": 25.0031}
+    out = {}
+    for name, perm in circuits.items():
+        secs, tcs = [], []
+        for t in range(trials):
+            p = Q.Problem.from_unitary(3, perm_unitary(perm), 0, 7, Q.default_params(3, seed=0x7AB1E + t))
+            t0 = time.perf_counter()
+            p.run_walks(stream=stream)
+            r = p.wait(600_000)
+            secs.append(time.perf_counter() - t0)
+            tcs.append(r["t_count"])
+            p.close()
+        out[name] = {"t_counts": sorted(set(tcs)), "mean_s": float(np.mean(secs)), "sd_s": float(np.std(secs)),
+                     "trials": trials, "paper_mean_s_4096_bgq_cores": paper[name]}
+    return out
+
+
 def run_serving(Q, W, torch, stream, tuned, n_requests=2000, rate=50.0, budget_bytes=2 << 30,
                 deadline_s=10.0, drain_s=15.0):
     """Config 5: a Poisson stream of seeded targets replayed in real time into
@@ -284,7 +338,7 @@ def run_ours(args):
     c = W.CONFIGS[CFG]
     gates, _ = W.config_target(CFG)
     params = Q.default_params(c["n"], walks=c["walks"], state_bits=c["L"], dp_bits=c["dtheta"],
-                              table_log2=c["table_log2"], seed=0x5EED0000 + rank)
+                              table_log2=c["table_log2"], seed=rank_seed(rank))
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -331,15 +385,7 @@ def run_ours(args):
     steps_done = r1["steps"] - r0["steps"]
     w_steps = r1["w_steps"] - r0["w_steps"]
     t_local = sum(step_ms) / 1e3
-    tt = torch.tensor([t_local, float(steps_done)], dtype=torch.float64, device=dev)
-    if world > 1:
-        t_max = tt[0].clone()
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        s_sum = tt[1].clone()
-        dist.all_reduce(s_sum, op=dist.ReduceOp.SUM)
-        t_all, steps_all = float(t_max), float(s_sum)
-    else:
-        t_all, steps_all = t_local, float(steps_done)
+    t_all, steps_all = combine_ranks(t_local, float(steps_done), world, dist if world > 1 else None, dev)
     value = steps_all / t_all
 
     # roofline of the walk kernel: algorithmic IMADs = W-side steps x 2 d^2
@@ -392,6 +438,7 @@ def run_ours(args):
             extra = {
                 "batched": batched,
                 "serving": run_serving(Q, W, torch, stream, batched["autotuned"]),
+                "table1_circuits": table1_circuits(Q, stream),
                 "n2_level3": level_throughput(Q, W, torch, 1, 3, 512, stream, imad_per_s=imad_per_s),
                 "n4_level7": level_throughput(Q, W, torch, 3, 7, 16, stream, imad_per_s=imad_per_s),
             }
