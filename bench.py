@@ -64,6 +64,29 @@ def workload_config(c):
     }
 
 
+# ------------------------------------------------------------------ ncu record
+# DRAM traffic of one k_walks<3> launch of the headline workload, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
+# kernel source it was taken on (hash of the walk kernel's source files)
+WALK_TRAFFIC = {"bytes_per_launch": None, "source_sha256_16": None}
+
+
+def walk_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("qcs_walk.cu", "qcs_internal.h"):
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1606_07413_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def walk_traffic():
+    if WALK_TRAFFIC["source_sha256_16"] != walk_source_hash():
+        return None  # the kernel changed since the counters were taken
+    return WALK_TRAFFIC["bytes_per_launch"]
+
+
 # ------------------------------------------------------------------ ranks
 def rank_seed(rank: int) -> int:
     """Walk seed of one rank.  Ranks are independent replicas of the level
@@ -164,7 +187,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ other workloads
-def level_throughput(Q, W, torch, cfg, k, steps, stream, launches=3, imad_per_s=None):
+def level_throughput(Q, W, torch, cfg, k, steps, stream, launches=3, alu_per_s=None):
     """Walk steps/s of one single-target level launch at a configured size."""
     c = W.CONFIGS[cfg]
     gates, _ = W.config_target(cfg)
@@ -189,8 +212,8 @@ def level_throughput(Q, W, torch, cfg, k, steps, stream, launches=3, imad_per_s=
     walk_s = sum(ms) / 1e3
     out = {"workload": f"n{c['n']}_level{k}_walks{c['walks']}_L{c['L']}_theta2^-{c['dtheta']}",
            "walk_steps_per_s": (r1["steps"] - r0["steps"]) / walk_s}
-    if imad_per_s:
-        out["imad_frac"] = (r1["w_steps"] - r0["w_steps"]) * 2 * d * d / walk_s / imad_per_s
+    if alu_per_s:  # the contraction's instruction rate (IMAD for n <= 2, dp4a for n >= 3)
+        out["alu_frac"] = (r1["w_steps"] - r0["w_steps"]) * 2 * d * d / walk_s / alu_per_s
     return out
 
 
@@ -247,7 +270,7 @@ def run_batched(Q, W, torch, stream, n_targets=256, rounds=12):
         "batched_fevals_per_s": fev / batched_s, "one_target_fevals_per_s": fev / one_s,
         "batched_walk_steps_per_s": walk / batched_s, "one_target_walk_steps_per_s": walk / one_s,
         "speedup": one_s / batched_s, "batched_s": batched_s, "one_target_s": one_s,
-        "imad_per_s_batched": imad / batched_s,
+        "contraction_ops_per_s_batched": imad / batched_s,
         "found": len(tts), "time_to_tcount_p50_s": q(0.5), "time_to_tcount_p99_s": q(0.99),
         "graph": "each batched round is one CUDA-graph replay",
     }
@@ -347,9 +370,11 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # measured integer-ALU peak (IMAD, the contraction's instruction)
+    # measured integer-ALU peaks: IMAD (the 32-bit contraction, n <= 2) and
+    # dp4a (the byte-plane contraction, n >= 3 with C^ in int8)
     Q.measure_int_peak("imad", 8, 512)
     imad_per_s, _ = Q.measure_int_peak("imad", 8, 4096)
+    dp4a_per_s, _ = Q.measure_int_peak("idp4a", 8, 4096)
 
     prob = Q.Problem.from_circuit(c["n"], gates, K_LEVEL, params)
     with torch.cuda.stream(stream):
@@ -388,14 +413,19 @@ def run_ours(args):
     t_all, steps_all = combine_ranks(t_local, float(steps_done), world, dist if world > 1 else None, dev)
     value = steps_all / t_all
 
-    # roofline of the walk kernel: algorithmic IMADs = W-side steps x 2 d^2
+    # roofline of the walk kernel: algorithmic multiply-adds = W-side steps x
+    # 2 d^2, each one dp4a of the byte-plane contraction (four byte products
+    # per 32-bit product), against the measured dp4a rate
     d = 4 ** c["n"] - 1
     walk_s = sum(walk_ms) / 1e3
     achieved = w_steps * 2 * d * d / walk_s
     roof = {"bound": "alu", "unit": "Gop/s", "kernel": "k_walks<3>",
-            "achieved": achieved / 1e9, "peak": imad_per_s / 1e9, "frac": achieved / imad_per_s,
-            "traffic": None, "peak_source": "measured IMAD microbenchmark (qcs_peak_imad), this run",
-            "algorithmic_ops": f"2*d^2 = {2 * d * d} int32 multiply-adds per W-side walk step",
+            "achieved": achieved / 1e9, "peak": dp4a_per_s / 1e9, "frac": achieved / dp4a_per_s,
+            "traffic": walk_traffic(), "traffic_unit": "bytes per launch",
+            "peak_source": "measured dp4a microbenchmark (qcs_peak_idp4a), this run; IMAD measured "
+                           f"{imad_per_s / 1e9:.0f} Gop/s",
+            "algorithmic_ops": f"2*d^2 = {2 * d * d} multiply-adds per W-side walk step "
+                               "(executed as byte-plane dp4a)",
             "walk_kernel_share": walk_s / t_local}
 
     # e2e through the public API: create from the host gate list, search
@@ -439,8 +469,8 @@ def run_ours(args):
                 "batched": batched,
                 "serving": run_serving(Q, W, torch, stream, batched["autotuned"]),
                 "table1_circuits": table1_circuits(Q, stream),
-                "n2_level3": level_throughput(Q, W, torch, 1, 3, 512, stream, imad_per_s=imad_per_s),
-                "n4_level7": level_throughput(Q, W, torch, 3, 7, 16, stream, imad_per_s=imad_per_s),
+                "n2_level3": level_throughput(Q, W, torch, 1, 3, 512, stream, alu_per_s=imad_per_s),
+                "n4_level7": level_throughput(Q, W, torch, 3, 7, 16, stream, alu_per_s=dp4a_per_s),
             }
     prob.close()
 

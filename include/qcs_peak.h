@@ -1,8 +1,8 @@
 /*
  * qcs_peak.h -- measurement utility shipped beside libqcs (libqcs_peak.so):
- * the sustained 32-bit integer multiply-add (IMAD) throughput of the current
- * GPU, used as the integer-ALU roofline of the walk kernel, whose dominant
- * work is 32-bit multiply-adds.  The paper has no counterpart; it is not part
+ * the sustained 32-bit integer multiply-add (IMAD) and byte dot-product
+ * (dp4a) throughput of the current GPU, used as the integer-ALU roofline of
+ * the walk kernel, whose dominant work is multiply-adds.  The paper has no counterpart; it is not part
  * of the search.
  */
 #ifndef QCS_PEAK_H
@@ -29,6 +29,11 @@ QCS_PEAK_API int qcs_peak_imad(int blocks_per_sm, int iters, double *imad_per_s,
 
 /* Same for the 32-bit integer add / logic pipe (IADD3 chains). */
 QCS_PEAK_API int qcs_peak_iadd(int blocks_per_sm, int iters, double *iadd_per_s, double *ms);
+
+/* Same for the four-way byte dot product with accumulate (dp4a, unsigned
+ * bytes times signed bytes), the instruction of the walk kernel's byte-plane
+ * contraction; reports dp4a instructions per second. */
+QCS_PEAK_API int qcs_peak_idp4a(int blocks_per_sm, int iters, double *dp4a_per_s, double *ms);
 
 #ifdef __cplusplus
 }

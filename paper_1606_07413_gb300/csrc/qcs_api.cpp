@@ -94,7 +94,7 @@ LevelCtx qcs::make_level(const qcs_problem *P, int k, uint32_t version, int dp_b
 {
     LevelCtx lv{};
     lv.C32 = P->dC32;
-    lv.C8 = reinterpret_cast<const uint4 *>(P->dC8);
+    lv.Cq = reinterpret_cast<const uint4 *>(P->dCq);
     lv.U = P->dU;
     lv.coef = P->dCoef;
     lv.n = P->n;
@@ -149,27 +149,38 @@ int upload_problem(qcs_problem *P)
             if (anti) coef[(size_t)p * 2 * R + t] |= 1u << l;
             if (plus) coef[(size_t)p * 2 * R + R + t] |= 1u << l;
         }
-    // n = 4: also C^ as int8 pairs when every entry fits; row i, lane l holds
-    // columns l + 32 t (t < 8) as bytes 2t (a) and 2t + 1 (b) of 16 bytes
-    std::vector<int8_t> c8;
-    if (n == 4) {
+    // n >= 3: also C^ as signed byte quads (rows 4q .. 4q+3 of a column in
+    // one word) when every entry fits in int8, laid out for the walk
+    // kernel's byte-plane contraction (LevelCtx::Cq)
+    std::vector<uint32_t> cq;
+    if (n >= 3) {
         bool fits = true;
         for (size_t i = 0; i < P->C.a.size() && fits; i++)
-            fits = P->C.a[i] >= -127 && P->C.a[i] <= 127 && P->C.b[i] >= -127 && P->C.b[i] <= 127;
+            fits = P->C.a[i] >= -128 && P->C.a[i] <= 127 && P->C.b[i] >= -128 && P->C.b[i] <= 127;
         if (fits) {
-            c8.resize((size_t)D * D * 2);
-            for (int i = 0; i < D; i++)
-                for (int Q = 0; Q < D; Q++) {
-                    const size_t o = ((size_t)i * 32 + (size_t)(Q % 32)) * 16 + 2 * (size_t)(Q / 32);
-                    c8[o] = (int8_t)P->C.a[(size_t)i * D + Q];
-                    c8[o + 1] = (int8_t)P->C.b[(size_t)i * D + Q];
-                }
+            const int quads = D / 4, half = R / 2;
+            cq.assign((size_t)D * D / 2, 0);
+            for (int q = 0; q < quads; q++)
+                for (int j = 0; j < half; j++)
+                    for (int lane = 0; lane < 32; lane++)
+                        for (int c = 0; c < 2; c++) {
+                            const int Q = lane + 64 * j + 32 * c;
+                            uint32_t wa = 0, wb = 0;
+                            for (int r = 0; r < 4; r++) {
+                                const size_t src = (size_t)(4 * q + r) * D + Q;
+                                wa |= (uint32_t)(uint8_t)(int8_t)P->C.a[src] << (8 * r);
+                                wb |= (uint32_t)(uint8_t)(int8_t)P->C.b[src] << (8 * r);
+                            }
+                            const size_t o = (((size_t)q * half + j) * 32 + lane) * 4 + 2 * c;
+                            cq[o] = wa;
+                            cq[o + 1] = wb;
+                        }
         }
     }
     CK(cudaGetDevice(&P->device));
-    if (!c8.empty()) {
-        CK(cudaMalloc(&P->dC8, c8.size()));
-        CK(cudaMemcpy(P->dC8, c8.data(), c8.size(), cudaMemcpyHostToDevice));
+    if (!cq.empty()) {
+        CK(cudaMalloc(&P->dCq, sizeof(uint32_t) * cq.size()));
+        CK(cudaMemcpy(P->dCq, cq.data(), sizeof(uint32_t) * cq.size(), cudaMemcpyHostToDevice));
     }
     CK(cudaMalloc(&P->dC32, sizeof(uint2) * c32.size()));
     CK(cudaMalloc(&P->dU, sizeof(uint2) * D));
@@ -198,7 +209,7 @@ int ensure_search_buffers(qcs_problem *P)
 
 void free_problem_memory(qcs_problem *P)
 {
-    cudaFree(P->dC32); cudaFree(P->dC8); cudaFree(P->dU); cudaFree(P->dCoef); cudaFree(P->dTable); cudaFree(P->dQueue); cudaFree(P->dQhead);
+    cudaFree(P->dC32); cudaFree(P->dCq); cudaFree(P->dU); cudaFree(P->dCoef); cudaFree(P->dTable); cudaFree(P->dQueue); cudaFree(P->dQhead);
     cudaFree(P->dCands); cudaFree(P->dWalks); cudaFree(P->dCounters);
     cudaFreeHost(P->hCounters); cudaFreeHost(P->hCands); cudaFreeHost(P->hQhead);
 }

@@ -34,9 +34,12 @@ struct LevelCtx {
     // 32 t (t < R = max(1, 4^n / 32)) sits at i * 4^n + lane * R + t, so one
     // lane's R columns of a row are contiguous.
     const uint2 *C32;
-    // n = 4: C^ as int8 pairs when every entry fits in [-127, 127], else null;
-    // row i, lane l holds columns l + 32 t (t < 8) as 16 bytes (a_t, b_t)
-    const uint4 *C8;
+    // n >= 3: C^ as signed byte quads when every entry fits in int8, else
+    // null.  Quad q holds rows 4q .. 4q+3 of a column as the bytes 0 .. 3 of
+    // one word.  uint4 number (q R/2 + j) 32 + lane carries, for the columns
+    // Q0 = lane + 64 j and Q1 = Q0 + 32, the words (a-quad Q0, b-quad Q0,
+    // a-quad Q1, b-quad Q1).
+    const uint4 *Cq;
     const uint2 *U;    // fingerprint weights (Ua, Ub) per row, 4^n
     // rotation coefficients: for Pauli p, 2R words; word t (t < R) has bit
     // lane set when row lane + 32 t anticommutes with p, word R + t when the
@@ -205,7 +208,7 @@ struct qcs_problem {
     qcs::PMat C; // reduced, exponent = sde
     // device data
     uint2 *dC32 = nullptr, *dU = nullptr;
-    int8_t *dC8 = nullptr; // n = 4 only, when every entry of C^ fits in int8
+    uint32_t *dCq = nullptr; // n >= 3, when every entry of C^ fits in int8
     uint32_t *dCoef = nullptr;
     qcs::Slot *dTable = nullptr;
     qcs::Pair *dQueue = nullptr;

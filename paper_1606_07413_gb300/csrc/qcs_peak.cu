@@ -37,6 +37,25 @@ __global__ void __launch_bounds__(256) k_iadd(uint32_t a, uint32_t b, int iters,
     if (s == 0x9E3779B9u) sink[0] = s;
 }
 
+// dp4a with unsigned bytes in the first operand and signed bytes in the
+// second, the instruction of the byte-plane contraction
+__global__ void __launch_bounds__(256) k_idp4a(uint32_t a, uint32_t b, int iters, uint32_t *sink)
+{
+    uint32_t x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6,
+             x7 = x0 + 7;
+#define QCS_DP4A(x) asm volatile("dp4a.u32.s32 %0, %1, %2, %0;" : "+r"(x) : "r"(a), "r"(b))
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int u = 0; u < 16; u++) {
+            QCS_DP4A(x0); QCS_DP4A(x1); QCS_DP4A(x2); QCS_DP4A(x3);
+            QCS_DP4A(x4); QCS_DP4A(x5); QCS_DP4A(x6); QCS_DP4A(x7);
+        }
+    }
+#undef QCS_DP4A
+    const uint32_t s = x0 ^ x1 ^ x2 ^ x3 ^ x4 ^ x5 ^ x6 ^ x7;
+    if (s == 0x9E3779B9u) sink[0] = s;
+}
+
 template <typename K>
 int run(K kern, int blocks_per_sm, int iters, double *ops_per_s, double *ms)
 {
@@ -76,4 +95,9 @@ extern "C" int qcs_peak_imad(int blocks_per_sm, int iters, double *imad_per_s, d
 extern "C" int qcs_peak_iadd(int blocks_per_sm, int iters, double *iadd_per_s, double *ms)
 {
     return run(k_iadd, blocks_per_sm, iters, iadd_per_s, ms);
+}
+
+extern "C" int qcs_peak_idp4a(int blocks_per_sm, int iters, double *dp4a_per_s, double *ms)
+{
+    return run(k_idp4a, blocks_per_sm, iters, dp4a_per_s, ms);
 }

@@ -29,19 +29,25 @@
 namespace qcs {
 namespace {
 
-// launch shape of the walk kernels (tuned on GB300; see the sweep notes)
+// launch shape of the walk kernels, tuned on GB300 by sweeping warps per CTA,
+// the register cap (minimum resident CTAs) and the contraction's unrolling
 #ifndef QCS_WARPS
 #define QCS_WARPS 8
 #endif
-#ifndef QCS_MIN_BLOCKS
-#define QCS_MIN_BLOCKS 1
+#ifndef QCS_MIN_BLOCKS3
+#define QCS_MIN_BLOCKS3 4 // n = 3: 64 registers, four CTAs of 8 warps per SM
 #endif
 #ifndef QCS_GEMV_UNROLL
-#define QCS_GEMV_UNROLL 2
+#define QCS_GEMV_UNROLL 2 // 32-bit word contraction (rows per unrolled step / 2)
+#endif
+#ifndef QCS_QUAD_UNROLL3
+#define QCS_QUAD_UNROLL3 8 // byte-quad contraction, n = 3 (16 quads)
+#endif
+#ifndef QCS_QUAD_UNROLL4
+#define QCS_QUAD_UNROLL4 4 // byte-quad contraction, n = 4 (64 quads)
 #endif
 constexpr int kWarps = QCS_WARPS;
 constexpr int kGemvUnroll = QCS_GEMV_UNROLL;
-constexpr int kThreads = kWarps * 32;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr uint32_t kMaxRewalkLen = 1u << 20; // longer trails are reported as no merge
 
@@ -58,18 +64,21 @@ struct Geo {
     static constexpr int D = DIM - 1;                    // non-identity Paulis
     static constexpr int RPL = DIM >= 32 ? DIM / 32 : 1; // rows (and columns) per lane
     static constexpr int SLOTS = RPL * 32;               // width of the fingerprint sort
-    // n <= 3: C^ low words staged whole (32 KB at n = 3); n = 4: C^ as int8
-    // pairs (128 KB) when every entry fits, else read through L2
+    // n <= 3: C^ staged whole, as byte quads (8 KB at n = 3) or else as low
+    // words (32 KB); n = 4: byte quads (128 KB) when every entry fits, else
+    // the low words are read through L2
     static constexpr bool C_SMEM = NQ <= 3;
-    static constexpr bool C8_SMEM = NQ == 4;
+    static constexpr bool CQ_SMEM = NQ == 4;
     static constexpr int WARPS = NQ == 4 ? 16 : kWarps;  // walks (warps) per CTA
     static constexpr int THREADS = WARPS * 32;
+    static constexpr int MIN_BLOCKS = NQ == 3 ? QCS_MIN_BLOCKS3 : 1;
+    static constexpr int QUAD_UNROLL = NQ == 4 ? QCS_QUAD_UNROLL4 : QCS_QUAD_UNROLL3;
     static constexpr int COEF_WORDS = DIM * 2 * RPL;     // rotation coefficient bits
     static constexpr int MAX_CHUNKS = 256;               // hash bases, one per chunk
     // shared memory: weights | C^ | coefficients | chunk bases | exchange buffers
     static constexpr size_t off_C = sizeof(uint2) * DIM;
     static constexpr size_t off_coef =
-        off_C + (C_SMEM ? sizeof(uint2) * DIM * DIM : 0) + (C8_SMEM ? 2 * DIM * DIM : 0);
+        off_C + (C_SMEM ? sizeof(uint2) * DIM * DIM : 0) + (CQ_SMEM ? 2 * DIM * DIM : 0);
     static constexpr size_t off_base = off_coef + sizeof(uint32_t) * COEF_WORDS;
     static constexpr size_t off_xchg = off_base + sizeof(uint64_t) * MAX_CHUNKS;
     static constexpr size_t smem_bytes = off_xchg + sizeof(uint2) * WARPS * DIM;
@@ -80,7 +89,7 @@ template <int NQ>
 struct Smem {
     uint2 *U;
     const uint2 *C;
-    const uint4 *C8;  // n = 4: int8 pairs, row i lane l at [32 i + l] (8 columns), or null
+    const uint4 *Cq;  // n >= 3: C^ as byte quads (LevelCtx::Cq layout), or null
     uint32_t *coef;
     uint64_t *base;
     uint2 *xchg; // this warp's exchange buffer
@@ -133,6 +142,46 @@ __device__ __forceinline__ void adj_stage(uint32_t p, uint32_t (&ua)[Geo<NQ>::RP
             ub[t] = anti ? nb : cb;
         }
     }
+    __syncwarp();
+}
+
+// d = c + sum_j a_j b_j over the four bytes, a unsigned and b signed (mod 2^32)
+__device__ __forceinline__ uint32_t dp4a_us(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// Byte planes of the weights for the byte-quad contraction.  The weight of a
+// row is u = sum_k 2^(8k) u_k with bytes u_k, so sum_i u_i c_i =
+// sum_k 2^(8k) sum_i u_{i,k} c_i: an exact identity mod 2^32 whose inner sums
+// are byte dot products.  Plane word (q, part, k) holds byte k of the part
+// (0: a, 1: b) weights of rows 4q .. 4q+3; it is written, in place of the
+// rows (uint2 per row) in the warp's exchange buffer, as word k of uint4
+// number 2q + part.
+template <int NQ>
+__device__ __forceinline__ void weight_planes(uint2 *su, int lane)
+{
+    using G = Geo<NQ>;
+    constexpr int JOBS = G::DIM >= 64 ? G::DIM / 64 : 1; // 2 parts x DIM/4 quads over 32 lanes
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(su);
+    uint4 pl[JOBS];
+#pragma unroll
+    for (int r = 0; r < JOBS; r++) {
+        const int job = lane + 32 * r, q = job >> 1, part = job & 1;
+        const uint4 r01 = s4[2 * q], r23 = s4[2 * q + 1]; // rows 4q, 4q+1 and 4q+2, 4q+3
+        const uint32_t u0 = part ? r01.y : r01.x, u1 = part ? r01.w : r01.z;
+        const uint32_t u2 = part ? r23.y : r23.x, u3 = part ? r23.w : r23.z;
+        const uint32_t lo01 = __byte_perm(u0, u1, 0x5140), hi01 = __byte_perm(u0, u1, 0x7362);
+        const uint32_t lo23 = __byte_perm(u2, u3, 0x5140), hi23 = __byte_perm(u2, u3, 0x7362);
+        pl[r] = make_uint4(__byte_perm(lo01, lo23, 0x5410), __byte_perm(lo01, lo23, 0x7632),
+                           __byte_perm(hi01, hi23, 0x5410), __byte_perm(hi01, hi23, 0x7632));
+    }
+    __syncwarp();
+    uint4 *w4 = reinterpret_cast<uint4 *>(su);
+#pragma unroll
+    for (int r = 0; r < JOBS; r++) w4[lane + 32 * r] = pl[r];
     __syncwarp();
 }
 
@@ -205,24 +254,36 @@ __device__ uint64_t warp_step(uint64_t x, uint32_t chunk, const LevelCtx &lv, co
         __syncwarp();
         // L(W e_Q) = sum_i U~_a[i] C_a[i][Q] + U~_b[i] C_b[i][Q]; row 0 has
         // zero weight and C[0][Q] = 0 for Q >= 1, so all rows may be summed.
-        if (G::C8_SMEM && sm.C8) {
-            // int8 pairs: byte 2t / 2t + 1 of a lane's 16 bytes are a / b of column lane + 32 t
-            const uint4 *su4 = reinterpret_cast<const uint4 *>(su);
-#pragma unroll 2
-            for (int i = 0; i < G::DIM; i += 2) {
-                const uint4 uu = su4[i >> 1];
-                const uint4 r0 = sm.C8[32 * i + lane], r1 = sm.C8[32 * (i + 1) + lane];
-                const uint32_t w0[4] = {r0.x, r0.y, r0.z, r0.w}, w1[4] = {r1.x, r1.y, r1.z, r1.w};
+        if (G::DIM >= 64 && sm.Cq) {
+            // byte-plane contraction: acc[t][k] = sum over rows of byte k of
+            // the weights times C^ (exact byte products), recombined below
+            weight_planes<NQ>(su, lane);
+            const uint4 *w4 = reinterpret_cast<const uint4 *>(su);
+            constexpr int CW = G::RPL / 2;
+            uint32_t acc[G::RPL][4];
 #pragma unroll
-                for (int t = 0; t < G::RPL; t++) {
-                    const int sh = 16 * (t & 1);
-                    const int32_t a0 = (int32_t)(int8_t)(w0[t >> 1] >> sh);
-                    const int32_t b0 = (int32_t)(int8_t)(w0[t >> 1] >> (sh + 8));
-                    const int32_t a1 = (int32_t)(int8_t)(w1[t >> 1] >> sh);
-                    const int32_t b1 = (int32_t)(int8_t)(w1[t >> 1] >> (sh + 8));
-                    Lc[t] += uu.x * (uint32_t)a0 + uu.y * (uint32_t)b0 + uu.z * (uint32_t)a1 + uu.w * (uint32_t)b1;
+            for (int t = 0; t < G::RPL; t++)
+#pragma unroll
+                for (int k = 0; k < 4; k++) acc[t][k] = 0;
+#pragma unroll G::QUAD_UNROLL
+            for (int q = 0; q < G::DIM / 4; q++) {
+                const uint4 wa = w4[2 * q], wb = w4[2 * q + 1];
+                const uint32_t pa[4] = {wa.x, wa.y, wa.z, wa.w}, pb[4] = {wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                for (int j = 0; j < CW; j++) {
+                    const uint4 c = sm.Cq[(q * CW + j) * 32 + lane];
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        acc[2 * j][k] = dp4a_us(pa[k], c.x, acc[2 * j][k]);
+                        acc[2 * j][k] = dp4a_us(pb[k], c.y, acc[2 * j][k]);
+                        acc[2 * j + 1][k] = dp4a_us(pa[k], c.z, acc[2 * j + 1][k]);
+                        acc[2 * j + 1][k] = dp4a_us(pb[k], c.w, acc[2 * j + 1][k]);
+                    }
                 }
             }
+#pragma unroll
+            for (int t = 0; t < G::RPL; t++)
+                Lc[t] = acc[t][0] + (acc[t][1] << 8) + (acc[t][2] << 16) + (acc[t][3] << 24);
         } else if (G::DIM >= 32) {
             const uint4 *su4 = reinterpret_cast<const uint4 *>(su);
 #pragma unroll kGemvUnroll
@@ -260,7 +321,7 @@ __device__ uint64_t warp_step(uint64_t x, uint32_t chunk, const LevelCtx &lv, co
     }
     // bitonic sort of SLOTS keys, ascending in e; strides below RPL stay in
     // registers, larger ones go through shuffles (there a lane's keys share
-    // the direction bits, which come from the lane part of e)
+    // the direction, which comes from the lane part of e)
 #pragma unroll
     for (int size = 2; size <= G::SLOTS; size <<= 1) {
 #pragma unroll
@@ -328,18 +389,24 @@ __device__ __forceinline__ Smem<NQ> stage(const LevelCtx &lv, unsigned char *raw
                              ((uint64_t)(uint32_t)lv.K << 32);
         sm.base[c] = smix(vmix ^ tag);
     }
-    sm.C8 = nullptr;
+    sm.Cq = nullptr;
     if (G::C_SMEM) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(lv.C32);
-        uint4 *dst = reinterpret_cast<uint4 *>(sC);
-        for (int i = threadIdx.x; i < G::DIM * G::DIM / 2; i += blockDim.x) dst[i] = src[i];
+        if (lv.Cq && G::DIM >= 64) {
+            uint4 *dst = reinterpret_cast<uint4 *>(sC);
+            for (int i = threadIdx.x; i < G::DIM * G::DIM * 2 / 16; i += blockDim.x) dst[i] = lv.Cq[i];
+            sm.Cq = dst;
+        } else {
+            const uint4 *src = reinterpret_cast<const uint4 *>(lv.C32);
+            uint4 *dst = reinterpret_cast<uint4 *>(sC);
+            for (int i = threadIdx.x; i < G::DIM * G::DIM / 2; i += blockDim.x) dst[i] = src[i];
+        }
         sm.C = sC;
     } else {
         sm.C = lv.C32;
-        if (G::C8_SMEM && lv.C8) {
+        if (G::CQ_SMEM && lv.Cq) {
             uint4 *dst = reinterpret_cast<uint4 *>(sC);
-            for (int i = threadIdx.x; i < G::DIM * G::DIM * 2 / 16; i += blockDim.x) dst[i] = lv.C8[i];
-            sm.C8 = dst;
+            for (int i = threadIdx.x; i < G::DIM * G::DIM * 2 / 16; i += blockDim.x) dst[i] = lv.Cq[i];
+            sm.Cq = dst;
         }
     }
     __syncthreads();
@@ -474,7 +541,7 @@ __device__ __forceinline__ void walk_one(const WL &w, const Smem<NQ> &sm, int wa
 }
 
 template <int NQ>
-__global__ void __launch_bounds__(Geo<NQ>::THREADS, QCS_MIN_BLOCKS) k_walks(WalkLaunch w)
+__global__ void __launch_bounds__(Geo<NQ>::THREADS, Geo<NQ>::MIN_BLOCKS) k_walks(WalkLaunch w)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Smem<NQ> sm = stage<NQ>(w.lv, smem_raw);
@@ -491,7 +558,7 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS, QCS_MIN_BLOCKS) k_walks(Walk
 // one of the task's WARPS walks.  The job's launch record is copied to
 // shared memory.
 template <int NQ>
-__global__ void __launch_bounds__(Geo<NQ>::THREADS, QCS_MIN_BLOCKS) k_walks_batch(BatchArgs a)
+__global__ void __launch_bounds__(Geo<NQ>::THREADS, Geo<NQ>::MIN_BLOCKS) k_walks_batch(BatchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ WalkLaunch sw;
@@ -732,7 +799,7 @@ cudaError_t walk_step_n(const LevelCtx &lv, int chunk, const uint64_t *in, uint6
 template <int NQ>
 cudaError_t walks_n(const WalkLaunch &w, cudaStream_t s)
 {
-    k_walks<NQ><<<grid_for<NQ>((size_t)w.n_walks), kThreads, Geo<NQ>::smem_bytes, s>>>(w);
+    k_walks<NQ><<<grid_for<NQ>((size_t)w.n_walks), Geo<NQ>::THREADS, Geo<NQ>::smem_bytes, s>>>(w);
     return cudaGetLastError();
 }
 

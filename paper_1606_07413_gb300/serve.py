@@ -80,9 +80,14 @@ class Server:
             need = self.batch.job_bytes(prob)
             if self.used + need > self.budget and self.running:
                 break  # memory is full: wait for a job to leave
+            try:
+                slot = self.batch.add(prob)
+            except Q.QcsError as e:
+                if e.code != Q.ERR_BUSY:
+                    raise
+                break  # every job slot of the batch is taken (also by jobs added directly)
             self.waiting.popleft()
-            r.prob, r.bytes = prob, need
-            r.slot = self.batch.add(prob)
+            r.prob, r.bytes, r.slot = prob, need, slot
             r.t_admit = self.clock()
             r.status = "running"
             self.used += need

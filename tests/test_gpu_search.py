@@ -129,6 +129,22 @@ def test_manual_level_api_finds_the_claw(orc, dev):
         assert res["steps"] > 0 and res["w_steps"] > 0 and res["launches"] >= 1
 
 
+@pytest.mark.parametrize("n,cfg_t,k", [(1, 3, 3), (2, 3, 3), (3, 5, 5), (4, 7, 6)])
+def test_every_walk_takes_every_step(dev, n, cfg_t, k):
+    # a launch advances each of the problem's walks by exactly `steps` steps
+    # (walk counts that are not a multiple of the walks per CTA included)
+    gates, _ = W.seeded_target(n, cfg_t, 31 + n)
+    walks, steps = 16 * 37 + 5, 6
+    p = Q.default_params(n, walks=walks)
+    with Q.Problem.from_circuit(n, gates, k, p) as prob:
+        prob.level_begin(k, version=0, dp_bits=p.dp_bits)
+        prob.level_walk(steps)
+        prob.level_rewalk()
+        res = prob.level_collect()
+        assert res["steps"] == walks * steps
+        assert 0 < res["w_steps"] < res["steps"]
+
+
 def test_budget_and_cancel(orc, dev):
     # k_max below the optimum: the ladder ends without a decomposition
     gates, _ = W.config_target(2)

@@ -71,6 +71,28 @@ def test_walk_step_bit_exact(orc, dev, n, t, k, chunk, count):
     prob.close()
 
 
+# (n, construction t, seed, whether some entry of C^ leaves int8): the walk
+# kernel contracts C^ as signed byte quads when every numerator fits in int8
+# and falls back to 32-bit words otherwise (staged, n = 3; through L2, n = 4)
+WIDTHS = [(3, 13, 4013, False), (3, 19, 4019, True), (4, 13, 4013, False), (4, 15, 4015, True)]
+
+
+@pytest.mark.parametrize("n,t,seed,wide", WIDTHS)
+def test_contraction_widths_bit_exact(orc, dev, n, t, seed, wide):
+    gates, _ = W.seeded_target(n, t, seed)
+    C = orc.channel_from_circuit(n, gates).reduced()
+    big = int(max(np.abs(C.a).max(), np.abs(C.b).max()))
+    assert (big > 127) == wide and big >= 32  # the high bits of the bytes are in use
+    params = Q.default_params(n)
+    prob = Q.Problem.from_circuit(n, gates, 5, params)
+    L = params.state_bits
+    for k, chunk in ((4, 0), (5, 7)):
+        states = W.seeded_states(45, L, 900 + k)
+        y, _ = gpu_step(prob, dev, k, chunk, 1, states)
+        assert np.array_equal(y, orc.walk_step(C, k, chunk, 1, L, states)), (n, t, k)
+    prob.close()
+
+
 def test_state_bits_and_dp_bits_follow_params(orc, dev):
     gates = target(2, 3, 5)
     for L, dth in ((20, 3), (40, 7), (64, 1)):
