@@ -98,6 +98,9 @@ typedef struct qcs_params {
     int32_t stop_on_claw;     /* 1: stop at the first verified claw; 0: keep walking to the step budget
                                  (the first decomposition is still reported) */
     int32_t theta_min_bits;   /* theta_policy 1 never raises theta above 2^-theta_min_bits (>= 1) */
+    int32_t exhaustive_log2;  /* a level whose V and W points number at most 2^exhaustive_log2 and
+                                 whose walk budget ends without a claw is settled exactly by
+                                 qcs_certify_level (0: never; at most 40) */
     uint64_t seed;            /* seed of trail starting points */
 } qcs_params;
 
@@ -120,6 +123,8 @@ typedef struct qcs_result {
     double seconds;      /* wall time since qcs_run_walks */
     int64_t w_steps;     /* walk steps taken on the W side (the 4^n x 4^n contraction) */
     int64_t rewalk_steps; /* evaluations of f made by the re-walk (Fig. 2 trace-back) */
+    int64_t certified_levels; /* levels proved claw-free by the exhaustive pass */
+    int64_t cert_points;      /* points (V and W) evaluated by the exhaustive pass */
 } qcs_result;
 
 typedef struct qcs_problem qcs_problem;
@@ -155,6 +160,23 @@ QCS_API int qcs_create_problem_circuit(int n_qubits, const int32_t *gates, int n
  * stay valid until the search ends (qcs_wait, or status != SEARCHING).
  * Errors: QCS_ERR_BUSY if a search is running, QCS_ERR_ARG. */
 QCS_API int qcs_run_walks(qcs_problem *prob, uint64_t step_budget, void *cuda_stream);
+
+/* Exhaustive meet-in-the-middle pass over level k (Sec. 2 Eq. mitm, the
+ * deterministic counterpart of the collision search): every V point
+ * R(q_h)..R(q_1) and every W point R(q_1)^T..R(q_h)^T [R(c)^T] C (all xi^h
+ * rotation tuples, all xi chunks c for odd k) is evaluated on the GPU with the
+ * walk's own product and fingerprint canonical form.  V points go into a
+ * device hash table of coset keys, W points probe it, and every key match is
+ * checked exactly on the host (exact canonical forms, then the decomposition
+ * is verified).  Equal cosets always have equal keys, so when no match
+ * verifies, level k has no decomposition: *has_claw = 0 is a proof.  With
+ * *has_claw = 1 the decomposition is recorded as by a FOUND search.  Runs
+ * synchronously on cuda_stream (NULL = legacy default stream); allocates
+ * 16 * 2^ceil(log2(2 xi^h)) bytes of table for the call.  k in [2, k_max].
+ * Errors: QCS_ERR_ARG, QCS_ERR_BUSY (a search is running), QCS_ERR_NOMEM,
+ * QCS_ERR_OVERFLOW (more than 65536 key matches in one slice of 2^22 W points
+ * and none verified: inconclusive), QCS_ERR_CUDA. */
+QCS_API int qcs_certify_level(qcs_problem *prob, int k, void *cuda_stream, int *has_claw);
 
 /* Non-blocking snapshot of the search (status, level, counters, and the
  * decomposition once FOUND). */

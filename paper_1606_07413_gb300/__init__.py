@@ -34,7 +34,7 @@ class Params(ctypes.Structure):
                 ("max_trail_factor", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
                 ("budget_factor", ctypes.c_int32), ("theta_policy", ctypes.c_int32),
                 ("version_factor", ctypes.c_int32), ("stop_on_claw", ctypes.c_int32), ("theta_min_bits", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("exhaustive_log2", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -48,7 +48,8 @@ class Result(ctypes.Structure):
                 ("same_side", ctypes.c_int64), ("claws", ctypes.c_int64), ("false_hash", ctypes.c_int64),
                 ("no_merge", ctypes.c_int64), ("abandoned", ctypes.c_int64), ("dropped", ctypes.c_int64),
                 ("queue_overflow", ctypes.c_int64), ("launches", ctypes.c_int64), ("seconds", ctypes.c_double),
-                ("w_steps", ctypes.c_int64), ("rewalk_steps", ctypes.c_int64)]
+                ("w_steps", ctypes.c_int64), ("rewalk_steps", ctypes.c_int64),
+                ("certified_levels", ctypes.c_int64), ("cert_points", ctypes.c_int64)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
@@ -111,6 +112,7 @@ def lib():
             "qcs_level_walk": (ctypes.c_int, [_vp, _u32, _vp]),
             "qcs_level_rewalk": (ctypes.c_int, [_vp, _vp]),
             "qcs_level_collect": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(Result)]),
+            "qcs_certify_level": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_int)]),
             "qcs_level_walk_static": (ctypes.c_int, [_vp, ctypes.c_int, _u32, ctypes.c_int, ctypes.c_int, _vp, _u32,
                                                      _u32, _vp, _u32, _vp, _vp]),
             "qcs_batch_default_params": (None, [ctypes.POINTER(BatchParams)]),
@@ -148,7 +150,10 @@ def _check(rc, where):
 def default_params(n: int, **overrides) -> Params:
     p = Params()
     lib().qcs_default_params(int(n), ctypes.byref(p))
+    names = {name for name, _ in Params._fields_}
     for k, v in overrides.items():
+        if k not in names:
+            raise TypeError(f"unknown search parameter {k!r}")
         setattr(p, k, v)
     return p
 
@@ -249,6 +254,13 @@ class Problem:
         r = Result()
         _check(lib().qcs_level_collect(self._h, _stream(stream), ctypes.byref(r)), "qcs_level_collect")
         return r.as_dict()
+
+    def certify_level(self, k, stream=None) -> bool:
+        """qcs_certify_level: exhaustive pass over level k; True iff a
+        decomposition with k rotations exists (it is then recorded)."""
+        has = ctypes.c_int(0)
+        _check(lib().qcs_certify_level(self._h, int(k), _stream(stream), ctypes.byref(has)), "qcs_certify_level")
+        return bool(has.value)
 
     def level_walk_static(self, k, version, dp_bits, begin, walk_states, steps, merges, counts, stream=None):
         """qcs_level_walk_static: the level walk without any device allocation.

@@ -82,6 +82,7 @@ bool params_ok(int n, int k_max, const qcs_params &p)
     if (p.walks < 1 || (uint32_t)p.walks > kMaxWalks || p.table_log2 < 4 || p.table_log2 > 34) return false;
     if (p.steps_per_launch < 1 || p.max_trail_factor < 1 || p.queue_capacity < 1) return false;
     if (p.budget_factor < 0 || p.version_factor < 0 || p.theta_min_bits < 0) return false;
+    if (p.exhaustive_log2 < 0 || p.exhaustive_log2 > 40) return false;
     // every rotation field must reach all 4^n - 1 Paulis: 2^ell > xi
     const int h = k_max / 2;
     return h == 0 || field_bits(p.state_bits, h) >= 2 * n;
@@ -445,6 +446,107 @@ LevelPlan qcs::plan_level(const qcs_problem *P, int k, const qcs_params &p)
     return pl;
 }
 
+uint64_t qcs::level_points(const qcs_problem *P, int k)
+{
+    const uint64_t xi = (uint64_t)(P->D - 1);
+    const long double v = (long double)upow(xi, k / 2), w = v * (long double)((k & 1) ? xi : 1);
+    return v + w > 1.8e19L ? ~0ull : (uint64_t)(v + w);
+}
+
+int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
+{
+    *got = false;
+    const int h = k / 2;
+    const uint64_t xi = (uint64_t)(P->D - 1), xi_h = upow(xi, h);
+    const uint64_t n_w = xi_h * ((k & 1) ? xi : 1);
+    uint64_t slots = 1024;
+    while (slots < 2 * xi_h) slots <<= 1;
+    constexpr uint32_t kCap = 1u << 16;
+    constexpr uint64_t kSlice = 1ull << 22;
+    CertArgs a{};
+    a.lv = make_level(P, k, 0, P->p.dp_bits);
+    a.xi_h = xi_h;
+    a.mask = slots - 1;
+    a.cap = kCap;
+    // one hash base for every chunk, so V and W keys of a coset agree
+    const uint64_t tag = (uint64_t)P->n | ((uint64_t)k << 8) | (0xFFFFull << 16) | ((uint64_t)(uint32_t)a.lv.K << 32);
+    a.base = smix_host(smix_host(kSeedH ^ 0xCE27u) ^ tag);
+    uint32_t *hN = nullptr;
+    uint64_t *hPairs = nullptr;
+    cudaError_t e = cudaMalloc(&a.table, sizeof(CertSlot) * slots);
+    if (e == cudaSuccess) e = cudaMalloc(&a.pairs, sizeof(uint64_t) * 2 * kCap);
+    if (e == cudaSuccess) e = cudaMalloc(&a.n_pairs, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&hN, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&hPairs, sizeof(uint64_t) * 2 * kCap);
+    int rc = QCS_OK;
+    bool overflow = false;
+    uint64_t done_w = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.table, 0xFF, sizeof(CertSlot) * slots, s);
+    if (e == cudaSuccess) {
+        a.side = 0;
+        a.first = 0;
+        a.count = xi_h;
+        e = launch_certify(a, s);
+    }
+    for (uint64_t first = 0; e == cudaSuccess && first < n_w && !*got; first += kSlice) {
+        if (P->cancel.load()) {
+            rc = QCS_ERR_BUSY;
+            break;
+        }
+        a.side = 1;
+        a.first = first;
+        a.count = std::min(kSlice, n_w - first);
+        if ((e = cudaMemsetAsync(a.n_pairs, 0, sizeof(uint32_t), s)) != cudaSuccess) break;
+        if ((e = launch_certify(a, s)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(hN, a.n_pairs, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(hPairs, a.pairs, sizeof(uint64_t) * 2 * kCap, cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess)
+            break;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+        done_w += a.count;
+        const uint32_t n = std::min(*hN, kCap);
+        if (*hN > kCap) overflow = true;
+        for (uint32_t i = 0; i < n && !*got; i++) {
+            // exact check of the key match: rotations from the point indices
+            uint32_t qv[kMaxH], qw[kMaxH], paulis[16] = {0};
+            uint64_t v = hPairs[2 * i], w = hPairs[2 * i + 1];
+            const int chunk = (k & 1) ? (int)(w / xi_h) + 1 : 0;
+            w %= xi_h;
+            for (int j = 0; j < h; j++) {
+                qv[j] = (uint32_t)(v % xi) + 1;
+                qw[j] = (uint32_t)(w % xi) + 1;
+                v /= xi;
+                w /= xi;
+            }
+            bool equal = false;
+            if (exact_same_coset(P->n, P->C, k, chunk, qv, qw, &equal) != QCS_OK || !equal) continue;
+            for (int j = 0; j < h; j++) {
+                paulis[j] = qv[j];
+                paulis[h + j] = qw[j];
+            }
+            if (k & 1) paulis[2 * h] = (uint32_t)chunk;
+            if (exact_verify(P->n, P->C, paulis, k, nullptr) == QCS_OK) {
+                found(P, k, paulis);
+                *got = true;
+            }
+        }
+    }
+    if (e != cudaSuccess) rc = cuda_fail(e);
+    cudaStreamSynchronize(s);
+    cudaFree(a.table);
+    cudaFree(a.pairs);
+    cudaFree(a.n_pairs);
+    cudaFreeHost(hN);
+    cudaFreeHost(hPairs);
+    {
+        std::lock_guard<std::mutex> g(P->mu);
+        P->res.cert_points += (int64_t)(xi_h + done_w);
+        if (rc == QCS_OK && !*got && !overflow) P->res.certified_levels += 1;
+    }
+    if (rc == QCS_OK && !*got && overflow) rc = QCS_ERR_OVERFLOW;
+    return rc;
+}
+
 namespace {
 
 bool have_decomposition(qcs_problem *P)
@@ -502,6 +604,13 @@ int drive(qcs_problem *P, uint64_t budget, cudaStream_t s)
         }
         version++;
         if (have_decomposition(P)) return QCS_OK; // the optimal level is the first with a claw
+        if (P->p.exhaustive_log2 > 0 && level_points(P, k) <= (1ull << P->p.exhaustive_log2)) {
+            // the walk budget ended without a claw: settle the level exactly
+            bool got = false;
+            const int rc = certify_level(P, k, s, &got);
+            if (rc != QCS_OK && rc != QCS_ERR_OVERFLOW) return rc;
+            if (got) return QCS_OK;
+        }
     }
     return QCS_ERR_TIMEOUT;
 }
@@ -556,6 +665,7 @@ void qcs_default_params(int n_qubits, qcs_params *p)
     p->version_factor = 2;
     p->stop_on_claw = 1;
     p->theta_min_bits = 1;
+    p->exhaustive_log2 = 24;
     p->seed = 0x2545F4914F6CDD1Dull;
 }
 
@@ -732,6 +842,20 @@ int qcs_level_collect(qcs_problem *P, void *stream, qcs_result *out)
     std::lock_guard<std::mutex> g(P->mu);
     if (got) P->res.status = QCS_FOUND;
     if (out) *out = P->res;
+    return rc;
+}
+
+int qcs_certify_level(qcs_problem *P, int k, void *stream, int *has_claw)
+{
+    if (!P || !has_claw || k < 2 || k > P->k_max) return QCS_ERR_ARG;
+    if (busy(P)) return QCS_ERR_BUSY;
+    bool got = false;
+    const int rc = certify_level(P, k, (cudaStream_t)stream, &got);
+    *has_claw = got ? 1 : 0;
+    if (rc == QCS_OK && got) {
+        std::lock_guard<std::mutex> g(P->mu);
+        P->res.status = QCS_FOUND;
+    }
     return rc;
 }
 

@@ -195,7 +195,7 @@ int enqueue_round(qcs_batch *B)
 }
 
 // fold one job's round into its result and advance its ladder
-void collect_job(Job &j, const unsigned long long *c, const uint32_t *heads, const Cand *cands)
+void collect_job(Job &j, const unsigned long long *c, const uint32_t *heads, const Cand *cands, cudaStream_t s)
 {
     qcs_problem *P = j.P;
     const int k = j.k, h = k / 2;
@@ -256,6 +256,23 @@ void collect_job(Job &j, const unsigned long long *c, const uint32_t *heads, con
         return;
     }
     if (j.launches >= j.pl.min_launches) { // level exhausted: the next one
+        if (P->p.exhaustive_log2 > 0 && level_points(P, k) <= (1ull << P->p.exhaustive_log2)) {
+            // settle the level exactly before moving on (a claw the walk missed)
+            bool claw = false;
+            const int rc = certify_level(P, k, s, &claw);
+            if (rc != QCS_OK && rc != QCS_ERR_OVERFLOW) {
+                std::lock_guard<std::mutex> g(P->mu);
+                P->res.error = rc;
+                j.status = QCS_ERROR;
+                j.active = false;
+                return;
+            }
+            if (claw) {
+                j.status = QCS_FOUND;
+                j.active = false;
+                return;
+            }
+        }
         j.k++;
         j.version++;
         j.launches = 0;
@@ -453,7 +470,7 @@ int qcs_batch_round(qcs_batch *B, int *n_active)
         Job &j = B->jobs[slot];
         if (!j.active) continue;
         collect_job(j, B->hCounters + slot * C_NCOUNTERS, B->hHeads + 2 * slot,
-                    B->hCands + slot * kBatchCandCap);
+                    B->hCands + slot * kBatchCandCap, B->s);
         if (!j.active) {
             publish_status(j);
             memset(&B->hJobs[slot], 0, sizeof(WalkLaunch));

@@ -137,6 +137,35 @@ struct BatchArgs {
     const uint32_t *job_ids;  // jobs of this qubit count
     const uint32_t *n_jobs;   // device scalar
 };
+// Exhaustive meet-in-the-middle pass over one level (Sec. 2 Eq. mitm, the
+// collision search's exact counterpart): every V point is hashed into an
+// open-addressing table of coset keys, then every W point probes it and each
+// key match is queued for the exact host check.  Point index -> rotations:
+// base-xi digits, q_j = digit_j + 1 (q_1 the lowest digit); a W index is
+// chunk-major, chunk = index / xi^h + 1 for odd k.
+struct alignas(16) CertSlot {
+    uint64_t key; // ~0: empty
+    uint64_t idx; // V point index
+};
+
+struct CertArgs {
+    LevelCtx lv;
+    int32_t side;      // 0: insert V points, 1: probe with W points
+    uint64_t first;    // point indices [first, first + count)
+    uint64_t count;
+    uint64_t xi_h;     // rotation tuples per side
+    uint64_t base;     // hash base of the keys, the same for every chunk
+    CertSlot *table;
+    uint64_t mask;     // table slots - 1 (a power of two, at least twice the V points)
+    uint64_t *pairs;   // key matches (V index, W index)
+    uint32_t *n_pairs; // matches found (may exceed cap; only cap are stored)
+    uint32_t cap;
+};
+cudaError_t launch_certify(const CertArgs &a, cudaStream_t s);
+// Host driver of the exhaustive pass (qcs_certify_level); *got = verified claw.
+int certify_level(::qcs_problem *P, int k, cudaStream_t s, bool *got);
+uint64_t level_points(const ::qcs_problem *P, int k); // V + W points of level k
+
 int walks_per_task(int n); // walks (warps) per CTA of the walk kernels for n qubits
 
 // ---- kernel launchers (qcs_walk.cu); all return cudaError_t of the launch ----

@@ -207,12 +207,16 @@ __device__ __forceinline__ Decoded decode(uint64_t x, const LevelCtx &lv)
     return d;
 }
 
-// f(x): all 32 lanes call it with the same x; every lane gets the result.
+// nu and h of one decoded point: the exact product of side `side` (0: V,
+// 1: W) for the rotations in qpack (and the chunk, odd k), its fingerprint
+// canonical form and the position-keyed hash with hash base `base`, as a
+// full 64-bit value.  All 32 lanes call it with the same point.
 template <int NQ>
-__device__ uint64_t warp_step(uint64_t x, uint32_t chunk, const LevelCtx &lv, const Smem<NQ> &sm, int lane)
+__device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_t base, const LevelCtx &lv,
+                               const Smem<NQ> &sm, int lane)
 {
     using G = Geo<NQ>;
-    const Decoded dx = decode(x, lv);
+    const Decoded dx{side, qpack};
 
     uint32_t ua[G::RPL], ub[G::RPL];
 #pragma unroll
@@ -351,7 +355,6 @@ __device__ uint64_t warp_step(uint64_t x, uint32_t chunk, const LevelCtx &lv, co
     }
 
     // position-keyed hash of the sorted fingerprints
-    const uint64_t base = sm.base[chunk];
     uint64_t acc = 0;
 #pragma unroll
     for (int t = 0; t < G::RPL; t++) {
@@ -365,7 +368,16 @@ __device__ uint64_t warp_step(uint64_t x, uint32_t chunk, const LevelCtx &lv, co
     const uint32_t s_l0 = __reduce_add_sync(kFull, lo & 0xFFFFu);
     const uint32_t s_l1 = __reduce_add_sync(kFull, lo >> 16);
     acc = ((uint64_t)s_hi << 32) + ((uint64_t)s_l1 << 16) + (uint64_t)s_l0;
-    return smix(acc) & lv.maskL;
+    return smix(acc);
+}
+
+// f(x): all 32 lanes call it with the same x; every lane gets the result.
+template <int NQ>
+__device__ __forceinline__ uint64_t warp_step(uint64_t x, uint32_t chunk, const LevelCtx &lv, const Smem<NQ> &sm,
+                                              int lane)
+{
+    const Decoded dx = decode(x, lv);
+    return coset_hash<NQ>(dx.side, dx.qpack, chunk, sm.base[chunk], lv, sm, lane) & lv.maskL;
 }
 
 // Stage the weights, the rotation coefficients, the per-chunk hash bases and
@@ -761,6 +773,62 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_rewalk_arrays(LevelCtx lv,
     }
 }
 
+// Exhaustive level pass (CertArgs): one warp per point, grid-stride.
+template <int NQ>
+__global__ void __launch_bounds__(Geo<NQ>::THREADS) k_certify(CertArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Smem<NQ> sm = stage<NQ>(a.lv, smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t xi = a.lv.xi;
+    for (uint64_t i = (uint64_t)blockIdx.x * Geo<NQ>::WARPS + warp; i < a.count;
+         i += (uint64_t)gridDim.x * Geo<NQ>::WARPS) {
+        const uint64_t idx = a.first + i;
+        uint64_t tuple = idx;
+        uint32_t chunk = 0;
+        if (a.side == 1 && (a.lv.k & 1)) {
+            chunk = (uint32_t)(idx / a.xi_h) + 1;
+            tuple = idx % a.xi_h;
+        }
+        uint64_t qpack = 0;
+        for (int j = 0; j < a.lv.h; j++) {
+            qpack |= (uint64_t)(tuple % xi + 1) << (8 * j);
+            tuple /= xi;
+        }
+        uint64_t key = coset_hash<NQ>(a.side, qpack, chunk, a.base, a.lv, sm, lane);
+        if (key == ~0ull) key = ~0ull - 1; // ~0 marks an empty slot
+        if (lane == 0) {
+            uint64_t s = smix(key) & a.mask;
+            if (a.side == 0) {
+                // the table is at most half full, so an empty slot is always found
+                for (uint64_t probe = 0; probe <= a.mask; probe++) {
+                    const unsigned long long prev = atomicCAS(
+                        reinterpret_cast<unsigned long long *>(&a.table[s].key), ~0ull, (unsigned long long)key);
+                    if (prev == ~0ull) {
+                        a.table[s].idx = idx;
+                        break;
+                    }
+                    s = (s + 1) & a.mask;
+                }
+            } else {
+                for (uint64_t probe = 0; probe <= a.mask; probe++) {
+                    const uint64_t k2 = a.table[s].key;
+                    if (k2 == ~0ull) break;
+                    if (k2 == key) {
+                        const uint32_t n = atomicAdd(a.n_pairs, 1u);
+                        if (n < a.cap) {
+                            a.pairs[2 * (size_t)n] = a.table[s].idx;
+                            a.pairs[2 * (size_t)n + 1] = idx;
+                        }
+                    }
+                    s = (s + 1) & a.mask;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
 int g_num_sms = 0;
 
 template <int NQ>
@@ -853,7 +921,27 @@ cudaError_t rewalk_arrays_n(const LevelCtx &lv, int chunk, const uint64_t *sa, c
     return cudaGetLastError();
 }
 
+template <int NQ>
+cudaError_t certify_n(const CertArgs &a, cudaStream_t s)
+{
+    cudaFuncSetAttribute(k_certify<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<NQ>::smem_bytes);
+    k_certify<NQ><<<grid_for<NQ>(a.count), Geo<NQ>::THREADS, Geo<NQ>::smem_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
 } // namespace
+
+cudaError_t launch_certify(const CertArgs &a, cudaStream_t s)
+{
+    if (a.count == 0) return cudaSuccess;
+    switch (a.lv.n) {
+    case 1: return certify_n<1>(a, s);
+    case 2: return certify_n<2>(a, s);
+    case 3: return certify_n<3>(a, s);
+    case 4: return certify_n<4>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 int num_sms()
 {

@@ -1,6 +1,7 @@
 """Host-side checks of the C ABI that need no GPU: the library loads, exports
 every entry point include/qcs.h declares, and its exact host paths
 (verification, input validation) agree with the oracle."""
+import os
 import re
 
 import numpy as np
@@ -111,3 +112,31 @@ def test_verify_rejects_bad_arguments(qlib):
     with pytest.raises(Q.QcsError):
         Q.verify_decomposition(2, u, 0, [16])
     assert Q.verify_decomposition(2, u, 0, [])
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # the ctypes mirrors of qcs_params, qcs_result and qcs_batch_params must
+    # have the header's field offsets and sizes (compiled here with gcc)
+    import ctypes
+    import subprocess
+
+    structs = {"qcs_params": Q.Params, "qcs_result": Q.Result, "qcs_batch_params": Q.BatchParams}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "qcs.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call(["gcc", "-I", inc, str(src), "-o", str(exe)])
+    got = {}
+    for ln in subprocess.check_output([str(exe)]).decode().splitlines():
+        cname, field, val = ln.split()
+        got[(cname, field)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
