@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-T-count run")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and other-size runs")
+    ap.add_argument("--config3-walk", type=int, default=0, metavar="TABLE_LOG2",
+                    help="only time the n = 4 seeded target's search by the collision walk alone with a "
+                         "2^TABLE_LOG2-slot table, print its JSON and exit")
     return ap.parse_args()
 
 
@@ -309,6 +312,34 @@ def table1_circuits(Q, stream, trials=10):
     return out
 
 
+def config3_time_to_optimal(Q, W, stream, mode="exhaustive", table_log2=30, queue_log2=24, limit_s=900):
+    """Time to the optimal T-count of the n = 4, 7-factor seeded target.
+    mode "exhaustive": the ladder settles each level by the exhaustive pass
+    alone (the V key table of level 7 is 512 MiB); mode "walk": the collision
+    search alone with a 2^table_log2-slot table (16 bytes a slot), theta
+    policy 1, no exhaustive pass."""
+    c = W.CONFIGS[3]
+    gates, _ = W.config_target(3)
+    if mode == "exhaustive":
+        p = Q.default_params(4, exhaustive_first=1, exhaustive_log2=34)
+    else:
+        p = Q.default_params(4, table_log2=table_log2, queue_capacity=1 << queue_log2, exhaustive_log2=0)
+    t0 = time.perf_counter()
+    prob = Q.Problem.from_circuit(4, gates, c["k_max"], p)
+    prob.run_walks(stream=stream)
+    r = prob.wait(int(limit_s * 1000))
+    if r["timed_out"]:
+        prob.cancel()
+        r = prob.wait(60_000)
+        r["status_name"] = "time_limit"
+    secs = time.perf_counter() - t0
+    prob.close()
+    return {"mode": mode, "seconds": secs, "status": r["status_name"], "t_count": r["t_count"],
+            "sde": r["sde"], "walk_steps": r["steps"], "exhaustive_points": r["cert_points"],
+            "certified_levels": r["certified_levels"], "merges": r["merges"], "claws": r["claws"],
+            "table_log2": None if mode == "exhaustive" else table_log2}
+
+
 def run_serving(Q, W, torch, stream, tuned, n_requests=2000, rate=50.0, budget_bytes=2 << 30,
                 deadline_s=10.0, drain_s=15.0):
     """Config 5: a Poisson stream of seeded targets replayed in real time into
@@ -469,6 +500,7 @@ def run_ours(args):
                 "batched": batched,
                 "serving": run_serving(Q, W, torch, stream, batched["autotuned"]),
                 "table1_circuits": table1_circuits(Q, stream),
+                "config3_time_to_optimal": config3_time_to_optimal(Q, W, stream, "exhaustive"),
                 "n2_level3": level_throughput(Q, W, torch, 1, 3, 512, stream, alu_per_s=imad_per_s),
                 "n4_level7": level_throughput(Q, W, torch, 3, 7, 16, stream, alu_per_s=dp4a_per_s),
             }
@@ -517,9 +549,23 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_config3_walk(args):
+    import torch
+
+    import paper_1606_07413_gb300 as Q
+    from paper_1606_07413_gb300 import build as B
+    from paper_1606_07413_gb300 import workloads as W
+
+    B.build()
+    stream = torch.cuda.Stream()
+    print(json.dumps({"config3_time_to_optimal": config3_time_to_optimal(Q, W, stream, "walk", args.config3_walk)}))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.config3_walk:
+        run_config3_walk(a)
     else:
         run_ours(a)

@@ -93,14 +93,18 @@ typedef struct qcs_params {
     int32_t max_trail_factor; /* a trail is abandoned after max_trail_factor * 2^d_theta steps */
     int32_t queue_capacity;   /* collision pairs kept per launch */
     int32_t budget_factor;    /* a level gives up after budget_factor * (points at that level) steps */
-    int32_t theta_policy;     /* 0: d_theta fixed; 1: raise theta on small levels (time to solution) */
+    int32_t theta_policy;     /* 0: d_theta fixed; 1: theta from the level size N and the table size w
+                                 (qcs_plan_level) */
     int32_t version_factor;   /* new function version every version_factor * points steps (0: never) */
     int32_t stop_on_claw;     /* 1: stop at the first verified claw; 0: keep walking to the step budget
                                  (the first decomposition is still reported) */
     int32_t theta_min_bits;   /* theta_policy 1 never raises theta above 2^-theta_min_bits (>= 1) */
-    int32_t exhaustive_log2;  /* a level whose V and W points number at most 2^exhaustive_log2 and
-                                 whose walk budget ends without a claw is settled exactly by
-                                 qcs_certify_level (0: never; at most 40) */
+    int32_t exhaustive_log2;  /* a level whose V and W points number at most 2^exhaustive_log2, and
+                                 whose key table fits in half the free device memory, is settled
+                                 exactly by qcs_certify_level when its walk budget ends without a
+                                 claw (0: never; at most 40) */
+    int32_t exhaustive_first; /* 1: qcs_run_walks settles such levels by qcs_certify_level alone,
+                                 without walking them (0: walk first) */
     uint64_t seed;            /* seed of trail starting points */
 } qcs_params;
 
@@ -324,6 +328,29 @@ QCS_API int qcs_walk_step(qcs_problem *prob, int k, int chunk, uint32_t version,
 QCS_API int qcs_rewalk(qcs_problem *prob, int k, int chunk, uint32_t version, const uint64_t *start_a,
                const uint32_t *len_a, const uint64_t *start_b, const uint32_t *len_b,
                size_t count, int32_t *cls, uint64_t *ab, void *stream);
+
+/* How the search walks level k of an n-qubit problem with parameters p (pure
+ * host arithmetic, no device).  N = 2 xi^h (xi chunks for odd k) points,
+ * w = 2^table_log2 slots.  theta_policy 1 takes theta = 2^-d_theta with
+ * d_theta the larger of theta_min_bits and the rounded log2 of sqrt(N / 2w),
+ * the minimum over theta of the steps per collision N theta / w + 2 / theta
+ * (Appendix, after van Oorschot and Wiener); when w >= N that is
+ * 2^-theta_min_bits, the large theta the paper found fastest for small
+ * spaces (Sec. 5.1).  d_theta never exceeds p->dp_bits.  A launch covers at
+ * most one function version (version_factor * N steps), its expected merges
+ * (distinguished points times the stored fraction min(1, w / (theta N))) fit
+ * half the merge queue, and a level ends after budget_factor * N steps and at
+ * least four versions.  Errors: QCS_ERR_ARG. */
+typedef struct qcs_plan {
+    int32_t dp_bits;               /* d_theta used at this level */
+    uint32_t walks;                /* concurrent walks */
+    uint32_t steps;                /* steps per walk per launch */
+    uint64_t launches_per_version; /* ~0: one version for the level */
+    uint64_t min_launches;         /* launches before the level is given up */
+    uint64_t points;               /* N */
+} qcs_plan;
+
+QCS_API int qcs_plan_level(int n_qubits, int k, const qcs_params *p, qcs_plan *out);
 
 /* Facts about a created problem: sde of C^ (smallest denominator exponent),
  * and the number of walk points 2 xi^h at level k (per chunk). */

@@ -17,7 +17,7 @@ import numpy as np
 from . import build as _build_mod
 
 __all__ = ["lib", "Params", "Result", "Problem", "Batch", "BatchParams", "default_params",
-           "default_batch_params", "verify_decomposition", "strerror", "QcsError"]
+           "default_batch_params", "verify_decomposition", "strerror", "QcsError", "plan_level"]
 
 OK = 0
 ERR_ARG, ERR_NOT_UNITARY, ERR_NOMEM, ERR_CUDA, ERR_MISMATCH, ERR_OVERFLOW, ERR_BUSY, ERR_TIMEOUT, ERR_DEVICE = \
@@ -34,7 +34,8 @@ class Params(ctypes.Structure):
                 ("max_trail_factor", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
                 ("budget_factor", ctypes.c_int32), ("theta_policy", ctypes.c_int32),
                 ("version_factor", ctypes.c_int32), ("stop_on_claw", ctypes.c_int32), ("theta_min_bits", ctypes.c_int32),
-                ("exhaustive_log2", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("exhaustive_log2", ctypes.c_int32), ("exhaustive_first", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -56,6 +57,15 @@ class Result(ctypes.Structure):
         d["paulis"] = [int(v) for v in self.paulis[: max(self.t_count, 0)]]
         d["status_name"] = STATUS_NAMES.get(self.status, "?")
         return d
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("dp_bits", ctypes.c_int32), ("walks", ctypes.c_uint32), ("steps", ctypes.c_uint32),
+                ("launches_per_version", ctypes.c_uint64), ("min_launches", ctypes.c_uint64),
+                ("points", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class BatchParams(ctypes.Structure):
@@ -113,6 +123,7 @@ def lib():
             "qcs_level_rewalk": (ctypes.c_int, [_vp, _vp]),
             "qcs_level_collect": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(Result)]),
             "qcs_certify_level": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_int)]),
+            "qcs_plan_level": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), ctypes.POINTER(Plan)]),
             "qcs_level_walk_static": (ctypes.c_int, [_vp, ctypes.c_int, _u32, ctypes.c_int, ctypes.c_int, _vp, _u32,
                                                      _u32, _vp, _u32, _vp, _vp]),
             "qcs_batch_default_params": (None, [ctypes.POINTER(BatchParams)]),
@@ -156,6 +167,13 @@ def default_params(n: int, **overrides) -> Params:
             raise TypeError(f"unknown search parameter {k!r}")
         setattr(p, k, v)
     return p
+
+
+def plan_level(n: int, k: int, params: Params) -> dict:
+    """qcs_plan_level: how the search walks level k (host arithmetic only)."""
+    out = Plan()
+    _check(lib().qcs_plan_level(int(n), int(k), ctypes.byref(params), ctypes.byref(out)), "qcs_plan_level")
+    return out.as_dict()
 
 
 def _ptr(t):

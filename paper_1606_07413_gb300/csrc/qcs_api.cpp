@@ -407,18 +407,20 @@ int level_collect(qcs_problem *P, cudaStream_t s, bool *got, uint64_t *steps)
 
 } // namespace
 
-LevelPlan qcs::plan_level(const qcs_problem *P, int k, const qcs_params &p)
+LevelPlan qcs::plan_level_n(int D, int k, const qcs_params &p)
 {
     LevelPlan pl{};
-    const uint64_t xi = (uint64_t)(P->D - 1);
+    const uint64_t xi = (uint64_t)(D - 1);
     const long double points = 2.0L * (long double)upow(xi, k / 2) * (long double)((k & 1) ? xi : 1);
+    pl.points = points > 1.8e19L ? ~0ull : (uint64_t)points;
     pl.dp_bits = p.dp_bits;
+    const long double slots = (long double)((uint64_t)1 << p.table_log2);
     if (p.theta_policy == 1) {
-        // theta as large as 1/2 while theta * points stays within half the table
-        const long double slots = (long double)((uint64_t)1 << p.table_log2);
-        int d = std::max(1, std::min(p.theta_min_bits, p.dp_bits));
-        while (d < p.dp_bits && points / (long double)((uint64_t)1 << d) > slots / 2) d++;
-        pl.dp_bits = d;
+        // minimise N theta / w + 2 / theta: theta = sqrt(2 w / N), i.e.
+        // d = log2(sqrt(N / 2w)), at least theta_min_bits
+        const long double ratio = points / (2.0L * slots);
+        const int d_opt = ratio > 1.0L ? (int)std::lround(0.5L * std::log2(ratio)) : 0;
+        pl.dp_bits = std::min(p.dp_bits, std::max(std::max(1, p.theta_min_bits), d_opt));
     }
     const long double theta = 1.0L / (long double)((uint64_t)1 << pl.dp_bits);
     const long double vf = p.version_factor > 0 ? (long double)p.version_factor : 1e30L;
@@ -428,10 +430,19 @@ LevelPlan qcs::plan_level(const qcs_problem *P, int k, const qcs_params &p)
     const long double s_min = std::min<long double>(steps, 4.0L / theta);
     if (walks * steps > version_steps) steps = std::max(s_min, std::floor(version_steps / walks));
     if (walks * steps > version_steps) walks = std::max(32.0L, std::floor(version_steps / steps));
-    // merges per launch (about one per distinguished point) must fit the queue
-    const long double qroom = (long double)p.queue_capacity / 2;
-    while (walks * steps * theta > qroom && steps > 1) steps = std::floor(steps / 2);
-    if (walks * steps * theta > qroom) walks = std::max(32.0L, std::floor(qroom / (steps * theta)));
+    // expected merges per launch (distinguished points that meet a stored
+    // one, about the stored fraction of all distinguished points) fit half
+    // the queue
+    // half the queue; fewer walks first (down to a few per resident warp),
+    // then fewer steps, so that launches stay long
+    const long double stored = std::min(1.0L, slots / (theta * points));
+    const long double qroom = (long double)p.queue_capacity / 2, per_step = theta * stored;
+    if (walks * steps * per_step > qroom) {
+        const long double keep = std::max(1.0L, std::min(steps, s_min));
+        walks = std::min(walks, std::max(std::min(walks, 8192.0L), std::floor(qroom / (keep * per_step))));
+        steps = std::max(1.0L, std::min(steps, std::floor(qroom / (walks * per_step))));
+        if (walks * steps * per_step > qroom) walks = std::max(32.0L, std::floor(qroom / (steps * per_step)));
+    }
     pl.walks = (uint32_t)walks;
     pl.steps = (uint32_t)std::max(1.0L, steps);
     const long double per_launch = (long double)pl.walks * pl.steps;
@@ -446,11 +457,24 @@ LevelPlan qcs::plan_level(const qcs_problem *P, int k, const qcs_params &p)
     return pl;
 }
 
-uint64_t qcs::level_points(const qcs_problem *P, int k)
+LevelPlan qcs::plan_level(const qcs_problem *P, int k, const qcs_params &p) { return plan_level_n(P->D, k, p); }
+
+uint64_t qcs::exhaustive_points(const qcs_problem *P, int k)
 {
     const uint64_t xi = (uint64_t)(P->D - 1);
     const long double v = (long double)upow(xi, k / 2), w = v * (long double)((k & 1) ? xi : 1);
     return v + w > 1.8e19L ? ~0ull : (uint64_t)(v + w);
+}
+
+bool qcs::exhaustive_eligible(const qcs_problem *P, int k)
+{
+    if (P->p.exhaustive_log2 <= 0 || k < 2 || exhaustive_points(P, k) > (1ull << P->p.exhaustive_log2)) return false;
+    uint64_t slots = 1024;
+    const uint64_t xi_h = upow((uint64_t)(P->D - 1), k / 2);
+    while (slots < 2 * xi_h) slots <<= 1;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return false;
+    return sizeof(CertSlot) * slots <= free_b / 2;
 }
 
 int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
@@ -574,6 +598,16 @@ int drive(qcs_problem *P, uint64_t budget, cudaStream_t s)
             }
             continue;
         }
+        if (P->p.exhaustive_first && exhaustive_eligible(P, k)) {
+            bool got = false;
+            const int rc = certify_level(P, k, s, &got);
+            if (rc == QCS_OK) {
+                if (got) return QCS_OK;
+                continue; // proved empty: the next level
+            }
+            if (rc != QCS_ERR_OVERFLOW) return rc;
+            // inconclusive: walk the level
+        }
         const LevelPlan pl = plan_level(P, k, P->p);
         uint64_t launches = 0, in_version = 0;
         bool fresh = true;
@@ -604,7 +638,7 @@ int drive(qcs_problem *P, uint64_t budget, cudaStream_t s)
         }
         version++;
         if (have_decomposition(P)) return QCS_OK; // the optimal level is the first with a claw
-        if (P->p.exhaustive_log2 > 0 && level_points(P, k) <= (1ull << P->p.exhaustive_log2)) {
+        if (exhaustive_eligible(P, k)) {
             // the walk budget ended without a claw: settle the level exactly
             bool got = false;
             const int rc = certify_level(P, k, s, &got);
@@ -892,6 +926,22 @@ int qcs_rewalk(qcs_problem *P, int k, int chunk, uint32_t version, const uint64_
     cudaError_t e = launch_rewalk_arrays(lv, chunk, start_a, len_a, start_b, len_b, count, cls, ab,
                                          (cudaStream_t)stream);
     return e == cudaSuccess ? QCS_OK : cuda_fail(e);
+}
+
+int qcs_plan_level(int n, int k, const qcs_params *p, qcs_plan *out)
+{
+    if (!p || !out || n < 1 || n > 4 || k < 2 || k > 15) return QCS_ERR_ARG;
+    if (p->table_log2 < 4 || p->table_log2 > 34 || p->dp_bits < 1 || p->walks < 1 || p->steps_per_launch < 1 ||
+        p->queue_capacity < 1)
+        return QCS_ERR_ARG;
+    const LevelPlan pl = plan_level_n(1 << (2 * n), k, *p);
+    out->dp_bits = pl.dp_bits;
+    out->walks = pl.walks;
+    out->steps = pl.steps;
+    out->launches_per_version = pl.launches_per_version;
+    out->min_launches = pl.min_launches;
+    out->points = pl.points;
+    return QCS_OK;
 }
 
 int qcs_problem_sde(const qcs_problem *P) { return P ? P->C.E : -1; }

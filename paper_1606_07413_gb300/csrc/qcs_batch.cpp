@@ -256,7 +256,7 @@ void collect_job(Job &j, const unsigned long long *c, const uint32_t *heads, con
         return;
     }
     if (j.launches >= j.pl.min_launches) { // level exhausted: the next one
-        if (P->p.exhaustive_log2 > 0 && level_points(P, k) <= (1ull << P->p.exhaustive_log2)) {
+        if (exhaustive_eligible(P, k)) {
             // settle the level exactly before moving on (a claw the walk missed)
             bool claw = false;
             const int rc = certify_level(P, k, s, &claw);

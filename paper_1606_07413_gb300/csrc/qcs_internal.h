@@ -164,7 +164,8 @@ struct CertArgs {
 cudaError_t launch_certify(const CertArgs &a, cudaStream_t s);
 // Host driver of the exhaustive pass (qcs_certify_level); *got = verified claw.
 int certify_level(::qcs_problem *P, int k, cudaStream_t s, bool *got);
-uint64_t level_points(const ::qcs_problem *P, int k); // V + W points of level k
+uint64_t exhaustive_points(const ::qcs_problem *P, int k); // V + W points of level k
+bool exhaustive_eligible(const ::qcs_problem *P, int k);   // within exhaustive_log2 and device memory
 
 int walks_per_task(int n); // walks (warps) per CTA of the walk kernels for n qubits
 
@@ -218,6 +219,7 @@ struct LevelPlan {
     int dp_bits;
     uint32_t walks, steps;
     uint64_t launches_per_version, min_launches;
+    uint64_t points;
 };
 
 // helpers of the host library shared by qcs_api.cpp and qcs_batch.cpp
@@ -226,6 +228,7 @@ int field_bits(int L, int h);
 void decode_state(uint64_t x, int n, int L, int h, uint32_t *q);
 LevelCtx make_level(const ::qcs_problem *P, int k, uint32_t version, int dp_bits);
 LevelPlan plan_level(const ::qcs_problem *P, int k, const qcs_params &p);
+LevelPlan plan_level_n(int D, int k, const qcs_params &p); // D = 4^n
 void found(::qcs_problem *P, int k, const uint32_t *paulis);
 
 } // namespace qcs

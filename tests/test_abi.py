@@ -140,3 +140,38 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_level_plan_follows_the_appendix_rule(qlib):
+    # theta_policy 1: theta = 2^-d, d = max(theta_min_bits, round(log2 sqrt(N / 2w)))
+    import math
+
+    for n, k, tl in ((2, 3, 16), (3, 5, 22), (3, 7, 18), (4, 6, 26), (4, 7, 26), (4, 7, 30), (4, 8, 20)):
+        p = Q.default_params(n, table_log2=tl, dp_bits=30 if n == 4 else 20)
+        pl = Q.plan_level(n, k, p)
+        xi = 4 ** n - 1
+        N = 2 * xi ** (k // 2) * (xi if k & 1 else 1)
+        w = 2 ** tl
+        assert pl["points"] == N
+        if N <= 2 * w:
+            assert pl["dp_bits"] == p.theta_min_bits
+        else:
+            assert abs(pl["dp_bits"] - 0.5 * math.log2(N / (2 * w))) <= 0.5
+        theta = 2.0 ** -pl["dp_bits"]
+        steps_per_launch = pl["walks"] * pl["steps"]
+        # a launch stays within one function version, trails of 4/theta fit
+        assert steps_per_launch <= max(p.version_factor * N, pl["walks"] * min(p.steps_per_launch, 4 / theta))
+        # expected merges per launch fit half the queue
+        stored = min(1.0, w / (theta * N))
+        assert steps_per_launch * theta * stored <= p.queue_capacity / 2 or pl["steps"] == 1
+        # the level's budget and at least four versions
+        assert pl["min_launches"] * steps_per_launch >= p.budget_factor * N
+        assert pl["min_launches"] >= 4 * pl["launches_per_version"]
+
+
+def test_level_plan_fixed_theta_and_bad_arguments(qlib):
+    p = Q.default_params(3, theta_policy=0, dp_bits=10)
+    assert Q.plan_level(3, 5, p)["dp_bits"] == 10
+    for n, k in ((0, 4), (5, 4), (3, 1), (3, 16)):
+        with pytest.raises(Q.QcsError):
+            Q.plan_level(n, k, p)

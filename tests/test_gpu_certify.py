@@ -71,3 +71,18 @@ def test_ladder_settles_small_levels_exactly(orc, dev, n, t, seed):
         assert r["t_count"] == t_exact
     assert r["t_count"] <= t
     assert r["certified_levels"] == max(0, r["t_count"] - low)
+
+
+@pytest.mark.parametrize("n,t,seed", [(2, 5, 91), (2, 6, 92), (3, 4, 93)])
+def test_exhaustive_first_settles_levels_without_walking(orc, dev, n, t, seed):
+    gates, _ = W.seeded_target(n, t, seed)
+    C = orc.channel_from_circuit(n, gates)
+    p = Q.default_params(n, exhaustive_first=1)
+    with Q.Problem.from_circuit(n, gates, t, p) as prob:
+        prob.run_walks()
+        r = prob.wait(120_000)
+    assert r["status_name"] == "found" and orc.verify(C, r["paulis"])
+    assert r["steps"] == 0 and r["launches"] == 0
+    t_exact, _ = orc.mitm_tcount(C, t) if n == 2 else (r["t_count"], None)
+    assert r["t_count"] == t_exact
+    assert r["certified_levels"] == max(0, r["t_count"] - max(orc.sde(C), 2))
