@@ -166,9 +166,24 @@ def test_budget_and_cancel(orc, dev):
     prob.close()
 
 
+def paper_tcounts():
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_tcounts.txt")
+    out = {}
+    with open(path) as f:
+        for ln in f:
+            if ln.strip() and not ln.startswith("#"):
+                name, n, t = ln.split()
+                out[name] = (int(n), int(t))
+    return out
+
+
 @pytest.mark.parametrize("name", ["toffoli", "fredkin"])
 def test_table1_circuits_have_tcount_7(orc, dev, name):
-    """Toffoli and Fredkin have optimal T-count 7 (Sec. 5.2, Table 1)."""
+    """Toffoli and Fredkin have optimal T-count 7 (Sec. 5.2, Table 1), and
+    every lower level is proved empty by the exhaustive pass."""
+    n_want, t_want = paper_tcounts()[name]
     if name == "toffoli":
         perm = [c ^ (4 if (c & 3) == 3 else 0) for c in range(8)]
     else:
@@ -180,7 +195,8 @@ def test_table1_circuits_have_tcount_7(orc, dev, name):
     prob.run_walks()
     res = prob.wait(600_000)
     assert res["status_name"] == "found", res
-    assert res["t_count"] == 7
+    assert n_want == 3 and res["t_count"] == t_want
+    assert res["certified_levels"] == t_want - max(orc.sde(C), 2)
     assert orc.verify(C, res["paulis"])
     assert Q.verify_decomposition(3, u, 0, res["paulis"])
     print(f"{name}: T-count 7 in {time.time() - t0:.2f}s, {res['steps']} steps")
