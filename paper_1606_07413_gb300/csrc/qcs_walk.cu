@@ -10,9 +10,9 @@
 //   h  : a coset-invariant hash back to an L-bit state.
 //
 // The hash is defined on the exact product M at exponent K: every column Q
-// gets the 32-bit linear fingerprint L_Q = sum_i Ua[i] a_iQ + Ub[i] b_iQ mod
-// 2^32, folded to phi_Q = min(L_Q, -L_Q) (so a column's sign does not matter),
-// and the sorted phi are hashed.  Because L is linear in M's integer
+// gets the 16-bit linear fingerprint L_Q = sum_i Ua[i] a_iQ + Ub[i] b_iQ mod
+// 2^16, folded to phi_Q = min(L_Q, -L_Q) (so a column's sign does not matter),
+// and the sorted phi are hashed in pairs.  Because L is linear in M's integer
 // numerators and every factor acts linearly on them, L(M e_Q) =
 // ((adjoint network) U)^T (M's right factor) e_Q: the kernel pushes the weight
 // vector U through the transposed sparse R^ butterflies (4^n entries, h
@@ -41,10 +41,10 @@ namespace {
 #define QCS_GEMV_UNROLL 2 // 32-bit word contraction (rows per unrolled step / 2)
 #endif
 #ifndef QCS_QUAD_UNROLL3
-#define QCS_QUAD_UNROLL3 8 // byte-quad contraction, n = 3 (16 quads)
+#define QCS_QUAD_UNROLL3 16 // byte-quad contraction, n = 3 (16 quads)
 #endif
 #ifndef QCS_QUAD_UNROLL4
-#define QCS_QUAD_UNROLL4 4 // byte-quad contraction, n = 4 (64 quads)
+#define QCS_QUAD_UNROLL4 8 // byte-quad contraction, n = 4 (64 quads)
 #endif
 constexpr int kWarps = QCS_WARPS;
 constexpr int kGemvUnroll = QCS_GEMV_UNROLL;
@@ -153,36 +153,49 @@ __device__ __forceinline__ uint32_t dp4a_us(uint32_t a, uint32_t b, uint32_t c)
     return d;
 }
 
-// Byte planes of the weights for the byte-quad contraction.  The weight of a
-// row is u = sum_k 2^(8k) u_k with bytes u_k, so sum_i u_i c_i =
-// sum_k 2^(8k) sum_i u_{i,k} c_i: an exact identity mod 2^32 whose inner sums
-// are byte dot products.  Plane word (q, part, k) holds byte k of the part
-// (0: a, 1: b) weights of rows 4q .. 4q+3; it is written, in place of the
-// rows (uint2 per row) in the warp's exchange buffer, as word k of uint4
-// number 2q + part.
+// Byte planes of the weights for the byte-quad contraction.  Fingerprints
+// live mod 2^16, so a row's weight is u = u_0 + 2^8 u_1 (mod 2^16) with bytes
+// u_0, u_1, and sum_i u_i c_i = sum_i u_{i,0} c_i + 2^8 sum_i u_{i,1} c_i
+// (mod 2^16): an exact identity whose inner sums are byte dot products.  The
+// plane words of quad q (rows 4q .. 4q+3) are written, in place of the rows
+// (uint2 per row) in the warp's exchange buffer, as uint4 number q:
+// (a plane 0, a plane 1, b plane 0, b plane 1), each word holding that byte
+// of the four rows' weights.
 template <int NQ>
 __device__ __forceinline__ void weight_planes(uint2 *su, int lane)
 {
     using G = Geo<NQ>;
     constexpr int JOBS = G::DIM >= 64 ? G::DIM / 64 : 1; // 2 parts x DIM/4 quads over 32 lanes
     const uint4 *s4 = reinterpret_cast<const uint4 *>(su);
-    uint4 pl[JOBS];
+    uint2 pl[JOBS];
 #pragma unroll
     for (int r = 0; r < JOBS; r++) {
         const int job = lane + 32 * r, q = job >> 1, part = job & 1;
         const uint4 r01 = s4[2 * q], r23 = s4[2 * q + 1]; // rows 4q, 4q+1 and 4q+2, 4q+3
         const uint32_t u0 = part ? r01.y : r01.x, u1 = part ? r01.w : r01.z;
         const uint32_t u2 = part ? r23.y : r23.x, u3 = part ? r23.w : r23.z;
-        const uint32_t lo01 = __byte_perm(u0, u1, 0x5140), hi01 = __byte_perm(u0, u1, 0x7362);
-        const uint32_t lo23 = __byte_perm(u2, u3, 0x5140), hi23 = __byte_perm(u2, u3, 0x7362);
-        pl[r] = make_uint4(__byte_perm(lo01, lo23, 0x5410), __byte_perm(lo01, lo23, 0x7632),
-                           __byte_perm(hi01, hi23, 0x5410), __byte_perm(hi01, hi23, 0x7632));
+        const uint32_t lo01 = __byte_perm(u0, u1, 0x5140), lo23 = __byte_perm(u2, u3, 0x5140);
+        pl[r] = make_uint2(__byte_perm(lo01, lo23, 0x5410), __byte_perm(lo01, lo23, 0x7632));
     }
     __syncwarp();
-    uint4 *w4 = reinterpret_cast<uint4 *>(su);
+    uint2 *w2 = su;
 #pragma unroll
-    for (int r = 0; r < JOBS; r++) w4[lane + 32 * r] = pl[r];
+    for (int r = 0; r < JOBS; r++) w2[lane + 32 * r] = pl[r];
     __syncwarp();
+}
+
+// packed 16-bit minimum and maximum of both halves
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
 }
 
 struct Decoded {
@@ -264,30 +277,27 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
             weight_planes<NQ>(su, lane);
             const uint4 *w4 = reinterpret_cast<const uint4 *>(su);
             constexpr int CW = G::RPL / 2;
-            uint32_t acc[G::RPL][4];
+            uint32_t acc[G::RPL][2];
 #pragma unroll
-            for (int t = 0; t < G::RPL; t++)
-#pragma unroll
-                for (int k = 0; k < 4; k++) acc[t][k] = 0;
+            for (int t = 0; t < G::RPL; t++) acc[t][0] = acc[t][1] = 0;
 #pragma unroll G::QUAD_UNROLL
             for (int q = 0; q < G::DIM / 4; q++) {
-                const uint4 wa = w4[2 * q], wb = w4[2 * q + 1];
-                const uint32_t pa[4] = {wa.x, wa.y, wa.z, wa.w}, pb[4] = {wb.x, wb.y, wb.z, wb.w};
+                const uint4 w = w4[q]; // a plane 0, a plane 1, b plane 0, b plane 1
 #pragma unroll
                 for (int j = 0; j < CW; j++) {
                     const uint4 c = sm.Cq[(q * CW + j) * 32 + lane];
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        acc[2 * j][k] = dp4a_us(pa[k], c.x, acc[2 * j][k]);
-                        acc[2 * j][k] = dp4a_us(pb[k], c.y, acc[2 * j][k]);
-                        acc[2 * j + 1][k] = dp4a_us(pa[k], c.z, acc[2 * j + 1][k]);
-                        acc[2 * j + 1][k] = dp4a_us(pb[k], c.w, acc[2 * j + 1][k]);
-                    }
+                    acc[2 * j][0] = dp4a_us(w.x, c.x, acc[2 * j][0]);
+                    acc[2 * j][0] = dp4a_us(w.z, c.y, acc[2 * j][0]);
+                    acc[2 * j][1] = dp4a_us(w.y, c.x, acc[2 * j][1]);
+                    acc[2 * j][1] = dp4a_us(w.w, c.y, acc[2 * j][1]);
+                    acc[2 * j + 1][0] = dp4a_us(w.x, c.z, acc[2 * j + 1][0]);
+                    acc[2 * j + 1][0] = dp4a_us(w.z, c.w, acc[2 * j + 1][0]);
+                    acc[2 * j + 1][1] = dp4a_us(w.y, c.z, acc[2 * j + 1][1]);
+                    acc[2 * j + 1][1] = dp4a_us(w.w, c.w, acc[2 * j + 1][1]);
                 }
             }
 #pragma unroll
-            for (int t = 0; t < G::RPL; t++)
-                Lc[t] = acc[t][0] + (acc[t][1] << 8) + (acc[t][2] << 16) + (acc[t][3] << 24);
+            for (int t = 0; t < G::RPL; t++) Lc[t] = acc[t][0] + (acc[t][1] << 8);
         } else if (G::DIM >= 32) {
             const uint4 *su4 = reinterpret_cast<const uint4 *>(su);
 #pragma unroll kGemvUnroll
@@ -312,54 +322,78 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
         __syncwarp();
     }
 
-    // sign-invariant column fingerprints; column 0 (the identity) and padding
-    // lanes sort last as 0xFFFFFFFF (every phi is at most 2^31).  Sort element
-    // e = RPL lane + t starts with this lane's column lane + 32 t (where the
-    // keys start does not matter to a sort).
+    // sign-invariant 16-bit column fingerprints; column 0 (the identity) and
+    // padding lanes sort last as 0xFFFF (every phi is at most 2^15).  Sort
+    // element e = RPL lane + t starts with this lane's column lane + 32 t
+    // (where the keys start does not matter to a sort).
     uint32_t key[G::RPL];
 #pragma unroll
     for (int t = 0; t < G::RPL; t++) {
         const int Q = lane + 32 * t;
-        const uint32_t l = Lc[t], nl = 0u - l;
-        key[t] = (Q >= 1 && Q <= G::D) ? min(l, nl) : 0xFFFFFFFFu;
+        const uint32_t l = Lc[t] & 0xFFFFu, nl = (0u - l) & 0xFFFFu;
+        key[t] = (Q >= 1 && Q <= G::D) ? min(l, nl) : 0xFFFFu;
     }
-    // bitonic sort of SLOTS keys, ascending in e; strides below RPL stay in
-    // registers, larger ones go through shuffles (there a lane's keys share
-    // the direction, which comes from the lane part of e)
+    uint64_t acc = 0;
+    if constexpr (G::RPL >= 2) {
+        // two keys per word: word u holds elements e = RPL lane + 2u (low
+        // half) and e + 1 (high half); bitonic sort ascending in e with
+        // packed 16-bit min/max.  Stride 1 pairs the halves of a word, strides
+        // below RPL pair words of the lane, larger strides pair lanes.
+        constexpr int NW = G::RPL / 2;
+        uint32_t kw[NW];
 #pragma unroll
-    for (int size = 2; size <= G::SLOTS; size <<= 1) {
+        for (int u = 0; u < NW; u++) kw[u] = key[2 * u] | (key[2 * u + 1] << 16);
 #pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            if (stride < G::RPL) {
+        for (int size = 2; size <= G::SLOTS; size <<= 1) {
 #pragma unroll
-                for (int t = 0; t < G::RPL; t++) {
-                    if ((t & stride) == 0) {
-                        const int e = G::RPL * lane + t;
-                        const bool up = (e & size) == 0;
-                        const uint32_t a = key[t], b = key[t | stride];
-                        const bool swap = (a > b) == up;
-                        key[t] = swap ? b : a;
-                        key[t | stride] = swap ? a : b;
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                if (stride == 1) {
+#pragma unroll
+                    for (int u = 0; u < NW; u++) {
+                        const bool up = ((G::RPL * lane + 2 * u) & size) == 0;
+                        const uint32_t sw = __byte_perm(kw[u], 0, 0x1032);
+                        const uint32_t mn = min_u16x2(kw[u], sw), mx = max_u16x2(kw[u], sw);
+                        kw[u] = up ? __byte_perm(mn, mx, 0x7610) : __byte_perm(mx, mn, 0x7610);
                     }
-                }
-            } else {
-                const int lstride = stride / G::RPL, eb = G::RPL * lane;
-                const bool keep_min = ((eb & stride) == 0) == ((eb & size) == 0);
+                } else if (stride < G::RPL) {
+                    const int ws = stride >> 1;
 #pragma unroll
-                for (int t = 0; t < G::RPL; t++) {
-                    const uint32_t o = __shfl_xor_sync(kFull, key[t], lstride);
-                    key[t] = ((key[t] < o) == keep_min) ? key[t] : o;
+                    for (int u = 0; u < NW; u++) {
+                        if ((u & ws) == 0) {
+                            const bool up = ((G::RPL * lane + 2 * u) & size) == 0;
+                            const uint32_t mn = min_u16x2(kw[u], kw[u | ws]), mx = max_u16x2(kw[u], kw[u | ws]);
+                            kw[u] = up ? mn : mx;
+                            kw[u | ws] = up ? mx : mn;
+                        }
+                    }
+                } else {
+                    const int lstride = stride / G::RPL, eb = G::RPL * lane;
+                    const bool keep_min = ((eb & stride) == 0) == ((eb & size) == 0);
+#pragma unroll
+                    for (int u = 0; u < NW; u++) {
+                        const uint32_t o = __shfl_xor_sync(kFull, kw[u], lstride);
+                        kw[u] = keep_min ? min_u16x2(kw[u], o) : max_u16x2(kw[u], o);
+                    }
                 }
             }
         }
-    }
-
-    // position-keyed hash of the sorted fingerprints
-    uint64_t acc = 0;
+        // position-keyed hash of the sorted pairs: pair p = NW lane + u
 #pragma unroll
-    for (int t = 0; t < G::RPL; t++) {
-        const int e = G::RPL * lane + t;
-        if (e < G::D) acc += smix(base ^ (((uint64_t)e << 32) | key[t]));
+        for (int u = 0; u < NW; u++) acc += smix(base ^ (((uint64_t)(NW * lane + u) << 32) | kw[u]));
+    } else {
+        // one key per lane (n <= 2): bitonic sort across the 32 lanes
+#pragma unroll
+        for (int size = 2; size <= G::SLOTS; size <<= 1) {
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
+                const uint32_t o = __shfl_xor_sync(kFull, key[0], stride);
+                key[0] = ((key[0] < o) == keep_min) ? key[0] : o;
+            }
+        }
+        // pair p = lane / 2 packs elements 2p and 2p + 1, for the 4^n / 2 pairs
+        const uint32_t nxt = __shfl_down_sync(kFull, key[0], 1);
+        if ((lane & 1) == 0 && lane < G::DIM) acc = smix(base ^ (((uint64_t)(lane >> 1) << 32) | key[0] | (nxt << 16)));
     }
     // warp sum mod 2^64 from three 32-bit reductions: the high words (mod
     // 2^32) and the two 16-bit halves of the low words (no overflow: 32 terms)
