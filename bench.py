@@ -61,7 +61,7 @@ def workload_config(c):
         "workload": f"n{c['n']}_t{c['t']}_level{K_LEVEL}_walks{c['walks']}_L{c['L']}_theta2^-{c['dtheta']}",
         "n_qubits": c["n"], "level_k": K_LEVEL, "chunks": 4 ** c["n"] - 1, "walks": c["walks"],
         "steps_per_walk_per_step": STEPS_PER_LAUNCH, "state_bits": c["L"], "dp_bits": c["dtheta"],
-        "table_slots": 1 << c["table_log2"], "coefficients": "int64 exact (fingerprints mod 2^32)",
+        "table_slots": 1 << c["table_log2"], "coefficients": "exact: int64 on the host, C^ as int8 byte quads on the device; fingerprints mod 2^16",
         "l2": f"flushed between steps ({FLUSH_BYTES >> 20} MiB write)",
         "parallelism": "replicas, one target per GPU",
     }
@@ -512,7 +512,7 @@ def run_ours(args):
         line = {
             "metric": "walk_steps_per_sec", "value": value, "unit": "walk_steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_all * 1e3 / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic (seeded target C0.R(P5)..R(P1), n=3)", "config": workload_config(c),
             "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e, "clocks": clk,
             "gpu_launches": 2 * args.steps, "time_to_optimal_t_count": tts,
