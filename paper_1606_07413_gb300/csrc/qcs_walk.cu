@@ -230,20 +230,54 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
 {
     using G = Geo<NQ>;
     const Decoded dx{side, qpack};
+    const int h = lv.h;
 
+    // The weights enter the side's first one or two adjoint stages from the
+    // stage tables (fingerprints live mod 2^16, and so do the tables): V
+    // takes R^(q_h)^* then R^(q_{h-1})^*, W takes (R^(q_1)^T)^* then
+    // (R^(q_2)^T)^*.  s0 stages are done by the lookup.
+    int s0 = 0;
+    const uint32_t *tab = nullptr;
+    uint32_t e = 0;
+    if (h >= 1) {
+        const int ba = dx.side == 0 ? h - 1 : 0, bb = dx.side == 0 ? h - 2 : 1;
+        const uint32_t qa = (uint32_t)(dx.qpack >> (8 * ba)) & 0xFFu;
+        if (h >= 2 && lv.T2[dx.side]) {
+            const uint32_t qb = (uint32_t)(dx.qpack >> (8 * bb)) & 0xFFu;
+            tab = lv.T2[dx.side];
+            e = (qa - 1) * lv.xi + (qb - 1);
+            s0 = 2;
+        } else if (lv.T1[dx.side]) {
+            tab = lv.T1[dx.side];
+            e = qa - 1;
+            s0 = 1;
+        }
+    }
     uint32_t ua[G::RPL], ub[G::RPL];
 #pragma unroll
     for (int t = 0; t < G::RPL; t++) {
         const int j = lane + 32 * t;
-        const uint2 u = (G::DIM >= 32 || j < G::DIM) ? sm.U[j] : make_uint2(0, 0);
-        ua[t] = u.x;
-        ub[t] = u.y;
+        if (G::DIM >= 32 || j < G::DIM) {
+            if (tab) {
+                const uint32_t w = __ldg(tab + (size_t)e * G::DIM + j);
+                ua[t] = w & 0xFFFFu;
+                ub[t] = w >> 16;
+            } else {
+                const uint2 u = sm.U[j];
+                ua[t] = u.x;
+                ub[t] = u.y;
+            }
+        } else {
+            ua[t] = ub[t] = 0;
+        }
     }
 
     uint32_t Lc[G::RPL];
     if (dx.side == 0) {
         // V side at exponent K: S R^(q_h)..R^(q_1) with S = multiply by
-        // sqrt2^ev.  Weights go through S^* first, then R^(q_h)^* .. R^(q_1)^*.
+        // sqrt2^ev.  Weights go through S^* and R^(q_h)^* .. R^(q_1)^*; S^*
+        // multiplies every row by the same power of sqrt2, so it commutes
+        // with the stages and is applied after the table's.
         const int ev = lv.ev, sh = ev >> 1;
 #pragma unroll
         for (int t = 0; t < G::RPL; t++) {
@@ -251,14 +285,14 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
             ua[t] = (ev & 1) ? shl32(b, sh) : shl32(a, sh);
             ub[t] = (ev & 1) ? shl32(a, sh + 1) : shl32(b, sh);
         }
-        for (int j = lv.h - 1; j >= 0; j--)
+        for (int j = h - 1 - s0; j >= 0; j--)
             adj_stage<NQ, false>((uint32_t)(dx.qpack >> (8 * j)) & 0xFFu, ua, ub, sm, lane);
 #pragma unroll
         for (int t = 0; t < G::RPL; t++) Lc[t] = ua[t]; // L(V e_Q) = (U~)_a[Q]
     } else {
         // W side: R^(q_1)^T .. R^(q_h)^T [R^(c)^T] C^; weights go through
         // (R^(q_1)^T)^* first, ..., (R^(q_h)^T)^*, then (R^(c)^T)^*.
-        for (int j = 0; j < lv.h; j++)
+        for (int j = s0; j < h; j++)
             adj_stage<NQ, true>((uint32_t)(dx.qpack >> (8 * j)) & 0xFFu, ua, ub, sm, lane);
         if (lv.k & 1) adj_stage<NQ, true>(chunk, ua, ub, sm, lane);
         uint2 *su = sm.xchg;
