@@ -110,6 +110,38 @@ void settle_small_levels(Job &j)
     }
 }
 
+// exhaustive_first: settle the job's levels that qualify by the exhaustive
+// pass alone, before any walk of theirs (returns a status code)
+int settle_exhaustive_levels(qcs_batch *B, Job &j)
+{
+    qcs_problem *P = j.P;
+    while (j.active && j.launches == 0 && P->p.exhaustive_first && exhaustive_eligible(P, j.k)) {
+        bool claw = false;
+        const int rc = certify_level(P, j.k, B->s, &claw);
+        if (rc == QCS_ERR_OVERFLOW) return QCS_OK; // inconclusive: walk the level
+        if (rc != QCS_OK) {
+            std::lock_guard<std::mutex> g(P->mu);
+            P->res.error = rc;
+            j.status = QCS_ERROR;
+            j.active = false;
+            return QCS_OK;
+        }
+        if (claw) {
+            j.status = QCS_FOUND;
+            j.active = false;
+            return QCS_OK;
+        }
+        j.k++;
+        j.version++;
+        j.need_begin = true;
+        if (j.k > P->k_max) {
+            j.status = QCS_BUDGET_EXHAUSTED;
+            j.active = false;
+        }
+    }
+    return QCS_OK;
+}
+
 // start level j.k (or a new function version of it): plan, clear, seed walks
 int begin_level(qcs_batch *B, Job &j, int slot)
 {
@@ -438,6 +470,12 @@ int qcs_batch_round(qcs_batch *B, int *n_active)
     for (size_t slot = 0; slot < B->jobs.size(); slot++) {
         Job &j = B->jobs[slot];
         if (!j.active) continue;
+        if (j.need_begin && (rc = settle_exhaustive_levels(B, j))) return rc;
+        if (!j.active) {
+            publish_status(j);
+            memset(&B->hJobs[slot], 0, sizeof(WalkLaunch));
+            continue;
+        }
         if (j.need_begin && (rc = begin_level(B, j, (int)slot))) return rc;
         active++;
     }

@@ -129,3 +129,24 @@ def test_jobs_join_and_leave_between_rounds(orc, dev):
             batch.poll(j_slow)
         p_slow.close()
         p_fast.close()
+
+
+def test_batch_exhaustive_first_settles_levels_without_walking(orc, dev):
+    cases = [(2, W.seeded_target(2, t, 400 + t)[0], t) for t in (3, 4, 5)]
+    cases.append((3, W.seeded_target(3, 4, 404)[0], 4))
+    probs, jobs = [], []
+    with Q.Batch(small_params(), torch.cuda.Stream()) as batch:
+        for n, gates, kmax in cases:
+            p = Q.Problem.from_circuit(n, gates, kmax, Q.default_params(n, exhaustive_first=1))
+            probs.append(p)
+            jobs.append(batch.add(p))
+        assert run_to_end(batch, 4)
+        for (n, gates, kmax), j in zip(cases, jobs):
+            r = batch.poll(j)
+            C = orc.channel_from_circuit(n, gates)
+            assert r["status_name"] == "found" and orc.verify(C, r["paulis"])
+            assert r["steps"] == 0
+            if n == 2:
+                assert r["t_count"] == orc.mitm_tcount(C, kmax)[0]
+    for p in probs:
+        p.close()
