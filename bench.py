@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-T-count run")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and other-size runs")
+    ap.add_argument("--level-only", choices=["n2_level3", "n4_level7"], default=None,
+                    help="only time that single-target level launch (walk-kernel throughput), print its JSON and exit")
     ap.add_argument("--config3-walk", type=int, default=0, metavar="TABLE_LOG2",
                     help="only time the n = 4 seeded target's search by the collision walk alone with a "
                          "2^TABLE_LOG2-slot table, print its JSON and exit")
@@ -551,6 +553,22 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_level_only(args):
+    import torch
+
+    import paper_1606_07413_gb300 as Q
+    from paper_1606_07413_gb300 import build as B
+    from paper_1606_07413_gb300 import workloads as W
+
+    B.build()
+    stream = torch.cuda.Stream()
+    cfg, k, steps = {"n2_level3": (1, 3, 512), "n4_level7": (3, 7, 16)}[args.level_only]
+    Q.measure_int_peak("imad", 8, 512)
+    peak = Q.measure_int_peak("imad" if cfg == 1 else "idp4a", 8, 4096)[0] * (1 if cfg == 1 else 2)
+    print(json.dumps({args.level_only: level_throughput(Q, W, torch, cfg, k, steps, stream, launches=args.steps,
+                                                        alu_per_s=peak)}))
+
+
 def run_config3_walk(args):
     import torch
 
@@ -569,5 +587,7 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.config3_walk:
         run_config3_walk(a)
+    elif a.level_only:
+        run_level_only(a)
     else:
         run_ours(a)

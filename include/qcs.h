@@ -18,9 +18,17 @@
  *    row-major, two int64 per entry (a, b) meaning (a + b sqrt2)/sqrt2^exp.
  *  - Walk states are L-bit strings in uint64 (L = params.state_bits).  A state
  *    x names side x & 1 (0: V = R(q_h)..R(q_1), 1: W = R(q_1)^T..R(q_h)^T
- *    [R(c)^T] C^ in channel form) and rotations q_j = digit_j + 1, the digits
- *    of (x >> 1) mod xi^h in base xi = 4^n - 1, least significant first
- *    (Sec. 2 mappings mu, nu and h; Sec. 3 chunks c for odd k).
+ *    [R(c)^T] C^ in channel form; Sec. 3 chunks c for odd k) and rotations
+ *    q_1..q_h: rotation j (0-based) reads the l-bit field v at bit 1 + l j,
+ *    l = min(16, (L - 1) / h), and q_{j+1} = floor(v xi / 2^l) + 1 with
+ *    xi = 4^n - 1 (Sec. 2 mapping mu: one code per rotation, concatenated).
+ *  - The next state (Sec. 2 mappings nu and h) hashes the product's Clifford
+ *    coset: per column Q >= 1 the 16-bit fingerprint L_Q = sum_i Ua_i a_iQ +
+ *    Ub_i b_iQ mod 2^16 (weights: SplitMix64 outputs, row 0 weight 0), folded
+ *    to min(L_Q, -L_Q); the folded values sorted ascending, padded with 0xFFFF
+ *    to 4^n, are hashed in position-keyed pairs with the SplitMix64 finaliser
+ *    under a base that mixes the function version, n, k, the chunk and the
+ *    common exponent K, and the sum's finaliser is cut to L bits.
  *
  * Ownership: every pointer argument stays owned by the caller; the library
  * copies what it keeps.  The library owns every device allocation it makes and
