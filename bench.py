@@ -73,7 +73,7 @@ def workload_config(c):
 # DRAM traffic of one k_walks<3> launch of the headline workload, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # kernel source it was taken on (hash of the walk kernel's source files)
-WALK_TRAFFIC = {"bytes_per_launch": 2152448, "source_sha256_16": "87e7454bd79c6dfe"}
+WALK_TRAFFIC = {"bytes_per_launch": 3417088, "source_sha256_16": "88876e41dc894e08"}
 
 
 def walk_source_hash() -> str:
@@ -352,7 +352,11 @@ def run_serving(Q, W, torch, stream, tuned, n_requests=2000, rate=50.0, budget_b
     bp = Q.default_batch_params(max_jobs=512, walks_per_job=tuned["walks_per_job"],
                                 steps_per_round=tuned["steps_per_round"], table_log2=18,
                                 queue_capacity=tuned["queue_capacity"])
-    with serve.Server(bp, budget_bytes, stream=stream, deadline_s=deadline_s) as srv:
+    # serving policy: levels of at most 2^26 V + W points are settled by the
+    # exact pass first, larger ones are walked
+    policy = {"theta_min_bits": tuned["theta_min_bits"], "exhaustive_first": 1, "exhaustive_log2": 26}
+    with serve.Server(bp, budget_bytes, stream=stream, deadline_s=deadline_s,
+                      params_for=lambda n: Q.default_params(n, **policy)) as srv:
         rids, wall = serve.replay_stream(srv, times, targets, time_limit_s=float(times[-1]) + drain_s)
         polls = [srv.poll(r) for r in rids]
         fevals, rounds, peak = srv.fevals, srv.rounds, srv.peak_used
@@ -366,6 +370,9 @@ def run_serving(Q, W, torch, stream, tuned, n_requests=2000, rate=50.0, budget_b
         "answered_p50_s": q(0.5), "answered_p99_s": q(0.99), "status_counts": status,
         "fevals_per_s": fevals / wall, "wall_s": wall, "rounds": rounds, "memory_budget_bytes": budget_bytes,
         "peak_admitted_bytes": peak, "deadline_s": deadline_s,
+        "policy": dict(policy, note="exhaustive pass first on levels of at most 2^26 V + W points, the walk "
+                                    "above; the pass's key table (up to 512 MiB) is allocated for its call and "
+                                    "is not part of the admitted bytes"),
     }
 
 

@@ -34,8 +34,11 @@ class Request:
 
 class Server:
     def __init__(self, batch_params: Q.BatchParams, memory_budget: int, stream=None, deadline_s: float | None = None,
-                 clock=time.perf_counter):
+                 clock=time.perf_counter, params_for=None):
+        """params_for(n) gives the search parameters of an n-qubit request
+        that comes without its own (default: Q.default_params(n))."""
         self.batch = Q.Batch(batch_params, stream)
+        self.params_for = params_for or Q.default_params
         self.slots = batch_params.max_jobs
         self.budget, self.used = int(memory_budget), 0
         self.deadline = deadline_s
@@ -57,7 +60,7 @@ class Server:
         self.next_id += 1
         r = Request(rid, n, np.asarray(gates, np.int32), k_max, params,
                     self.clock() if t_arrival is None else t_arrival)
-        r.future = self.pool.submit(Q.Problem.from_circuit, n, r.gates, k_max, params or Q.default_params(n))
+        r.future = self.pool.submit(Q.Problem.from_circuit, n, r.gates, k_max, params or self.params_for(n))
         self.requests[rid] = r
         self.waiting.append(r)
         return rid
