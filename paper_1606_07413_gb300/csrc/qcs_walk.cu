@@ -48,7 +48,6 @@ namespace {
 #endif
 constexpr int kWarps = QCS_WARPS;
 constexpr int kGemvUnroll = QCS_GEMV_UNROLL;
-constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr uint32_t kMaxRewalkLen = 1u << 20; // longer trails are reported as no merge
 
 __device__ __forceinline__ uint64_t smix(uint64_t z)
@@ -62,15 +61,20 @@ template <int NQ>
 struct Geo {
     static constexpr int DIM = 1 << (2 * NQ);            // 4^n rows and columns
     static constexpr int D = DIM - 1;                    // non-identity Paulis
-    static constexpr int RPL = DIM >= 32 ? DIM / 32 : 1; // rows (and columns) per lane
-    static constexpr int SLOTS = RPL * 32;               // width of the fingerprint sort
+    // one walk is evaluated by LPW consecutive lanes of a warp (4^n lanes for
+    // n <= 2, the whole warp above), GROUPS walks per warp
+    static constexpr int LPW = DIM < 32 ? DIM : 32;
+    static constexpr int GROUPS = 32 / LPW;
+    static constexpr int RPL = DIM / LPW;                // rows (and columns) per lane
+    static constexpr int SLOTS = RPL * LPW;              // width of the fingerprint sort
     // n <= 3: C^ staged whole, as byte quads (8 KB at n = 3) or else as low
     // words (32 KB); n = 4: byte quads (128 KB) when every entry fits, else
     // the low words are read through L2
     static constexpr bool C_SMEM = NQ <= 3;
     static constexpr bool CQ_SMEM = NQ == 4;
-    static constexpr int WARPS = NQ == 4 ? 16 : kWarps;  // walks (warps) per CTA
+    static constexpr int WARPS = NQ == 4 ? 16 : kWarps;  // warps per CTA
     static constexpr int THREADS = WARPS * 32;
+    static constexpr int WALKS = WARPS * GROUPS;         // walks (lane groups) per CTA
     static constexpr int MIN_BLOCKS = NQ == 3 ? QCS_MIN_BLOCKS3 : 1;
     static constexpr int QUAD_UNROLL = NQ == 4 ? QCS_QUAD_UNROLL4 : QCS_QUAD_UNROLL3;
     static constexpr int COEF_WORDS = DIM * 2 * RPL;     // rotation coefficient bits
@@ -81,7 +85,7 @@ struct Geo {
         off_C + (C_SMEM ? sizeof(uint2) * DIM * DIM : 0) + (CQ_SMEM ? 2 * DIM * DIM : 0);
     static constexpr size_t off_base = off_coef + sizeof(uint32_t) * COEF_WORDS;
     static constexpr size_t off_xchg = off_base + sizeof(uint64_t) * MAX_CHUNKS;
-    static constexpr size_t smem_bytes = off_xchg + sizeof(uint2) * WARPS * DIM;
+    static constexpr size_t smem_bytes = off_xchg + sizeof(uint2) * WALKS * DIM;
 };
 
 // Shared-memory views of one CTA (C may point to global memory for n = 4).
@@ -92,14 +96,37 @@ struct Smem {
     const uint4 *Cq;  // n >= 3: C^ as byte quads (LevelCtx::Cq layout), or null
     uint32_t *coef;
     uint64_t *base;
-    uint2 *xchg; // this warp's exchange buffer
+    uint2 *xchg; // this lane group's exchange buffer
 };
 
 __device__ __forceinline__ uint32_t shl32(uint32_t v, int s) { return s >= 32 ? 0u : v << s; }
 
-// One adjoint butterfly stage on the weight vector held by the warp (row
-// j = lane + 32 t in registers ua/ub; the warp's exchange buffer carries the
-// partner rows).  The forward R^(p) maps a row that commutes with p to sqrt2
+// The lanes evaluating one walk: sub is the lane's index in its group of
+// LPW lanes, mask the group's lanes (every shuffle, reduction and warp
+// barrier names only the group, so the groups of a warp run independently).
+struct Lanes {
+    int sub;
+    unsigned mask;
+};
+
+template <int NQ>
+__device__ __forceinline__ Lanes thread_lanes()
+{
+    constexpr int L = Geo<NQ>::LPW;
+    const int lane = threadIdx.x & 31, sub = lane % L;
+    return Lanes{sub, (0xFFFFFFFFu >> (32 - L)) << (lane - sub)};
+}
+
+// index of the thread's lane group in its CTA
+template <int NQ>
+__device__ __forceinline__ int group_in_cta()
+{
+    return (int)(threadIdx.x >> 5) * Geo<NQ>::GROUPS + (int)(threadIdx.x & 31) / Geo<NQ>::LPW;
+}
+
+// One adjoint butterfly stage on the weight vector held by the lane group
+// (row j = sub + LPW t in registers ua/ub; the group's exchange buffer carries
+// the partner rows).  The forward R^(p) maps a row that commutes with p to sqrt2
 // times itself, (a, b) -> (2b, a), and an anticommuting row i to
 // M_i + s(p, i^p) M_{i^p}; R^(p)^T uses s(p, i) instead, and
 // s(p, i^p) = -s(p, i).  The adjoints are (ua, ub) -> (ub, 2 ua) on commuting
@@ -108,16 +135,13 @@ __device__ __forceinline__ uint32_t shl32(uint32_t v, int s) { return s >= 32 ? 
 // per-Pauli bit masks staged in shared memory.
 template <int NQ, bool ADJ_OF_TRANSPOSE>
 __device__ __forceinline__ void adj_stage(uint32_t p, uint32_t (&ua)[Geo<NQ>::RPL],
-                                          uint32_t (&ub)[Geo<NQ>::RPL], const Smem<NQ> &sm, int lane)
+                                          uint32_t (&ub)[Geo<NQ>::RPL], const Smem<NQ> &sm, Lanes g)
 {
     using G = Geo<NQ>;
     uint2 *su = sm.xchg;
 #pragma unroll
-    for (int t = 0; t < G::RPL; t++) {
-        const int j = lane + 32 * t;
-        if (G::DIM >= 32 || j < G::DIM) su[j] = make_uint2(ua[t], ub[t]);
-    }
-    __syncwarp();
+    for (int t = 0; t < G::RPL; t++) su[g.sub + G::LPW * t] = make_uint2(ua[t], ub[t]);
+    __syncwarp(g.mask);
     const uint32_t *cwp = sm.coef + p * (2 * G::RPL);
     uint32_t cw[2 * G::RPL];
     if (G::RPL == 2) {
@@ -129,20 +153,18 @@ __device__ __forceinline__ void adj_stage(uint32_t p, uint32_t (&ua)[Geo<NQ>::RP
     }
 #pragma unroll
     for (int t = 0; t < G::RPL; t++) {
-        const int j = lane + 32 * t;
-        if (G::DIM >= 32 || j < G::DIM) {
-            const bool anti = (cw[t] >> lane) & 1u;
-            const bool plus = (cw[G::RPL + t] >> lane) & 1u;
-            const uint2 v = su[j ^ (int)p];
-            const bool add = (plus != ADJ_OF_TRANSPOSE);
-            const uint32_t na = add ? ua[t] + v.x : ua[t] - v.x;
-            const uint32_t nb = add ? ub[t] + v.y : ub[t] - v.y;
-            const uint32_t ca = ub[t], cb = ua[t] << 1;
-            ua[t] = anti ? na : ca;
-            ub[t] = anti ? nb : cb;
-        }
+        const int j = g.sub + G::LPW * t;
+        const bool anti = (cw[t] >> g.sub) & 1u;
+        const bool plus = (cw[G::RPL + t] >> g.sub) & 1u;
+        const uint2 v = su[j ^ (int)p];
+        const bool add = (plus != ADJ_OF_TRANSPOSE);
+        const uint32_t na = add ? ua[t] + v.x : ua[t] - v.x;
+        const uint32_t nb = add ? ub[t] + v.y : ub[t] - v.y;
+        const uint32_t ca = ub[t], cb = ua[t] << 1;
+        ua[t] = anti ? na : ca;
+        ub[t] = anti ? nb : cb;
     }
-    __syncwarp();
+    __syncwarp(g.mask);
 }
 
 // d = c + sum_j a_j b_j over the four bytes, a unsigned and b signed (mod 2^32)
@@ -162,8 +184,9 @@ __device__ __forceinline__ uint32_t dp4a_us(uint32_t a, uint32_t b, uint32_t c)
 // (a plane 0, a plane 1, b plane 0, b plane 1), each word holding that byte
 // of the four rows' weights.
 template <int NQ>
-__device__ __forceinline__ void weight_planes(uint2 *su, int lane)
+__device__ __forceinline__ void weight_planes(uint2 *su, Lanes g)
 {
+    const int lane = g.sub; // n >= 3: the group is the whole warp
     using G = Geo<NQ>;
     constexpr int JOBS = G::DIM >= 64 ? G::DIM / 64 : 1; // 2 parts x DIM/4 quads over 32 lanes
     const uint4 *s4 = reinterpret_cast<const uint4 *>(su);
@@ -177,11 +200,11 @@ __device__ __forceinline__ void weight_planes(uint2 *su, int lane)
         const uint32_t lo01 = __byte_perm(u0, u1, 0x5140), lo23 = __byte_perm(u2, u3, 0x5140);
         pl[r] = make_uint2(__byte_perm(lo01, lo23, 0x5410), __byte_perm(lo01, lo23, 0x7632));
     }
-    __syncwarp();
+    __syncwarp(g.mask);
     uint2 *w2 = su;
 #pragma unroll
     for (int r = 0; r < JOBS; r++) w2[lane + 32 * r] = pl[r];
-    __syncwarp();
+    __syncwarp(g.mask);
 }
 
 // packed 16-bit minimum and maximum of both halves
@@ -223,13 +246,14 @@ __device__ __forceinline__ Decoded decode(uint64_t x, const LevelCtx &lv)
 // nu and h of one decoded point: the exact product of side `side` (0: V,
 // 1: W) for the rotations in qpack (and the chunk, odd k), its fingerprint
 // canonical form and the position-keyed hash with hash base `base`, as a
-// full 64-bit value.  All 32 lanes call it with the same point.
+// full 64-bit value.  All lanes of the group call it with the same point.
 template <int NQ>
 __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_t base, const LevelCtx &lv,
-                               const Smem<NQ> &sm, int lane)
+                               const Smem<NQ> &sm, Lanes g)
 {
     using G = Geo<NQ>;
     const Decoded dx{side, qpack};
+    const int lane = g.sub;
     const int h = lv.h;
 
     // The weights enter the side's first one or two adjoint stages from the
@@ -256,19 +280,15 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
     uint32_t ua[G::RPL], ub[G::RPL];
 #pragma unroll
     for (int t = 0; t < G::RPL; t++) {
-        const int j = lane + 32 * t;
-        if (G::DIM >= 32 || j < G::DIM) {
-            if (tab) {
-                const uint32_t w = __ldg(tab + (size_t)e * G::DIM + j);
-                ua[t] = w & 0xFFFFu;
-                ub[t] = w >> 16;
-            } else {
-                const uint2 u = sm.U[j];
-                ua[t] = u.x;
-                ub[t] = u.y;
-            }
+        const int j = lane + G::LPW * t;
+        if (tab) {
+            const uint32_t w = __ldg(tab + (size_t)e * G::DIM + j);
+            ua[t] = w & 0xFFFFu;
+            ub[t] = w >> 16;
         } else {
-            ua[t] = ub[t] = 0;
+            const uint2 u = sm.U[j];
+            ua[t] = u.x;
+            ub[t] = u.y;
         }
     }
 
@@ -286,29 +306,28 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
             ub[t] = (ev & 1) ? shl32(a, sh + 1) : shl32(b, sh);
         }
         for (int j = h - 1 - s0; j >= 0; j--)
-            adj_stage<NQ, false>((uint32_t)(dx.qpack >> (8 * j)) & 0xFFu, ua, ub, sm, lane);
+            adj_stage<NQ, false>((uint32_t)(dx.qpack >> (8 * j)) & 0xFFu, ua, ub, sm, g);
 #pragma unroll
         for (int t = 0; t < G::RPL; t++) Lc[t] = ua[t]; // L(V e_Q) = (U~)_a[Q]
     } else {
         // W side: R^(q_1)^T .. R^(q_h)^T [R^(c)^T] C^; weights go through
         // (R^(q_1)^T)^* first, ..., (R^(q_h)^T)^*, then (R^(c)^T)^*.
         for (int j = s0; j < h; j++)
-            adj_stage<NQ, true>((uint32_t)(dx.qpack >> (8 * j)) & 0xFFu, ua, ub, sm, lane);
-        if (lv.k & 1) adj_stage<NQ, true>(chunk, ua, ub, sm, lane);
+            adj_stage<NQ, true>((uint32_t)(dx.qpack >> (8 * j)) & 0xFFu, ua, ub, sm, g);
+        if (lv.k & 1) adj_stage<NQ, true>(chunk, ua, ub, sm, g);
         uint2 *su = sm.xchg;
 #pragma unroll
         for (int t = 0; t < G::RPL; t++) {
-            const int j = lane + 32 * t;
-            if (G::DIM >= 32 || j < G::DIM) su[j] = make_uint2(ua[t], ub[t]);
+            su[lane + G::LPW * t] = make_uint2(ua[t], ub[t]);
             Lc[t] = 0;
         }
-        __syncwarp();
+        __syncwarp(g.mask);
         // L(W e_Q) = sum_i U~_a[i] C_a[i][Q] + U~_b[i] C_b[i][Q]; row 0 has
         // zero weight and C[0][Q] = 0 for Q >= 1, so all rows may be summed.
         if (G::DIM >= 64 && sm.Cq) {
             // byte-plane contraction: acc[t][k] = sum over rows of byte k of
             // the weights times C^ (exact byte products), recombined below
-            weight_planes<NQ>(su, lane);
+            weight_planes<NQ>(su, g);
             const uint4 *w4 = reinterpret_cast<const uint4 *>(su);
             constexpr int CW = G::RPL / 2;
             uint32_t acc[G::RPL][2];
@@ -319,7 +338,7 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
                 const uint4 w = w4[q]; // a plane 0, a plane 1, b plane 0, b plane 1
 #pragma unroll
                 for (int j = 0; j < CW; j++) {
-                    const uint4 c = sm.Cq[(q * CW + j) * 32 + lane];
+                    const uint4 c = sm.Cq[(q * CW + j) * G::LPW + lane];
                     acc[2 * j][0] = dp4a_us(w.x, c.x, acc[2 * j][0]);
                     acc[2 * j][0] = dp4a_us(w.z, c.y, acc[2 * j][0]);
                     acc[2 * j][1] = dp4a_us(w.y, c.x, acc[2 * j][1]);
@@ -347,23 +366,23 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
                     Lc[t + 1] += uu.x * a.z + uu.y * a.w + uu.z * b.z + uu.w * b.w;
                 }
             }
-        } else if (lane < G::DIM) {
+        } else {
             for (int i = 0; i < G::DIM; i++) {
                 const uint2 u = su[i], c = sm.C[i * G::DIM + lane];
                 Lc[0] += u.x * c.x + u.y * c.y;
             }
         }
-        __syncwarp();
+        __syncwarp(g.mask);
     }
 
     // sign-invariant 16-bit column fingerprints; column 0 (the identity) and
-    // padding lanes sort last as 0xFFFF (every phi is at most 2^15).  Sort
-    // element e = RPL lane + t starts with this lane's column lane + 32 t
+    // padding sorts last as 0xFFFF (every phi is at most 2^15).  Sort
+    // element e = RPL sub + t starts with this lane's column sub + LPW t
     // (where the keys start does not matter to a sort).
     uint32_t key[G::RPL];
 #pragma unroll
     for (int t = 0; t < G::RPL; t++) {
-        const int Q = lane + 32 * t;
+        const int Q = lane + G::LPW * t;
         const uint32_t l = Lc[t] & 0xFFFFu, nl = (0u - l) & 0xFFFFu;
         key[t] = (Q >= 1 && Q <= G::D) ? min(l, nl) : 0xFFFFu;
     }
@@ -405,7 +424,7 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
                     const bool keep_min = ((eb & stride) == 0) == ((eb & size) == 0);
 #pragma unroll
                     for (int u = 0; u < NW; u++) {
-                        const uint32_t o = __shfl_xor_sync(kFull, kw[u], lstride);
+                        const uint32_t o = __shfl_xor_sync(g.mask, kw[u], lstride);
                         kw[u] = keep_min ? min_u16x2(kw[u], o) : max_u16x2(kw[u], o);
                     }
                 }
@@ -415,37 +434,37 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
 #pragma unroll
         for (int u = 0; u < NW; u++) acc += smix(base ^ (((uint64_t)(NW * lane + u) << 32) | kw[u]));
     } else {
-        // one key per lane (n <= 2): bitonic sort across the 32 lanes
+        // one key per lane (n <= 2): bitonic sort across the group's 4^n lanes
 #pragma unroll
         for (int size = 2; size <= G::SLOTS; size <<= 1) {
 #pragma unroll
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
                 const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
-                const uint32_t o = __shfl_xor_sync(kFull, key[0], stride);
+                const uint32_t o = __shfl_xor_sync(g.mask, key[0], stride);
                 key[0] = ((key[0] < o) == keep_min) ? key[0] : o;
             }
         }
         // pair p = lane / 2 packs elements 2p and 2p + 1, for the 4^n / 2 pairs
-        const uint32_t nxt = __shfl_down_sync(kFull, key[0], 1);
-        if ((lane & 1) == 0 && lane < G::DIM) acc = smix(base ^ (((uint64_t)(lane >> 1) << 32) | key[0] | (nxt << 16)));
+        const uint32_t nxt = __shfl_down_sync(g.mask, key[0], 1, G::LPW);
+        if ((lane & 1) == 0) acc = smix(base ^ (((uint64_t)(lane >> 1) << 32) | key[0] | (nxt << 16)));
     }
     // warp sum mod 2^64 from three 32-bit reductions: the high words (mod
     // 2^32) and the two 16-bit halves of the low words (no overflow: 32 terms)
     const uint32_t lo = (uint32_t)acc, hi = (uint32_t)(acc >> 32);
-    const uint32_t s_hi = __reduce_add_sync(kFull, hi);
-    const uint32_t s_l0 = __reduce_add_sync(kFull, lo & 0xFFFFu);
-    const uint32_t s_l1 = __reduce_add_sync(kFull, lo >> 16);
+    const uint32_t s_hi = __reduce_add_sync(g.mask, hi);
+    const uint32_t s_l0 = __reduce_add_sync(g.mask, lo & 0xFFFFu);
+    const uint32_t s_l1 = __reduce_add_sync(g.mask, lo >> 16);
     acc = ((uint64_t)s_hi << 32) + ((uint64_t)s_l1 << 16) + (uint64_t)s_l0;
     return smix(acc);
 }
 
-// f(x): all 32 lanes call it with the same x; every lane gets the result.
+// f(x): all lanes of the group call it with the same x; each gets the result.
 template <int NQ>
 __device__ __forceinline__ uint64_t warp_step(uint64_t x, uint32_t chunk, const LevelCtx &lv, const Smem<NQ> &sm,
-                                              int lane)
+                                              Lanes g)
 {
     const Decoded dx = decode(x, lv);
-    return coset_hash<NQ>(dx.side, dx.qpack, chunk, sm.base[chunk], lv, sm, lane) & lv.maskL;
+    return coset_hash<NQ>(dx.side, dx.qpack, chunk, sm.base[chunk], lv, sm, g) & lv.maskL;
 }
 
 // Stage the weights, the rotation coefficients, the per-chunk hash bases and
@@ -459,7 +478,7 @@ __device__ __forceinline__ Smem<NQ> stage(const LevelCtx &lv, unsigned char *raw
     uint2 *sC = reinterpret_cast<uint2 *>(raw + G::off_C);
     sm.coef = reinterpret_cast<uint32_t *>(raw + G::off_coef);
     sm.base = reinterpret_cast<uint64_t *>(raw + G::off_base);
-    sm.xchg = reinterpret_cast<uint2 *>(raw + G::off_xchg) + (threadIdx.x >> 5) * G::DIM;
+    sm.xchg = reinterpret_cast<uint2 *>(raw + G::off_xchg) + group_in_cta<NQ>() * G::DIM;
     for (int i = threadIdx.x; i < G::DIM; i += blockDim.x) sm.U[i] = lv.U[i];
     for (int i = threadIdx.x; i < G::COEF_WORDS; i += blockDim.x) sm.coef[i] = lv.coef[i];
     // base(chunk) = smix(smix(seed_H ^ version) ^ (n | k << 8 | chunk << 16 | K << 32))
@@ -500,10 +519,11 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_walk_step(LevelCtx lv, uin
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Smem<NQ> sm = stage<NQ>(lv, smem_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (size_t i = (size_t)blockIdx.x * Geo<NQ>::WARPS + warp; i < count; i += (size_t)gridDim.x * Geo<NQ>::WARPS) {
-        const uint64_t y = warp_step<NQ>(in[i], chunk, lv, sm, lane);
-        if (lane == 0) {
+    const Lanes g = thread_lanes<NQ>();
+    for (size_t i = (size_t)blockIdx.x * Geo<NQ>::WALKS + group_in_cta<NQ>(); i < count;
+         i += (size_t)gridDim.x * Geo<NQ>::WALKS) {
+        const uint64_t y = warp_step<NQ>(in[i], chunk, lv, sm, g);
+        if (g.sub == 0) {
             out[i] = y;
             if (is_dp) is_dp[i] = (uint8_t)((y >> lv.dshift) == 0);
         }
@@ -541,14 +561,14 @@ __device__ __forceinline__ void new_trail(WalkState &st, uint32_t walk, const Le
     st.chunk = trail_chunk(lv, st.start);
 }
 
-// per-warp tallies, added to the job's counters by lane 0 (flush_tally)
+// per-walk-group tallies, added to the job's counters by the group's first lane
 struct Tally {
     unsigned long long steps = 0, w = 0, dp = 0, ab = 0, evicted = 0, duplicate = 0, pairs = 0;
 };
 
-__device__ __forceinline__ void flush_tally(unsigned long long *counters, Tally &t, int lane)
+__device__ __forceinline__ void flush_tally(unsigned long long *counters, Tally &t, Lanes g)
 {
-    if (lane == 0) {
+    if (g.sub == 0) {
         if (t.steps) atomicAdd(&counters[C_STEPS], t.steps);
         if (t.w) atomicAdd(&counters[C_WSTEPS], t.w);
         if (t.dp) atomicAdd(&counters[C_DPS], t.dp);
@@ -593,22 +613,22 @@ __device__ void dp_insert(const WL &w, uint64_t dp, uint64_t ref, Tally &c)
 
 // Advance one walk by w.steps steps (Sec. 3 trails): a trail that reaches a
 // distinguished point is stored and a new one starts; a trail longer than
-// the cut-off is abandoned.  All lanes of the warp call it.
+// the cut-off is abandoned.  All lanes of the group call it.
 template <int NQ, typename WL>
-__device__ __forceinline__ void walk_one(const WL &w, const Smem<NQ> &sm, int walk, int lane, Tally &t)
+__device__ __forceinline__ void walk_one(const WL &w, const Smem<NQ> &sm, int walk, Lanes g, Tally &t)
 {
     WalkState st = w.walks[walk];
     const uint32_t steps = w.steps, max_len = w.max_len;
     const int dshift = w.lv.dshift;
     for (uint32_t s = 0; s < steps; s++) {
-        const uint64_t y = warp_step<NQ>(st.cur, st.chunk, w.lv, sm, lane);
+        const uint64_t y = warp_step<NQ>(st.cur, st.chunk, w.lv, sm, g);
         t.steps++;
         t.w += st.cur & 1;
         st.len++;
         if ((y >> dshift) == 0) {
             t.dp++;
-            if (lane == 0) dp_insert(w, y, make_ref((uint32_t)walk, st.seq, st.len), t);
-            __syncwarp();
+            if (g.sub == 0) dp_insert(w, y, make_ref((uint32_t)walk, st.seq, st.len), t);
+            __syncwarp(g.mask);
             new_trail(st, (uint32_t)walk, w.lv);
         } else if (st.len >= max_len) {
             t.ab++;
@@ -617,7 +637,7 @@ __device__ __forceinline__ void walk_one(const WL &w, const Smem<NQ> &sm, int wa
             st.cur = y;
         }
     }
-    if (lane == 0) w.walks[walk] = st;
+    if (g.sub == 0) w.walks[walk] = st;
 }
 
 template <int NQ>
@@ -625,24 +645,25 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS, Geo<NQ>::MIN_BLOCKS) k_walks
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Smem<NQ> sm = stage<NQ>(w.lv, smem_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Lanes g = thread_lanes<NQ>();
     Tally t;
-    for (int walk = blockIdx.x * Geo<NQ>::WARPS + warp; walk < w.n_walks; walk += gridDim.x * Geo<NQ>::WARPS)
-        walk_one<NQ>(w, sm, walk, lane, t);
-    flush_tally(w.counters, t, lane);
+    for (int walk = blockIdx.x * Geo<NQ>::WALKS + group_in_cta<NQ>(); walk < w.n_walks;
+         walk += gridDim.x * Geo<NQ>::WALKS)
+        walk_one<NQ>(w, sm, walk, g, t);
+    flush_tally(w.counters, t, g);
 }
 
 // Many jobs (targets, each at its own level) in one persistent launch: the
 // CTA takes a contiguous range of tasks (job, first walk) of this qubit
-// count, restages the job's data when the job changes, and each warp walks
-// one of the task's WARPS walks.  The job's launch record is copied to
+// count, restages the job's data when the job changes, and each lane group
+// walks one of the task's WALKS walks.  The job's launch record is copied to
 // shared memory.
 template <int NQ>
 __global__ void __launch_bounds__(Geo<NQ>::THREADS, Geo<NQ>::MIN_BLOCKS) k_walks_batch(BatchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ WalkLaunch sw;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Lanes g = thread_lanes<NQ>();
     const uint32_t nt = *a.n_tasks;
     int cur = -1;
     Smem<NQ> sm;
@@ -654,17 +675,17 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS, Geo<NQ>::MIN_BLOCKS) k_walks
         const int job = (int)a.tasks[2 * task];
         const int first = (int)a.tasks[2 * task + 1];
         if (job != cur) {
-            if (cur >= 0) flush_tally(sw.counters, t, lane);
+            if (cur >= 0) flush_tally(sw.counters, t, g);
             __syncthreads(); // every warp is done with the previous job's data
             if (threadIdx.x == 0) sw = a.jobs[job];
             __syncthreads();
             sm = stage<NQ>(sw.lv, smem_raw);
             cur = job;
         }
-        const int walk = first + warp;
-        if (walk < sw.n_walks) walk_one<NQ>(sw, sm, walk, lane, t);
+        const int walk = first + group_in_cta<NQ>();
+        if (walk < sw.n_walks) walk_one<NQ>(sw, sm, walk, g, t);
     }
-    if (cur >= 0) flush_tally(sw.counters, t, lane);
+    if (cur >= 0) flush_tally(sw.counters, t, g);
 }
 
 __global__ void k_init_walks(WalkLaunch w)
@@ -683,7 +704,7 @@ __global__ void k_init_walks(WalkLaunch w)
 // maximum trail length, so both loops end.
 template <int NQ>
 __device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa, uint32_t la, uint64_t sb,
-                                uint32_t lb, const Smem<NQ> &sm, int lane, unsigned long long *fevals = nullptr)
+                                uint32_t lb, const Smem<NQ> &sm, Lanes g, unsigned long long *fevals = nullptr)
 {
     RewalkOut r;
     unsigned long long nf = 0;
@@ -699,7 +720,7 @@ __device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa,
         uint32_t tl = la; la = lb; lb = tl;
     }
     uint64_t a = sa, b = sb;
-    for (uint32_t s = 0; s < la - lb; s++) a = warp_step<NQ>(a, chunk, lv, sm, lane);
+    for (uint32_t s = 0; s < la - lb; s++) a = warp_step<NQ>(a, chunk, lv, sm, g);
     nf += la - lb;
     if (fevals) *fevals += nf;
     if (a == b) {
@@ -708,8 +729,8 @@ __device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa,
         return r;
     }
     for (uint32_t s = 0; s < lb; s++) {
-        const uint64_t fa = warp_step<NQ>(a, chunk, lv, sm, lane);
-        const uint64_t fb = warp_step<NQ>(b, chunk, lv, sm, lane);
+        const uint64_t fa = warp_step<NQ>(a, chunk, lv, sm, g);
+        const uint64_t fb = warp_step<NQ>(b, chunk, lv, sm, g);
         if (fevals) *fevals += 2;
         if (fa == fb) {
             const Decoded da = decode(a, lv), db = decode(b, lv);
@@ -729,10 +750,10 @@ __device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa,
 }
 
 // Re-walk this CTA's share of one job's queued merges; classes are counted
-// per warp and claw candidates appended to the job's candidate list.
+// per lane group and claw candidates appended to the job's candidate list.
 template <int NQ, typename WL>
 __device__ __forceinline__ void rewalk_job(const WL &w, const Smem<NQ> &sm, uint32_t p_begin, uint32_t p_end,
-                                           uint32_t p_stride, int lane)
+                                           uint32_t p_stride, Lanes g)
 {
     unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0; // per class, in registers
     unsigned long long fev = 0;
@@ -747,7 +768,7 @@ __device__ __forceinline__ void rewalk_job(const WL &w, const Smem<NQ> &sm, uint
         if (ca != cb) { // the same value reached in two chunks' functions: no merge
             r.cls = 5;
         } else {
-            r = rewalk_one<NQ>(w.lv, ca, xa, la, xb, lb, sm, lane, &fev);
+            r = rewalk_one<NQ>(w.lv, ca, xa, la, xb, lb, sm, g, &fev);
         }
         c0 += r.cls == 0;
         c1 += r.cls == 1;
@@ -755,7 +776,7 @@ __device__ __forceinline__ void rewalk_job(const WL &w, const Smem<NQ> &sm, uint
         c3 += r.cls == 3;
         c4 += r.cls == 4;
         c5 += r.cls == 5;
-        if (r.cls == 3 && lane == 0) {
+        if (r.cls == 3 && g.sub == 0) {
             const uint32_t idx = atomicAdd(w.ccount, 1u);
             if (idx < w.ccap) {
                 Cand c;
@@ -767,7 +788,7 @@ __device__ __forceinline__ void rewalk_job(const WL &w, const Smem<NQ> &sm, uint
             }
         }
     }
-    if (lane == 0) {
+    if (g.sub == 0) {
         const unsigned long long cc[6] = {c0, c1, c2, c3, c4, c5};
 #pragma unroll
         for (int c = 0; c < 6; c++)
@@ -782,10 +803,10 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_rewalk_pairs(WalkLaunch w)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t cnt = min(*w.qhead, w.qcap);
-    if (cnt <= blockIdx.x * Geo<NQ>::WARPS) return; // no pair for this CTA (uniform)
+    if (cnt <= blockIdx.x * Geo<NQ>::WALKS) return; // no pair for this CTA (uniform)
     const Smem<NQ> sm = stage<NQ>(w.lv, smem_raw);
-    rewalk_job<NQ>(w, sm, blockIdx.x * Geo<NQ>::WARPS + (threadIdx.x >> 5), cnt, gridDim.x * Geo<NQ>::WARPS,
-                   threadIdx.x & 31);
+    rewalk_job<NQ>(w, sm, blockIdx.x * Geo<NQ>::WALKS + group_in_cta<NQ>(), cnt, gridDim.x * Geo<NQ>::WALKS,
+                   thread_lanes<NQ>());
 }
 
 // The batched re-walk: the queued merges of all jobs of this qubit count
@@ -803,7 +824,7 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_rewalk_batch(BatchArgs a)
         total += min(*w.qhead, w.qcap);
     }
     const uint64_t lo = total * blockIdx.x / gridDim.x, hi = total * (blockIdx.x + 1) / gridDim.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Lanes g = thread_lanes<NQ>();
     uint64_t base = 0;
     for (uint32_t j = 0; j < nj && base < hi; j++) {
         const int job = (int)a.job_ids[j];
@@ -818,7 +839,7 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_rewalk_batch(BatchArgs a)
         if (threadIdx.x == 0) sw = a.jobs[job];
         __syncthreads();
         const Smem<NQ> sm = stage<NQ>(sw.lv, smem_raw);
-        rewalk_job<NQ>(sw, sm, p_begin + warp, p_end, Geo<NQ>::WARPS, lane);
+        rewalk_job<NQ>(sw, sm, p_begin + group_in_cta<NQ>(), p_end, Geo<NQ>::WALKS, g);
     }
 }
 
@@ -830,10 +851,11 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_rewalk_arrays(LevelCtx lv,
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Smem<NQ> sm = stage<NQ>(lv, smem_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (size_t p = (size_t)blockIdx.x * Geo<NQ>::WARPS + warp; p < count; p += (size_t)gridDim.x * Geo<NQ>::WARPS) {
-        const RewalkOut r = rewalk_one<NQ>(lv, chunk, sa[p], la[p], sb[p], lb[p], sm, lane);
-        if (lane == 0) {
+    const Lanes g = thread_lanes<NQ>();
+    for (size_t p = (size_t)blockIdx.x * Geo<NQ>::WALKS + group_in_cta<NQ>(); p < count;
+         p += (size_t)gridDim.x * Geo<NQ>::WALKS) {
+        const RewalkOut r = rewalk_one<NQ>(lv, chunk, sa[p], la[p], sb[p], lb[p], sm, g);
+        if (g.sub == 0) {
             cls[p] = r.cls;
             ab[2 * p] = r.a;
             ab[2 * p + 1] = r.b;
@@ -841,16 +863,16 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_rewalk_arrays(LevelCtx lv,
     }
 }
 
-// Exhaustive level pass (CertArgs): one warp per point, grid-stride.
+// Exhaustive level pass (CertArgs): one lane group per point, grid-stride.
 template <int NQ>
 __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_certify(CertArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Smem<NQ> sm = stage<NQ>(a.lv, smem_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Lanes g = thread_lanes<NQ>();
     const uint32_t xi = a.lv.xi;
-    for (uint64_t i = (uint64_t)blockIdx.x * Geo<NQ>::WARPS + warp; i < a.count;
-         i += (uint64_t)gridDim.x * Geo<NQ>::WARPS) {
+    for (uint64_t i = (uint64_t)blockIdx.x * Geo<NQ>::WALKS + group_in_cta<NQ>(); i < a.count;
+         i += (uint64_t)gridDim.x * Geo<NQ>::WALKS) {
         const uint64_t idx = a.first + i;
         uint64_t tuple = idx;
         uint32_t chunk = 0;
@@ -863,9 +885,9 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_certify(CertArgs a)
             qpack |= (uint64_t)(tuple % xi + 1) << (8 * j);
             tuple /= xi;
         }
-        uint64_t key = coset_hash<NQ>(a.side, qpack, chunk, a.base, a.lv, sm, lane);
+        uint64_t key = coset_hash<NQ>(a.side, qpack, chunk, a.base, a.lv, sm, g);
         if (key == ~0ull) key = ~0ull - 1; // ~0 marks an empty slot
-        if (lane == 0) {
+        if (g.sub == 0) {
             uint64_t s = smix(key) & a.mask;
             if (a.side == 0) {
                 // the table is at most half full, so an empty slot is always found
@@ -893,7 +915,7 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_certify(CertArgs a)
                 }
             }
         }
-        __syncwarp();
+        __syncwarp(g.mask);
     }
 }
 
@@ -913,10 +935,10 @@ int blocks_per_sm()
 }
 
 template <int NQ>
-unsigned grid_for(size_t warps_needed)
+unsigned grid_for(size_t units)
 {
     const size_t cap = (size_t)num_sms() * (size_t)blocks_per_sm<NQ>();
-    size_t g = (warps_needed + Geo<NQ>::WARPS - 1) / Geo<NQ>::WARPS;
+    size_t g = (units + Geo<NQ>::WALKS - 1) / Geo<NQ>::WALKS;
     if (g > cap) g = cap;
     if (g == 0) g = 1;
     return (unsigned)g;
@@ -1022,7 +1044,7 @@ int num_sms()
     return g_num_sms;
 }
 
-int walks_per_task(int n) { return n == 4 ? Geo<4>::WARPS : n == 3 ? Geo<3>::WARPS : n == 2 ? Geo<2>::WARPS : Geo<1>::WARPS; }
+int walks_per_task(int n) { return n == 4 ? Geo<4>::WALKS : n == 3 ? Geo<3>::WALKS : n == 2 ? Geo<2>::WALKS : Geo<1>::WALKS; }
 
 int walk_blocks_per_sm(int n)
 {
