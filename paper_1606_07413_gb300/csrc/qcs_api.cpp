@@ -203,14 +203,14 @@ namespace {
 int upload_problem(qcs_problem *P)
 {
     const int D = P->D, n = P->n;
-    const int R = D >= 32 ? D / 32 : 1; // columns per lane in the walk kernel
-    // C^ low words; for D >= 32 row i keeps lane l's columns l + 32 t (t < R)
-    // next to each other at i * D + l * R + t
+    const int Wl = lanes_per_walk(n), R = D / Wl; // lanes per walk and columns per lane in the walk kernel
+    // C^ low words; row i keeps lane l's columns l + Wl t (t < R) next to
+    // each other at i * D + l * R + t
     std::vector<uint2> c32((size_t)D * D), u(D);
     for (int i = 0; i < D; i++)
         for (int Q = 0; Q < D; Q++) {
             const size_t src = (size_t)i * D + Q;
-            const size_t dst = D >= 32 ? (size_t)i * D + (size_t)(Q % 32) * R + (size_t)(Q / 32) : src;
+            const size_t dst = (size_t)i * D + (size_t)(Q % Wl) * R + (size_t)(Q / Wl);
             c32[dst] = make_uint2((uint32_t)(uint64_t)P->C.a[src], (uint32_t)(uint64_t)P->C.b[src]);
         }
     // fingerprint weights: the SplitMix64 stream seeded with kSeedU, outputs
@@ -221,13 +221,13 @@ int upload_problem(qcs_problem *P)
         uint64_t wb = smix_host(kSeedU + (2ull * i + 2) * kGamma);
         u[i] = make_uint2((uint32_t)wa, (uint32_t)wb);
     }
-    // rotation coefficients per Pauli p: word t, bit l: row l + 32 t
+    // rotation coefficients per Pauli p: word t, bit l: row l + Wl t
     // anticommutes with p; word R + t, bit l: s(p, row) = +1 (lambda = 1)
     std::vector<uint32_t> coef((size_t)D * 2 * R, 0);
     const uint32_t m = (1u << n) - 1;
     for (uint32_t p = 0; p < (uint32_t)D; p++)
         for (uint32_t j = 0; j < (uint32_t)D; j++) {
-            const uint32_t t = j / 32, l = j % 32;
+            const uint32_t t = j / (uint32_t)Wl, l = j % (uint32_t)Wl;
             const bool anti = (__builtin_popcount(((p >> n) & (j & m)) ^ ((p & m) & (j >> n))) & 1) != 0;
             const bool plus = pauli_phase(n, p, j) == 1;
             if (anti) coef[(size_t)p * 2 * R + t] |= 1u << l;
@@ -246,16 +246,16 @@ int upload_problem(qcs_problem *P)
             cq.assign((size_t)D * D / 2, 0);
             for (int q = 0; q < quads; q++)
                 for (int j = 0; j < half; j++)
-                    for (int lane = 0; lane < 32; lane++)
+                    for (int lane = 0; lane < Wl; lane++)
                         for (int c = 0; c < 2; c++) {
-                            const int Q = lane + 64 * j + 32 * c;
+                            const int Q = lane + 2 * Wl * j + Wl * c;
                             uint32_t wa = 0, wb = 0;
                             for (int r = 0; r < 4; r++) {
                                 const size_t src = (size_t)(4 * q + r) * D + Q;
                                 wa |= (uint32_t)(uint8_t)(int8_t)P->C.a[src] << (8 * r);
                                 wb |= (uint32_t)(uint8_t)(int8_t)P->C.b[src] << (8 * r);
                             }
-                            const size_t o = (((size_t)q * half + j) * 32 + lane) * 4 + 2 * c;
+                            const size_t o = (((size_t)q * half + j) * Wl + lane) * 4 + 2 * c;
                             cq[o] = wa;
                             cq[o + 1] = wb;
                         }

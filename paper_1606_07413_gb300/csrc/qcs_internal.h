@@ -30,15 +30,15 @@ constexpr uint64_t kSeedH = 0xBB67AE8584CAA73Bull;
 
 // Everything a warp needs to evaluate one step f of the walk at one level.
 struct LevelCtx {
-    // C^ numerators mod 2^32 as (a, b), 4^n x 4^n.  Row i, column Q = lane +
-    // 32 t (t < R = max(1, 4^n / 32)) sits at i * 4^n + lane * R + t, so one
-    // lane's R columns of a row are contiguous.
+    // C^ numerators mod 2^32 as (a, b), 4^n x 4^n.  With W = lanes_per_walk(n)
+    // and R = 4^n / W, row i, column Q = sub + W t sits at i * 4^n + sub * R +
+    // t, so one lane's R columns of a row are contiguous.
     const uint2 *C32;
     // n >= 3: C^ as signed byte quads when every entry fits in int8, else
     // null.  Quad q holds rows 4q .. 4q+3 of a column as the bytes 0 .. 3 of
-    // one word.  uint4 number (q R/2 + j) 32 + lane carries, for the columns
-    // Q0 = lane + 64 j and Q1 = Q0 + 32, the words (a-quad Q0, b-quad Q0,
-    // a-quad Q1, b-quad Q1).
+    // one word.  uint4 number (q R/2 + j) W + sub carries, for the columns
+    // Q0 = sub + 2 W j and Q1 = Q0 + W, the words (a-quad Q0, b-quad Q0,
+    // a-quad Q1, b-quad Q1) (W, R as above).
     const uint4 *Cq;
     const uint2 *U;    // fingerprint weights (Ua, Ub) per row, 4^n
     // The weights after the first one (T1) or two (T2) adjoint stages of a
@@ -49,7 +49,7 @@ struct LevelCtx {
     const uint32_t *T1[2];
     const uint32_t *T2[2];
     // rotation coefficients: for Pauli p, 2R words; word t (t < R) has bit
-    // lane set when row lane + 32 t anticommutes with p, word R + t when the
+    // sub set when row sub + W t anticommutes with p, word R + t when the
     // sign s(p, row) is +1.  4^n x 2R uint32.
     const uint32_t *coef;
     uint64_t xi_h;     // xi^h, the number of rotation tuples per side
@@ -174,7 +174,8 @@ int certify_level(::qcs_problem *P, int k, cudaStream_t s, bool *got);
 uint64_t exhaustive_points(const ::qcs_problem *P, int k); // V + W points of level k
 bool exhaustive_eligible(const ::qcs_problem *P, int k);   // within exhaustive_log2 and device memory
 
-int walks_per_task(int n); // walks (warps) per CTA of the walk kernels for n qubits
+int walks_per_task(int n); // walks (lane groups) per CTA of the walk kernels for n qubits
+int lanes_per_walk(int n); // lanes of a warp that evaluate one walk (the device layouts follow it)
 
 // ---- kernel launchers (qcs_walk.cu); all return cudaError_t of the launch ----
 cudaError_t launch_walks_batch(int n, const BatchArgs &a, cudaStream_t s);

@@ -34,8 +34,11 @@ namespace {
 #ifndef QCS_WARPS
 #define QCS_WARPS 8
 #endif
+#ifndef QCS_LPW3
+#define QCS_LPW3 16 // lanes per walk at n = 3 (two walks per warp)
+#endif
 #ifndef QCS_MIN_BLOCKS3
-#define QCS_MIN_BLOCKS3 4 // n = 3: 64 registers, four CTAs of 8 warps per SM
+#define QCS_MIN_BLOCKS3 3 // n = 3: 80 registers, three CTAs of 8 warps (16 walks) per SM
 #endif
 #ifndef QCS_GEMV_UNROLL
 #define QCS_GEMV_UNROLL 2 // 32-bit word contraction (rows per unrolled step / 2)
@@ -63,7 +66,7 @@ struct Geo {
     static constexpr int D = DIM - 1;                    // non-identity Paulis
     // one walk is evaluated by LPW consecutive lanes of a warp (4^n lanes for
     // n <= 2, the whole warp above), GROUPS walks per warp
-    static constexpr int LPW = DIM < 32 ? DIM : 32;
+    static constexpr int LPW = DIM < 32 ? DIM : (NQ == 3 ? QCS_LPW3 : 32);
     static constexpr int GROUPS = 32 / LPW;
     static constexpr int RPL = DIM / LPW;                // rows (and columns) per lane
     static constexpr int SLOTS = RPL * LPW;              // width of the fingerprint sort
@@ -144,9 +147,13 @@ __device__ __forceinline__ void adj_stage(uint32_t p, uint32_t (&ua)[Geo<NQ>::RP
     __syncwarp(g.mask);
     const uint32_t *cwp = sm.coef + p * (2 * G::RPL);
     uint32_t cw[2 * G::RPL];
-    if (G::RPL == 2) {
-        const uint4 v4 = *reinterpret_cast<const uint4 *>(cwp);
-        cw[0] = v4.x; cw[1] = v4.y; cw[2] = v4.z; cw[3 % (2 * G::RPL)] = v4.w;
+    if ((2 * G::RPL) % 4 == 0) {
+#pragma unroll
+        for (int t = 0; t < 2 * G::RPL; t += 4) {
+            const uint4 v4 = *reinterpret_cast<const uint4 *>(cwp + t);
+            cw[t] = v4.x; cw[(t + 1) % (2 * G::RPL)] = v4.y;
+            cw[(t + 2) % (2 * G::RPL)] = v4.z; cw[(t + 3) % (2 * G::RPL)] = v4.w;
+        }
     } else {
 #pragma unroll
         for (int t = 0; t < 2 * G::RPL; t++) cw[t] = cwp[t];
@@ -186,14 +193,14 @@ __device__ __forceinline__ uint32_t dp4a_us(uint32_t a, uint32_t b, uint32_t c)
 template <int NQ>
 __device__ __forceinline__ void weight_planes(uint2 *su, Lanes g)
 {
-    const int lane = g.sub; // n >= 3: the group is the whole warp
+    const int lane = g.sub;
     using G = Geo<NQ>;
-    constexpr int JOBS = G::DIM >= 64 ? G::DIM / 64 : 1; // 2 parts x DIM/4 quads over 32 lanes
+    constexpr int JOBS = G::DIM >= 2 * G::LPW ? G::DIM / (2 * G::LPW) : 1; // 2 parts x DIM/4 quads over the lanes
     const uint4 *s4 = reinterpret_cast<const uint4 *>(su);
     uint2 pl[JOBS];
 #pragma unroll
     for (int r = 0; r < JOBS; r++) {
-        const int job = lane + 32 * r, q = job >> 1, part = job & 1;
+        const int job = lane + G::LPW * r, q = job >> 1, part = job & 1;
         const uint4 r01 = s4[2 * q], r23 = s4[2 * q + 1]; // rows 4q, 4q+1 and 4q+2, 4q+3
         const uint32_t u0 = part ? r01.y : r01.x, u1 = part ? r01.w : r01.z;
         const uint32_t u2 = part ? r23.y : r23.x, u3 = part ? r23.w : r23.z;
@@ -203,7 +210,7 @@ __device__ __forceinline__ void weight_planes(uint2 *su, Lanes g)
     __syncwarp(g.mask);
     uint2 *w2 = su;
 #pragma unroll
-    for (int r = 0; r < JOBS; r++) w2[lane + 32 * r] = pl[r];
+    for (int r = 0; r < JOBS; r++) w2[lane + G::LPW * r] = pl[r];
     __syncwarp(g.mask);
 }
 
@@ -1043,6 +1050,8 @@ int num_sms()
     }
     return g_num_sms;
 }
+
+int lanes_per_walk(int n) { return n == 4 ? Geo<4>::LPW : n == 3 ? Geo<3>::LPW : n == 2 ? Geo<2>::LPW : Geo<1>::LPW; }
 
 int walks_per_task(int n) { return n == 4 ? Geo<4>::WALKS : n == 3 ? Geo<3>::WALKS : n == 2 ? Geo<2>::WALKS : Geo<1>::WALKS; }
 
