@@ -99,10 +99,7 @@ LevelCtx qcs::make_level(const qcs_problem *P, int k, uint32_t version, int dp_b
     lv.C32 = P->dC32;
     lv.Cq = reinterpret_cast<const uint4 *>(P->dCq);
     lv.U = P->dU;
-    for (int side = 0; side < 2; side++) {
-        lv.T1[side] = P->dT1[side];
-        lv.T2[side] = P->dT2[side];
-    }
+    for (int side = 0; side < 2; side++) lv.T1[side] = P->dT1[side];
     lv.coef = P->dCoef;
     lv.n = P->n;
     lv.k = k;
@@ -149,11 +146,11 @@ void host_adj_stage(int n, uint32_t p, bool adj_of_transpose, std::vector<uint32
 }
 
 std::mutex g_tab_mu;
-std::map<std::pair<int, int>, std::array<uint32_t *, 4>> g_tabs; // (device, n) -> T1v, T1w, T2v, T2w
+std::map<std::pair<int, int>, std::array<uint32_t *, 2>> g_tabs; // (device, n) -> T1v, T1w
 
 } // namespace
 
-int qcs::stage_tables(int n, const uint32_t *t1[2], const uint32_t *t2[2])
+int qcs::stage_tables(int n, const uint32_t *t1[2])
 {
     int dev = 0;
     CK(cudaGetDevice(&dev));
@@ -166,35 +163,21 @@ int qcs::stage_tables(int n, const uint32_t *t1[2], const uint32_t *t2[2])
             u0a[i] = (uint32_t)smix_host(kSeedU + (2ull * i + 1) * kGamma) & 0xFFFFu;
             u0b[i] = (uint32_t)smix_host(kSeedU + (2ull * i + 2) * kGamma) & 0xFFFFu;
         }
-        const bool two = n <= 3; // T2 at n = 4 would take 66 MB a side
-        std::array<uint32_t *, 4> tabs{nullptr, nullptr, nullptr, nullptr};
+        std::array<uint32_t *, 2> tabs{nullptr, nullptr};
         for (int side = 0; side < 2; side++) {
-            std::vector<uint32_t> t1((size_t)xi * D), t2(two ? (size_t)xi * xi * D : 0);
+            std::vector<uint32_t> t1((size_t)xi * D);
             for (uint32_t qa = 1; qa <= xi; qa++) {
                 std::vector<uint32_t> ua = u0a, ub = u0b;
                 host_adj_stage(n, qa, side == 1, ua, ub);
                 for (uint32_t j = 0; j < D; j++) t1[(size_t)(qa - 1) * D + j] = ua[j] | (ub[j] << 16);
-                if (!two) continue;
-                for (uint32_t qb = 1; qb <= xi; qb++) {
-                    std::vector<uint32_t> va = ua, vb = ub;
-                    host_adj_stage(n, qb, side == 1, va, vb);
-                    const size_t e = (size_t)(qa - 1) * xi + (qb - 1);
-                    for (uint32_t j = 0; j < D; j++) t2[e * D + j] = va[j] | (vb[j] << 16);
-                }
             }
             CK(cudaMalloc(&tabs[side], sizeof(uint32_t) * t1.size()));
             CK(cudaMemcpy(tabs[side], t1.data(), sizeof(uint32_t) * t1.size(), cudaMemcpyHostToDevice));
-            if (two) {
-                CK(cudaMalloc(&tabs[2 + side], sizeof(uint32_t) * t2.size()));
-                CK(cudaMemcpy(tabs[2 + side], t2.data(), sizeof(uint32_t) * t2.size(), cudaMemcpyHostToDevice));
-            }
         }
         it = g_tabs.emplace(std::make_pair(dev, n), tabs).first;
     }
     t1[0] = it->second[0];
     t1[1] = it->second[1];
-    t2[0] = it->second[2];
-    t2[1] = it->second[3];
     return QCS_OK;
 }
 
@@ -262,7 +245,7 @@ int upload_problem(qcs_problem *P)
         }
     }
     CK(cudaGetDevice(&P->device));
-    if (int rc = stage_tables(n, P->dT1, P->dT2)) return rc;
+    if (int rc = stage_tables(n, P->dT1)) return rc;
     if (!cq.empty()) {
         CK(cudaMalloc(&P->dCq, sizeof(uint32_t) * cq.size()));
         CK(cudaMemcpy(P->dCq, cq.data(), sizeof(uint32_t) * cq.size(), cudaMemcpyHostToDevice));

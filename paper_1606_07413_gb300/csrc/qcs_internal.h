@@ -41,13 +41,10 @@ struct LevelCtx {
     // a-quad Q1, b-quad Q1) (W, R as above).
     const uint4 *Cq;
     const uint2 *U;    // fingerprint weights (Ua, Ub) per row, 4^n
-    // The weights after the first one (T1) or two (T2) adjoint stages of a
-    // side (index 0: V, 1: W), mod 2^16, for every Pauli (pair): entry e =
-    // (q_a - 1) or (q_a - 1) xi + (q_b - 1), where q_a, q_b are the side's
-    // first and second stage rotations (V: q_h, q_{h-1}; W: q_1, q_2); word
-    // e 4^n + row = Ua | Ub << 16.  Null where not built (T2 for n = 4).
+    // The weights after the first adjoint stage of a side (index 0: V, 1: W),
+    // mod 2^16, for every Pauli: entry e = q_a - 1, where q_a is the side's
+    // first stage rotation (V: q_h; W: q_1); word e 4^n + row = Ua | Ub << 16.
     const uint32_t *T1[2];
-    const uint32_t *T2[2];
     // rotation coefficients: for Pauli p, 2R words; word t (t < R) has bit
     // sub set when row sub + W t anticommutes with p, word R + t when the
     // sign s(p, row) is +1.  4^n x 2R uint32.
@@ -220,9 +217,9 @@ int exact_verify(int n, const PMat &C, const uint32_t *paulis, int t, PMat *Dout
 int exact_same_coset(int n, const PMat &C, int k, int chunk, const uint32_t *qv, const uint32_t *qw,
                      bool *equal);
 int pauli_phase(int n, uint32_t p, uint32_t q); // P(p)P(q) = i^lambda P(p^q)
-// device tables of the first adjoint stages (LevelCtx::T1, T2), built once per
+// device tables of the first adjoint stage (LevelCtx::T1), built once per
 // device and qubit count and kept for the life of the process
-int stage_tables(int n, const uint32_t *t1[2], const uint32_t *t2[2]);
+int stage_tables(int n, const uint32_t *t1[2]);
 
 // How a level is walked (Sec. 3 and Appendix): theta, the launch shape, the
 // function-version period and the level's step budget.
@@ -252,7 +249,7 @@ struct qcs_problem {
     // device data
     uint2 *dC32 = nullptr, *dU = nullptr;
     uint32_t *dCq = nullptr; // n >= 3, when every entry of C^ fits in int8
-    const uint32_t *dT1[2] = {nullptr, nullptr}, *dT2[2] = {nullptr, nullptr}; // shared stage tables
+    const uint32_t *dT1[2] = {nullptr, nullptr}; // shared stage tables
     uint32_t *dCoef = nullptr;
     qcs::Slot *dTable = nullptr;
     qcs::Pair *dQueue = nullptr;

@@ -263,26 +263,19 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
     const int lane = g.sub;
     const int h = lv.h;
 
-    // The weights enter the side's first one or two adjoint stages from the
-    // stage tables (fingerprints live mod 2^16, and so do the tables): V
-    // takes R^(q_h)^* then R^(q_{h-1})^*, W takes (R^(q_1)^T)^* then
-    // (R^(q_2)^T)^*.  s0 stages are done by the lookup.
+    // The weights enter the side's first adjoint stage from the stage table
+    // (fingerprints live mod 2^16, and so does the table): V takes
+    // R^(q_h)^* first, W takes (R^(q_1)^T)^* first.  The V side uses it only
+    // when further stages follow, so no product is ever a bare lookup; the W
+    // side always goes on to the contraction with C^.
     int s0 = 0;
     const uint32_t *tab = nullptr;
     uint32_t e = 0;
-    if (h >= 1) {
-        const int ba = dx.side == 0 ? h - 1 : 0, bb = dx.side == 0 ? h - 2 : 1;
-        const uint32_t qa = (uint32_t)(dx.qpack >> (8 * ba)) & 0xFFu;
-        if (h >= 2 && lv.T2[dx.side]) {
-            const uint32_t qb = (uint32_t)(dx.qpack >> (8 * bb)) & 0xFFu;
-            tab = lv.T2[dx.side];
-            e = (qa - 1) * lv.xi + (qb - 1);
-            s0 = 2;
-        } else if (lv.T1[dx.side]) {
-            tab = lv.T1[dx.side];
-            e = qa - 1;
-            s0 = 1;
-        }
+    if (h >= (dx.side == 0 ? 2 : 1) && lv.T1[dx.side]) {
+        const uint32_t qa = (uint32_t)(dx.qpack >> (8 * (dx.side == 0 ? h - 1 : 0))) & 0xFFu;
+        tab = lv.T1[dx.side];
+        e = qa - 1;
+        s0 = 1;
     }
     uint32_t ua[G::RPL], ub[G::RPL];
 #pragma unroll
