@@ -2,7 +2,8 @@
 // of the deterministic-walk T-count search (Di Matteo & Mosca, Sec. 2-3),
 // hand-written for sm_103a.
 //
-// One warp evaluates one step f = h o nu o mu of one walk (Sec. 2, Fig. 1):
+// A group of lanes (a warp, or 16 / 4^n lanes for n <= 3) evaluates one step
+// f = h o nu o mu of one walk (Sec. 2, Fig. 1):
 //   mu : decode the state into a side b and rotations q_1..q_h (Sec. 3, z_b);
 //   nu : the exact product V = R^(q_h)..R^(q_1) or W = R^(q_1)^T..R^(q_h)^T
 //        [R^(c)^T] C^ over Z[1/sqrt2] (Eq. mitm in channel form), taken modulo
@@ -18,8 +19,9 @@
 // vector U through the transposed sparse R^ butterflies (4^n entries, h
 // stages) instead of pushing all 4^n - 1 columns through them.  The V side is
 // then read off directly (its right factor is the identity), and the W side is
-// one contraction of the transformed weights with C^, staged in shared memory.
-// The result is bit-identical to hashing the explicitly formed product.
+// one contraction of the transformed weights with C^, staged in shared memory
+// as signed byte quads and contracted by byte-plane dp4a.  The result is
+// bit-identical to hashing the explicitly formed product.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -30,7 +32,8 @@ namespace qcs {
 namespace {
 
 // launch shape of the walk kernels, tuned on GB300 by sweeping warps per CTA,
-// the register cap (minimum resident CTAs) and the contraction's unrolling
+// lanes per walk, the register cap (minimum resident CTAs) and the
+// contraction's unrolling
 #ifndef QCS_WARPS
 #define QCS_WARPS 8
 #endif
@@ -65,7 +68,7 @@ struct Geo {
     static constexpr int DIM = 1 << (2 * NQ);            // 4^n rows and columns
     static constexpr int D = DIM - 1;                    // non-identity Paulis
     // one walk is evaluated by LPW consecutive lanes of a warp (4^n lanes for
-    // n <= 2, the whole warp above), GROUPS walks per warp
+    // n <= 2, QCS_LPW3 at n = 3, the whole warp at n = 4), GROUPS walks per warp
     static constexpr int LPW = DIM < 32 ? DIM : (NQ == 3 ? QCS_LPW3 : 32);
     static constexpr int GROUPS = 32 / LPW;
     static constexpr int RPL = DIM / LPW;                // rows (and columns) per lane
