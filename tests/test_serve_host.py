@@ -1,0 +1,131 @@
+"""Host logic of the serving loop (paper_1606_07413_gb300.serve) on CPU: a
+fake batch engine stands in for the device, so admission by memory and job
+slots, arrival order, deadlines and full-batch handling are checked without a
+GPU."""
+import pytest
+
+import paper_1606_07413_gb300 as Q
+from paper_1606_07413_gb300 import serve
+
+
+class FakeProblem:
+    def __init__(self, n, gates, k_max, params):
+        self.n, self.k_max, self.closed = n, k_max, False
+        self.rounds_needed = int(gates[0][0])  # encoded by the test
+
+    def close(self):
+        self.closed = True
+
+
+class FakeBatch:
+    """Job slots; a job finishes after its rounds_needed rounds."""
+
+    def __init__(self, params, stream=None):
+        self.max_jobs = params.max_jobs
+        self.jobs = {}
+        self.added = []
+        self.busy_once = False
+
+    def job_bytes(self, prob):
+        return 100 * prob.n
+
+    def add(self, prob):
+        if self.busy_once:
+            self.busy_once = False
+            raise Q.QcsError(Q.ERR_BUSY, "qcs_batch_add")
+        free = [s for s in range(self.max_jobs) if s not in self.jobs]
+        if not free:
+            raise Q.QcsError(Q.ERR_BUSY, "qcs_batch_add")
+        self.jobs[free[0]] = [prob, 0]
+        self.added.append(prob)
+        return free[0]
+
+    def remove(self, slot):
+        del self.jobs[slot]
+
+    def round(self):
+        for j in self.jobs.values():
+            j[1] += 1
+        return len(self.jobs)
+
+    def poll(self, slot):
+        prob, r = self.jobs[slot]
+        done = r >= prob.rounds_needed
+        return {"status_name": "found" if done else "searching", "t_count": prob.k_max if done else -1,
+                "paulis": [1] * prob.k_max if done else [], "steps": 10 * r, "rewalk_steps": r}
+
+    def close(self):
+        pass
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+
+@pytest.fixture
+def fake(monkeypatch):
+    monkeypatch.setattr(Q, "Batch", FakeBatch)
+    monkeypatch.setattr(Q.Problem, "from_circuit", classmethod(lambda cls, *a: FakeProblem(*a)))
+    monkeypatch.setattr(Q, "default_params", lambda n, **kw: None)
+
+
+def bparams(J):
+    p = Q.BatchParams()
+    p.max_jobs = J
+    return p
+
+
+def test_admission_follows_memory_slots_and_arrival_order(fake):
+    clock = Clock()
+    with serve.Server(bparams(3), memory_budget=450, clock=clock) as srv:
+        # n = 2 jobs take 200 bytes each: at most two fit the budget at once
+        rids = [srv.submit(2, [[3 + i, 0, 0]], 2) for i in range(5)]
+        peak_running = 0
+        for _ in range(100):
+            clock.t += 0.01
+            srv.step()
+            peak_running = max(peak_running, len(srv.running))
+            assert srv.used <= 450
+            if srv.idle():
+                break
+        assert srv.idle() and peak_running == 2 and srv.peak_used == 400
+        admits = [srv.poll(r)["t_admit"] for r in rids]
+        assert admits == sorted(admits)  # first come, first admitted
+        assert all(srv.poll(r)["status"] == "found" for r in rids)
+        assert srv.fevals == sum(10 * (3 + i) + (3 + i) for i in range(5))
+
+
+def test_a_single_job_larger_than_the_budget_still_runs_alone(fake):
+    with serve.Server(bparams(2), memory_budget=100, clock=Clock()) as srv:
+        rid = srv.submit(4, [[2, 0, 0]], 3)  # 400 bytes > budget
+        for _ in range(10):
+            srv.step()
+        assert srv.poll(rid)["status"] == "found"
+
+
+def test_deadline_ends_a_job_and_frees_its_memory(fake):
+    clock = Clock()
+    with serve.Server(bparams(2), memory_budget=10_000, deadline_s=1.0, clock=clock) as srv:
+        slow = srv.submit(3, [[1000, 0, 0]], 5)
+        fast = srv.submit(2, [[2, 0, 0]], 3)
+        for _ in range(30):
+            clock.t += 0.1
+            srv.step()
+        assert srv.poll(slow)["status"] == "deadline"
+        assert srv.poll(fast)["status"] == "found"
+        assert srv.used == 0 and not srv.running
+
+
+def test_a_full_batch_leaves_the_request_queued(fake):
+    with serve.Server(bparams(2), memory_budget=10_000, clock=Clock()) as srv:
+        srv.batch.busy_once = True  # the batch refuses the next add once
+        rid = srv.submit(2, [[2, 0, 0]], 3)
+        srv.step()
+        assert srv.poll(rid)["status"] == "queued"
+        for _ in range(5):
+            srv.step()
+        assert srv.poll(rid)["status"] == "found"
