@@ -96,7 +96,7 @@ typedef struct qcs_params {
     int32_t state_bits;       /* L, 32..64 */
     int32_t dp_bits;          /* d_theta, theta = 2^-d_theta (Sec. 3), 1 .. L-1 */
     int32_t walks;            /* concurrent walks (one warp each) */
-    int32_t table_log2;       /* distinguished-point table holds 2^table_log2 slots (32 B each) */
+    int32_t table_log2;       /* distinguished-point table holds 2^table_log2 slots (16 B each) */
     int32_t steps_per_launch; /* walk steps each walk advances per kernel launch */
     int32_t max_trail_factor; /* a trail is abandoned after max_trail_factor * 2^d_theta steps */
     int32_t queue_capacity;   /* collision pairs kept per launch */
@@ -271,7 +271,7 @@ typedef struct qcs_batch qcs_batch;
 
 typedef struct qcs_batch_params {
     int32_t max_jobs;        /* job slots, 1..65536 */
-    int32_t walks_per_job;   /* concurrent walks of each job (multiple of 8) */
+    int32_t walks_per_job;   /* concurrent walks of each job (multiple of 16, at least 16) */
     int32_t steps_per_round; /* walk steps per walk per round (upper bound) */
     int32_t table_log2;      /* distinguished-point table of each job: 2^table_log2 slots */
     int32_t queue_capacity;  /* merges kept per job per round */
