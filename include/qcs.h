@@ -266,7 +266,10 @@ QCS_API int qcs_level_walk_static(qcs_problem *prob, int k, uint32_t version, in
  * level (walk, re-walk, exact claw checks), with all jobs of one qubit count
  * in one persistent walk kernel and one persistent re-walk kernel.  With
  * use_graph = 1 a round is one replay of a CUDA graph captured at the first
- * round.  Jobs may be added and removed between rounds. */
+ * round.  Jobs may be added and removed between rounds.  A job's levels are
+ * settled by the exhaustive pass (qcs_certify_level, synchronously within
+ * the round) as its problem's exhaustive_log2 / exhaustive_first ask: before
+ * the level's walk (exhaustive_first) or when its walk budget ends. */
 typedef struct qcs_batch qcs_batch;
 
 typedef struct qcs_batch_params {
