@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-T-count run")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and other-size runs")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only run the batched-search comparison (config 4), print its JSON and exit")
     ap.add_argument("--level-only", choices=["n2_level3", "n4_level7"], default=None,
                     help="only time that single-target level launch (walk-kernel throughput), print its JSON and exit")
     ap.add_argument("--config3-walk", type=int, default=0, metavar="TABLE_LOG2",
@@ -576,6 +578,17 @@ def run_level_only(args):
                                                         alu_per_s=peak)}))
 
 
+def run_batched_only(args):
+    import torch
+
+    import paper_1606_07413_gb300 as Q
+    from paper_1606_07413_gb300 import build as B
+    from paper_1606_07413_gb300 import workloads as W
+
+    B.build()
+    print(json.dumps({"batched": run_batched(Q, W, torch, torch.cuda.Stream())}))
+
+
 def run_config3_walk(args):
     import torch
 
@@ -596,5 +609,7 @@ if __name__ == "__main__":
         run_config3_walk(a)
     elif a.level_only:
         run_level_only(a)
+    elif a.batched_only:
+        run_batched_only(a)
     else:
         run_ours(a)

@@ -63,6 +63,11 @@ struct qcs_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t rounds = 0;
+    // one branch per qubit count: its walk and re-walk kernels run on their
+    // own stream, forked from and joined back into s, so the classes' kernels
+    // (and the long tail of one class's re-walks) overlap
+    cudaStream_t cs[kClasses] = {};
+    cudaEvent_t fork = nullptr, join[kClasses] = {};
 };
 
 namespace {
@@ -209,15 +214,15 @@ int enqueue_round(qcs_batch *B)
     if (!e) e = cudaMemcpyAsync(B->dCounts, B->hCounts, sizeof(uint32_t) * kClasses * 2, cudaMemcpyHostToDevice, s);
     if (!e) e = cudaMemsetAsync(B->dHeads, 0, sizeof(uint32_t) * 2 * J, s);
     if (!e) e = cudaMemsetAsync(B->dCounters, 0, sizeof(unsigned long long) * C_NCOUNTERS * J, s);
+    if (!e) e = cudaEventRecord(B->fork, s);
     for (int c = 1; c < kClasses && !e; c++) {
         BatchArgs a{B->dJobs, B->dTasks + (size_t)c * 2 * B->max_tasks, B->dCounts + 2 * c, B->dIds + (size_t)c * J,
                     B->dCounts + 2 * c + 1};
-        e = launch_walks_batch(c, a, s);
-    }
-    for (int c = 1; c < kClasses && !e; c++) {
-        BatchArgs a{B->dJobs, B->dTasks + (size_t)c * 2 * B->max_tasks, B->dCounts + 2 * c, B->dIds + (size_t)c * J,
-                    B->dCounts + 2 * c + 1};
-        e = launch_rewalk_batch(c, a, s);
+        e = cudaStreamWaitEvent(B->cs[c], B->fork, 0);
+        if (!e) e = launch_walks_batch(c, a, B->cs[c]);
+        if (!e) e = launch_rewalk_batch(c, a, B->cs[c]);
+        if (!e) e = cudaEventRecord(B->join[c], B->cs[c]);
+        if (!e) e = cudaStreamWaitEvent(s, B->join[c], 0);
     }
     if (!e) e = cudaMemcpyAsync(B->hCounters, B->dCounters, sizeof(unsigned long long) * C_NCOUNTERS * J,
                                 cudaMemcpyDeviceToHost, s);
@@ -362,6 +367,15 @@ int qcs_batch_create(const qcs_batch_params *pin, void *stream, qcs_batch **out)
             return QCS_ERR_CUDA;
         }
         B->own_stream = true;
+    }
+    cudaError_t es = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
+    for (int c = 1; c < kClasses && es == cudaSuccess; c++) {
+        es = cudaStreamCreateWithFlags(&B->cs[c], cudaStreamNonBlocking);
+        if (es == cudaSuccess) es = cudaEventCreateWithFlags(&B->join[c], cudaEventDisableTiming);
+    }
+    if (es != cudaSuccess) {
+        qcs_batch_destroy(B);
+        return QCS_ERR_CUDA;
     }
     B->jobs.resize((size_t)bp.max_jobs);
     B->max_tasks = (uint32_t)bp.max_jobs * ((uint32_t)bp.walks_per_job / 8); // at least 8 walks per task
@@ -545,6 +559,11 @@ void qcs_batch_destroy(qcs_batch *B)
     cudaFree(B->dTasks); cudaFreeHost(B->hTasks);
     cudaFree(B->dIds); cudaFreeHost(B->hIds);
     cudaFree(B->dCounts); cudaFreeHost(B->hCounts);
+    for (int c = 1; c < kClasses; c++) {
+        if (B->cs[c]) cudaStreamDestroy(B->cs[c]);
+        if (B->join[c]) cudaEventDestroy(B->join[c]);
+    }
+    if (B->fork) cudaEventDestroy(B->fork);
     if (B->own_stream) cudaStreamDestroy(B->s);
     delete B;
 }
