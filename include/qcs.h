@@ -179,8 +179,8 @@ QCS_API int qcs_run_walks(qcs_problem *prob, uint64_t step_budget, void *cuda_st
  * rotation tuples, all xi chunks c for odd k) is evaluated on the GPU with the
  * walk's own product and fingerprint canonical form.  V points go into a
  * device hash table of coset keys, W points probe it, and every key match is
- * checked exactly on the host (exact canonical forms, then the decomposition
- * is verified).  Equal cosets always have equal keys, so when no match
+ * checked exactly on the host (its decomposition is verified: D^ must be a
+ * signed permutation).  Equal cosets always have equal keys, so when no match
  * verifies, level k has no decomposition: *has_claw = 0 is a proof.  With
  * *has_claw = 1 the decomposition is recorded as by a FOUND search.  Runs
  * synchronously on cuda_stream (NULL = legacy default stream); allocates

@@ -328,15 +328,30 @@ void set_status(qcs_problem *P, int status, int error)
 
 } // namespace
 
+bool qcs::verify_claw(const qcs_problem *P, int k, int chunk, const uint32_t *qv, const uint32_t *qw,
+                      uint32_t *paulis, PMat *Dh)
+{
+    const int h = k / 2;
+    for (int j = 0; j < 16; j++) paulis[j] = 0;
+    for (int j = 0; j < h; j++) {
+        paulis[j] = qv[j];
+        paulis[h + j] = qw[j];
+    }
+    if (k & 1) paulis[2 * h] = (uint32_t)chunk;
+    return exact_verify(P->n, P->C, paulis, k, Dh) == QCS_OK;
+}
+
 void qcs::found(qcs_problem *P, int k, const uint32_t *paulis)
 {
-    {
-        std::lock_guard<std::mutex> g(P->mu);
-        if (P->have_D) return; // keep the first decomposition
-    }
     PMat Dh;
     exact_verify(P->n, P->C, paulis, k, &Dh);
+    found(P, k, paulis, std::move(Dh));
+}
+
+void qcs::found(qcs_problem *P, int k, const uint32_t *paulis, PMat &&Dh)
+{
     std::lock_guard<std::mutex> g(P->mu);
+    if (P->have_D) return; // keep the first decomposition
     P->res.t_count = k;
     P->res.k = k;
     for (int j = 0; j < 16; j++) P->res.paulis[j] = j < k ? paulis[j] : 0;
@@ -419,6 +434,7 @@ int level_collect(qcs_problem *P, cudaStream_t s, bool *got, uint64_t *steps)
     const uint32_t npairs = std::min(P->hQhead[0], L.w.qcap);
     const uint32_t ncand = std::min(P->hQhead[1], kCandCap);
     uint32_t paulis[16] = {0};
+    PMat Dh;
     int64_t claws = 0, false_hash = 0;
     *got = false;
     for (uint32_t i = 0; i < ncand && !*got; i++) {
@@ -429,19 +445,10 @@ int level_collect(qcs_problem *P, cudaStream_t s, bool *got, uint64_t *steps)
         decode_state(xv, P->n, P->p.state_bits, h, qv);
         decode_state(xw, P->n, P->p.state_bits, h, qw);
         const int chunk = (k & 1) ? (int)r.chunk : 0;
-        bool equal = false;
-        if (exact_same_coset(P->n, P->C, k, chunk, qv, qw, &equal) != QCS_OK) equal = false;
-        if (equal) {
-            for (int j = 0; j < h; j++) {
-                paulis[j] = qv[j];
-                paulis[h + j] = qw[j];
-            }
-            if (k & 1) paulis[2 * h] = (uint32_t)chunk;
-            if (exact_verify(P->n, P->C, paulis, k, nullptr) == QCS_OK) {
-                claws++;
-                *got = true;
-                continue;
-            }
+        if (verify_claw(P, k, chunk, qv, qw, paulis, &Dh)) {
+            claws++;
+            *got = true;
+            continue;
         }
         false_hash++;
     }
@@ -466,7 +473,7 @@ int level_collect(qcs_problem *P, cudaStream_t s, bool *got, uint64_t *steps)
         R.launches += 1;
         R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - P->t0).count();
     }
-    if (*got) found(P, k, paulis);
+    if (*got) found(P, k, paulis, std::move(Dh));
     return QCS_OK;
 }
 
@@ -609,15 +616,9 @@ int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
                 v /= xi;
                 w /= xi;
             }
-            bool equal = false;
-            if (exact_same_coset(P->n, P->C, k, chunk, qv, qw, &equal) != QCS_OK || !equal) continue;
-            for (int j = 0; j < h; j++) {
-                paulis[j] = qv[j];
-                paulis[h + j] = qw[j];
-            }
-            if (k & 1) paulis[2 * h] = (uint32_t)chunk;
-            if (exact_verify(P->n, P->C, paulis, k, nullptr) == QCS_OK) {
-                found(P, k, paulis);
+            PMat Dh;
+            if (verify_claw(P, k, chunk, qv, qw, paulis, &Dh)) {
+                found(P, k, paulis, std::move(Dh));
                 *got = true;
             }
         }

@@ -239,6 +239,7 @@ void collect_job(Job &j, const unsigned long long *c, const uint32_t *heads, con
     const uint32_t npairs = std::min(heads[0], (uint32_t)j.jp.queue_capacity);
     const uint32_t ncand = std::min(heads[1], kBatchCandCap);
     uint32_t paulis[16] = {0};
+    PMat Dh;
     int64_t claws = 0, false_hash = 0;
     bool got = false;
     for (uint32_t i = 0; i < ncand && !got; i++) {
@@ -248,19 +249,10 @@ void collect_job(Job &j, const unsigned long long *c, const uint32_t *heads, con
         decode_state(xv, P->n, P->p.state_bits, h, qv);
         decode_state(xw, P->n, P->p.state_bits, h, qw);
         const int chunk = (k & 1) ? (int)r.chunk : 0;
-        bool equal = false;
-        if (exact_same_coset(P->n, P->C, k, chunk, qv, qw, &equal) != QCS_OK) equal = false;
-        if (equal) {
-            for (int q = 0; q < h; q++) {
-                paulis[q] = qv[q];
-                paulis[h + q] = qw[q];
-            }
-            if (k & 1) paulis[2 * h] = (uint32_t)chunk;
-            if (exact_verify(P->n, P->C, paulis, k, nullptr) == QCS_OK) {
-                claws++;
-                got = true;
-                continue;
-            }
+        if (verify_claw(P, k, chunk, qv, qw, paulis, &Dh)) {
+            claws++;
+            got = true;
+            continue;
         }
         false_hash++;
     }
@@ -287,7 +279,7 @@ void collect_job(Job &j, const unsigned long long *c, const uint32_t *heads, con
     j.launches++;
     j.in_version++;
     if (got) {
-        found(P, k, paulis);
+        found(P, k, paulis, std::move(Dh));
         j.status = QCS_FOUND;
         j.active = false;
         return;

@@ -1,7 +1,6 @@
 // qcs_exact.cpp -- exact host arithmetic of libqcs: targets over Z[omega],
-// channel representations over Z[1/sqrt2] (Sec. 4.1), sparse R^(P) products,
-// exact canonical forms modulo Clifford and verification of decompositions
-// (Eq. tcount_synthesis).  Used at problem set-up and for the rare claw checks;
+// channel representations over Z[1/sqrt2] (Sec. 4.1), sparse R^(P) products
+// and verification of decompositions (Eq. tcount_synthesis).  Used at problem set-up and for the rare claw checks;
 // the walk itself runs on the GPU (qcs_walk.cu).
 #include <algorithm>
 #include <cstring>
@@ -171,47 +170,6 @@ int apply_gate(int n, UMat &U, int op, int a, int b, Ovf &o)
     default:
         return QCS_ERR_ARG;
     }
-}
-
-void raise(PMat &M, int s) // same value, numerators times sqrt2^s
-{
-    for (int t = 0; t < s; t++) {
-        for (size_t i = 0; i < M.a.size(); i++) {
-            int64_t a = M.a[i];
-            M.a[i] = 2 * M.b[i];
-            M.b[i] = a;
-        }
-        M.E++;
-    }
-}
-
-int zs_sign(int64_t a, int64_t b)
-{
-    if (!a && !b) return 0;
-    if (a >= 0 && b >= 0) return 1;
-    if (a <= 0 && b <= 0) return -1;
-    __int128 a2 = (__int128)a * a, b2 = (__int128)2 * b * b;
-    return a > 0 ? (a2 > b2 ? 1 : -1) : (b2 > a2 ? 1 : -1);
-}
-
-// columns 1..D-1 sign-normalised and sorted, at minimal sde
-void canonical(const PMat &Min, std::vector<std::vector<int64_t>> *cols, int *sde)
-{
-    PMat M = Min;
-    exact_reduce(&M);
-    const int D = M.D;
-    cols->assign(D - 1, std::vector<int64_t>(2 * (D - 1)));
-    for (int Q = 1; Q < D; Q++) {
-        int s = 0;
-        for (int i = 1; i < D && !s; i++) s = zs_sign(M.a[i * D + Q], M.b[i * D + Q]);
-        auto &c = (*cols)[Q - 1];
-        for (int i = 1; i < D; i++) {
-            c[2 * (i - 1)] = s * M.a[i * D + Q];
-            c[2 * (i - 1) + 1] = s * M.b[i * D + Q];
-        }
-    }
-    std::sort(cols->begin(), cols->end());
-    *sde = M.E;
 }
 
 } // namespace
@@ -405,42 +363,6 @@ int exact_verify(int n, const PMat &C, const uint32_t *paulis, int t, PMat *Dout
         *Dout = M;
     }
     return ok ? QCS_OK : QCS_ERR_MISMATCH;
-}
-
-int exact_same_coset(int n, const PMat &C, int k, int chunk, const uint32_t *qv, const uint32_t *qw, bool *equal)
-{
-    const int D = C.D, h = k / 2;
-    PMat V;
-    V.D = D;
-    V.E = 0;
-    V.a.assign((size_t)D * D, 0);
-    V.b.assign((size_t)D * D, 0);
-    for (int i = 0; i < D; i++) V.a[(size_t)i * D + i] = 1;
-    for (int j = 0; j < h; j++) {
-        PMat T;
-        int rc = exact_rhat_left(n, qv[j], false, V, &T);
-        if (rc) return rc;
-        V = std::move(T);
-    }
-    PMat Wm = C;
-    if (k & 1) {
-        PMat T;
-        int rc = exact_rhat_left(n, (uint32_t)chunk, true, Wm, &T);
-        if (rc) return rc;
-        Wm = std::move(T);
-    }
-    for (int j = h - 1; j >= 0; j--) {
-        PMat T;
-        int rc = exact_rhat_left(n, qw[j], true, Wm, &T);
-        if (rc) return rc;
-        Wm = std::move(T);
-    }
-    std::vector<std::vector<int64_t>> cv, cw;
-    int ev, ew;
-    canonical(V, &cv, &ev);
-    canonical(Wm, &cw, &ew);
-    *equal = (ev == ew) && cv == cw;
-    return QCS_OK;
 }
 
 } // namespace qcs

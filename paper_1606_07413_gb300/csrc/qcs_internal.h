@@ -213,9 +213,6 @@ bool exact_is_clifford(const PMat &M);
 int exact_rhat_left(int n, uint32_t p, bool transpose, const PMat &M, PMat *out);
 // D^ = R^(P_1)^T .. R^(P_t)^T C^; QCS_OK if a signed permutation, else QCS_ERR_MISMATCH
 int exact_verify(int n, const PMat &C, const uint32_t *paulis, int t, PMat *Dout);
-// are V_qv and W_qw (level k, chunk) one Clifford coset?  (exact canonical forms)
-int exact_same_coset(int n, const PMat &C, int k, int chunk, const uint32_t *qv, const uint32_t *qw,
-                     bool *equal);
 int pauli_phase(int n, uint32_t p, uint32_t q); // P(p)P(q) = i^lambda P(p^q)
 // device tables of the first adjoint stage (LevelCtx::T1), built once per
 // device and qubit count and kept for the life of the process
@@ -237,7 +234,14 @@ void decode_state(uint64_t x, int n, int L, int h, uint32_t *q);
 LevelCtx make_level(const ::qcs_problem *P, int k, uint32_t version, int dp_bits);
 LevelPlan plan_level(const ::qcs_problem *P, int k, const qcs_params &p);
 LevelPlan plan_level_n(int D, int k, const qcs_params &p); // D = 4^n
-void found(::qcs_problem *P, int k, const uint32_t *paulis);
+void found(::qcs_problem *P, int k, const uint32_t *paulis, PMat &&Dh); // keeps the first decomposition
+void found(::qcs_problem *P, int k, const uint32_t *paulis);              // forms D^ itself
+// Exact check of a claw candidate (Eq. tcount_synthesis): paulis gets
+// (q_1..q_h, q'_1..q'_h [, c]) from the V rotations qv, the W rotations qw and
+// the chunk, and the candidate is a claw iff D^ = R^(P_1)^T..R^(P_k)^T C^ is a
+// signed permutation; *Dh gets D^ then.
+bool verify_claw(const ::qcs_problem *P, int k, int chunk, const uint32_t *qv, const uint32_t *qw,
+                 uint32_t *paulis, PMat *Dh);
 
 } // namespace qcs
 
