@@ -279,7 +279,9 @@ typedef struct qcs_batch_params {
     int32_t table_log2;      /* distinguished-point table of each job: 2^table_log2 slots */
     int32_t queue_capacity;  /* merges kept per job per round */
     int32_t use_graph;       /* 1: each round is one CUDA-graph replay */
-    int32_t reserved[2];
+    int32_t rewalk_budget;   /* evaluations of f one re-walk may take per round; an unfinished
+                                re-walk resumes in the next round (0: no bound) */
+    int32_t reserved;
 } qcs_batch_params;
 
 QCS_API void qcs_batch_default_params(qcs_batch_params *p);

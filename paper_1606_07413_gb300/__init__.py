@@ -72,7 +72,7 @@ class BatchParams(ctypes.Structure):
     _fields_ = [("max_jobs", ctypes.c_int32), ("walks_per_job", ctypes.c_int32),
                 ("steps_per_round", ctypes.c_int32), ("table_log2", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("rewalk_budget", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
@@ -339,7 +339,10 @@ class Problem:
 def default_batch_params(**overrides) -> BatchParams:
     p = BatchParams()
     lib().qcs_batch_default_params(ctypes.byref(p))
+    names = {name for name, _ in BatchParams._fields_}
     for k, v in overrides.items():
+        if k not in names or k == "reserved":
+            raise TypeError(f"unknown batch parameter {k!r}")
         setattr(p, k, v)
     return p
 

@@ -25,6 +25,7 @@ namespace {
 
 constexpr uint32_t kBatchCandCap = 1024; // claw candidates kept per job per round
 constexpr int kClasses = 5;              // qubit counts 1..4 (index 0 unused)
+constexpr int kHeads = 4;                // per slot: merge queue, candidates, carried re-walks, unused
 
 struct Job {
     qcs_problem *P = nullptr;
@@ -39,6 +40,9 @@ struct Job {
     WalkState *walks = nullptr;
     Slot *table = nullptr;
     Pair *queue = nullptr;
+    Pending *pend[2] = {nullptr, nullptr}; // re-walks carried between rounds (double-buffered)
+    int pp = 0;                            // pend[pp] feeds the next round
+    uint32_t pend_n = 0;
     std::chrono::steady_clock::time_point t0;
 };
 
@@ -54,7 +58,7 @@ struct qcs_batch {
     // pooled device arrays and their pinned host mirrors
     WalkLaunch *dJobs = nullptr, *hJobs = nullptr;
     unsigned long long *dCounters = nullptr, *hCounters = nullptr; // [slot][C_NCOUNTERS]
-    uint32_t *dHeads = nullptr, *hHeads = nullptr;                 // [slot][2]
+    uint32_t *dHeads = nullptr, *hHeads = nullptr;                 // [slot][kHeads]
     Cand *dCands = nullptr, *hCands = nullptr;                     // [slot][kBatchCandCap]
     uint32_t *dTasks = nullptr, *hTasks = nullptr;                 // [class][2 * max_tasks]
     uint32_t *dIds = nullptr, *hIds = nullptr;                     // [class][max_jobs]
@@ -75,7 +79,7 @@ namespace {
 size_t job_bytes(const qcs_batch_params &bp)
 {
     return sizeof(WalkState) * (size_t)bp.walks_per_job + (sizeof(Slot) << bp.table_log2) +
-           sizeof(Pair) * (size_t)bp.queue_capacity;
+           (sizeof(Pair) + 2 * sizeof(Pending)) * (size_t)bp.queue_capacity;
 }
 
 void free_job(Job &j)
@@ -83,6 +87,8 @@ void free_job(Job &j)
     cudaFree(j.walks);
     cudaFree(j.table);
     cudaFree(j.queue);
+    cudaFree(j.pend[0]);
+    cudaFree(j.pend[1]);
     j = Job();
 }
 
@@ -162,10 +168,10 @@ int begin_level(qcs_batch *B, Job &j, int slot)
     w.table = j.table;
     w.table_mask = ((uint64_t)1 << j.jp.table_log2) - 1;
     w.queue = j.queue;
-    w.qhead = B->dHeads + 2 * slot;
+    w.qhead = B->dHeads + kHeads * slot;
     w.qcap = (uint32_t)j.jp.queue_capacity;
     w.cands = B->dCands + (size_t)slot * kBatchCandCap;
-    w.ccount = B->dHeads + 2 * slot + 1;
+    w.ccount = B->dHeads + kHeads * slot + 1;
     w.ccap = kBatchCandCap;
     w.counters = B->dCounters + (size_t)slot * C_NCOUNTERS;
     cudaError_t e = cudaMemsetAsync(j.table, 0xFF, sizeof(Slot) << j.jp.table_log2, B->s);
@@ -174,6 +180,7 @@ int begin_level(qcs_batch *B, Job &j, int slot)
     B->hJobs[slot] = w;
     j.in_version = 0;
     j.need_begin = false;
+    j.pend_n = 0; // re-walks of the previous function version do not carry over
     std::lock_guard<std::mutex> g(P->mu);
     P->res.k = j.k;
     P->res.version = j.version;
@@ -212,7 +219,7 @@ int enqueue_round(qcs_batch *B)
                                 cudaMemcpyHostToDevice, s);
     if (!e) e = cudaMemcpyAsync(B->dIds, B->hIds, sizeof(uint32_t) * kClasses * J, cudaMemcpyHostToDevice, s);
     if (!e) e = cudaMemcpyAsync(B->dCounts, B->hCounts, sizeof(uint32_t) * kClasses * 2, cudaMemcpyHostToDevice, s);
-    if (!e) e = cudaMemsetAsync(B->dHeads, 0, sizeof(uint32_t) * 2 * J, s);
+    if (!e) e = cudaMemsetAsync(B->dHeads, 0, sizeof(uint32_t) * kHeads * J, s);
     if (!e) e = cudaMemsetAsync(B->dCounters, 0, sizeof(unsigned long long) * C_NCOUNTERS * J, s);
     if (!e) e = cudaEventRecord(B->fork, s);
     for (int c = 1; c < kClasses && !e; c++) {
@@ -226,7 +233,7 @@ int enqueue_round(qcs_batch *B)
     }
     if (!e) e = cudaMemcpyAsync(B->hCounters, B->dCounters, sizeof(unsigned long long) * C_NCOUNTERS * J,
                                 cudaMemcpyDeviceToHost, s);
-    if (!e) e = cudaMemcpyAsync(B->hHeads, B->dHeads, sizeof(uint32_t) * 2 * J, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(B->hHeads, B->dHeads, sizeof(uint32_t) * kHeads * J, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(B->hCands, B->dCands, sizeof(Cand) * kBatchCandCap * J, cudaMemcpyDeviceToHost, s);
     return e ? fail(e) : QCS_OK;
 }
@@ -237,6 +244,10 @@ void collect_job(Job &j, const unsigned long long *c, const uint32_t *heads, con
     qcs_problem *P = j.P;
     const int k = j.k, h = k / 2;
     const uint32_t npairs = std::min(heads[0], (uint32_t)j.jp.queue_capacity);
+    // re-walks that ran out of budget resume from the other buffer next round
+    const uint32_t carried = heads[2];
+    j.pend_n = std::min(carried, (uint32_t)j.jp.queue_capacity);
+    j.pp ^= 1;
     const uint32_t ncand = std::min(heads[1], kBatchCandCap);
     uint32_t paulis[16] = {0};
     PMat Dh;
@@ -266,7 +277,7 @@ void collect_job(Job &j, const unsigned long long *c, const uint32_t *heads, con
         R.abandoned += (int64_t)c[C_ABANDONED];
         R.dropped += (int64_t)c[C_EVICTED];
         R.merges += (int64_t)npairs;
-        R.queue_overflow += (int64_t)(c[C_PAIRS] - npairs);
+        R.queue_overflow += (int64_t)(c[C_PAIRS] - npairs) + (int64_t)(carried - j.pend_n);
         R.robin_hood += (int64_t)c[C_CLS0 + QCS_MERGE_ROBIN_HOOD];
         R.trivial += (int64_t)c[C_CLS0 + QCS_MERGE_TRIVIAL];
         R.same_side += (int64_t)c[C_CLS0 + QCS_MERGE_SAME_SIDE];
@@ -337,6 +348,7 @@ void qcs_batch_default_params(qcs_batch_params *p)
     p->table_log2 = 18;
     p->queue_capacity = 1 << 16;
     p->use_graph = 1;
+    p->rewalk_budget = 64;
 }
 
 int qcs_batch_create(const qcs_batch_params *pin, void *stream, qcs_batch **out)
@@ -347,7 +359,7 @@ int qcs_batch_create(const qcs_batch_params *pin, void *stream, qcs_batch **out)
     if (pin) bp = *pin; else qcs_batch_default_params(&bp);
     if (bp.max_jobs < 1 || bp.max_jobs > 65536 || bp.walks_per_job < 16 ||
         (uint32_t)bp.walks_per_job > kMaxWalks || bp.walks_per_job % 16 || bp.steps_per_round < 1 ||
-        bp.table_log2 < 4 || bp.table_log2 > 30 || bp.queue_capacity < 16)
+        bp.table_log2 < 4 || bp.table_log2 > 30 || bp.queue_capacity < 16 || bp.rewalk_budget < 0)
         return QCS_ERR_ARG;
     qcs_batch *B = new (std::nothrow) qcs_batch();
     if (!B) return QCS_ERR_NOMEM;
@@ -382,8 +394,8 @@ int qcs_batch_create(const qcs_batch_params *pin, void *stream, qcs_batch **out)
     pin_((void **)&B->hJobs, sizeof(WalkLaunch) * J);
     dev((void **)&B->dCounters, sizeof(unsigned long long) * C_NCOUNTERS * J);
     pin_((void **)&B->hCounters, sizeof(unsigned long long) * C_NCOUNTERS * J);
-    dev((void **)&B->dHeads, sizeof(uint32_t) * 2 * J);
-    pin_((void **)&B->hHeads, sizeof(uint32_t) * 2 * J);
+    dev((void **)&B->dHeads, sizeof(uint32_t) * kHeads * J);
+    pin_((void **)&B->hHeads, sizeof(uint32_t) * kHeads * J);
     dev((void **)&B->dCands, sizeof(Cand) * kBatchCandCap * J);
     pin_((void **)&B->hCands, sizeof(Cand) * kBatchCandCap * J);
     dev((void **)&B->dTasks, sizeof(uint32_t) * kClasses * 2 * B->max_tasks);
@@ -441,6 +453,8 @@ int qcs_batch_add(qcs_batch *B, qcs_problem *P, int *job)
     cudaError_t e = cudaMalloc(&j.walks, sizeof(WalkState) * (size_t)j.jp.walks);
     if (!e) e = cudaMalloc(&j.table, sizeof(Slot) << j.jp.table_log2);
     if (!e) e = cudaMalloc(&j.queue, sizeof(Pair) * (size_t)j.jp.queue_capacity);
+    if (!e) e = cudaMalloc(&j.pend[0], sizeof(Pending) * (size_t)j.jp.queue_capacity);
+    if (!e) e = cudaMalloc(&j.pend[1], sizeof(Pending) * (size_t)j.jp.queue_capacity);
     if (e) {
         free_job(j);
         return e == cudaErrorMemoryAllocation ? QCS_ERR_NOMEM : fail(e);
@@ -483,6 +497,14 @@ int qcs_batch_round(qcs_batch *B, int *n_active)
             continue;
         }
         if (j.need_begin && (rc = begin_level(B, j, (int)slot))) return rc;
+        // this round's re-walk budget and the carried re-walks it resumes
+        WalkLaunch &w = B->hJobs[slot];
+        w.rewalk_budget = (uint32_t)B->bp.rewalk_budget;
+        w.pend_cap = (uint32_t)j.jp.queue_capacity;
+        w.pend_in = j.pend[j.pp];
+        w.pend_in_n = j.pend_n;
+        w.pend_out = j.pend[j.pp ^ 1];
+        w.pend_out_n = B->dHeads + kHeads * slot + 2;
         active++;
     }
     if (n_active) *n_active = active;
@@ -513,7 +535,7 @@ int qcs_batch_round(qcs_batch *B, int *n_active)
     for (size_t slot = 0; slot < B->jobs.size(); slot++) {
         Job &j = B->jobs[slot];
         if (!j.active) continue;
-        collect_job(j, B->hCounters + slot * C_NCOUNTERS, B->hHeads + 2 * slot,
+        collect_job(j, B->hCounters + slot * C_NCOUNTERS, B->hHeads + kHeads * slot,
                     B->hCands + slot * kBatchCandCap, B->s);
         if (!j.active) {
             publish_status(j);

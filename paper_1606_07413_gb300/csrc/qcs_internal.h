@@ -89,6 +89,13 @@ struct Cand {
     uint32_t chunk, pad;
 };
 
+// A re-walk carried over to the next round (batched search): the two
+// states, the steps each trail still has to its shared point, the chunk.
+struct Pending {
+    unsigned long long a, b;
+    uint32_t la, lb, chunk, pad;
+};
+
 struct RewalkOut {
     int32_t cls;    // QCS_MERGE_* (claw = candidate before the exact check)
     uint32_t chunk; // chunk of the pair (odd k)
@@ -130,6 +137,14 @@ struct WalkLaunch {
     uint32_t *ccount;
     uint32_t ccap;
     unsigned long long *counters;
+    // batched search: a re-walk gets rewalk_budget evaluations of f per
+    // round (0: no bound); unfinished ones go to pend_out and come back as
+    // pend_in in the next round, before that round's new merges
+    uint32_t rewalk_budget;
+    uint32_t pend_in_n, pend_cap;
+    const Pending *pend_in;
+    Pending *pend_out;
+    uint32_t *pend_out_n;
 };
 
 // Many jobs in one launch: per qubit count, the device list of tasks

@@ -703,52 +703,74 @@ __global__ void k_init_walks(WalkLaunch w)
 }
 
 // Sec. 3, Fig. 2: align the longer trail, step both until the images agree,
-// and classify the two distinct preimages.  Lengths are bounded by the
-// maximum trail length, so both loops end.
+// and classify the two distinct preimages.  At most `budget` evaluations of f
+// (0: no bound); returns false with (a, la, b, lb) advanced when the budget
+// ends first, so the re-walk can resume from there.  Lengths are bounded by
+// the maximum trail length, so the loops end.
 template <int NQ>
-__device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa, uint32_t la, uint64_t sb,
-                                uint32_t lb, const Smem<NQ> &sm, Lanes g, unsigned long long *fevals = nullptr)
+__device__ bool rewalk_resume(const LevelCtx &lv, uint32_t chunk, uint64_t &a, uint32_t &la, uint64_t &b,
+                              uint32_t &lb, uint32_t budget, const Smem<NQ> &sm, Lanes g, unsigned long long &nf,
+                              RewalkOut &r)
 {
-    RewalkOut r;
-    unsigned long long nf = 0;
     r.chunk = chunk;
     if (la > kMaxRewalkLen || lb > kMaxRewalkLen) {
         r.cls = 5;
-        r.a = sa;
-        r.b = sb;
-        return r;
+        r.a = a;
+        r.b = b;
+        return true;
     }
     if (la < lb) {
-        uint64_t tx = sa; sa = sb; sb = tx;
+        uint64_t tx = a; a = b; b = tx;
         uint32_t tl = la; la = lb; lb = tl;
     }
-    uint64_t a = sa, b = sb;
-    for (uint32_t s = 0; s < la - lb; s++) a = warp_step<NQ>(a, chunk, lv, sm, g);
-    nf += la - lb;
-    if (fevals) *fevals += nf;
+    uint32_t used = 0;
+    while (la > lb) {
+        if (budget && used >= budget) return false;
+        a = warp_step<NQ>(a, chunk, lv, sm, g);
+        la--;
+        used++;
+        nf++;
+    }
+    // aligned: equal states mean one start lies on the other trail (after a
+    // lockstep step this cannot first happen, the images are compared there)
     if (a == b) {
         r.cls = 0; // Robin Hood
         r.a = r.b = a;
-        return r;
+        return true;
     }
-    for (uint32_t s = 0; s < lb; s++) {
+    while (lb > 0) {
+        if (budget && used + 2 > budget) return false;
         const uint64_t fa = warp_step<NQ>(a, chunk, lv, sm, g);
         const uint64_t fb = warp_step<NQ>(b, chunk, lv, sm, g);
-        if (fevals) *fevals += 2;
+        used += 2;
+        nf += 2;
         if (fa == fb) {
             const Decoded da = decode(a, lv), db = decode(b, lv);
             r.a = a;
             r.b = b;
             if (da.side == db.side) r.cls = (da.qpack == db.qpack) ? 1 : 2; // trivial / same side
             else r.cls = 3;                                          // claw candidate
-            return r;
+            return true;
         }
         a = fa;
         b = fb;
+        la--;
+        lb--;
     }
     r.cls = 5; // no merge
     r.a = a;
     r.b = b;
+    return true;
+}
+
+template <int NQ>
+__device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa, uint32_t la, uint64_t sb,
+                                uint32_t lb, const Smem<NQ> &sm, Lanes g, unsigned long long *fevals = nullptr)
+{
+    RewalkOut r;
+    unsigned long long nf = 0;
+    rewalk_resume<NQ>(lv, chunk, sa, la, sb, lb, 0, sm, g, nf, r);
+    if (fevals) *fevals += nf;
     return r;
 }
 
@@ -761,17 +783,46 @@ __device__ __forceinline__ void rewalk_job(const WL &w, const Smem<NQ> &sm, uint
     unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0; // per class, in registers
     unsigned long long fev = 0;
     for (uint32_t p = p_begin; p < p_end; p += p_stride) {
-        const Pair P = w.queue[p];
-        uint32_t wa, sa, la, wb, sb, lb;
-        split_ref(P.ref_a, wa, sa, la);
-        split_ref(P.ref_b, wb, sb, lb);
-        const uint64_t xa = trail_start(w.lv, wa, sa), xb = trail_start(w.lv, wb, sb);
-        const uint32_t ca = trail_chunk(w.lv, xa), cb = trail_chunk(w.lv, xb);
+        // the job's work list: first the re-walks carried from the previous
+        // round (batched search), then this launch's queued merges
+        uint64_t xa, xb;
+        uint32_t la, lb, ca, cb;
+        if (p < w.pend_in_n) {
+            const Pending q = w.pend_in[p];
+            xa = q.a;
+            xb = q.b;
+            la = q.la;
+            lb = q.lb;
+            ca = cb = q.chunk;
+        } else {
+            const Pair P = w.queue[p - w.pend_in_n];
+            uint32_t wa, sa, wb, sb;
+            split_ref(P.ref_a, wa, sa, la);
+            split_ref(P.ref_b, wb, sb, lb);
+            xa = trail_start(w.lv, wa, sa);
+            xb = trail_start(w.lv, wb, sb);
+            ca = trail_chunk(w.lv, xa);
+            cb = trail_chunk(w.lv, xb);
+        }
         RewalkOut r;
         if (ca != cb) { // the same value reached in two chunks' functions: no merge
             r.cls = 5;
-        } else {
-            r = rewalk_one<NQ>(w.lv, ca, xa, la, xb, lb, sm, g, &fev);
+        } else if (!rewalk_resume<NQ>(w.lv, ca, xa, la, xb, lb, w.rewalk_budget, sm, g, fev, r)) {
+            // budget spent: carry the re-walk to the next round (if there is room)
+            if (g.sub == 0) {
+                const uint32_t idx = atomicAdd(w.pend_out_n, 1u);
+                if (idx < w.pend_cap) {
+                    Pending q;
+                    q.a = xa;
+                    q.b = xb;
+                    q.la = la;
+                    q.lb = lb;
+                    q.chunk = ca;
+                    q.pad = 0;
+                    w.pend_out[idx] = q;
+                }
+            }
+            continue;
         }
         c0 += r.cls == 0;
         c1 += r.cls == 1;
@@ -805,7 +856,7 @@ template <int NQ>
 __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_rewalk_pairs(WalkLaunch w)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const uint32_t cnt = min(*w.qhead, w.qcap);
+    const uint32_t cnt = w.pend_in_n + min(*w.qhead, w.qcap);
     if (cnt <= blockIdx.x * Geo<NQ>::WALKS) return; // no pair for this CTA (uniform)
     const Smem<NQ> sm = stage<NQ>(w.lv, smem_raw);
     rewalk_job<NQ>(w, sm, blockIdx.x * Geo<NQ>::WALKS + group_in_cta<NQ>(), cnt, gridDim.x * Geo<NQ>::WALKS,
@@ -824,14 +875,14 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_rewalk_batch(BatchArgs a)
     uint64_t total = 0;
     for (uint32_t j = 0; j < nj; j++) {
         const WalkLaunch &w = a.jobs[a.job_ids[j]];
-        total += min(*w.qhead, w.qcap);
+        total += w.pend_in_n + min(*w.qhead, w.qcap);
     }
     const uint64_t lo = total * blockIdx.x / gridDim.x, hi = total * (blockIdx.x + 1) / gridDim.x;
     const Lanes g = thread_lanes<NQ>();
     uint64_t base = 0;
     for (uint32_t j = 0; j < nj && base < hi; j++) {
         const int job = (int)a.job_ids[j];
-        const uint32_t cnt = min(*a.jobs[job].qhead, a.jobs[job].qcap);
+        const uint32_t cnt = a.jobs[job].pend_in_n + min(*a.jobs[job].qhead, a.jobs[job].qcap);
         if (base + cnt <= lo) {
             base += cnt;
             continue;

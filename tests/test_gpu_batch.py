@@ -34,7 +34,10 @@ def run_to_end(batch, max_rounds=400):
     return False
 
 
-def test_batch_reaches_optimal_tcounts(orc, dev):
+@pytest.mark.parametrize("budget", [0, 3, 64])
+def test_batch_reaches_optimal_tcounts(orc, dev, budget):
+    # budget: evaluations of f a re-walk may take per round (0: no bound);
+    # a re-walk that runs out resumes in the next round
     cases = []
     g1, _ = W.config_target(1)
     cases.append((2, g1, 3))
@@ -46,12 +49,12 @@ def test_batch_reaches_optimal_tcounts(orc, dev):
         gs, _ = W.seeded_target(2, 2, s)
         cases.append((2, gs, 3))
     probs, jobs = [], []
-    with Q.Batch(small_params(), torch.cuda.Stream()) as batch:
+    with Q.Batch(small_params(rewalk_budget=budget), torch.cuda.Stream()) as batch:
         for n, gates, kmax in cases:
             p = Q.Problem.from_circuit(n, gates, kmax, Q.default_params(n))
             probs.append(p)
             jobs.append(batch.add(p))
-        assert run_to_end(batch)
+        assert run_to_end(batch, 4000)
         for (n, gates, kmax), j in zip(cases, jobs):
             r = batch.poll(j)
             C = orc.channel_from_circuit(n, gates)
