@@ -723,44 +723,65 @@ __device__ bool rewalk_resume(const LevelCtx &lv, uint32_t chunk, uint64_t &a, u
         uint64_t tx = a; a = b; b = tx;
         uint32_t tl = la; la = lb; lb = tl;
     }
+    // one evaluation of f per iteration through a single call site (the step
+    // is large at n = 4; inlining it once keeps the kernel's code compact):
+    // align the longer trail, then step a and b in turn
     uint32_t used = 0;
-    while (la > lb) {
-        if (budget && used >= budget) return false;
-        a = warp_step<NQ>(a, chunk, lv, sm, g);
-        la--;
+    uint64_t fa = 0;
+    bool second = false, checked = false;
+    for (;;) {
+        uint64_t x;
+        if (la > lb) {
+            if (budget && used >= budget) return false;
+            x = a;
+        } else if (!second) {
+            // aligned: equal states mean one start lies on the other trail
+            // (after a lockstep step this cannot first happen: the images
+            // are compared there)
+            if (!checked) {
+                checked = true;
+                if (a == b) {
+                    r.cls = 0; // Robin Hood
+                    r.a = r.b = a;
+                    return true;
+                }
+            }
+            if (lb == 0) {
+                r.cls = 5; // no merge
+                r.a = a;
+                r.b = b;
+                return true;
+            }
+            if (budget && used + 2 > budget) return false;
+            x = a;
+        } else {
+            x = b;
+        }
+        const uint64_t y = warp_step<NQ>(x, chunk, lv, sm, g);
         used++;
         nf++;
-    }
-    // aligned: equal states mean one start lies on the other trail (after a
-    // lockstep step this cannot first happen, the images are compared there)
-    if (a == b) {
-        r.cls = 0; // Robin Hood
-        r.a = r.b = a;
-        return true;
-    }
-    while (lb > 0) {
-        if (budget && used + 2 > budget) return false;
-        const uint64_t fa = warp_step<NQ>(a, chunk, lv, sm, g);
-        const uint64_t fb = warp_step<NQ>(b, chunk, lv, sm, g);
-        used += 2;
-        nf += 2;
-        if (fa == fb) {
-            const Decoded da = decode(a, lv), db = decode(b, lv);
-            r.a = a;
-            r.b = b;
-            if (da.side == db.side) r.cls = (da.qpack == db.qpack) ? 1 : 2; // trivial / same side
-            else r.cls = 3;                                          // claw candidate
-            return true;
+        if (la > lb) {
+            a = y;
+            la--;
+        } else if (!second) {
+            fa = y;
+            second = true;
+        } else {
+            second = false;
+            if (fa == y) {
+                const Decoded da = decode(a, lv), db = decode(b, lv);
+                r.a = a;
+                r.b = b;
+                if (da.side == db.side) r.cls = (da.qpack == db.qpack) ? 1 : 2; // trivial / same side
+                else r.cls = 3;                                          // claw candidate
+                return true;
+            }
+            a = fa;
+            b = y;
+            la--;
+            lb--;
         }
-        a = fa;
-        b = fb;
-        la--;
-        lb--;
     }
-    r.cls = 5; // no merge
-    r.a = a;
-    r.b = b;
-    return true;
 }
 
 template <int NQ>
