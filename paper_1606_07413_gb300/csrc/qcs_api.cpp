@@ -559,6 +559,12 @@ int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
     const uint64_t n_w = xi_h * ((k & 1) ? xi : 1);
     uint64_t slots = 1024;
     while (slots < 2 * xi_h) slots <<= 1;
+    {
+        // the key table must fit: refuse before allocating
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b));
+        if (sizeof(CertSlot) * slots > free_b) return QCS_ERR_NOMEM;
+    }
     constexpr uint32_t kCap = 1u << 16;
     constexpr uint64_t kSlice = 1ull << 22;
     CertArgs a{};

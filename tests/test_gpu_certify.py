@@ -54,6 +54,16 @@ def test_certify_rejects_bad_levels(dev):
                 prob.certify_level(k)
 
 
+def test_certify_refuses_a_key_table_beyond_device_memory(dev):
+    # n = 4, level 12: 255^6 V points would need a 2^49-slot table; the host
+    # refuses before allocating or launching anything
+    gates, _ = W.seeded_target(4, 3, 8)
+    with Q.Problem.from_circuit(4, gates, 12, Q.default_params(4)) as prob:
+        with pytest.raises(Q.QcsError) as ei:
+            prob.certify_level(12)
+        assert ei.value.code == Q.ERR_NOMEM
+
+
 @pytest.mark.parametrize("n,t,seed", [(2, 5, 91), (2, 6, 92), (3, 4, 93), (3, 5, 94)])
 def test_ladder_settles_small_levels_exactly(orc, dev, n, t, seed):
     # walks far too short to find anything: the exhaustive pass decides
