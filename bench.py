@@ -88,6 +88,17 @@ def walk_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on the GB300s (MEASURED_PEAKS.json
+    beside this file), else the fallback figure of one earlier measurement."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (no measured peaks file)"
+
+
 def walk_traffic():
     if WALK_TRAFFIC["source_sha256_16"] != walk_source_hash():
         return None  # the kernel changed since the counters were taken
@@ -463,9 +474,16 @@ def run_ours(args):
     walk_s = sum(walk_ms) / 1e3
     achieved = w_steps * 2 * d * d / walk_s
     peak = 2 * dp4a_per_s
+    traffic = walk_traffic()
+    hbm_peak, hbm_src = measured_hbm_gbs()
+    hbm = None
+    if traffic is not None:
+        per_launch_s = walk_s / max(1, args.steps)
+        hbm = {"achieved_gbs": traffic / per_launch_s / 1e9, "peak_gbs": hbm_peak,
+               "frac": traffic / per_launch_s / 1e9 / hbm_peak, "peak_source": hbm_src}
     roof = {"bound": "alu", "unit": "Gop/s", "kernel": "k_walks<3>",
             "achieved": achieved / 1e9, "peak": peak / 1e9, "frac": achieved / peak,
-            "traffic": walk_traffic(), "traffic_unit": "bytes per launch",
+            "traffic": traffic, "traffic_unit": "bytes per launch", "hbm": hbm,
             "peak_source": "2 x measured dp4a rate (qcs_peak_idp4a, this run: "
                            f"{dp4a_per_s / 1e9:.0f} G dp4a/s); IMAD measured {imad_per_s / 1e9:.0f} Gop/s",
             "algorithmic_ops": f"2*d^2 = {2 * d * d} 16-bit-weight multiply-adds per W-side walk step "
