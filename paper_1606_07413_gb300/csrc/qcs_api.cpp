@@ -372,7 +372,6 @@ int level_begin(qcs_problem *P, int k, uint32_t version, int dp_bits, uint32_t n
     L.k = k;
     L.h = k / 2;
     L.dp_bits = dp_bits;
-    L.xi = (uint64_t)(P->D - 1);
     WalkLaunch &w = L.w;
     w = WalkLaunch{};
     w.lv = make_level(P, k, version, dp_bits);
@@ -429,7 +428,6 @@ int level_collect(qcs_problem *P, cudaStream_t s, bool *got, uint64_t *steps)
     CK(cudaStreamSynchronize(s));
     const auto &L = P->lvl;
     const int k = L.k, h = L.h;
-    const uint64_t xi = L.xi;
     const unsigned long long *c = P->hCounters;
     const uint32_t npairs = std::min(P->hQhead[0], L.w.qcap);
     const uint32_t ncand = std::min(P->hQhead[1], kCandCap);

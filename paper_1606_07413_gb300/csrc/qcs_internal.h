@@ -294,7 +294,6 @@ struct qcs_problem {
     struct {
         bool active = false;
         int k = 0, h = 0, dp_bits = 0;
-        uint64_t xi = 0;
         qcs::WalkLaunch w{};
     } lvl;
 };
