@@ -205,14 +205,19 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ other workloads
-def level_throughput(Q, W, torch, cfg, k, steps, stream, launches=3, alu_per_s=None):
-    """Walk steps/s of one single-target level launch at a configured size."""
+def level_throughput(Q, W, torch, cfg, k, steps, stream, launches=3, alu_per_s=None, dp_bits=None, table_log2=None):
+    """Walk steps/s of one single-target level launch at a configured size
+    (dp_bits / table_log2 override the configuration's theta and table), and
+    the distinguished-point table's algorithmic traffic: one 16-byte
+    exchange (read and write) per distinguished point, 24 bytes per queued
+    merge."""
     c = W.CONFIGS[cfg]
     gates, _ = W.config_target(cfg)
-    p = Q.default_params(c["n"], walks=c["walks"], state_bits=c["L"], dp_bits=c["dtheta"],
-                         table_log2=min(c["table_log2"], 24))
+    dpb = dp_bits or c["dtheta"]
+    p = Q.default_params(c["n"], walks=c["walks"], state_bits=c["L"], dp_bits=dpb,
+                         table_log2=table_log2 or min(c["table_log2"], 24))
     prob = Q.Problem.from_circuit(c["n"], gates, c["k_max"], p)
-    prob.level_begin(k, 0, c["dtheta"], stream=stream)
+    prob.level_begin(k, 0, dpb, stream=stream)
     prob.level_walk(steps, stream); prob.level_rewalk(stream); prob.level_collect(stream)
     r0 = prob.poll()
     ms = []
@@ -228,8 +233,10 @@ def level_throughput(Q, W, torch, cfg, k, steps, stream, launches=3, alu_per_s=N
     prob.close()
     d = 4 ** c["n"] - 1
     walk_s = sum(ms) / 1e3
-    out = {"workload": f"n{c['n']}_level{k}_walks{c['walks']}_L{c['L']}_theta2^-{c['dtheta']}",
-           "walk_steps_per_s": (r1["steps"] - r0["steps"]) / walk_s}
+    table_bytes = 32 * (r1["dps"] - r0["dps"]) + 24 * (r1["merges"] - r0["merges"])
+    out = {"workload": f"n{c['n']}_level{k}_walks{c['walks']}_L{c['L']}_theta2^-{dpb}",
+           "walk_steps_per_s": (r1["steps"] - r0["steps"]) / walk_s,
+           "table_gbs": table_bytes / walk_s / 1e9}
     if alu_per_s:  # multiply-adds per second at the contraction's peak (IMAD for n <= 2; 2 x dp4a for n >= 3)
         out["alu_frac"] = (r1["w_steps"] - r0["w_steps"]) * 2 * d * d / walk_s / alu_per_s
     return out
@@ -536,6 +543,9 @@ def run_ours(args):
                 "config3_time_to_optimal": config3_time_to_optimal(Q, W, stream, "exhaustive"),
                 "n2_level3": level_throughput(Q, W, torch, 1, 3, 512, stream, alu_per_s=imad_per_s),
                 "n4_level7": level_throughput(Q, W, torch, 3, 7, 16, stream, alu_per_s=2 * dp4a_per_s),
+                # the table at its busiest: half the points distinguished
+                "n3_level5_theta_half": level_throughput(Q, W, torch, 2, 5, 64, stream, alu_per_s=2 * dp4a_per_s,
+                                                         dp_bits=1, table_log2=26),
             }
     prob.close()
 
