@@ -190,7 +190,7 @@ __device__ __forceinline__ uint32_t dp4a_us(uint32_t a, uint32_t b, uint32_t c)
 // u_0, u_1, and sum_i u_i c_i = sum_i u_{i,0} c_i + 2^8 sum_i u_{i,1} c_i
 // (mod 2^16): an exact identity whose inner sums are byte dot products.  The
 // plane words of quad q (rows 4q .. 4q+3) are written, in place of the rows
-// (uint2 per row) in the warp's exchange buffer, as uint4 number q:
+// (uint2 per row) in the lane group's exchange buffer, as uint4 number q:
 // (a plane 0, a plane 1, b plane 0, b plane 1), each word holding that byte
 // of the four rows' weights.
 template <int NQ>
