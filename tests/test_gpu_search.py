@@ -206,3 +206,18 @@ def test_table1_circuits_have_tcount_7(orc, dev, name):
     assert Q.verify_decomposition(3, u, 0, res["paulis"])
     print(f"{name}: T-count 7 in {time.time() - t0:.2f}s, {res['steps']} steps")
     prob.close()
+
+
+@pytest.mark.parametrize("version_factor,queue", [(1, 1 << 20), (2, 64)])
+def test_walk_alone_finds_the_optimum_under_version_rotation_and_a_tiny_queue(orc, dev, version_factor, queue):
+    # the walk alone (no exhaustive pass): frequent function versions, or a
+    # tiny merge queue (the plan shrinks the launches to fit it), still reach
+    # the optimum
+    gates, _ = W.config_target(1)
+    C = orc.channel_from_circuit(2, gates)
+    t_exact, _ = orc.mitm_tcount(C, 3)
+    prob, res = search(2, gates, 3, version_factor=version_factor, queue_capacity=queue, exhaustive_log2=0,
+                       budget_factor=256)
+    assert res["status_name"] == "found" and res["t_count"] == t_exact
+    assert orc.verify(C, res["paulis"])
+    prob.close()
