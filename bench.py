@@ -73,9 +73,10 @@ def workload_config(c):
 
 # ------------------------------------------------------------------ ncu record
 # DRAM traffic of one k_walks<3> launch of the headline workload, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
-# kernel source it was taken on (hash of the walk kernel's source files)
-WALK_TRAFFIC = {"bytes_per_launch": 2184960, "source_sha256_16": "067d582b358e7167"}
+# capture (dram__bytes_read.sum + dram__bytes_write.sum, mean of the two
+# captured launches), valid only for the kernel source it was taken on (hash
+# of the walk kernel's source files)
+WALK_TRAFFIC = {"bytes_per_launch": 2736128, "source_sha256_16": "f960478d9a08c204"}
 
 
 def walk_source_hash() -> str:
@@ -369,6 +370,22 @@ def config3_time_to_optimal(Q, W, stream, mode="exhaustive", table_log2=30, queu
             "table_log2": None if mode == "exhaustive" else table_log2}
 
 
+def exhaustive_level_pass(Q, W, stream, n=4, k=7, t=9, seed=4009):
+    """One whole exhaustive pass over level k of a seeded n-qubit target whose
+    sde is t > k, so no claw exists and every point is evaluated: the worst
+    case of the pass at config 3's level (n = 4, k = 7: 255^3 stored points,
+    255^4 streamed)."""
+    gates, _ = W.seeded_target(n, t, seed)
+    with Q.Problem.from_circuit(n, gates, max(k, t), Q.default_params(n, exhaustive_log2=34)) as prob:
+        t0 = time.perf_counter()
+        has = prob.certify_level(k, stream=stream)
+        secs = time.perf_counter() - t0
+        r = prob.poll()
+    return {"workload": f"n{n}_level{k}_exhaustive (seeded target of sde {r['sde']}, no claw)",
+            "seconds": secs, "points": r["cert_points"], "points_per_s": r["cert_points"] / secs,
+            "has_claw": bool(has), "certified_levels": r["certified_levels"]}
+
+
 def run_serving(Q, W, torch, stream, tuned, n_requests=2000, rate=50.0, budget_bytes=2 << 30,
                 deadline_s=10.0, drain_s=15.0):
     """Config 5: a Poisson stream of seeded targets replayed in real time into
@@ -546,6 +563,7 @@ def run_ours(args):
                 "serving": run_serving(Q, W, torch, stream, batched["autotuned"]),
                 "table1_circuits": table1_circuits(Q, stream),
                 "config3_time_to_optimal": config3_time_to_optimal(Q, W, stream, "exhaustive"),
+                "n4_level7_exhaustive_pass": exhaustive_level_pass(Q, W, stream),
                 "n2_level3": level_throughput(Q, W, torch, 1, 3, 512, stream, alu_per_s=imad_per_s),
                 "n4_level7": level_throughput(Q, W, torch, 3, 7, 16, stream, alu_per_s=2 * dp4a_per_s),
                 # the table at its busiest: half the points distinguished

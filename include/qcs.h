@@ -174,20 +174,26 @@ QCS_API int qcs_create_problem_circuit(int n_qubits, const int32_t *gates, int n
 QCS_API int qcs_run_walks(qcs_problem *prob, uint64_t step_budget, void *cuda_stream);
 
 /* Exhaustive meet-in-the-middle pass over level k (Sec. 2 Eq. mitm, the
- * deterministic counterpart of the collision search): every V point
- * R(q_h)..R(q_1) and every W point R(q_1)^T..R(q_h)^T [R(c)^T] C (all xi^h
- * rotation tuples, all xi chunks c for odd k) is evaluated on the GPU with the
- * walk's own product and fingerprint canonical form.  V points go into a
- * device hash table of coset keys, W points probe it, and every key match is
- * checked exactly on the host (its decomposition is verified: D^ must be a
- * signed permutation).  Equal cosets always have equal keys, so when no match
- * verifies, level k has no decomposition: *has_claw = 0 is a proof.  With
- * *has_claw = 1 the decomposition is recorded as by a FOUND search.  Runs
- * synchronously on cuda_stream (NULL = legacy default stream); allocates
- * 16 * 2^ceil(log2(2 xi^h)) bytes of table for the call.  k in [2, k_max].
- * Errors: QCS_ERR_ARG, QCS_ERR_BUSY (a search is running), QCS_ERR_NOMEM,
- * QCS_ERR_OVERFLOW (more than 65536 key matches in one slice of 2^22 W points
- * and none verified: inconclusive), QCS_ERR_CUDA. */
+ * deterministic counterpart of the collision search): the k rotations are
+ * split between a product of rotations alone (V side) and a product of
+ * transposed rotations applied to C (W side), and every point of both sides
+ * is evaluated on the GPU with the walk's own product and fingerprint
+ * canonical form.  Even k, or sde(C) = 0: V = R(q_h)..R(q_1) and W =
+ * R(q_1)^T..R(q_h)^T [R(c)^T] C (all xi^h tuples, all xi chunks c for odd
+ * k).  Odd k with sde(C) >= 1: V = R(r_(h+1))..R(r_1) (xi^(h+1) points) and
+ * W = R(s_1)^T..R(s_h)^T C (xi^h points), so the larger side needs no
+ * product with C.  The xi^h points of the smaller side go into a device
+ * hash table of coset keys, the other side's points probe it, and every key
+ * match is checked exactly on the host (its decomposition is verified: D^
+ * must be a signed permutation).  Equal cosets always have equal keys, so
+ * when no match verifies, level k has no decomposition: *has_claw = 0 is a
+ * proof.  With *has_claw = 1 the decomposition is recorded as by a FOUND
+ * search.  Runs synchronously on cuda_stream (NULL = legacy default stream);
+ * allocates 16 * 2^ceil(log2(2 xi^h)) bytes of table for the call.  k in
+ * [2, k_max].  Errors: QCS_ERR_ARG, QCS_ERR_BUSY (a search is running),
+ * QCS_ERR_NOMEM, QCS_ERR_OVERFLOW (more than 65536 key matches in one slice
+ * of at most 2^24 probing points and none verified: inconclusive),
+ * QCS_ERR_CUDA. */
 QCS_API int qcs_certify_level(qcs_problem *prob, int k, void *cuda_stream, int *has_claw);
 
 /* Non-blocking snapshot of the search (status, level, counters, and the

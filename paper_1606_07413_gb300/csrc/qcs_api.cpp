@@ -554,7 +554,16 @@ int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
     *got = false;
     const int h = k / 2;
     const uint64_t xi = (uint64_t)(P->D - 1), xi_h = upow(xi, h);
-    const uint64_t n_w = xi_h * ((k & 1) ? xi : 1);
+    // Odd k puts 2h + 1 rotations into two products, so one side gets h + 1
+    // and has xi times the points of the other.  With a denominator in C^
+    // (E >= 1) the extra rotation goes on V: the xi^(h+1) streamed points are
+    // products V' = R(r_(h+1))..R(r_1) with no contraction against C^, and
+    // the stored xi^h points are W' = R(s_1)^T..R(s_h)^T C^, both at exponent
+    // E + h (V' raised from h + 1 by sqrt2^(E-1)).  A claw V' ~ W' is
+    // C^ ~ R(s_h)..R(s_1) R(r_(h+1))..R(r_1).  Otherwise (even k, or E = 0)
+    // V = h rotations is stored and W (with the chunk rotation) streamed.
+    const bool v_heavy = (k & 1) && P->C.E >= 1;
+    const uint64_t n_probe = xi_h * ((k & 1) ? xi : 1);
     uint64_t slots = 1024;
     while (slots < 2 * xi_h) slots <<= 1;
     {
@@ -564,14 +573,23 @@ int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
         if (sizeof(CertSlot) * slots > free_b) return QCS_ERR_NOMEM;
     }
     constexpr uint32_t kCap = 1u << 16;
-    constexpr uint64_t kSlice = 1ull << 22;
+    // probing points per launch: slices start small, so that a claw early in
+    // the stream ends the pass soon, and double up to 2^24 (about 25 ms at
+    // n = 4), so that a long pass pays little per-slice overhead
+    constexpr uint64_t kSliceMin = 1ull << 20, kSliceMax = 1ull << 24;
+    LevelCtx lv_store = make_level(P, v_heavy ? 2 * h : k, 0, P->p.dp_bits);
+    LevelCtx lv_probe = make_level(P, v_heavy ? 2 * h + 2 : k, 0, P->p.dp_bits);
+    if (v_heavy) {
+        lv_probe.K = lv_store.K; // E + h
+        lv_probe.ev = P->C.E - 1;
+    }
     CertArgs a{};
-    a.lv = make_level(P, k, 0, P->p.dp_bits);
     a.xi_h = xi_h;
     a.mask = slots - 1;
     a.cap = kCap;
-    // one hash base for every chunk, so V and W keys of a coset agree
-    const uint64_t tag = (uint64_t)P->n | ((uint64_t)k << 8) | (0xFFFFull << 16) | ((uint64_t)(uint32_t)a.lv.K << 32);
+    // one hash base for every chunk, so the keys of a coset agree on both sides
+    const uint64_t tag =
+        (uint64_t)P->n | ((uint64_t)k << 8) | (0xFFFFull << 16) | ((uint64_t)(uint32_t)lv_store.K << 32);
     a.base = smix_host(smix_host(kSeedH ^ 0xCE27u) ^ tag);
     uint32_t *hN = nullptr;
     uint64_t *hPairs = nullptr;
@@ -582,46 +600,66 @@ int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
     if (e == cudaSuccess) e = cudaMallocHost(&hPairs, sizeof(uint64_t) * 2 * kCap);
     int rc = QCS_OK;
     bool overflow = false;
-    uint64_t done_w = 0;
+    uint64_t done_probe = 0;
     if (e == cudaSuccess) e = cudaMemsetAsync(a.table, 0xFF, sizeof(CertSlot) * slots, s);
     if (e == cudaSuccess) {
-        a.side = 0;
+        a.lv = lv_store;
+        a.side = v_heavy ? 1 : 0;
+        a.insert = 1;
         a.first = 0;
         a.count = xi_h;
         e = launch_certify(a, s);
     }
-    for (uint64_t first = 0; e == cudaSuccess && first < n_w && !*got; first += kSlice) {
+    a.lv = lv_probe;
+    a.side = v_heavy ? 0 : 1;
+    a.insert = 0;
+    uint64_t slice = kSliceMin;
+    for (uint64_t first = 0; e == cudaSuccess && first < n_probe && !*got;
+         first += slice, slice = std::min(2 * slice, kSliceMax)) {
         if (P->cancel.load()) {
             rc = QCS_ERR_BUSY;
             break;
         }
-        a.side = 1;
         a.first = first;
-        a.count = std::min(kSlice, n_w - first);
+        a.count = std::min(slice, n_probe - first);
         if ((e = cudaMemsetAsync(a.n_pairs, 0, sizeof(uint32_t), s)) != cudaSuccess) break;
         if ((e = launch_certify(a, s)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(hN, a.n_pairs, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
-        if ((e = cudaMemcpyAsync(hPairs, a.pairs, sizeof(uint64_t) * 2 * kCap, cudaMemcpyDeviceToHost, s)) !=
-            cudaSuccess)
-            break;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
-        done_w += a.count;
+        done_probe += a.count;
         const uint32_t n = std::min(*hN, kCap);
         if (*hN > kCap) overflow = true;
+        if (n > 0) {
+            // read back only the matches the slice queued
+            if ((e = cudaMemcpyAsync(hPairs, a.pairs, sizeof(uint64_t) * 2 * n, cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess)
+                break;
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+        }
         for (uint32_t i = 0; i < n && !*got; i++) {
             // exact check of the key match: rotations from the point indices
-            uint32_t qv[kMaxH], qw[kMaxH], paulis[16] = {0};
-            uint64_t v = hPairs[2 * i], w = hPairs[2 * i + 1];
-            const int chunk = (k & 1) ? (int)(w / xi_h) + 1 : 0;
-            w %= xi_h;
-            for (int j = 0; j < h; j++) {
-                qv[j] = (uint32_t)(v % xi) + 1;
-                qw[j] = (uint32_t)(w % xi) + 1;
-                v /= xi;
-                w /= xi;
-            }
+            uint32_t paulis[16] = {0};
+            uint64_t st = hPairs[2 * i], pr = hPairs[2 * i + 1];
             PMat Dh;
-            if (verify_claw(P, k, chunk, qv, qw, paulis, &Dh)) {
+            bool ok;
+            if (v_heavy) {
+                // P_1..P_(h+1) = r_1..r_(h+1) (probing V'), P_(h+2)..P_k = s_1..s_h (stored W')
+                for (int j = 0; j <= h; j++, pr /= xi) paulis[j] = (uint32_t)(pr % xi) + 1;
+                for (int j = 0; j < h; j++, st /= xi) paulis[h + 1 + j] = (uint32_t)(st % xi) + 1;
+                ok = exact_verify(P->n, P->C, paulis, k, &Dh) == QCS_OK;
+            } else {
+                uint32_t qv[kMaxH], qw[kMaxH];
+                const int chunk = (k & 1) ? (int)(pr / xi_h) + 1 : 0;
+                pr %= xi_h;
+                for (int j = 0; j < h; j++) {
+                    qv[j] = (uint32_t)(st % xi) + 1;
+                    qw[j] = (uint32_t)(pr % xi) + 1;
+                    st /= xi;
+                    pr /= xi;
+                }
+                ok = verify_claw(P, k, chunk, qv, qw, paulis, &Dh);
+            }
+            if (ok) {
                 found(P, k, paulis, std::move(Dh));
                 *got = true;
             }
@@ -636,7 +674,7 @@ int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
     cudaFreeHost(hPairs);
     {
         std::lock_guard<std::mutex> g(P->mu);
-        P->res.cert_points += (int64_t)(xi_h + done_w);
+        P->res.cert_points += (int64_t)(xi_h + done_probe);
         if (rc == QCS_OK && !*got && !overflow) P->res.certified_levels += 1;
     }
     if (rc == QCS_OK && !*got && overflow) rc = QCS_ERR_OVERFLOW;

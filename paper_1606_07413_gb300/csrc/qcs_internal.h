@@ -157,26 +157,28 @@ struct BatchArgs {
     const uint32_t *n_jobs;   // device scalar
 };
 // Exhaustive meet-in-the-middle pass over one level (Sec. 2 Eq. mitm, the
-// collision search's exact counterpart): every V point is hashed into an
-// open-addressing table of coset keys, then every W point probes it and each
-// key match is queued for the exact host check.  Point index -> rotations:
-// base-xi digits, q_j = digit_j + 1 (q_1 the lowest digit); a W index is
-// chunk-major, chunk = index / xi^h + 1 for odd k.
+// collision search's exact counterpart): the points of the smaller side are
+// hashed into an open-addressing table of coset keys, then every point of
+// the other side probes it and each key match is queued for the exact host
+// check.  Point index -> rotations: base-xi digits, q_j = digit_j + 1 (q_1
+// the lowest digit); a W index of a level context with odd k is chunk-major,
+// chunk = index / xi^h + 1.
 struct alignas(16) CertSlot {
     uint64_t key; // ~0: empty
-    uint64_t idx; // V point index
+    uint64_t idx; // stored point index
 };
 
 struct CertArgs {
-    LevelCtx lv;
-    int32_t side;      // 0: insert V points, 1: probe with W points
+    LevelCtx lv;       // the side's level context (lv.h rotations per point)
+    int32_t side;      // which product a point is: 0 V, 1 W
+    int32_t insert;    // 1: insert the points' keys, 0: probe the table with them
     uint64_t first;    // point indices [first, first + count)
     uint64_t count;
-    uint64_t xi_h;     // rotation tuples per side
+    uint64_t xi_h;     // rotation tuples of the h-rotation W side (chunk stride)
     uint64_t base;     // hash base of the keys, the same for every chunk
     CertSlot *table;
-    uint64_t mask;     // table slots - 1 (a power of two, at least twice the V points)
-    uint64_t *pairs;   // key matches (V index, W index)
+    uint64_t mask;     // table slots - 1 (a power of two, at least twice the stored points)
+    uint64_t *pairs;   // key matches (stored index, probing index)
     uint32_t *n_pairs; // matches found (may exceed cap; only cap are stored)
     uint32_t cap;
 };

@@ -92,6 +92,12 @@ struct Geo {
     static constexpr size_t off_base = off_coef + sizeof(uint32_t) * COEF_WORDS;
     static constexpr size_t off_xchg = off_base + sizeof(uint64_t) * MAX_CHUNKS;
     static constexpr size_t smem_bytes = off_xchg + sizeof(uint2) * WALKS * DIM;
+    // the same without C^, for kernels that evaluate V products only:
+    // weights | coefficients | chunk bases | exchange buffers
+    static constexpr size_t off_coef_v = off_C;
+    static constexpr size_t off_base_v = off_coef_v + sizeof(uint32_t) * COEF_WORDS;
+    static constexpr size_t off_xchg_v = off_base_v + sizeof(uint64_t) * MAX_CHUNKS;
+    static constexpr size_t smem_bytes_v = off_xchg_v + sizeof(uint2) * WALKS * DIM;
 };
 
 // Shared-memory views of one CTA (C may point to global memory for n = 4).
@@ -471,17 +477,19 @@ __device__ __forceinline__ uint64_t warp_step(uint64_t x, uint32_t chunk, const 
 }
 
 // Stage the weights, the rotation coefficients, the per-chunk hash bases and
-// (n <= 3) all of C^ into shared memory; returns this warp's views.
-template <int NQ>
+// (n <= 3) all of C^ into shared memory; returns this warp's views.  WITH_C
+// false: the smaller layout without C^ (smem_bytes_v), whose views of C^ are
+// null; only V products may then be evaluated.
+template <int NQ, bool WITH_C = true>
 __device__ __forceinline__ Smem<NQ> stage(const LevelCtx &lv, unsigned char *raw)
 {
     using G = Geo<NQ>;
     Smem<NQ> sm;
     sm.U = reinterpret_cast<uint2 *>(raw);
     uint2 *sC = reinterpret_cast<uint2 *>(raw + G::off_C);
-    sm.coef = reinterpret_cast<uint32_t *>(raw + G::off_coef);
-    sm.base = reinterpret_cast<uint64_t *>(raw + G::off_base);
-    sm.xchg = reinterpret_cast<uint2 *>(raw + G::off_xchg) + group_in_cta<NQ>() * G::DIM;
+    sm.coef = reinterpret_cast<uint32_t *>(raw + (WITH_C ? G::off_coef : G::off_coef_v));
+    sm.base = reinterpret_cast<uint64_t *>(raw + (WITH_C ? G::off_base : G::off_base_v));
+    sm.xchg = reinterpret_cast<uint2 *>(raw + (WITH_C ? G::off_xchg : G::off_xchg_v)) + group_in_cta<NQ>() * G::DIM;
     for (int i = threadIdx.x; i < G::DIM; i += blockDim.x) sm.U[i] = lv.U[i];
     for (int i = threadIdx.x; i < G::COEF_WORDS; i += blockDim.x) sm.coef[i] = lv.coef[i];
     // base(chunk) = smix(smix(seed_H ^ version) ^ (n | k << 8 | chunk << 16 | K << 32))
@@ -492,7 +500,9 @@ __device__ __forceinline__ Smem<NQ> stage(const LevelCtx &lv, unsigned char *raw
         sm.base[c] = smix(vmix ^ tag);
     }
     sm.Cq = nullptr;
-    if (G::C_SMEM) {
+    if (!WITH_C) {
+        sm.C = nullptr;
+    } else if (G::C_SMEM) {
         if (lv.Cq && G::DIM >= 64) {
             uint4 *dst = reinterpret_cast<uint4 *>(sC);
             for (int i = threadIdx.x; i < G::DIM * G::DIM * 2 / 16; i += blockDim.x) dst[i] = lv.Cq[i];
@@ -939,11 +949,14 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_rewalk_arrays(LevelCtx lv,
 }
 
 // Exhaustive level pass (CertArgs): one lane group per point, grid-stride.
-template <int NQ>
+// VONLY: the points are V products (a.side == 0), which never touch C^, so
+// the CTA stages the smaller layout without it.
+template <int NQ, bool VONLY>
 __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_certify(CertArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Smem<NQ> sm = stage<NQ>(a.lv, smem_raw);
+    const Smem<NQ> sm = stage<NQ, !VONLY>(a.lv, smem_raw);
+    const int side = VONLY ? 0 : a.side;
     const Lanes g = thread_lanes<NQ>();
     const uint32_t xi = a.lv.xi;
     for (uint64_t i = (uint64_t)blockIdx.x * Geo<NQ>::WALKS + group_in_cta<NQ>(); i < a.count;
@@ -951,7 +964,7 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_certify(CertArgs a)
         const uint64_t idx = a.first + i;
         uint64_t tuple = idx;
         uint32_t chunk = 0;
-        if (a.side == 1 && (a.lv.k & 1)) {
+        if (side == 1 && (a.lv.k & 1)) {
             chunk = (uint32_t)(idx / a.xi_h) + 1;
             tuple = idx % a.xi_h;
         }
@@ -960,11 +973,11 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_certify(CertArgs a)
             qpack |= (uint64_t)(tuple % xi + 1) << (8 * j);
             tuple /= xi;
         }
-        uint64_t key = coset_hash<NQ>(a.side, qpack, chunk, a.base, a.lv, sm, g);
+        uint64_t key = coset_hash<NQ>(side, qpack, chunk, a.base, a.lv, sm, g);
         if (key == ~0ull) key = ~0ull - 1; // ~0 marks an empty slot
         if (g.sub == 0) {
             uint64_t s = smix(key) & a.mask;
-            if (a.side == 0) {
+            if (a.insert) {
                 // the table is at most half full, so an empty slot is always found
                 for (uint64_t probe = 0; probe <= a.mask; probe++) {
                     const unsigned long long prev = atomicCAS(
@@ -1086,12 +1099,28 @@ cudaError_t rewalk_arrays_n(const LevelCtx &lv, int chunk, const uint64_t *sa, c
     return cudaGetLastError();
 }
 
+template <int NQ, bool VONLY>
+cudaError_t certify_nv(const CertArgs &a, cudaStream_t s)
+{
+    constexpr size_t smem = VONLY ? Geo<NQ>::smem_bytes_v : Geo<NQ>::smem_bytes;
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaFuncSetAttribute(k_certify<NQ, VONLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_certify<NQ, VONLY>, Geo<NQ>::THREADS, smem);
+        per_sm = b > 0 ? b : 1;
+    }
+    const size_t cap = (size_t)num_sms() * (size_t)per_sm;
+    size_t grid = (a.count + Geo<NQ>::WALKS - 1) / Geo<NQ>::WALKS;
+    if (grid > cap) grid = cap;
+    k_certify<NQ, VONLY><<<(unsigned)grid, Geo<NQ>::THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int NQ>
 cudaError_t certify_n(const CertArgs &a, cudaStream_t s)
 {
-    cudaFuncSetAttribute(k_certify<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<NQ>::smem_bytes);
-    k_certify<NQ><<<grid_for<NQ>(a.count), Geo<NQ>::THREADS, Geo<NQ>::smem_bytes, s>>>(a);
-    return cudaGetLastError();
+    return a.side == 0 ? certify_nv<NQ, true>(a, s) : certify_nv<NQ, false>(a, s);
 }
 
 } // namespace

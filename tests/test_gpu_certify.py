@@ -22,10 +22,13 @@ def dev():
 
 
 # (n, construction t, seed, highest level checked): the oracle's pass over
-# n = 3 above level 4 takes too long for a test
-CASES = [(1, t, 60 + t, 8) for t in (2, 3, 5, 6)] + \
-        [(2, t, 70 + t, 7) for t in (2, 3, 4, 5, 6)] + \
-        [(3, 3, 83, 4), (3, 4, 84, 4), (3, 5, 85, 4)]
+# n = 3 above level 4 takes too long for a test.  An odd level of a target
+# with a denominator (sde >= 1) stores the h-rotation side with C^ and
+# streams the (h + 1)-rotation side; a Clifford target (t = 0, sde 0) takes
+# the other split, so both are covered.
+CASES = [(1, t, 60 + t, 8) for t in (0, 2, 3, 5, 6)] + \
+        [(2, t, 70 + t, 7) for t in (0, 2, 3, 4, 5, 6)] + \
+        [(3, 3, 83, 4), (3, 4, 84, 4), (3, 5, 85, 5)]
 
 
 @pytest.mark.parametrize("n,t,seed,kmax", CASES)
