@@ -25,10 +25,10 @@
  *  - The next state (Sec. 2 mappings nu and h) hashes the product's Clifford
  *    coset: per column Q >= 1 the 16-bit fingerprint L_Q = sum_i Ua_i a_iQ +
  *    Ub_i b_iQ mod 2^16 (weights: SplitMix64 outputs, row 0 weight 0), folded
- *    to min(L_Q, -L_Q); the folded values sorted ascending, padded with 0xFFFF
- *    to 4^n, are hashed in position-keyed pairs with the SplitMix64 finaliser
- *    under a base that mixes the function version, n, k, the chunk and the
- *    common exponent K, and the sum's finaliser is cut to L bits.
+ *    to phi_Q = min(L_Q, -L_Q); the multiset of the phi_Q is hashed as the
+ *    sum mod 2^64 of the SplitMix64 finaliser of base ^ phi_Q, where the base
+ *    mixes the function version, n, k, the chunk and the common exponent K,
+ *    and the sum's finaliser is cut to L bits.
  *
  * Ownership: every pointer argument stays owned by the caller; the library
  * copies what it keeps.  The library owns every device allocation it makes and

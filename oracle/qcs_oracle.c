@@ -26,10 +26,11 @@
  *    Both are represented at K = sde(C) + (k & 1) + h.
  *  - Walk hash: per column Q >= 1 a 16-bit linear fingerprint
  *    L_Q = sum_{i>=1} Ua[i] a_iQ + Ub[i] b_iQ (mod 2^16), folded to
- *    phi_Q = min(L_Q, -L_Q mod 2^16) (invariant under the column's sign); the
- *    phi are sorted ascending, padded with 0xFFFF to 4^n entries, and hashed
- *    in position-keyed pairs through the SplitMix64 finaliser (Steele, Lea &
- *    Flood 2014).
+ *    phi_Q = min(L_Q, -L_Q mod 2^16) (invariant under the column's sign).  The
+ *    multiset {phi_Q} is what a Clifford (a signed permutation of the columns
+ *    Q >= 1) leaves unchanged; it is hashed as the sum mod 2^64 of the
+ *    SplitMix64 finaliser (Steele, Lea & Flood 2014) of base ^ phi_Q over the
+ *    columns, finalised once more.
  */
 #include <stdint.h>
 #include <stdio.h>
@@ -613,41 +614,29 @@ OR_API void or_fp_weights(int n, uint32_t *ua, uint32_t *ub)
     }
 }
 
-static int cmp_u16(const void *x, const void *y)
-{
-    uint16_t a = *(const uint16_t *)x, b = *(const uint16_t *)y;
-    return (a > b) - (a < b);
-}
-
 static uint64_t mask_bits(int L) { return L >= 64 ? ~0ull : ((1ull << L) - 1); }
 
 /* hash of the Clifford coset of M (given at exponent K) into an L-bit state:
- * the d = 4^n - 1 folded 16-bit column fingerprints, sorted ascending, padded
- * with 0xFFFF (above every folded value) to 4^n entries; pair p packs entries
- * 2p (low half) and 2p + 1 (high half) and is hashed with its position p. */
+ * the d = 4^n - 1 folded 16-bit column fingerprints phi_Q (Q = 1..d) as a
+ * multiset, hashed as smix(sum_Q smix(base ^ phi_Q) mod 2^64), where base
+ * mixes the version and the tag (n, k, chunk, K). */
 static uint64_t coset_hash(int n, const pmat *M, int k, int chunk, uint32_t version, int L)
 {
     int D = 1 << (2 * n), d = D - 1;
     uint32_t *ua = (uint32_t *)xcalloc(D, 4), *ub = (uint32_t *)xcalloc(D, 4);
-    uint16_t *phi = (uint16_t *)xcalloc(D, 2);
     or_fp_weights(n, ua, ub);
+    uint64_t tag = (uint64_t)n | ((uint64_t)k << 8) | ((uint64_t)chunk << 16) | ((uint64_t)M->E << 32);
+    uint64_t base = smix(smix(SEED_H ^ (uint64_t)version) ^ tag);
+    uint64_t acc = 0;
     for (int Q = 1; Q <= d; Q++) {
         uint32_t Lq = 0;
         for (int i = 1; i <= d; i++)
             Lq += ua[i] * (uint32_t)M->a[i * D + Q] + ub[i] * (uint32_t)M->b[i * D + Q];
         uint16_t l16 = (uint16_t)(Lq & 0xFFFFu), neg = (uint16_t)((0x10000u - l16) & 0xFFFFu);
-        phi[Q - 1] = l16 < neg ? l16 : neg;
+        uint16_t phi = l16 < neg ? l16 : neg;
+        acc += smix(base ^ (uint64_t)phi);
     }
-    qsort(phi, d, sizeof(uint16_t), cmp_u16);
-    phi[d] = 0xFFFF;
-    uint64_t tag = (uint64_t)n | ((uint64_t)k << 8) | ((uint64_t)chunk << 16) | ((uint64_t)M->E << 32);
-    uint64_t base = smix(smix(SEED_H ^ (uint64_t)version) ^ tag);
-    uint64_t acc = 0;
-    for (int p = 0; p < D / 2; p++) {
-        uint32_t pair = (uint32_t)phi[2 * p] | ((uint32_t)phi[2 * p + 1] << 16);
-        acc += smix(base ^ (((uint64_t)p << 32) | pair));
-    }
-    free(ua); free(ub); free(phi);
+    free(ua); free(ub);
     return smix(acc) & mask_bits(L);
 }
 

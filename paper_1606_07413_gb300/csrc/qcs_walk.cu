@@ -13,7 +13,9 @@
 // The hash is defined on the exact product M at exponent K: every column Q
 // gets the 16-bit linear fingerprint L_Q = sum_i Ua[i] a_iQ + Ub[i] b_iQ mod
 // 2^16, folded to phi_Q = min(L_Q, -L_Q) (so a column's sign does not matter),
-// and the sorted phi are hashed in pairs.  Because L is linear in M's integer
+// and the multiset of the phi_Q (Q >= 1) is hashed by summing
+// smix(base ^ phi_Q), so a permutation of the columns does not matter either.
+// Because L is linear in M's integer
 // numerators and every factor acts linearly on them, L(M e_Q) =
 // ((adjoint network) U)^T (M's right factor) e_Q: the kernel pushes the weight
 // vector U through the transposed sparse R^ butterflies (4^n entries, h
@@ -72,7 +74,6 @@ struct Geo {
     static constexpr int LPW = DIM < 32 ? DIM : (NQ == 3 ? QCS_LPW3 : 32);
     static constexpr int GROUPS = 32 / LPW;
     static constexpr int RPL = DIM / LPW;                // rows (and columns) per lane
-    static constexpr int SLOTS = RPL * LPW;              // width of the fingerprint sort
     // n <= 3: C^ staged whole, as byte quads (8 KB at n = 3) or else as low
     // words (32 KB); n = 4: byte quads (128 KB) when every entry fits, else
     // the low words are read through L2
@@ -223,20 +224,6 @@ __device__ __forceinline__ void weight_planes(uint2 *su, Lanes g)
     __syncwarp(g.mask);
 }
 
-// packed 16-bit minimum and maximum of both halves
-__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
-{
-    uint32_t d;
-    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-    return d;
-}
-__device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b)
-{
-    uint32_t d;
-    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-    return d;
-}
-
 struct Decoded {
     int side;
     uint64_t qpack; // q_1 .. q_h, 8 bits each (q <= 255)
@@ -384,78 +371,17 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
         __syncwarp(g.mask);
     }
 
-    // sign-invariant 16-bit column fingerprints; column 0 (the identity) and
-    // padding sorts last as 0xFFFF (every phi is at most 2^15).  Sort
-    // element e = RPL sub + t starts with this lane's column sub + LPW t
-    // (where the keys start does not matter to a sort).
-    uint32_t key[G::RPL];
+    // sign-invariant 16-bit column fingerprints phi_Q of the columns Q >= 1
+    // (column 0, the identity, does not enter), hashed as a multiset: the sum
+    // mod 2^64 of smix(base ^ phi_Q), a function of the multiset alone.  This
+    // lane holds the columns sub + LPW t.
+    uint64_t acc = 0;
 #pragma unroll
     for (int t = 0; t < G::RPL; t++) {
         const int Q = lane + G::LPW * t;
         const uint32_t l = Lc[t] & 0xFFFFu, nl = (0u - l) & 0xFFFFu;
-        key[t] = (Q >= 1 && Q <= G::D) ? min(l, nl) : 0xFFFFu;
-    }
-    uint64_t acc = 0;
-    if constexpr (G::RPL >= 2) {
-        // two keys per word: word u holds elements e = RPL lane + 2u (low
-        // half) and e + 1 (high half); bitonic sort ascending in e with
-        // packed 16-bit min/max.  Stride 1 pairs the halves of a word, strides
-        // below RPL pair words of the lane, larger strides pair lanes.
-        constexpr int NW = G::RPL / 2;
-        uint32_t kw[NW];
-#pragma unroll
-        for (int u = 0; u < NW; u++) kw[u] = key[2 * u] | (key[2 * u + 1] << 16);
-#pragma unroll
-        for (int size = 2; size <= G::SLOTS; size <<= 1) {
-#pragma unroll
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                if (stride == 1) {
-#pragma unroll
-                    for (int u = 0; u < NW; u++) {
-                        const bool up = ((G::RPL * lane + 2 * u) & size) == 0;
-                        const uint32_t sw = __byte_perm(kw[u], 0, 0x1032);
-                        const uint32_t mn = min_u16x2(kw[u], sw), mx = max_u16x2(kw[u], sw);
-                        kw[u] = up ? __byte_perm(mn, mx, 0x7610) : __byte_perm(mx, mn, 0x7610);
-                    }
-                } else if (stride < G::RPL) {
-                    const int ws = stride >> 1;
-#pragma unroll
-                    for (int u = 0; u < NW; u++) {
-                        if ((u & ws) == 0) {
-                            const bool up = ((G::RPL * lane + 2 * u) & size) == 0;
-                            const uint32_t mn = min_u16x2(kw[u], kw[u | ws]), mx = max_u16x2(kw[u], kw[u | ws]);
-                            kw[u] = up ? mn : mx;
-                            kw[u | ws] = up ? mx : mn;
-                        }
-                    }
-                } else {
-                    const int lstride = stride / G::RPL, eb = G::RPL * lane;
-                    const bool keep_min = ((eb & stride) == 0) == ((eb & size) == 0);
-#pragma unroll
-                    for (int u = 0; u < NW; u++) {
-                        const uint32_t o = __shfl_xor_sync(g.mask, kw[u], lstride);
-                        kw[u] = keep_min ? min_u16x2(kw[u], o) : max_u16x2(kw[u], o);
-                    }
-                }
-            }
-        }
-        // position-keyed hash of the sorted pairs: pair p = NW lane + u
-#pragma unroll
-        for (int u = 0; u < NW; u++) acc += smix(base ^ (((uint64_t)(NW * lane + u) << 32) | kw[u]));
-    } else {
-        // one key per lane (n <= 2): bitonic sort across the group's 4^n lanes
-#pragma unroll
-        for (int size = 2; size <= G::SLOTS; size <<= 1) {
-#pragma unroll
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
-                const uint32_t o = __shfl_xor_sync(g.mask, key[0], stride);
-                key[0] = ((key[0] < o) == keep_min) ? key[0] : o;
-            }
-        }
-        // pair p = lane / 2 packs elements 2p and 2p + 1, for the 4^n / 2 pairs
-        const uint32_t nxt = __shfl_down_sync(g.mask, key[0], 1, G::LPW);
-        if ((lane & 1) == 0) acc = smix(base ^ (((uint64_t)(lane >> 1) << 32) | key[0] | (nxt << 16)));
+        const uint64_t e = smix(base ^ (uint64_t)min(l, nl));
+        acc += (Q >= 1) ? e : 0ull;
     }
     // warp sum mod 2^64 from three 32-bit reductions: the high words (mod
     // 2^32) and the two 16-bit halves of the low words (no overflow: 32 terms)

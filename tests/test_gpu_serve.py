@@ -74,27 +74,35 @@ def test_requests_join_a_running_batch_and_match_the_oracle(orc, dev):
         slow.close()
 
 
+def peak_concurrency(polls):
+    """Most requests in flight at once, from their admit and done times (a
+    job admitted and finished within one round still counts)."""
+    return max(sum(1 for s in polls if s["t_admit"] <= r["t_admit"] < s["t_done"]) for r in polls)
+
+
 def test_admission_respects_slots_and_memory(dev):
     with serve.Server(params(J=8), memory_budget=1, stream=torch.cuda.Stream()) as srv:
         # a budget below one job admits exactly one job at a time
         rids = [srv.submit(n, g, k) for n, g, k in small_targets(5, seed=500)]
-        most = 0
         for _ in range(3000):
             srv.step()
-            most = max(most, len(srv.running))
+            assert len(srv.running) <= 1
             if srv.idle():
                 break
-        assert srv.idle() and most == 1
-        assert all(srv.poll(r)["status"] == "found" for r in rids)
+        polls = [srv.poll(r) for r in rids]
+        assert srv.idle() and all(p["status"] == "found" for p in polls)
+        assert peak_concurrency(polls) == 1
     with serve.Server(params(J=2), memory_budget=1 << 34, stream=torch.cuda.Stream()) as srv:
+        # two job slots: two requests run together, never three
         rids = [srv.submit(n, g, k) for n, g, k in small_targets(6, seed=600)]
-        most = 0
         for _ in range(3000):
             srv.step()
-            most = max(most, len(srv.running))
+            assert len(srv.running) <= 2
             if srv.idle():
                 break
-        assert srv.idle() and most == 2
+        polls = [srv.poll(r) for r in rids]
+        assert srv.idle() and all(p["status"] == "found" for p in polls)
+        assert peak_concurrency(polls) == 2
 
 
 def test_same_answer_alone_and_in_the_mix(orc, dev):

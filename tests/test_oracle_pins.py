@@ -217,6 +217,32 @@ def test_canonical_form_and_walk_hash_are_clifford_invariant(orc, n):
     assert orc.matrix_hash(C, 4, 0, 5, 48) != orc.matrix_hash(other, 4, 0, 5, 48)
 
 
+def test_walk_hash_is_a_function_of_the_column_multiset(orc):
+    """The hash sees the product only through the multiset of its sign-folded
+    non-identity column fingerprints: any signed permutation of the columns
+    Q >= 1 keeps it (a Clifford is one such), and a repeated column counts
+    with its multiplicity (two matrices whose multisets differ only in which
+    column is doubled hash apart, which an accumulation that cancels pairs
+    would miss)."""
+    rng = np.random.default_rng(77)
+    gates, _ = W.seeded_target(2, 3, 5)
+    C = orc.channel_from_circuit(2, gates)
+    D = C.a.shape[0]
+    h0 = orc.matrix_hash(C, 4, 0, 5, 64)
+    for _ in range(3):
+        perm = np.concatenate([[0], 1 + rng.permutation(D - 1)])
+        sgn = np.concatenate([[1], rng.choice([-1, 1], size=D - 1)])
+        M = orc.Chan(2, C.a[:, perm] * sgn, C.b[:, perm] * sgn, C.E)
+        assert orc.matrix_hash(M, 4, 0, 5, 64) == h0
+    assert not np.array_equal(np.abs(C.a[:, 1]), np.abs(C.a[:, 2]))
+    a1, b1, a2, b2 = C.a.copy(), C.b.copy(), C.a.copy(), C.b.copy()
+    a1[:, 2], b1[:, 2] = C.a[:, 1], C.b[:, 1]  # column 1 twice, column 2 gone
+    a2[:, 1], b2[:, 1] = C.a[:, 2], C.b[:, 2]  # column 2 twice, column 1 gone
+    h1 = orc.matrix_hash(orc.Chan(2, a1, b1, C.E), 4, 0, 5, 64)
+    h2 = orc.matrix_hash(orc.Chan(2, a2, b2, C.E), 4, 0, 5, 64)
+    assert len({h0, h1, h2}) == 3
+
+
 def test_hash_depends_on_version_and_tag(orc):
     gates, _ = W.seeded_target(2, 3, 5)
     C = orc.channel_from_circuit(2, gates)
