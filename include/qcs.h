@@ -95,7 +95,7 @@ extern "C" {
 typedef struct qcs_params {
     int32_t state_bits;       /* L, 32..64 */
     int32_t dp_bits;          /* d_theta, theta = 2^-d_theta (Sec. 3), 1 .. L-1 */
-    int32_t walks;            /* concurrent walks (one lane group each: min(32, 4^n) lanes, 16 at n = 3) */
+    int32_t walks;            /* concurrent walks (one lane group each: min(32, 4^n) lanes) */
     int32_t table_log2;       /* distinguished-point table holds 2^table_log2 slots (16 B each) */
     int32_t steps_per_launch; /* walk steps each walk advances per kernel launch */
     int32_t max_trail_factor; /* a trail is abandoned after max_trail_factor * 2^d_theta steps */

@@ -148,7 +148,7 @@ struct WalkLaunch {
 };
 
 // Many jobs in one launch: per qubit count, the device list of tasks
-// (job index, first walk) with kWarps walks each, and of job indices.
+// (job index, first walk) with walks_per_task(n) walks each, and of job indices.
 struct BatchArgs {
     const WalkLaunch *jobs;   // device array indexed by job
     const uint32_t *tasks;    // 2 * n_tasks entries

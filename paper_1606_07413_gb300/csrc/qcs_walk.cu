@@ -37,13 +37,16 @@ namespace {
 // lanes per walk, the register cap (minimum resident CTAs) and the
 // contraction's unrolling
 #ifndef QCS_WARPS
-#define QCS_WARPS 8
+#define QCS_WARPS 8 // warps per CTA, n <= 2
+#endif
+#ifndef QCS_WARPS3
+#define QCS_WARPS3 16 // warps per CTA, n = 3
 #endif
 #ifndef QCS_LPW3
-#define QCS_LPW3 16 // lanes per walk at n = 3 (two walks per warp)
+#define QCS_LPW3 32 // lanes per walk at n = 3 (one walk per warp)
 #endif
 #ifndef QCS_MIN_BLOCKS3
-#define QCS_MIN_BLOCKS3 3 // n = 3: 80 registers, three CTAs of 8 warps (16 walks) per SM
+#define QCS_MIN_BLOCKS3 2 // n = 3: 64 registers, two CTAs of 16 warps (16 walks) per SM
 #endif
 #ifndef QCS_GEMV_UNROLL
 #define QCS_GEMV_UNROLL 2 // 32-bit word contraction (rows per unrolled step / 2)
@@ -52,9 +55,10 @@ namespace {
 #define QCS_QUAD_UNROLL3 16 // byte-quad contraction, n = 3 (16 quads)
 #endif
 #ifndef QCS_QUAD_UNROLL4
-#define QCS_QUAD_UNROLL4 8 // byte-quad contraction, n = 4 (64 quads)
+#define QCS_QUAD_UNROLL4 16 // byte-quad contraction, n = 4 (64 quads)
 #endif
 constexpr int kWarps = QCS_WARPS;
+constexpr int kWarps3 = QCS_WARPS3;
 constexpr int kGemvUnroll = QCS_GEMV_UNROLL;
 constexpr uint32_t kMaxRewalkLen = 1u << 20; // longer trails are reported as no merge
 
@@ -79,7 +83,7 @@ struct Geo {
     // the low words are read through L2
     static constexpr bool C_SMEM = NQ <= 3;
     static constexpr bool CQ_SMEM = NQ == 4;
-    static constexpr int WARPS = NQ == 4 ? 16 : kWarps;  // warps per CTA
+    static constexpr int WARPS = NQ == 4 ? 16 : NQ == 3 ? kWarps3 : kWarps; // warps per CTA
     static constexpr int THREADS = WARPS * 32;
     static constexpr int WALKS = WARPS * GROUPS;         // walks (lane groups) per CTA
     static constexpr int MIN_BLOCKS = NQ == 3 ? QCS_MIN_BLOCKS3 : 1;
