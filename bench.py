@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--config3-walk", type=int, default=0, metavar="TABLE_LOG2",
                     help="only time the n = 4 seeded target's search by the collision walk alone with a "
                          "2^TABLE_LOG2-slot table, print its JSON and exit")
+    ap.add_argument("--adder-walk", type=int, default=0, metavar="TABLE_LOG2",
+                    help="only time the 4-qubit full adder's search by the collision walk alone with a "
+                         "2^TABLE_LOG2-slot table, print its JSON and exit")
     return ap.parse_args()
 
 
@@ -308,25 +311,29 @@ def run_batched(Q, W, torch, stream, n_targets=256, rounds=12, mac_peak=None):
     }
 
 
-def table1_circuits(Q, stream, trials=10):
-    """Time to the optimal T-count of the Toffoli and Fredkin gates (textbook
-    permutation matrices), the paper's Table 1 circuits with published means
-    25.9870 s and 25.0031 s on 4096 Blue Gene/Q cores (context, not a target:
-    other hardware).  Each trial is a full ladder from sde = 2 through the
-    public API with its own walk seed."""
-    def perm_unitary(perm):
-        u = np.zeros((8, 8, 4), np.int64)
-        for c, r in enumerate(perm):
-            u[r, c, 0] = 1
-        return u
+def perm_unitary(perm):
+    """The permutation matrix of a basis-state permutation, as Z[omega]
+    coefficients (4 int64 per entry) over sqrt2^0."""
+    d = len(perm)
+    u = np.zeros((d, d, 4), np.int64)
+    for c, r in enumerate(perm):
+        u[r, c, 0] = 1
+    return u
 
-    circuits = {
-        "toffoli": [c ^ (4 if (c & 3) == 3 else 0) for c in range(8)],
-        "fredkin": [(c & 1) | ((((c >> 2) & 1) << 1) | (((c >> 1) & 1) << 2)) if c & 1 else c for c in range(8)],
-    }
+
+def table1_circuits(Q, W, stream, trials=10):
+    """Time to the optimal T-count of the paper's named circuits.  Toffoli and
+    Fredkin (Table 1; published means 25.9870 s and 25.0031 s on 4096 Blue
+    Gene/Q cores, context only: other hardware): each trial is a full ladder
+    from sde = 2 through the public API with its own walk seed.  The 4-qubit
+    full adder (Sec. 5.3; the paper's first synthesis took 12.5 hours on 4096
+    cores): one deterministic ladder settled by the exhaustive pass alone
+    (every level exact); `--adder-walk` times the walk alone."""
+    targets = W.permutation_targets()
     paper = {"toffoli": 25.9870, "fredkin": 25.0031}
     out = {}
-    for name, perm in circuits.items():
+    for name in ("toffoli", "fredkin"):
+        _, perm = targets[name]
         secs, tcs = [], []
         for t in range(trials):
             p = Q.Problem.from_unitary(3, perm_unitary(perm), 0, 7, Q.default_params(3, seed=0x7AB1E + t))
@@ -338,15 +345,24 @@ def table1_circuits(Q, stream, trials=10):
             p.close()
         out[name] = {"t_counts": sorted(set(tcs)), "mean_s": float(np.mean(secs)), "sd_s": float(np.std(secs)),
                      "trials": trials, "paper_mean_s_4096_bgq_cores": paper[name]}
+    out["adder"] = dict(n4_time_to_optimal(Q, W, stream, "exhaustive", unitary=perm_unitary(targets["adder"][1])),
+                        paper_first_synthesis_s_4096_bgq_cores=12.5 * 3600)
     return out
 
 
 def config3_time_to_optimal(Q, W, stream, mode="exhaustive", table_log2=30, queue_log2=24, limit_s=900):
-    """Time to the optimal T-count of the n = 4, 7-factor seeded target.
-    mode "exhaustive": the ladder settles each level by the exhaustive pass
-    alone (the V key table of level 7 is 512 MiB); mode "walk": the collision
-    search alone with a 2^table_log2-slot table (16 bytes a slot), theta
-    policy 1, no exhaustive pass."""
+    """Time to the optimal T-count of the n = 4, 7-factor seeded target (see
+    n4_time_to_optimal)."""
+    return n4_time_to_optimal(Q, W, stream, mode, table_log2, queue_log2, limit_s)
+
+
+def n4_time_to_optimal(Q, W, stream, mode="exhaustive", table_log2=30, queue_log2=24, limit_s=900, unitary=None):
+    """Time to the optimal T-count (at most 7) of an n = 4 target: config 3's
+    seeded 7-factor target, or the given unitary (Z[omega] coefficients over
+    sqrt2^0).  mode "exhaustive": the ladder settles each level by the
+    exhaustive pass alone (the key table of level 7 is 512 MiB); mode "walk":
+    the collision search alone with a 2^table_log2-slot table (16 bytes a
+    slot), theta policy 1, no exhaustive pass."""
     c = W.CONFIGS[3]
     gates, _ = W.config_target(3)
     if mode == "exhaustive":
@@ -354,7 +370,10 @@ def config3_time_to_optimal(Q, W, stream, mode="exhaustive", table_log2=30, queu
     else:
         p = Q.default_params(4, table_log2=table_log2, queue_capacity=1 << queue_log2, exhaustive_log2=0)
     t0 = time.perf_counter()
-    prob = Q.Problem.from_circuit(4, gates, c["k_max"], p)
+    if unitary is None:
+        prob = Q.Problem.from_circuit(4, gates, c["k_max"], p)
+    else:
+        prob = Q.Problem.from_unitary(4, unitary, 0, c["k_max"], p)
     prob.run_walks(stream=stream)
     r = prob.wait(int(limit_s * 1000))
     if r["timed_out"]:
@@ -560,7 +579,7 @@ def run_ours(args):
             extra = {
                 "batched": batched,
                 "serving": run_serving(Q, W, torch, stream, batched["autotuned"]),
-                "table1_circuits": table1_circuits(Q, stream),
+                "table1_circuits": table1_circuits(Q, W, stream),
                 "config3_time_to_optimal": config3_time_to_optimal(Q, W, stream, "exhaustive"),
                 "n4_level7_exhaustive_pass": exhaustive_level_pass(Q, W, stream),
                 "n2_level3": level_throughput(Q, W, torch, 1, 3, 512, stream, alu_per_s=imad_per_s),
@@ -652,14 +671,20 @@ def run_config3_walk(args):
 
     B.build()
     stream = torch.cuda.Stream()
-    print(json.dumps({"config3_time_to_optimal": config3_time_to_optimal(Q, W, stream, "walk", args.config3_walk)}))
+    if args.adder_walk:
+        u = perm_unitary(W.permutation_targets()["adder"][1])
+        print(json.dumps({"adder_time_to_optimal": n4_time_to_optimal(Q, W, stream, "walk", args.adder_walk,
+                                                                     unitary=u)}))
+    else:
+        print(json.dumps({"config3_time_to_optimal": config3_time_to_optimal(Q, W, stream, "walk",
+                                                                             args.config3_walk)}))
 
 
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    elif a.config3_walk:
+    elif a.config3_walk or a.adder_walk:
         run_config3_walk(a)
     elif a.level_only:
         run_level_only(a)

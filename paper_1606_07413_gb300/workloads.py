@@ -16,6 +16,10 @@ the same shape are drawn here):
 * a walk state is a uniform ``L``-bit string (Sec. 3: trails start at random
   points of the walk space).
 
+The paper's named circuits that the text fixes are given as basis-state
+permutations (``permutation_targets``): the Toffoli and Fredkin gates
+(Table 1) and a 4-qubit 1-bit full adder (Sec. 5.3).
+
 Gate lists are ``(m, 3)`` int32 arrays of ``(op, a, b)`` rows in time order
 (first row acts first, so the circuit unitary is ``G_m ... G_1``).
 """
@@ -50,6 +54,31 @@ def clifford_word(rng: np.random.Generator, n: int, length: int = 200) -> np.nda
             t = t + 1 if t >= c else t
             rows.append((OP_CNOT, c, t))
     return np.asarray(rows, dtype=np.int32).reshape(-1, 3)
+
+
+def permutation_targets() -> dict:
+    """name -> (n, perm): classical reversible circuits as permutations of the
+    computational basis, basis state c mapped to perm[c]; qubit q is bit q.
+
+    * toffoli: bit 2 ^= bit 0 AND bit 1 (Table 1);
+    * fredkin: bits 1 and 2 swapped when bit 0 is set (Table 1);
+    * adder: the 1-bit full adder (Sec. 5.3) on (a, b, c, d) = bits 0..3,
+      (a, b, c, d) -> (a, b, a ^ b ^ c, d ^ maj(a, b, c)).  With u = a ^ c
+      and v = b ^ c, maj(a, b, c) = u v ^ c, so the adder is a Toffoli on
+      (u, v -> d) between two CNOT circuits: the affine equivalence to the
+      Toffoli that Sec. 5.3 reports.
+    """
+    def bit(c, q):
+        return (c >> q) & 1
+
+    tof = [c ^ (4 if (c & 3) == 3 else 0) for c in range(8)]
+    fred = [(c & 1) | (bit(c, 2) << 1) | (bit(c, 1) << 2) if c & 1 else c for c in range(8)]
+    adder = []
+    for c in range(16):
+        a, b, ci, d = bit(c, 0), bit(c, 1), bit(c, 2), bit(c, 3)
+        maj = (a & b) | (a & ci) | (b & ci)
+        adder.append(a | (b << 1) | ((a ^ b ^ ci) << 2) | ((d ^ maj) << 3))
+    return {"toffoli": (3, tof), "fredkin": (3, fred), "adder": (4, adder)}
 
 
 def random_paulis(rng: np.random.Generator, n: int, t: int) -> np.ndarray:

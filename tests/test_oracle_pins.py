@@ -301,6 +301,51 @@ def test_mitm_matches_brute_force_on_tiny_instances(orc):
     assert len(seen) >= 2
 
 
+def _perm_unitary(perm):
+    d = len(perm)
+    u = np.zeros((d, d, 4), np.int64)
+    for c, r in enumerate(perm):
+        u[r, c, 0] = 1
+    return u
+
+
+def test_full_adder_is_a_toffoli_between_cnot_circuits(orc):
+    """Sec. 5.3: the 4-qubit 1-bit full adder is affine equivalent to the
+    Toffoli (equal up to CNOTs), so it has the Toffoli's T-count.  Pinned as
+    permutations (adder = L2 . Toffoli(u, v -> d) . L1 with L1, L2 linear maps
+    of the bits) and in channel form, where L1 and L2 are Cliffords (signed
+    permutations, sde 0) and the channel of the composition is the product
+    of the channels."""
+    n, adder = W.permutation_targets()["adder"]
+    assert n == 4 and sorted(adder) == list(range(16))
+
+    def bits(c):
+        return [(c >> q) & 1 for q in range(4)]
+
+    def word(b):
+        return b[0] | (b[1] << 1) | (b[2] << 2) | (b[3] << 3)
+
+    def l1(c):  # (a, b, c, d) -> (a ^ c, b ^ c, c, d)
+        a, b, ci, d = bits(c)
+        return word([a ^ ci, b ^ ci, ci, d])
+
+    def tof(c):  # d ^= u v
+        u, v, ci, d = bits(c)
+        return word([u, v, ci, d ^ (u & v)])
+
+    def l2(c):  # (u, v, c, d) -> (u ^ c, v ^ c, u ^ v ^ c, d ^ c)
+        u, v, ci, d = bits(c)
+        return word([u ^ ci, v ^ ci, u ^ v ^ ci, d ^ ci])
+
+    assert [l2(tof(l1(c))) for c in range(16)] == adder
+    P1, PT, P2 = ([f(c) for c in range(16)] for f in (l1, tof, l2))
+    C1, CT, C2, CA = (orc.channel_from_unitary(4, _perm_unitary(p), 0) for p in (P1, PT, P2, adder))
+    for Cl in (C1, C2):
+        assert orc.sde(Cl) == 0 and orc.is_clifford(Cl)
+    assert CA.equals(C2 @ CT @ C1)
+    assert orc.sde(CA) == orc.sde(CT)
+
+
 def test_construction_bound_and_sde_lower_bound(orc):
     for cfg in (1, 2):
         c = W.CONFIGS[cfg]
