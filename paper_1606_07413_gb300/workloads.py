@@ -1,7 +1,8 @@
 """Seeded synthetic inputs for the deterministic-walk T-count search.
 
-This module only draws random choices: Pauli codes, Clifford gate words and
-walk states.  It holds none of the method's arithmetic (no unitary or channel
+This module draws random choices (Pauli codes, Clifford gate words and walk
+states) and lists the named circuits the paper's text fixes, as basis-state
+permutations.  It holds none of the method's arithmetic (no unitary or channel
 products, no rotation matrices, no canonical form, no hash); both the CUDA path
 and the CPU oracle receive these choices and build every matrix themselves.
 
