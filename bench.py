@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--config3-walk", type=int, default=0, metavar="TABLE_LOG2",
                     help="only time the n = 4 seeded target's search by the collision walk alone with a "
                          "2^TABLE_LOG2-slot table, print its JSON and exit")
+    ap.add_argument("--exhaustive-only", action="store_true",
+                    help="only time one whole n = 4 level-7 exhaustive pass (no claw), print its JSON and exit")
     ap.add_argument("--adder-walk", type=int, default=0, metavar="TABLE_LOG2",
                     help="only time the 4-qubit full adder's search by the collision walk alone with a "
                          "2^TABLE_LOG2-slot table, print its JSON and exit")
@@ -78,7 +80,7 @@ def workload_config(c):
 # DRAM traffic of one k_walks<3> launch of the headline workload, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # kernel source it was taken on (hash of the walk kernel's source files)
-WALK_TRAFFIC = {"bytes_per_launch": 2175232, "source_sha256_16": "6a9f002080cc70fd"}
+WALK_TRAFFIC = {"bytes_per_launch": 2521856, "source_sha256_16": "e79a13e5d494f0d1"}
 
 
 def walk_source_hash() -> str:
@@ -680,10 +682,23 @@ def run_config3_walk(args):
                                                                              args.config3_walk)}))
 
 
+def run_exhaustive_only(args):
+    import torch
+
+    import paper_1606_07413_gb300 as Q
+    from paper_1606_07413_gb300 import build as B
+    from paper_1606_07413_gb300 import workloads as W
+
+    B.build()
+    print(json.dumps({"n4_level7_exhaustive_pass": exhaustive_level_pass(Q, W, torch.cuda.Stream())}))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.exhaustive_only:
+        run_exhaustive_only(a)
     elif a.config3_walk or a.adder_walk:
         run_config3_walk(a)
     elif a.level_only:

@@ -878,9 +878,40 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_rewalk_arrays(LevelCtx lv,
     }
 }
 
+// The nd low base-xi digits of v, digit j in byte j (xi <= 255).
+__device__ __forceinline__ uint64_t base_xi_digits(uint64_t v, uint32_t xi, int nd)
+{
+    uint64_t r = 0;
+    for (int j = 0; j < nd; j++) {
+        r |= (v % xi) << (8 * j);
+        v /= xi;
+    }
+    return r;
+}
+
+// (d + s) mod xi^nd on packed base-xi digits (digit j in byte j, nd <= 8).
+__device__ __forceinline__ uint64_t add_base_xi(uint64_t d, uint64_t s, uint32_t xi, int nd)
+{
+    uint64_t r = 0;
+    uint32_t carry = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        if (j < nd) {
+            uint32_t t = (uint32_t)((d >> (8 * j)) & 0xFFu) + (uint32_t)((s >> (8 * j)) & 0xFFu) + carry;
+            carry = t >= xi ? 1u : 0u;
+            t -= carry * xi;
+            r |= (uint64_t)t << (8 * j);
+        }
+    }
+    return r;
+}
+
 // Exhaustive level pass (CertArgs): one lane group per point, grid-stride.
 // VONLY: the points are V products (a.side == 0), which never touch C^, so
-// the CTA stages the smaller layout without it.
+// the CTA stages the smaller layout without it.  A point index is nd base-xi
+// digits: the h rotation digits (q_j = digit + 1), then for a W point of odd
+// k the chunk digit (chunk = digit + 1).  Each thread divides only for its
+// first index and its stride; every further index adds the stride's digits.
 template <int NQ, bool VONLY>
 __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_certify(CertArgs a)
 {
@@ -889,20 +920,23 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_certify(CertArgs a)
     const int side = VONLY ? 0 : a.side;
     const Lanes g = thread_lanes<NQ>();
     const uint32_t xi = a.lv.xi;
-    for (uint64_t i = (uint64_t)blockIdx.x * Geo<NQ>::WALKS + group_in_cta<NQ>(); i < a.count;
-         i += (uint64_t)gridDim.x * Geo<NQ>::WALKS) {
+    const int h = a.lv.h;
+    const bool has_chunk = side == 1 && (a.lv.k & 1);
+    const int nd = h + (has_chunk ? 1 : 0);
+    const uint64_t hmask = h >= 8 ? ~0ull : (1ull << (8 * h)) - 1;
+    const uint64_t stride = (uint64_t)gridDim.x * Geo<NQ>::WALKS;
+    uint64_t i = (uint64_t)blockIdx.x * Geo<NQ>::WALKS + group_in_cta<NQ>();
+    // While i + stride < count, the stride is below xi^nd and its nd digits
+    // are exact; otherwise the loop ends before the sum is used.
+    uint64_t dig = 0, sdig = 0;
+    if (i < a.count) {
+        dig = base_xi_digits(a.first + i, xi, nd);
+        sdig = base_xi_digits(stride, xi, nd);
+    }
+    for (; i < a.count; i += stride, dig = add_base_xi(dig, sdig, xi, nd)) {
         const uint64_t idx = a.first + i;
-        uint64_t tuple = idx;
-        uint32_t chunk = 0;
-        if (side == 1 && (a.lv.k & 1)) {
-            chunk = (uint32_t)(idx / a.xi_h) + 1;
-            tuple = idx % a.xi_h;
-        }
-        uint64_t qpack = 0;
-        for (int j = 0; j < a.lv.h; j++) {
-            qpack |= (uint64_t)(tuple % xi + 1) << (8 * j);
-            tuple /= xi;
-        }
+        const uint64_t qpack = (dig & hmask) + (0x0101010101010101ull & hmask);
+        const uint32_t chunk = has_chunk ? (uint32_t)((dig >> (8 * h)) & 0xFFu) + 1 : 0u;
         uint64_t key = coset_hash<NQ>(side, qpack, chunk, a.base, a.lv, sm, g);
         if (key == ~0ull) key = ~0ull - 1; // ~0 marks an empty slot
         if (g.sub == 0) {
