@@ -496,3 +496,37 @@ def test_known_normal_form_is_a_claw(orc, n, t):
     assert y[0] == y[1]
     cls, paulis = orc.classify(C, t, chunk, L, xv, xw)
     assert cls == orc.CLAW and paulis == ps
+
+
+@pytest.mark.parametrize("n,t", [(2, 3), (2, 5), (3, 5)])
+def test_moving_a_rotation_across_the_split_keeps_the_claw(orc, n, t):
+    """Eq. mitm with the odd level's extra rotation on the other side, as
+    the exhaustive pass splits it when C^ has a denominator: for a
+    decomposition C = R(P_t)...R(P_1) D, V' = R(P_(h+1))...R(P_1) and
+    W' = R(P_(h+2))^T...R(P_t)^T C lie in one Clifford coset, and a wrong
+    order of W' factors (or another rotation) breaks it (exact products,
+    checked by the oracle's exact coset test)."""
+    rng = np.random.default_rng(300 + 10 * n + t)
+    ps = _noncommuting_chain(orc, rng, n, t)
+    rows = [tuple(r) for r in W.clifford_word(rng, n, 40)] + [(W.OP_RP, p, 0) for p in ps]
+    C = orc.channel_from_circuit(n, np.asarray(rows, np.int32))
+    assert orc.sde(C) >= 1
+    h = t // 2
+    Vp = orc.identity(n)
+    for p in ps[:h + 1]:
+        Vp = orc.rhat(n, p) @ Vp
+    Wp = C
+    for p in reversed(ps[h + 1:]):
+        Wp = orc.rhat(n, p, transpose=True) @ Wp
+    assert orc.same_coset(Vp, Wp)
+    wrong = list(ps[h + 1:])
+    if len(wrong) >= 2:
+        wrong[0], wrong[1] = wrong[1], wrong[0]  # non-commuting neighbours in the wrong order
+    else:
+        wrong[0] = wrong[0] % (4 ** n - 1) + 1  # another rotation
+    Ws = C
+    for p in reversed(wrong):
+        Ws = orc.rhat(n, p, transpose=True) @ Ws
+    assert not orc.same_coset(Vp, Ws)
+    assert orc.verify(C, ps)
+
