@@ -251,8 +251,8 @@ __device__ __forceinline__ Decoded decode(uint64_t x, const LevelCtx &lv)
 }
 
 // nu and h of one decoded point: the exact product of side `side` (0: V,
-// 1: W) for the rotations in qpack (and the chunk, odd k), its fingerprint
-// canonical form and the position-keyed hash with hash base `base`, as a
+// 1: W) for the rotations in qpack (and the chunk, odd k), its column
+// fingerprints and their multiset hash with hash base `base`, as a
 // full 64-bit value.  All lanes of the group call it with the same point.
 template <int NQ>
 __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_t base, const LevelCtx &lv,
