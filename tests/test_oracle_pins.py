@@ -530,3 +530,57 @@ def test_moving_a_rotation_across_the_split_keeps_the_claw(orc, n, t):
     assert not orc.same_coset(Vp, Ws)
     assert orc.verify(C, ps)
 
+
+def _is_signed_permutation_product(V, Wm):
+    """V^T W in exact (a, b) arithmetic: value (a + b sqrt2) / sqrt2^E with
+    E = E_V + E_W; a signed permutation has one entry of value +-1 in every
+    row and column and zeros elsewhere."""
+    Va, Vb, Wa, Wb = (np.asarray(x, dtype=object) for x in (V.a, V.b, Wm.a, Wm.b))
+    Pa = Va.T.dot(Wa) + 2 * Vb.T.dot(Wb)
+    Pb = Va.T.dot(Wb) + Vb.T.dot(Wa)
+    E = V.E + Wm.E
+
+    def unit(a, b):
+        if E % 2 == 0:
+            return b == 0 and abs(a) == 2 ** (E // 2)
+        return a == 0 and abs(b) == 2 ** ((E - 1) // 2)
+
+    D = Pa.shape[0]
+    for i in range(D):
+        units = 0
+        for j in range(D):
+            a, b = int(Pa[i, j]), int(Pb[i, j])
+            if unit(a, b):
+                units += 1
+            elif a != 0 or b != 0:
+                return False
+        if units != 1:
+            return False
+    return True
+
+
+@pytest.mark.parametrize("n,t,seed", [(1, 2, 21), (1, 3, 22), (2, 2, 23), (2, 3, 24)])
+def test_same_coset_is_the_signed_permutation_test_by_brute_force(orc, n, t, seed):
+    """Sec. 4.1: two channel matrices lie in one Clifford coset exactly when
+    V^T W is a signed permutation (both are orthogonal, and a Clifford's
+    channel is a signed permutation).  Over every V and W point of the
+    level (every chunk for odd t), the oracle's canonical-form equality
+    agrees with that test done here in exact integer arithmetic, and the
+    construction's level has at least one such pair."""
+    import itertools
+
+    gates, _ = W.seeded_target(n, t, seed)
+    C = orc.channel_from_circuit(n, gates)
+    k, h, xi = t, t // 2, 4 ** n - 1
+    found = 0
+    for chunk in (range(1, xi + 1) if k & 1 else [0]):
+        tuples = [list(q) for q in itertools.product(range(1, xi + 1), repeat=h)]
+        Vs = [orc.half_product(C, k, chunk, 0, q) for q in tuples]
+        Ws = [orc.half_product(C, k, chunk, 1, q) for q in tuples]
+        for V in Vs:
+            for Wm in Ws:
+                want = _is_signed_permutation_product(V, Wm)
+                assert orc.same_coset(V, Wm) == want
+                found += want
+    assert found >= 1
+
