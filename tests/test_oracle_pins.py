@@ -584,3 +584,70 @@ def test_same_coset_is_the_signed_permutation_test_by_brute_force(orc, n, t, see
                 found += want
     assert found >= 1
 
+
+@pytest.mark.parametrize("n,t,seed,chunk", [(1, 3, 31, 2), (2, 2, 32, 0), (2, 3, 33, 5)])
+def test_rewalk_matches_brute_force_trail_enumeration(orc, n, t, seed, chunk):
+    """Sec. 3, Fig. 2 on a walk small enough to tabulate (2^6 states): for
+    trails that end at a common point, the re-walk must report the first
+    point where they meet, found here by enumerating both trails.  A start
+    that lies on the other trail is Robin Hood; otherwise the two distinct
+    predecessors of the meeting point are classified by their decoded sides
+    and rotations and, across sides, by exact coset equality.  Trails that
+    never meet within their lengths are no merge.  Six-bit states make hash
+    collisions between distinct points common, so every class occurs."""
+    gates, _ = W.seeded_target(n, t, seed)
+    C = orc.channel_from_circuit(n, gates)
+    k, L, version = t, 6, 3
+    F = orc.walk_step(C, k, chunk, version, L, np.arange(1 << L, dtype=np.uint64)).astype(np.int64)
+
+    def trail(x, m):
+        out = [x]
+        for _ in range(m):
+            out.append(int(F[out[-1]]))
+        return out
+
+    def expected_class(a, b):
+        sa, qa = orc.decode(n, k, L, a)
+        sb, qb = orc.decode(n, k, L, b)
+        if sa == sb:
+            return orc.TRIVIAL if qa == qb else orc.SAME_SIDE
+        qv, qw = (qa, qb) if sa == 0 else (qb, qa)
+        V = orc.half_product(C, k, chunk, 0, qv)
+        Wm = orc.half_product(C, k, chunk, 1, qw)
+        return orc.CLAW if orc.same_coset(V, Wm) else orc.FALSE_HASH
+
+    rng = np.random.default_rng(seed)
+    seen = {}
+    for _ in range(400):
+        a, b = (int(v) for v in rng.integers(0, 1 << L, size=2))
+        A, B = trail(a, 60), trail(b, 60)
+        pos_a = {}
+        for i, x in enumerate(A):
+            pos_a.setdefault(x, i)
+        meet = next(((pos_a[y], j) for j, y in enumerate(B) if y in pos_a), None)
+        if meet is None or a == b:
+            continue
+        i0, j0 = meet
+        tail = 3  # both trails go on to a common end point
+        la, lb = i0 + tail, j0 + tail
+        cls, x, y, paulis = orc.rewalk(C, k, chunk, version, L, a, la, b, lb)
+        if j0 == 0 or i0 == 0:
+            want = orc.ROBIN_HOOD
+            assert (x, y) == ((b, b) if j0 == 0 else (a, a)) and cls == want
+        else:
+            want = expected_class(A[i0 - 1], B[j0 - 1])
+            assert cls == want and {x, y} == {A[i0 - 1], B[j0 - 1]}
+            if want == orc.CLAW:
+                assert orc.verify(C, paulis)
+        seen[want] = seen.get(want, 0) + 1
+    # two trails that do not meet within their lengths
+    for _ in range(200):
+        a, b = (int(v) for v in rng.integers(0, 1 << L, size=2))
+        A, B = trail(a, 1), trail(b, 1)
+        if not set(A) & set(B):
+            assert orc.rewalk(C, k, chunk, version, L, a, 1, b, 1)[0] == orc.NO_MERGE
+            seen[orc.NO_MERGE] = seen.get(orc.NO_MERGE, 0) + 1
+            break
+    assert seen.get(orc.ROBIN_HOOD, 0) >= 1 and seen.get(orc.NO_MERGE, 0) == 1
+    assert sum(seen.get(c, 0) for c in (orc.TRIVIAL, orc.SAME_SIDE, orc.CLAW, orc.FALSE_HASH)) >= 10
+
