@@ -651,3 +651,27 @@ def test_rewalk_matches_brute_force_trail_enumeration(orc, n, t, seed, chunk):
     assert seen.get(orc.ROBIN_HOOD, 0) >= 1 and seen.get(orc.NO_MERGE, 0) == 1
     assert sum(seen.get(c, 0) for c in (orc.TRIVIAL, orc.SAME_SIDE, orc.CLAW, orc.FALSE_HASH)) >= 10
 
+
+def test_fingerprint_weights_are_the_splitmix64_stream(orc):
+    """The fingerprint weights (Ua, Ub) of row i >= 1 are outputs 2i and 2i + 1
+    of the SplitMix64 stream (Steele, Lea & Flood 2014) seeded with
+    0x6A09E667F3BCC908, and row 0 has weight 0.  The generator is written
+    here from its published definition and checked against its published
+    first output for seed 0."""
+    M64 = (1 << 64) - 1
+    gamma = 0x9E3779B97F4A7C15
+
+    def output(seed, j):  # j-th output (0-based) of the stream seeded with seed
+        z = (seed + (j + 1) * gamma) & M64
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+        return z ^ (z >> 31)
+
+    assert output(0, 0) == 0xE220A8397B1DCDAF
+    for n in (1, 2, 3):
+        ua, ub = orc.fp_weights(n)
+        assert ua[0] == 0 and ub[0] == 0
+        for i in range(1, 4 ** n):
+            assert int(ua[i]) == output(0x6A09E667F3BCC908, 2 * i) & 0xFFFFFFFF
+            assert int(ub[i]) == output(0x6A09E667F3BCC908, 2 * i + 1) & 0xFFFFFFFF
+
