@@ -4,7 +4,10 @@ Requests (a target and its k_max) arrive at any time.  Between two rounds of
 the batched search (qcs_batch_*) the server admits waiting requests while a
 job slot and enough device memory for the job's walk states, distinguished-
 point table and merge queue are free, then runs one round for every admitted
-job, so new work overlaps on the device with the work already there.  A job
+job, so new work overlaps on the device with the work already there.  The
+exhaustive level pass that a round may run for one job at a time allocates
+a key table for the call; the budget keeps room for the largest such table
+among the admitted jobs.  A job
 leaves the batch as soon as it has its answer (or passes its deadline) and
 its memory is released for the next request.  Times are measured from each
 request's arrival to its answer.
@@ -21,14 +24,23 @@ import numpy as np
 import paper_1606_07413_gb300 as Q
 
 
+def exhaustive_table_bytes(params) -> int:
+    """Upper bound on the key table of one exhaustive level pass under these
+    search parameters: a level of at most 2^exhaustive_log2 points stores at
+    most half of them, in a power-of-two table of at least twice as many
+    slots (and at least 1024), 16 bytes a slot."""
+    e = int(getattr(params, "exhaustive_log2", 0) or 0)
+    return 16 << max(e, 10) if e > 0 else 0
+
+
 class Request:
     __slots__ = ("rid", "n", "gates", "k_max", "params", "t_arrival", "t_admit", "t_done", "prob", "slot",
-                 "bytes", "status", "result", "future")
+                 "bytes", "table_bytes", "status", "result", "future")
 
     def __init__(self, rid, n, gates, k_max, params, t_arrival):
         self.rid, self.n, self.gates, self.k_max, self.params = rid, n, gates, k_max, params
         self.t_arrival, self.t_admit, self.t_done = t_arrival, None, None
-        self.prob, self.slot, self.bytes = None, None, 0
+        self.prob, self.slot, self.bytes, self.table_bytes = None, None, 0, 0
         self.status, self.result, self.future = "queued", None, None
 
 
@@ -60,7 +72,9 @@ class Server:
         self.next_id += 1
         r = Request(rid, n, np.asarray(gates, np.int32), k_max, params,
                     self.clock() if t_arrival is None else t_arrival)
-        r.future = self.pool.submit(Q.Problem.from_circuit, n, r.gates, k_max, params or self.params_for(n))
+        p = params or self.params_for(n)
+        r.table_bytes = exhaustive_table_bytes(p)
+        r.future = self.pool.submit(Q.Problem.from_circuit, n, r.gates, k_max, p)
         self.requests[rid] = r
         self.waiting.append(r)
         return rid
@@ -81,7 +95,8 @@ class Server:
                 break  # arrival order: wait for the head's set-up
             prob = r.future.result()
             need = self.batch.job_bytes(prob)
-            if self.used + need > self.budget and self.running:
+            table = max([r.table_bytes] + [o.table_bytes for o in self.running.values()])
+            if self.used + need + table > self.budget and self.running:
                 break  # memory is full: wait for a job to leave
             try:
                 slot = self.batch.add(prob)

@@ -129,3 +129,31 @@ def test_a_full_batch_leaves_the_request_queued(fake):
         for _ in range(5):
             srv.step()
         assert srv.poll(rid)["status"] == "found"
+
+
+def test_admission_keeps_room_for_one_exhaustive_key_table(fake):
+    """A round may run the exhaustive pass for one job, whose key table is
+    allocated for the call: admission keeps room for the largest such table
+    among the admitted jobs (16 bytes x 2^exhaustive_log2 at most)."""
+    from types import SimpleNamespace
+
+    assert serve.exhaustive_table_bytes(SimpleNamespace(exhaustive_log2=10)) == 16 << 10
+    assert serve.exhaustive_table_bytes(SimpleNamespace(exhaustive_log2=0)) == 0
+    assert serve.exhaustive_table_bytes(None) == 0
+    table = 16 << 10
+    for budget, most in ((table + 450, 2), (table + 250, 1)):
+        clock = Clock()
+        with serve.Server(bparams(4), memory_budget=budget, clock=clock,
+                          params_for=lambda n: SimpleNamespace(exhaustive_log2=10)) as srv:
+            rids = [srv.submit(2, [[3, 0, 0]], 2) for _ in range(4)]
+            peak = 0
+            for _ in range(100):
+                clock.t += 0.01
+                srv.step()
+                peak = max(peak, len(srv.running))
+                assert not srv.running or srv.used + table <= budget or len(srv.running) == 1
+                if srv.idle():
+                    break
+            assert srv.idle() and peak == most
+            assert all(srv.poll(r)["status"] == "found" for r in rids)
+
