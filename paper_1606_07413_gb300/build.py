@@ -66,23 +66,29 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         if s.endswith(".cu"):
             cmd += ["-Xptxas", "-v"] if verbose else []
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
-    failed = []
-    for cmd, p in procs:
-        out, _ = p.communicate()
-        if verbose or p.returncode:
-            sys.stderr.write(out.decode(errors="replace"))
-        if p.returncode:
-            failed.append(" ".join(cmd))
-    if failed:
-        raise RuntimeError("libqcs build failed:\n" + "\n".join(failed))
-    vers = os.path.join(BUILD, "exports.map")
-    with open(vers, "w") as f:
-        f.write("{ global: qcs_*; local: *; };\n")
     tmp = LIB + f".{os.getpid()}.tmp"
-    link = [cc, "-shared", *ARCH, "-o", tmp, *objs, "-Xlinker", f"--version-script={vers}", "-lpthread"]
-    subprocess.check_call(link)
-    os.replace(tmp, LIB)
-    os.replace(peak_tmp, PEAK_LIB)
+    try:
+        failed = []
+        for cmd, p in procs:
+            out, _ = p.communicate()
+            if verbose or p.returncode:
+                sys.stderr.write(out.decode(errors="replace"))
+            if p.returncode:
+                failed.append(" ".join(cmd))
+        if failed:
+            raise RuntimeError("libqcs build failed:\n" + "\n".join(failed))
+        vers = os.path.join(BUILD, "exports.map")
+        with open(vers, "w") as f:
+            f.write("{ global: qcs_*; local: *; };\n")
+        link = [cc, "-shared", *ARCH, "-o", tmp, *objs, "-Xlinker", f"--version-script={vers}", "-lpthread"]
+        subprocess.check_call(link)
+        os.replace(tmp, LIB)
+        os.replace(peak_tmp, PEAK_LIB)
+    finally:
+        # a failed build leaves no half-written library behind
+        for f in (tmp, peak_tmp):
+            if os.path.exists(f):
+                os.remove(f)
     return LIB
 
 
