@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-T-count run")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and other-size runs")
     ap.add_argument("--batched-only", action="store_true",
-                    help="only run the batched-search comparison (config 4), print its JSON and exit")
+                    help="only run the batched-search comparison (256 seeded targets), print its JSON and exit")
     ap.add_argument("--level-only", choices=["n2_level3", "n4_level7"], default=None,
                     help="only time that single-target level launch (walk-kernel throughput), print its JSON and exit")
     ap.add_argument("--config3-walk", type=int, default=0, metavar="TABLE_LOG2",
@@ -253,7 +253,7 @@ def level_throughput(Q, W, torch, cfg, k, steps, stream, launches=3, alu_per_s=N
 
 
 def run_batched(Q, W, torch, stream, n_targets=256, rounds=12, mac_peak=None):
-    """Config 4: many seeded targets in one persistent launch per qubit count
+    """The batched workload: many seeded targets in one persistent launch per qubit count
     (one CUDA-graph replay per round) against the same jobs launched one
     target at a time, on identical work (the trajectories are deterministic)."""
     from paper_1606_07413_gb300 import autotune
@@ -359,8 +359,8 @@ def config3_time_to_optimal(Q, W, stream, mode="exhaustive", table_log2=30, queu
 
 
 def n4_time_to_optimal(Q, W, stream, mode="exhaustive", table_log2=30, queue_log2=24, limit_s=900, unitary=None):
-    """Time to the optimal T-count (at most 7) of an n = 4 target: config 3's
-    seeded 7-factor target, or the given unitary (Z[omega] coefficients over
+    """Time to the optimal T-count (at most 7) of an n = 4 target: the seeded
+    7-factor target, or the given unitary (Z[omega] coefficients over
     sqrt2^0).  mode "exhaustive": the ladder settles each level by the
     exhaustive pass alone (the key table of level 7 is 512 MiB); mode "walk":
     the collision search alone with a 2^table_log2-slot table (16 bytes a
@@ -393,7 +393,7 @@ def n4_time_to_optimal(Q, W, stream, mode="exhaustive", table_log2=30, queue_log
 def exhaustive_level_pass(Q, W, stream, n=4, k=7, t=9, seed=4009):
     """One whole exhaustive pass over level k of a seeded n-qubit target whose
     sde is t > k, so no claw exists and every point is evaluated: the worst
-    case of the pass at config 3's level (n = 4, k = 7: 255^3 stored points,
+    case of the pass at the n = 4 seven-factor target's level (k = 7: 255^3 stored points,
     255^4 streamed)."""
     gates, _ = W.seeded_target(n, t, seed)
     with Q.Problem.from_circuit(n, gates, max(k, t), Q.default_params(n, exhaustive_log2=34)) as prob:
@@ -408,7 +408,7 @@ def exhaustive_level_pass(Q, W, stream, n=4, k=7, t=9, seed=4009):
 
 def run_serving(Q, W, torch, stream, tuned, n_requests=2000, rate=50.0, budget_bytes=2 << 30,
                 deadline_s=10.0, drain_s=15.0):
-    """Config 5: a Poisson stream of seeded targets replayed in real time into
+    """The serving workload: a Poisson stream of seeded targets replayed in real time into
     the continuous-batching server; latency is arrival to answer."""
     from paper_1606_07413_gb300 import serve
 

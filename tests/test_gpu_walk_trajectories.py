@@ -1,5 +1,5 @@
 """The walk kernel the benchmark times, at the benchmark's size and launch
-shape (config 2: n = 3, level 5, 2^16 walks, 512 steps per walk in one launch,
+shape (n = 3, level 5, 2^16 walks, 512 steps per walk in one launch,
 theta = 2^-10), checked against the oracle.  qcs_level_walk_static runs that
 kernel on caller-owned walk states, so every walk's trail can be read back:
 its current state must be the oracle's f applied `len` times to the trail's
