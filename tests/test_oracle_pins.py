@@ -675,3 +675,41 @@ def test_fingerprint_weights_are_the_splitmix64_stream(orc):
             assert int(ua[i]) == output(0x6A09E667F3BCC908, 2 * i) & 0xFFFFFFFF
             assert int(ub[i]) == output(0x6A09E667F3BCC908, 2 * i + 1) & 0xFFFFFFFF
 
+
+@pytest.mark.parametrize("n,t,seed,kmax", [(1, 3, 41, 7), (1, 5, 42, 7), (2, 3, 43, 5), (2, 5, 44, 5),
+                                            (2, 7, 45, 5), (2, 7, 46, 5)])
+def test_the_other_odd_split_finds_the_same_levels(orc, n, t, seed, kmax):
+    """The exhaustive pass of an odd level k = 2h + 1 may put the extra
+    rotation on V: V' = R(r_(h+1))..R(r_1) against W' = R(s_1)^T..R(s_h)^T C
+    (Eq. mitm with the split moved by one).  Both splits enumerate every
+    product of k rotations, so a level has a claw under one exactly when it
+    has one under the other: brute force over every V' and W' (canonical
+    forms joined in a dictionary) against the oracle's meet in the middle."""
+    import itertools
+
+    gates, _ = W.seeded_target(n, t, seed)
+    C = orc.channel_from_circuit(n, gates)
+    xi = 4 ** n - 1
+
+    def key(M):
+        f, sde = orc.canon(M)
+        return sde, f.tobytes()
+
+    for k in range(3, kmax + 1, 2):
+        h = k // 2
+        stored = set()
+        for s_ in itertools.product(range(1, xi + 1), repeat=h):
+            Wp = C
+            for p in reversed(s_):
+                Wp = orc.rhat(n, p, transpose=True) @ Wp
+            stored.add(key(Wp))
+        claw = False
+        for r in itertools.product(range(1, xi + 1), repeat=h + 1):
+            Vp = orc.identity(n)
+            for p in r:
+                Vp = orc.rhat(n, p) @ Vp
+            if key(Vp) in stored:
+                claw = True
+                break
+        assert claw == (orc.mitm_level(C, k) is not None), (n, t, k)
+
