@@ -65,13 +65,12 @@ def float_unitary(n, gates):
 
 
 def float_channel(n, U):
+    """C[i][j] = Tr(P_i U P_j U^dagger) / 2^n over Kronecker Paulis: with
+    A_j = U P_j U^dagger, Tr(P_i A_j) = sum_ab P_i[b, a] A_j[a, b]."""
     D = 4 ** n
-    Ps = [kron_pauli(n, j) for j in range(D)]
-    C = np.zeros((D, D))
-    for i in range(D):
-        for j in range(D):
-            C[i, j] = np.trace(Ps[i] @ U @ Ps[j] @ U.conj().T).real / 2 ** n
-    return C
+    Ps = np.stack([kron_pauli(n, j) for j in range(D)])
+    A = np.einsum("ab,jbc,dc->jad", U, Ps, U.conj())
+    return np.einsum("iba,jab->ij", Ps, A).real / 2 ** n
 
 
 def random_circuit(rng, n, length, t_gates=True):
@@ -143,11 +142,11 @@ def test_T_closed_form(orc):
     assert T.reduced().E == 1
 
 
-@pytest.mark.parametrize("n", [1, 2])
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
 def test_channel_matches_float_trace_over_kronecker_paulis(orc, n):
     rng = np.random.default_rng(10 + n)
-    for _ in range(3):
-        gates = random_circuit(rng, n, 30)
+    for _ in range(3 if n < 4 else 1):
+        gates = random_circuit(rng, n, 30 if n < 4 else 16)
         C = orc.channel_from_circuit(n, gates)
         assert np.allclose(C.values(), float_channel(n, float_unitary(n, gates)), atol=1e-9)
 
