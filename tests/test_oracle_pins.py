@@ -193,9 +193,25 @@ def test_rhat_invariants(orc, n):
 
 
 def test_rp_gate_channel_equals_rhat(orc):
-    for n in (1, 2, 3):
+    for n in (1, 2, 3, 4):
         for p in (1, 4 ** n - 1, 5 % (4 ** n - 1) + 1):
             assert orc.channel_from_circuit(n, [(W.OP_RP, p, 0)]).equals(orc.rhat(n, p))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_rhat_equals_the_float_channel_of_the_rotation(orc, n):
+    """Sec. 4.1: R(P) = e^(i pi/8) exp(-i pi P/8) = ((1 + w) I + (1 - w) P) / 2
+    with w = e^(i pi/4), built here from Kronecker Paulis; its channel,
+    evaluated in floating point over the trace definition, equals the
+    oracle's exact R^(P) and (as the transpose) R^(P)^T."""
+    rng = np.random.default_rng(60 + n)
+    ps = {1, 4 ** n - 1} | {int(v) for v in rng.integers(1, 4 ** n, size=6)}
+    d = 1 << n
+    for p in sorted(ps):
+        R = 0.5 * (1 + w8) * np.eye(d) + 0.5 * (1 - w8) * kron_pauli(n, p)
+        F = float_channel(n, R)
+        assert np.allclose(orc.rhat(n, p).values(), F, atol=1e-12)
+        assert np.allclose(orc.rhat(n, p, transpose=True).values(), F.T, atol=1e-12)
 
 
 # ------------------------------------------------------ canonical form modulo Clifford
