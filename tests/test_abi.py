@@ -74,6 +74,24 @@ def test_verify_agrees_with_oracle_on_random_sequences(qlib, orc):
         assert Q.verify_decomposition(n, u, e, cand) == orc.verify(C, cand)
 
 
+def test_verify_agrees_with_oracle_at_four_qubits(qlib, orc):
+    """The library's exact host verification (Eq. tcount_synthesis: D^ must
+    be a signed permutation) on 4-qubit targets with up to seven rotations,
+    against the oracle: the true decomposition, a reordered one and a
+    corrupted one."""
+    rng = np.random.default_rng(44)
+    for t in (4, 7):
+        ps = [int(v) for v in rng.integers(1, 256, size=t)]
+        rows = [tuple(r) for r in W.clifford_word(rng, 4, 30)] + [(W.OP_RP, p, 0) for p in ps]
+        u, e = orc.unitary_from_circuit(4, np.asarray(rows, np.int32))
+        C = orc.channel_from_circuit(4, np.asarray(rows, np.int32))
+        bad = list(ps)
+        bad[t // 2] = bad[t // 2] % 255 + 1
+        for cand in (ps, ps[::-1], bad):
+            assert Q.verify_decomposition(4, u, e, cand) == orc.verify(C, cand)
+        assert Q.verify_decomposition(4, u, e, ps)
+
+
 def test_create_problem_rejects_bad_input_before_any_device_work(qlib):
     d = 4
     u = np.zeros((d, d, 4), np.int64)
