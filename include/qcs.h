@@ -379,6 +379,16 @@ QCS_API uint64_t qcs_level_points(const qcs_problem *prob, int k);
 /* Copy C^ (reduced) to host arrays a, b (4^n x 4^n) and its exponent. */
 QCS_API int qcs_get_channel(const qcs_problem *prob, int64_t *a, int64_t *b, int32_t *exp);
 
+/* The channel representation C^ of a target unitary (Sec. 4.1: entry
+ * (i, j) = Tr(P_i U P_j U^dagger) / 2^n over the Pauli codes), exactly and
+ * reduced to its smallest exponent: entry (i, j) = (a + b sqrt2) / sqrt2^exp
+ * at a[i 4^n + j], b[i 4^n + j] (row-major, 4^n x 4^n, caller-owned), and
+ * *exp = sde(C^).  target as in qcs_create_problem.  Pure host, no GPU; the
+ * same arithmetic that qcs_create_problem uses.  QCS_OK, or QCS_ERR_ARG /
+ * QCS_ERR_NOT_UNITARY / QCS_ERR_OVERFLOW. */
+QCS_API int qcs_channel_from_unitary(int n_qubits, const int64_t *target, int32_t target_exp, int64_t *a,
+                                     int64_t *b, int32_t *exp);
+
 /* Synchronises and frees everything the problem owns.  NULL is a no-op. */
 QCS_API void qcs_destroy_problem(qcs_problem *prob);
 

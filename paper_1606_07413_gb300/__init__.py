@@ -17,7 +17,8 @@ import numpy as np
 from . import build as _build_mod
 
 __all__ = ["lib", "Params", "Result", "Problem", "Batch", "BatchParams", "default_params",
-           "default_batch_params", "verify_decomposition", "strerror", "QcsError", "plan_level"]
+           "default_batch_params", "verify_decomposition", "channel_from_unitary", "strerror", "QcsError",
+           "plan_level"]
 
 OK = 0
 ERR_ARG, ERR_NOT_UNITARY, ERR_NOMEM, ERR_CUDA, ERR_MISMATCH, ERR_OVERFLOW, ERR_BUSY, ERR_TIMEOUT, ERR_DEVICE = \
@@ -137,6 +138,7 @@ def lib():
             "qcs_problem_sde": (ctypes.c_int, [_vp]),
             "qcs_level_points": (_u64, [_vp, ctypes.c_int]),
             "qcs_get_channel": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(_i32)]),
+            "qcs_channel_from_unitary": (ctypes.c_int, [ctypes.c_int, _vp, _i32, _vp, _vp, ctypes.POINTER(_i32)]),
             "qcs_destroy_problem": (None, [_vp]),
             "qcs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "qcs_last_cuda_error": (ctypes.c_char_p, []),
@@ -419,6 +421,20 @@ def measure_int_peak(kind: str = "imad", blocks_per_sm: int = 8, iters: int = 40
     if rc != 0:
         raise RuntimeError(f"qcs_peak_{kind} failed with CUDA error {-rc}")
     return ops.value, ms.value
+
+
+def channel_from_unitary(n, target, exp):
+    """qcs_channel_from_unitary: the exact channel representation of a target
+    unitary, reduced: (a, b, sde) with entries (a + b sqrt2) / sqrt2^sde (no
+    GPU needed)."""
+    u = np.ascontiguousarray(np.asarray(target, np.int64))
+    D = 4 ** int(n)
+    a = np.zeros((D, D), np.int64)
+    b = np.zeros((D, D), np.int64)
+    e = _i32(0)
+    _check(lib().qcs_channel_from_unitary(int(n), u.ctypes.data_as(_vp), int(exp), a.ctypes.data_as(_vp),
+                                          b.ctypes.data_as(_vp), ctypes.byref(e)), "qcs_channel_from_unitary")
+    return a, b, int(e.value)
 
 
 def verify_decomposition(n, target, exp, paulis) -> bool:

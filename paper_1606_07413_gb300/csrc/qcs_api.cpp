@@ -1014,6 +1014,19 @@ int qcs_verify_decomposition(int n, const int64_t *target, int32_t target_exp, c
     return exact_verify(n, C, paulis, t, nullptr);
 }
 
+int qcs_channel_from_unitary(int n, const int64_t *target, int32_t target_exp, int64_t *a, int64_t *b,
+                             int32_t *exp)
+{
+    if (n < 1 || n > 4 || !target || !a || !b || !exp) return QCS_ERR_ARG;
+    PMat C;
+    const int rc = exact_channel_from_unitary(n, target, target_exp, &C);
+    if (rc) return rc;
+    memcpy(a, C.a.data(), sizeof(int64_t) * C.a.size());
+    memcpy(b, C.b.data(), sizeof(int64_t) * C.b.size());
+    *exp = C.E;
+    return QCS_OK;
+}
+
 int qcs_walk_step(qcs_problem *P, int k, int chunk, uint32_t version, const uint64_t *in, uint64_t *out,
                   uint8_t *is_dp, size_t count, void *stream)
 {

@@ -92,6 +92,23 @@ def test_verify_agrees_with_oracle_at_four_qubits(qlib, orc):
         assert Q.verify_decomposition(4, u, e, ps)
 
 
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_channel_from_unitary_agrees_with_the_oracle(qlib, orc, n):
+    """qcs_channel_from_unitary (the library's exact host channel, Sec. 4.1)
+    equals the oracle's on Clifford+T circuits, reduced to the sde."""
+    rng = np.random.default_rng(70 + n)
+    for t in (0, 3):
+        ps = [int(v) for v in rng.integers(1, 4 ** n, size=t)]
+        rows = [tuple(r) for r in W.clifford_word(rng, n, 30)] + [(W.OP_RP, p, 0) for p in ps]
+        u, e = orc.unitary_from_circuit(n, np.asarray(rows, np.int32))
+        a, b, E = Q.channel_from_unitary(n, u, e)
+        C = orc.channel_from_unitary(n, u, e)
+        assert orc.Chan(n, a, b, E).equals(C) and E == orc.sde(C)
+    with pytest.raises(Q.QcsError) as ei:
+        Q.channel_from_unitary(n, np.zeros((1 << n, 1 << n, 4), np.int64), 0)
+    assert ei.value.code == Q.ERR_NOT_UNITARY
+
+
 def test_create_problem_rejects_bad_input_before_any_device_work(qlib):
     d = 4
     u = np.zeros((d, d, 4), np.int64)
