@@ -1,0 +1,53 @@
+"""The committed benchmark record (profiles/bench_n3_level5_walks65536.json)
+is one JSON line of bench.py's contract, internally consistent: the
+roofline fraction is achieved / peak, the reported DRAM traffic belongs to
+the walk-kernel source it was captured on, the clocks saw no throttling, and
+the end-to-end figure moved bytes each step."""
+import json
+import os
+
+import bench
+
+RECORD = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "profiles",
+                      "bench_n3_level5_walks65536.json")
+
+
+def load():
+    with open(RECORD) as f:
+        lines = [ln for ln in f if ln.strip()]
+    assert len(lines) == 1
+    return json.loads(lines[0])
+
+
+def test_record_has_the_contract_keys():
+    r = load()
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e", "clocks",
+                "gpu_launches"):
+        assert key in r, key
+    assert r["metric"] == "walk_steps_per_sec" and r["unit"] == "walk_steps/s" and r["higher_is_better"]
+    assert r["warmup"] >= 3 and r["steps"] >= 1 and r["gpu_launches"] > 0
+    assert r["config"]["workload"].startswith("n3_t5_level5")
+
+
+def test_roofline_and_timing_are_consistent():
+    r = load()
+    roof = r["roofline"]
+    assert roof["bound"] == "alu" and roof["peak"] > 0
+    assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-9
+    # steps per bench step / seconds per bench step = the headline value
+    steps_per_step = r["config"]["walks"] * r["config"]["steps_per_walk_per_step"]
+    assert abs(r["value"] - steps_per_step / (r["ms_per_step"] / 1e3)) / r["value"] < 0.02
+    if roof["traffic"] is not None:
+        assert roof["traffic"] == bench.WALK_TRAFFIC["bytes_per_launch"]
+
+
+def test_clocks_and_e2e():
+    r = load()
+    clk = r["clocks"]
+    assert not {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"} & set(clk["reasons"])
+    assert clk["sm_mhz"] >= 0.9 * clk["sm_max_mhz"]
+    e2e = r["e2e"]
+    assert e2e["unit"] == r["unit"] and e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
+    cpu = r["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] > 0
