@@ -17,9 +17,10 @@ the same shape are drawn here):
 * a walk state is a uniform ``L``-bit string (Sec. 3: trails start at random
   points of the walk space).
 
-The paper's named circuits that the text fixes are given as basis-state
-permutations (``permutation_targets``): the Toffoli and Fredkin gates
-(Table 1) and a 4-qubit 1-bit full adder (Sec. 5.3).
+The paper's named circuits that a textbook definition or the text fixes are
+given as basis-state permutations (``permutation_targets``): the Toffoli,
+Fredkin, Peres and OR gates (Table 1) and a 4-qubit 1-bit full adder
+(Sec. 5.3).
 
 Gate lists are ``(m, 3)`` int32 arrays of ``(op, a, b)`` rows in time order
 (first row acts first, so the circuit unitary is ``G_m ... G_1``).
@@ -63,6 +64,9 @@ def permutation_targets() -> dict:
 
     * toffoli: bit 2 ^= bit 0 AND bit 1 (Table 1);
     * fredkin: bits 1 and 2 swapped when bit 0 is set (Table 1);
+    * peres: (a, b, c) -> (a, a ^ b, c ^ a b), a Toffoli then a CNOT (Table 1);
+    * quantum_or: bit 2 ^= bit 0 OR bit 1 (Table 1); since a OR b =
+      1 ^ (NOT a AND NOT b), it is a Toffoli between X gates;
     * adder: the 1-bit full adder (Sec. 5.3) on (a, b, c, d) = bits 0..3,
       (a, b, c, d) -> (a, b, a ^ b ^ c, d ^ maj(a, b, c)).  With u = a ^ c
       and v = b ^ c, maj(a, b, c) = u v ^ c, so the adder is a Toffoli on
@@ -79,7 +83,11 @@ def permutation_targets() -> dict:
         a, b, ci, d = bit(c, 0), bit(c, 1), bit(c, 2), bit(c, 3)
         maj = (a & b) | (a & ci) | (b & ci)
         adder.append(a | (b << 1) | ((a ^ b ^ ci) << 2) | ((d ^ maj) << 3))
-    return {"toffoli": (3, tof), "fredkin": (3, fred), "adder": (4, adder)}
+    peres = [(c & 1) | ((bit(c, 0) ^ bit(c, 1)) << 1) | ((bit(c, 2) ^ (bit(c, 0) & bit(c, 1))) << 2)
+             for c in range(8)]
+    qor = [c ^ (4 if (c & 3) else 0) for c in range(8)]
+    return {"toffoli": (3, tof), "fredkin": (3, fred), "peres": (3, peres), "quantum_or": (3, qor),
+            "adder": (4, adder)}
 
 
 def random_paulis(rng: np.random.Generator, n: int, t: int) -> np.ndarray:

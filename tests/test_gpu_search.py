@@ -184,10 +184,11 @@ def paper_tcounts():
     return out
 
 
-@pytest.mark.parametrize("name", ["toffoli", "fredkin"])
+@pytest.mark.parametrize("name", ["toffoli", "fredkin", "peres", "quantum_or"])
 def test_table1_circuits_have_tcount_7(orc, dev, name):
-    """Toffoli and Fredkin have optimal T-count 7 (Sec. 5.2, Table 1), and
-    every lower level is proved empty by the exhaustive pass."""
+    """The Toffoli, Fredkin, Peres and OR gates have optimal T-count 7
+    (Sec. 5.2, Table 1), and every lower level is proved empty by the
+    exhaustive pass."""
     n_want, t_want = paper_tcounts()[name]
     _, perm = W.permutation_targets()[name]
     u = perm_unitary(perm)

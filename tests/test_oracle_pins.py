@@ -361,6 +361,29 @@ def test_full_adder_is_a_toffoli_between_cnot_circuits(orc):
     assert orc.sde(CA) == orc.sde(CT)
 
 
+@pytest.mark.parametrize("name", ["peres", "quantum_or"])
+def test_table1_gates_are_toffolis_between_cliffords(orc, name):
+    """Table 1: the Peres gate is a Toffoli followed by CNOT(0 -> 1), and the
+    OR gate (bit 2 ^= bit 0 OR bit 1) is a Toffoli between X layers, since
+    a OR b = 1 ^ (NOT a AND NOT b).  Pinned as permutations and in channel
+    form, where the outer layers are Cliffords (signed permutations), so
+    each gate has the Toffoli's T-count."""
+    n, perm = W.permutation_targets()[name]
+    _, tof = W.permutation_targets()["toffoli"]
+    assert n == 3 and sorted(perm) == list(range(8))
+    if name == "peres":
+        l1 = list(range(8))
+        l2 = [c ^ ((c & 1) << 1) for c in range(8)]  # CNOT 0 -> 1
+    else:
+        l1 = [c ^ 3 for c in range(8)]  # X on bits 0, 1
+        l2 = [c ^ 7 for c in range(8)]  # X on bits 0, 1, 2
+    assert [l2[tof[l1[c]]] for c in range(8)] == perm
+    C1, CT, C2, CG = (orc.channel_from_unitary(3, _perm_unitary(p), 0) for p in (l1, tof, l2, perm))
+    for Cl in (C1, C2):
+        assert orc.is_clifford(Cl)
+    assert CG.equals(C2 @ CT @ C1) and orc.sde(CG) == orc.sde(CT)
+
+
 def test_construction_bound_and_sde_lower_bound(orc):
     for cfg in (1, 2):
         c = W.CONFIGS[cfg]
