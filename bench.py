@@ -328,10 +328,10 @@ def table1_circuits(Q, W, stream, trials=10):
     Fredkin, Peres and OR (Table 1; published means 25.9870 s, 25.0031 s,
     25.4931 s and 24.1854 s on 4096 Blue Gene/Q cores, context only: other
     hardware): each trial is a full ladder from sde = 2 through the public
-    API with its own walk seed.  The 4-qubit
-    full adder (Sec. 5.3; the paper's first synthesis took 12.5 hours on 4096
-    cores): one deterministic ladder settled by the exhaustive pass alone
-    (every level exact); `--adder-walk` times the walk alone."""
+    API with its own walk seed.  The 4-qubit full adder (Sec. 5.3; the
+    paper's first synthesis took 12.5 hours on 4096 cores): one deterministic
+    ladder settled by the exhaustive pass alone (every level exact);
+    `--adder-walk` times the walk alone."""
     targets = W.permutation_targets()
     paper = {"toffoli": 25.9870, "fredkin": 25.0031, "peres": 25.4931, "quantum_or": 24.1854}
     out = {}
