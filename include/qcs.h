@@ -137,6 +137,12 @@ typedef struct qcs_result {
     int64_t rewalk_steps; /* evaluations of f made by the re-walk (Fig. 2 trace-back) */
     int64_t certified_levels; /* levels proved claw-free by the exhaustive pass */
     int64_t cert_points;      /* points (V and W) evaluated by the exhaustive pass */
+    int64_t h2d_bytes;        /* bytes this problem copied host to device: the upload of C^, its
+                                 weights and rotation tables at creation (and the shared stage tables
+                                 when this creation uploaded them); device-side resets not counted */
+    int64_t d2h_bytes;        /* bytes copied device to host for this problem: per launch the
+                                 counters and queue heads, plus the claw candidates and exhaustive-pass
+                                 matches actually queued (batch jobs: 0, the batch copies per round) */
 } qcs_result;
 
 typedef struct qcs_problem qcs_problem;
@@ -165,9 +171,18 @@ QCS_API int qcs_create_problem_channel(int n_qubits, const int64_t *chan_ab, int
 QCS_API int qcs_create_problem_circuit(int n_qubits, const int32_t *gates, int n_gates, int k_max,
                                const qcs_params *p, qcs_problem **out);
 
-/* Start the T-count ladder (levels sde(C^) .. k_max) on the given CUDA stream
- * (a cudaStream_t; NULL = legacy default stream; a PyTorch stream handle is
- * fine).  Returns at once: a library-owned host thread drives the launches.
+/* Start the T-count ladder on the given CUDA stream (a cudaStream_t; NULL =
+ * legacy default stream; a PyTorch stream handle is fine).  Sec. 4.1, Eq.
+ * tcount_synthesis: the optimal T-count is the smallest t for which C =
+ * R(P_t)..R(P_1) D has a solution, so levels t = sde(C^) .. k_max are
+ * searched in increasing order (sde(C^) is a lower bound: every R^(P) adds
+ * one power of sqrt2 to the denominator, and D^ is an integer matrix), and
+ * the first level with a verified claw between the halves of Eq. mitm
+ * (Sec. 3: a V point and a W point in one Clifford coset) is the answer.
+ * Levels 0 and 1 are checked directly; each higher level is walked by the
+ * parallel collision search of Sec. 3 (distinguished points, trails,
+ * re-walks of merges, Fig. 2) with the theta of Sec. 5.1 and the Appendix.
+ * Returns at once: a library-owned host thread drives the launches.
  * step_budget bounds the total walk steps (0 = no bound).  The stream must
  * stay valid until the search ends (qcs_wait, or status != SEARCHING).
  * Errors: QCS_ERR_BUSY if a search is running, QCS_ERR_ARG. */
@@ -196,8 +211,12 @@ QCS_API int qcs_run_walks(qcs_problem *prob, uint64_t step_budget, void *cuda_st
  * QCS_ERR_CUDA. */
 QCS_API int qcs_certify_level(qcs_problem *prob, int k, void *cuda_stream, int *has_claw);
 
-/* Non-blocking snapshot of the search (status, level, counters, and the
- * decomposition once FOUND). */
+/* Non-blocking snapshot of the search: status, level, the collision
+ * counters of Sec. 3 (distinguished points reached, merges re-walked and how
+ * Fig. 2's re-walk classified them: Robin Hood, trivial, same side, claw,
+ * false hash), and once FOUND the decomposition of Eq. tcount_synthesis
+ * (P_1 .. P_t in out->paulis; D via qcs_get_clifford), which the library has
+ * verified exactly before reporting it. */
 QCS_API int qcs_poll_collisions(qcs_problem *prob, qcs_result *out);
 
 /* Block until the running search ends or timeout_ms passes (< 0: forever);
@@ -238,19 +257,23 @@ QCS_API int qcs_level_collect(qcs_problem *prob, void *stream, qcs_result *out);
 
 /* qcs_level_walk_static: the walk of qcs_level_walk (begin = 1: preceded by
  * the reset of qcs_level_begin) for callers that must not allocate device
- * memory -- code recorded into a CUDA graph (cudaMalloc cannot be captured),
- * code whose device memory belongs to a framework's caching allocator, and
- * loops that cannot take cudaMalloc's implicit synchronisation.  The paper has
- * no counterpart; this is a property of the library, not of the method.
+ * memory: code whose device memory belongs to a framework's caching allocator
+ * or to a fixed arena (a stray cudaMalloc fragments it, or fails once the
+ * arena has reserved the free memory), and loops that cannot take
+ * cudaMalloc's implicit device synchronisation.  The paper has no
+ * counterpart; this is a property of the library, not of the method.
  *
  * It allocates nothing: the distinguished-point table is a static device
  * array of 2^18 16-byte slots (4 MiB) that every GPU loading libqcs holds
  * until exit, so the problem's params.table_log2 must be <= 18 (QCS_ERR_ARG
  * otherwise).  The problem itself must already exist (its creation does
- * allocate).  The first call on each device looks up the array's device
- * address with that device current; make that first call before any stream
- * capture.  All calls on a device share the one table and it keeps the last
- * call's contents: begin = 1 clears it, and calls that overlap on the GPU
+ * allocate), and its device must be the current device (QCS_ERR_ARG
+ * otherwise; the call never switches devices).  The first call on each
+ * device is its set-up: with that device current it looks up the array's
+ * device address, marks every slot empty and synchronises `stream` once;
+ * make that first call before any stream capture.  All calls on a device
+ * share the one table and it keeps the last call's contents: begin = 1
+ * clears the problem's 2^table_log2 slots, and calls that overlap on the GPU
  * race on it.
  *
  * The caller passes, as DEVICE pointers: walk_states, n_walks records of 32
@@ -258,9 +281,11 @@ QCS_API int qcs_level_collect(qcs_problem *prob, void *stream, qcs_result *out);
  * merges, merge_cap triples {trail ref a, trail ref b, distinguished point};
  * counts, 8 uint64 zeroed by the call: [0] walk steps, [1] W-side steps,
  * [2] distinguished points, [3] abandoned trails, [4] overwritten points,
- * [5] duplicate inserts, [6] merges found, [7] merges stored (low 32 bits).
- * k, version, dp_bits (0 = params.dp_bits) as in qcs_level_begin; n_walks
- * <= 2^24.  Asynchronous on `stream`. */
+ * [5] duplicate inserts, [6] merges found, [7] merges pushed (low 32 bits;
+ * it counts pushes past merge_cap too, so the valid triples number
+ * min(counts[7], merge_cap)).  k, version, dp_bits (0 = params.dp_bits) as
+ * in qcs_level_begin; n_walks <= 2^24.  Asynchronous on `stream` after the
+ * set-up. */
 QCS_API int qcs_level_walk_static(qcs_problem *prob, int k, uint32_t version, int dp_bits, int begin,
                                   void *walk_states, uint32_t n_walks, uint32_t steps, uint64_t *merges,
                                   uint32_t merge_cap, uint64_t *counts, void *stream);

@@ -51,7 +51,8 @@ class Result(ctypes.Structure):
                 ("no_merge", ctypes.c_int64), ("abandoned", ctypes.c_int64), ("dropped", ctypes.c_int64),
                 ("queue_overflow", ctypes.c_int64), ("launches", ctypes.c_int64), ("seconds", ctypes.c_double),
                 ("w_steps", ctypes.c_int64), ("rewalk_steps", ctypes.c_int64),
-                ("certified_levels", ctypes.c_int64), ("cert_points", ctypes.c_int64)]
+                ("certified_levels", ctypes.c_int64), ("cert_points", ctypes.c_int64),
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
@@ -285,7 +286,16 @@ class Problem:
     def level_walk_static(self, k, version, dp_bits, begin, walk_states, steps, merges, counts, stream=None):
         """qcs_level_walk_static: the level walk without any device allocation.
         walk_states: int64 tensor of 4 * n_walks entries; merges: int64 tensor
-        of 3 * cap entries; counts: int64 tensor of 8 entries."""
+        of 3 * cap entries; counts: int64 tensor of 8 entries.  All three
+        must be contiguous int64 CUDA tensors: their sizes become the
+        kernel's bounds."""
+        import torch
+
+        for name, t in (("walk_states", walk_states), ("merges", merges), ("counts", counts)):
+            if t.dtype != torch.int64 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous int64 CUDA tensor")
+        if walk_states.numel() % 4 or merges.numel() % 3 or counts.numel() < 8:
+            raise ValueError("walk_states needs 4 int64 per walk, merges 3 per triple, counts at least 8")
         n_walks = walk_states.numel() // 4
         rc = lib().qcs_level_walk_static(self._h, int(k), int(version), int(dp_bits), int(begin),
                                          _ptr(walk_states), n_walks, int(steps), _ptr(merges),

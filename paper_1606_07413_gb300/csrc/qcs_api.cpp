@@ -150,7 +150,7 @@ std::map<std::pair<int, int>, std::array<uint32_t *, 2>> g_tabs; // (device, n) 
 
 } // namespace
 
-int qcs::stage_tables(int n, const uint32_t *t1[2])
+int qcs::stage_tables(int n, const uint32_t *t1[2], int64_t *uploaded)
 {
     int dev = 0;
     CK(cudaGetDevice(&dev));
@@ -173,6 +173,7 @@ int qcs::stage_tables(int n, const uint32_t *t1[2])
             }
             CK(cudaMalloc(&tabs[side], sizeof(uint32_t) * t1.size()));
             CK(cudaMemcpy(tabs[side], t1.data(), sizeof(uint32_t) * t1.size(), cudaMemcpyHostToDevice));
+            if (uploaded) *uploaded += (int64_t)(sizeof(uint32_t) * t1.size());
         }
         it = g_tabs.emplace(std::make_pair(dev, n), tabs).first;
     }
@@ -245,10 +246,12 @@ int upload_problem(qcs_problem *P)
         }
     }
     CK(cudaGetDevice(&P->device));
-    if (int rc = stage_tables(n, P->dT1)) return rc;
+    int64_t h2d = 0;
+    if (int rc = stage_tables(n, P->dT1, &h2d)) return rc;
     if (!cq.empty()) {
         CK(cudaMalloc(&P->dCq, sizeof(uint32_t) * cq.size()));
         CK(cudaMemcpy(P->dCq, cq.data(), sizeof(uint32_t) * cq.size(), cudaMemcpyHostToDevice));
+        h2d += (int64_t)(sizeof(uint32_t) * cq.size());
     }
     CK(cudaMalloc(&P->dC32, sizeof(uint2) * c32.size()));
     CK(cudaMalloc(&P->dU, sizeof(uint2) * D));
@@ -256,6 +259,8 @@ int upload_problem(qcs_problem *P)
     CK(cudaMemcpy(P->dC32, c32.data(), sizeof(uint2) * c32.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->dU, u.data(), sizeof(uint2) * D, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->dCoef, coef.data(), sizeof(uint32_t) * coef.size(), cudaMemcpyHostToDevice));
+    h2d += (int64_t)(sizeof(uint2) * c32.size() + sizeof(uint2) * D + sizeof(uint32_t) * coef.size());
+    P->res.h2d_bytes += h2d;
     return QCS_OK;
 }
 
@@ -416,7 +421,6 @@ int level_rewalk(qcs_problem *P, cudaStream_t s)
     CK(cudaMemcpyAsync(P->hCounters, P->dCounters, sizeof(unsigned long long) * C_NCOUNTERS,
                        cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(P->hQhead, P->dQhead, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(P->hCands, P->dCands, sizeof(Cand) * kCandCap, cudaMemcpyDeviceToHost, s));
     return QCS_OK;
 }
 
@@ -431,6 +435,13 @@ int level_collect(qcs_problem *P, cudaStream_t s, bool *got, uint64_t *steps)
     const unsigned long long *c = P->hCounters;
     const uint32_t npairs = std::min(P->hQhead[0], L.w.qcap);
     const uint32_t ncand = std::min(P->hQhead[1], kCandCap);
+    int64_t d2h = (int64_t)(sizeof(unsigned long long) * C_NCOUNTERS + 2 * sizeof(uint32_t));
+    if (ncand > 0) {
+        // read back only the candidates the re-walk queued
+        CK(cudaMemcpyAsync(P->hCands, P->dCands, sizeof(Cand) * ncand, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        d2h += (int64_t)(sizeof(Cand) * ncand);
+    }
     uint32_t paulis[16] = {0};
     PMat Dh;
     int64_t claws = 0, false_hash = 0;
@@ -469,6 +480,7 @@ int level_collect(qcs_problem *P, cudaStream_t s, bool *got, uint64_t *steps)
         R.claws += claws;
         R.false_hash += false_hash;
         R.launches += 1;
+        R.d2h_bytes += d2h;
         R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - P->t0).count();
     }
     if (*got) found(P, k, paulis, std::move(Dh));
@@ -601,6 +613,7 @@ int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
     int rc = QCS_OK;
     bool overflow = false;
     uint64_t done_probe = 0;
+    int64_t d2h = 0;
     if (e == cudaSuccess) e = cudaMemsetAsync(a.table, 0xFF, sizeof(CertSlot) * slots, s);
     if (e == cudaSuccess) {
         a.lv = lv_store;
@@ -626,6 +639,7 @@ int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
         if ((e = launch_certify(a, s)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(hN, a.n_pairs, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+        d2h += (int64_t)sizeof(uint32_t);
         done_probe += a.count;
         const uint32_t n = std::min(*hN, kCap);
         if (*hN > kCap) overflow = true;
@@ -635,6 +649,7 @@ int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
                 cudaSuccess)
                 break;
             if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+            d2h += (int64_t)(sizeof(uint64_t) * 2 * n);
         }
         for (uint32_t i = 0; i < n && !*got; i++) {
             // exact check of the key match: rotations from the point indices
@@ -675,6 +690,7 @@ int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
     {
         std::lock_guard<std::mutex> g(P->mu);
         P->res.cert_points += (int64_t)(xi_h + done_probe);
+        P->res.d2h_bytes += d2h;
         if (rc == QCS_OK && !*got && !overflow) P->res.certified_levels += 1;
     }
     if (rc == QCS_OK && !*got && overflow) rc = QCS_ERR_OVERFLOW;

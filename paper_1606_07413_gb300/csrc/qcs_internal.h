@@ -233,7 +233,8 @@ int exact_verify(int n, const PMat &C, const uint32_t *paulis, int t, PMat *Dout
 int pauli_phase(int n, uint32_t p, uint32_t q); // P(p)P(q) = i^lambda P(p^q)
 // device tables of the first adjoint stage (LevelCtx::T1), built once per
 // device and qubit count and kept for the life of the process
-int stage_tables(int n, const uint32_t *t1[2]);
+// (*uploaded, when given, grows by the bytes this call copied to the device)
+int stage_tables(int n, const uint32_t *t1[2], int64_t *uploaded = nullptr);
 
 // How a level is walked (Sec. 3 and Appendix): theta, the launch shape, the
 // function-version period and the level's step budget.

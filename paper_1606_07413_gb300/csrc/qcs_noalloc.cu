@@ -1,14 +1,14 @@
 // qcs_noalloc.cu -- qcs_level_walk_static: the walk of qcs_level_walk for
 // callers that must not allocate device memory.
 //
-// Who cannot allocate: code that records work into a CUDA graph (cudaMalloc
-// cannot be captured), code running where a framework's caching allocator
-// owns the device memory (a stray cudaMalloc fragments it or fails its memory
-// accounting), and real-time loops that cannot afford cudaMalloc's implicit
-// device synchronisation.  qcs_level_begin allocates the distinguished-point
-// table, merge queue and walk states on first use; this entry point instead
-// keeps the table in a fixed array of static device memory, and the caller
-// passes the walk states, the merge list and the counters.
+// Who cannot allocate: code running where a framework's caching allocator or
+// a fixed arena owns the device memory (a stray cudaMalloc fragments it, or
+// fails its memory accounting once the arena has reserved what is free), and
+// real-time loops that cannot afford cudaMalloc's implicit device
+// synchronisation.  qcs_level_begin allocates the distinguished-point table,
+// merge queue and walk states on first use; this entry point instead keeps
+// the table in a fixed array of static device memory, and the caller passes
+// the walk states, the merge list and the counters.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -30,18 +30,19 @@ constexpr int kMaxDevices = 256;
 std::mutex g_mu;
 qcs::Slot *g_table_addr[kMaxDevices] = {};
 
-// Device address of g_static_table on the current device, looked up once per
-// device (with that device current) and cached.
-int static_table(qcs::Slot **out)
+// Device address of g_static_table on device `dev` (which must be current),
+// looked up once per device and cached.  The array starts zero-filled, and a
+// zero slot would read as point 0 stored by trail reference 0, so the set-up
+// also marks every slot empty (all ones) and waits for that on `s`.
+int static_table(int dev, cudaStream_t s, qcs::Slot **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return qcs::record_cuda_error(e);
     if (dev < 0 || dev >= kMaxDevices) return QCS_ERR_ARG;
     std::lock_guard<std::mutex> g(g_mu);
     if (!g_table_addr[dev]) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_table);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_table);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p, 0xFF, sizeof(g_static_table), s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return qcs::record_cuda_error(e);
         g_table_addr[dev] = static_cast<qcs::Slot *>(p);
     }
@@ -63,10 +64,16 @@ extern "C" int qcs_level_walk_static(qcs_problem *prob, int k, uint32_t version,
     if (table_log2 > kStaticTableLog2) return QCS_ERR_ARG; // the problem's table is larger than the static one
     if (!walk_states || !counts || n_walks == 0 || n_walks > qcs::kMaxWalks || steps == 0) return QCS_ERR_ARG;
     if (merge_cap && !merges) return QCS_ERR_ARG;
-    qcs::Slot *table = nullptr;
-    if ((rc = static_table(&table)) != QCS_OK) return rc;
-
+    // the problem's matrices live on its own device: launching elsewhere
+    // would hand the kernel another GPU's addresses
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return qcs::record_cuda_error(e);
+    if (dev != prob->device) return QCS_ERR_ARG;
     const cudaStream_t s = (cudaStream_t)stream;
+    qcs::Slot *table = nullptr;
+    if ((rc = static_table(dev, s, &table)) != QCS_OK) return rc;
+
     qcs::WalkLaunch w{};
     w.lv = lv;
     w.walks = static_cast<qcs::WalkState *>(walk_states);
@@ -79,7 +86,7 @@ extern "C" int qcs_level_walk_static(qcs_problem *prob, int k, uint32_t version,
     w.qhead = reinterpret_cast<uint32_t *>(counts + 7); // low word of counts[7]
     w.qcap = merge_cap;
     w.counters = reinterpret_cast<unsigned long long *>(counts);
-    cudaError_t e = cudaMemsetAsync(counts, 0, 8 * sizeof(uint64_t), s);
+    e = cudaMemsetAsync(counts, 0, 8 * sizeof(uint64_t), s);
     if (e == cudaSuccess && begin) {
         e = cudaMemsetAsync(table, 0xFF, sizeof(qcs::Slot) << table_log2, s);
         if (e == cudaSuccess) e = qcs::launch_init_walks(w, s);
