@@ -1,21 +1,24 @@
 #!/usr/bin/env python3
 """Benchmark of the deterministic-walk T-count search hot path on GB300.
 
-Workload (the configuration the metric is quoted on): n = 3 qubits, one
-seeded target C0 R(P5)..R(P1), level k = 5 (two rotations per side, 63 chunks),
-2^16 concurrent walks, 48-bit states, distinguished fraction 2^-10, a
-2^22-slot distinguished-point table.  One bench step is one pass of the whole
-hot path over the batch: every walk advances 64 walk steps (decode, exact half
-product hashed modulo Clifford, distinguished-point test, table insert), the
-queued merges are re-walked and classified on the device, and claw candidates
-are checked exactly on the host.
+Workload (the largest single-GPU configuration): n = 4 qubits, one seeded
+target C0 R(P7)..R(P1), level k = 7 (three rotations per side, 255 chunks,
+N = 2 x 255^4 = 8.5e9 walk points), 2^20 concurrent walks, 64-bit states,
+distinguished fraction 2^-12, a 2^26-slot distinguished-point table.  One
+bench step is one pass of the whole hot path over the batch: every walk
+advances 64 walk steps (decode, exact half product hashed modulo Clifford,
+distinguished-point test, table insert), the queued merges are re-walked and
+classified on the device, and claw candidates are checked exactly on the host.
 
 value   = walk steps per second over the timed steps (all ranks).
 e2e     = the same metric through the public API (problem creation from the
-          host gate list, search launches, per-launch result reads).
-Also reported: the time to the optimal T-count of this target (full ladder),
-the roofline of the dominant kernel against the measured IMAD throughput,
-and the CPU oracle timed on the host cores.
+          host gate list, qcs_run_walks, qcs_poll_collisions), with the bytes
+          the library reports it copied each way.
+Also reported: the roofline of the dominant kernel (contraction multiply-adds
+against twice the measured dp4a rate, and issue slots from its ncu record),
+the time to the optimal T-count of configurations 1-3 by the collision walk
+alone and by the exhaustive pass, the n = 3 level-5 record, the batched and
+serving workloads, and the CPU oracle timed on the host cores.
 
 --impl reference times the CPU oracle (the reference arm of this build).
 """
@@ -34,16 +37,17 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-CFG = 2
-K_LEVEL = 5
-STEPS_PER_LAUNCH = 512
+CFG = 3
+K_LEVEL = 7
+STEPS_PER_LAUNCH = 64
 FLUSH_BYTES = 256 << 20
+LEVELS = {1: 3, 2: 5, 3: 7}  # the level each configuration's construction T-count puts its claw on
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget")
@@ -52,7 +56,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and other-size runs")
     ap.add_argument("--batched-only", action="store_true",
                     help="only run the batched-search comparison (256 seeded targets), print its JSON and exit")
-    ap.add_argument("--level-only", choices=["n2_level3", "n4_level7"], default=None,
+    ap.add_argument("--level-only", choices=["n2_level3", "n3_level5", "n4_level7"], default=None,
                     help="only time that single-target level launch (walk-kernel throughput), print its JSON and exit")
     ap.add_argument("--config3-walk", type=int, default=0, metavar="TABLE_LOG2",
                     help="only time the n = 4 seeded target's search by the collision walk alone with a "
@@ -62,25 +66,38 @@ def parse():
     ap.add_argument("--adder-walk", type=int, default=0, metavar="TABLE_LOG2",
                     help="only time the 4-qubit full adder's search by the collision walk alone with a "
                          "2^TABLE_LOG2-slot table, print its JSON and exit")
+    ap.add_argument("--tto-sweep", action="store_true",
+                    help="only time the n = 4 seeded target's collision walk over a grid of table sizes and "
+                         "distinguished fractions, print its JSON and exit")
     return ap.parse_args()
 
 
-def workload_config(c):
+def workload_config(c, k=None, steps=None):
+    k = K_LEVEL if k is None else k
+    steps = STEPS_PER_LAUNCH if steps is None else steps
     return {
-        "workload": f"n{c['n']}_t{c['t']}_level{K_LEVEL}_walks{c['walks']}_L{c['L']}_theta2^-{c['dtheta']}",
-        "n_qubits": c["n"], "level_k": K_LEVEL, "chunks": 4 ** c["n"] - 1, "walks": c["walks"],
-        "steps_per_walk_per_step": STEPS_PER_LAUNCH, "state_bits": c["L"], "dp_bits": c["dtheta"],
+        "workload": f"n{c['n']}_t{c['t']}_level{k}_walks{c['walks']}_L{c['L']}_theta2^-{c['dtheta']}",
+        "n_qubits": c["n"], "level_k": k, "chunks": 4 ** c["n"] - 1, "walks": c["walks"],
+        "level_points": 2 * (4 ** c["n"] - 1) ** (k // 2) * ((4 ** c["n"] - 1) if k & 1 else 1),
+        "steps_per_walk_per_step": steps, "state_bits": c["L"], "dp_bits": c["dtheta"],
         "table_slots": 1 << c["table_log2"], "coefficients": "exact: int64 on the host, C^ as int8 byte quads on the device; fingerprints mod 2^16",
         "l2": f"flushed between steps ({FLUSH_BYTES >> 20} MiB write)",
         "parallelism": "replicas, one target per GPU",
     }
 
 
-# ------------------------------------------------------------------ ncu record
-# DRAM traffic of one k_walks<3> launch of the headline workload, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
-# kernel source it was taken on (hash of the walk kernel's source files)
-WALK_TRAFFIC = {"bytes_per_launch": 2521856, "source_sha256_16": "e79a13e5d494f0d1"}
+# ------------------------------------------------------------------ ncu records
+# Per walk kernel, from ncu captures of the commands named in profiles/: DRAM
+# traffic of one launch of the bench's workload (dram__bytes_read.sum +
+# dram__bytes_write.sum) and warp instructions issued per walk step
+# (smsp__inst_executed.sum / walk steps of the captured launch).  A record
+# holds only for the kernel source it was captured on (hash of the walk
+# kernel's source files, comments and layout removed); otherwise its figures
+# are reported as null.
+WALK_NCU = {
+    "k_walks<4>": {"source_sha256_16": None, "dram_bytes_per_launch": None, "warp_inst_per_step": None},
+    "k_walks<3>": {"source_sha256_16": None, "dram_bytes_per_launch": None, "warp_inst_per_step": None},
+}
 
 
 def walk_source_hash() -> str:
@@ -109,10 +126,47 @@ def measured_hbm_gbs():
         return 6800.0, "fallback (no measured peaks file)"
 
 
-def walk_traffic():
-    if WALK_TRAFFIC["source_sha256_16"] != walk_source_hash():
-        return None  # the kernel changed since the counters were taken
-    return WALK_TRAFFIC["bytes_per_launch"]
+def ncu_record(kernel: str):
+    """The kernel's ncu record if it was captured on the current source, else None."""
+    rec = WALK_NCU.get(kernel)
+    if not rec or rec["source_sha256_16"] != walk_source_hash():
+        return None
+    return rec
+
+
+def walk_roofline(kernel, n, w_steps, steps, walk_s, launches, dp4a_per_s, clock_mhz, num_sms):
+    """Roofline of a walk kernel ("bound": "alu").  achieved = the W side's
+    contraction multiply-adds (W-side steps x 2 d^2, d = 4^n - 1: 16-bit
+    fingerprint weights times C^) per second of the kernel's CUDA-event time;
+    peak = twice the measured dp4a rate (a dp4a makes four byte products, a
+    16-bit-weight multiply-add needs two).  The issue-slot fraction takes the
+    warp instructions per walk step from the kernel's ncu record against 4
+    issue slots per SM per clock at the clock sampled during the run."""
+    d = 4 ** n - 1
+    achieved = w_steps * 2 * d * d / walk_s
+    peak = 2 * dp4a_per_s
+    rec = ncu_record(kernel)
+    traffic = rec["dram_bytes_per_launch"] if rec else None
+    hbm_peak, hbm_src = measured_hbm_gbs()
+    hbm = None
+    if traffic is not None:
+        per_launch_s = walk_s / max(1, launches)
+        hbm = {"achieved_gbs": traffic / per_launch_s / 1e9, "peak_gbs": hbm_peak,
+               "frac": traffic / per_launch_s / 1e9 / hbm_peak, "peak_source": hbm_src}
+    issue = None
+    if rec and rec.get("warp_inst_per_step") and clock_mhz:
+        issue_rate = rec["warp_inst_per_step"] * steps / walk_s
+        issue_peak = num_sms * 4 * clock_mhz * 1e6
+        issue = {"warp_inst_per_step": rec["warp_inst_per_step"], "achieved_per_s": issue_rate,
+                 "peak_per_s": issue_peak, "frac": issue_rate / issue_peak,
+                 "peak_source": f"{num_sms} SMs x 4 schedulers x {clock_mhz:.0f} MHz (median sampled SM clock)"}
+    return {"bound": "alu", "unit": "Gop/s", "kernel": kernel,
+            "achieved": achieved / 1e9, "peak": peak / 1e9, "frac": achieved / peak,
+            "traffic": traffic, "traffic_unit": "bytes per launch", "hbm": hbm, "issue_slots": issue,
+            "peak_source": "2 x measured dp4a rate (qcs_peak_idp4a, this run: "
+                           f"{dp4a_per_s / 1e9:.0f} G dp4a/s)",
+            "algorithmic_ops": f"2*d^2 = {2 * d * d} 16-bit-weight multiply-adds per W-side walk step "
+                               "(executed as two byte-plane dp4a per four multiply-adds)"}
 
 
 # ------------------------------------------------------------------ ranks
@@ -147,22 +201,24 @@ def _oracle_worker(args):
     return len(states), time.perf_counter() - t0
 
 
-def cpu_oracle_rate(budget_s: float):
-    """Oracle walk steps/s on all host cores (spawned pool, one process per core)."""
+def cpu_oracle_rate(budget_s: float, cfg: int = CFG, k: int = K_LEVEL):
+    """Oracle walk steps/s on all host cores (spawned pool, one process per
+    core) on a bounded sample of the configuration's level-k walk steps."""
     import multiprocessing as mp
 
     import oracle
     from paper_1606_07413_gb300 import workloads as W
 
     oracle.build()
-    c = W.CONFIGS[CFG]
-    gates, _ = W.config_target(CFG)
+    c = W.CONFIGS[cfg]
+    gates, _ = W.config_target(cfg)
     cores = os.cpu_count() or 1
+    xi = 4 ** c["n"] - 1
     # calibrate one process on a small batch
-    _, dt = _oracle_worker((c["n"], gates, K_LEVEL, 3, c["L"], W.seeded_states(64, c["L"], 1)))
-    per_step = max(dt / 64, 1e-7)
+    _, dt = _oracle_worker((c["n"], gates, k, 3, c["L"], W.seeded_states(16, c["L"], 1)))
+    per_step = max(dt / 16, 1e-7)
     per_core = max(16, int(budget_s / per_step / 4))  # about budget_s/4 of wall time per worker
-    jobs = [(c["n"], gates, K_LEVEL, 1 + (i % 63), c["L"], W.seeded_states(per_core, c["L"], 100 + i))
+    jobs = [(c["n"], gates, k, 1 + (i % xi), c["L"], W.seeded_states(per_core, c["L"], 100 + i))
             for i in range(cores)]
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
@@ -172,8 +228,8 @@ def cpu_oracle_rate(budget_s: float):
     steps = sum(o[0] for o in out)
     busy = max(o[1] for o in out)
     return {"value": steps / busy, "unit": "walk_steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{steps} oracle walk steps (n=3, level 5, 48-bit states) in {cores} spawned "
-                      f"processes, {busy:.1f}s of compute ({wall:.1f}s wall incl. start-up)"}
+            "sample": f"{steps} oracle walk steps (n={c['n']}, level {k}, {c['L']}-bit states, seeded) in "
+                      f"{cores} spawned processes, {busy:.1f}s of compute ({wall:.1f}s wall incl. start-up)"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -215,18 +271,25 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ other workloads
-def level_throughput(Q, W, torch, cfg, k, steps, stream, launches=3, alu_per_s=None, dp_bits=None, table_log2=None):
+def level_throughput(Q, W, torch, cfg, k, steps, stream, launches=3, alu_per_s=None, dp_bits=None, table_log2=None,
+                     target=None):
     """Walk steps/s of one single-target level launch at a configured size
-    (dp_bits / table_log2 override the configuration's theta and table), and
-    the distinguished-point table's algorithmic traffic: one 16-byte
+    (dp_bits / table_log2 override the configuration's theta and table;
+    target = (n, t, seed) takes another seeded target of that size class),
+    and the distinguished-point table's algorithmic traffic: one 16-byte
     exchange (read and write) per distinguished point, 24 bytes per queued
     merge."""
     c = W.CONFIGS[cfg]
-    gates, _ = W.config_target(cfg)
+    if target is None:
+        gates, _ = W.config_target(cfg)
+        k_max = c["k_max"]
+    else:
+        gates, _ = W.seeded_target(*target)
+        k_max = max(k, target[1])
     dpb = dp_bits or c["dtheta"]
     p = Q.default_params(c["n"], walks=c["walks"], state_bits=c["L"], dp_bits=dpb,
                          table_log2=table_log2 or min(c["table_log2"], 24))
-    prob = Q.Problem.from_circuit(c["n"], gates, c["k_max"], p)
+    prob = Q.Problem.from_circuit(c["n"], gates, k_max, p)
     prob.level_begin(k, 0, dpb, stream=stream)
     prob.level_walk(steps, stream); prob.level_rewalk(stream); prob.level_collect(stream)
     r0 = prob.poll()
@@ -244,18 +307,24 @@ def level_throughput(Q, W, torch, cfg, k, steps, stream, launches=3, alu_per_s=N
     d = 4 ** c["n"] - 1
     walk_s = sum(ms) / 1e3
     table_bytes = 32 * (r1["dps"] - r0["dps"]) + 24 * (r1["merges"] - r0["merges"])
-    out = {"workload": f"n{c['n']}_level{k}_walks{c['walks']}_L{c['L']}_theta2^-{dpb}",
-           "walk_steps_per_s": (r1["steps"] - r0["steps"]) / walk_s,
-           "table_gbs": table_bytes / walk_s / 1e9}
-    if alu_per_s:  # multiply-adds per second at the contraction's peak (IMAD for n <= 2; 2 x dp4a for n >= 3)
+    name = f"n{c['n']}_level{k}_walks{c['walks']}_L{c['L']}_theta2^-{dpb}"
+    if target is not None:
+        name += f"_target_n{target[0]}_t{target[1]}_seed{target[2]}"
+    out = {"workload": name, "walk_steps_per_s": (r1["steps"] - r0["steps"]) / walk_s,
+           "table_gbs": table_bytes / walk_s / 1e9, "launches": launches, "steps_per_walk_per_launch": steps,
+           "walk_kernel_s": walk_s}
+    if alu_per_s:  # multiply-adds per second at the contraction's peak
         out["alu_frac"] = (r1["w_steps"] - r0["w_steps"]) * 2 * d * d / walk_s / alu_per_s
     return out
 
 
-def run_batched(Q, W, torch, stream, n_targets=256, rounds=12, mac_peak=None):
-    """The batched workload: many seeded targets in one persistent launch per qubit count
-    (one CUDA-graph replay per round) against the same jobs launched one
-    target at a time, on identical work (the trajectories are deterministic)."""
+def run_batched(Q, W, torch, stream, n_targets=256, mac_peak=None, min_seconds=1.0, repeats=3):
+    """The batched workload: many seeded targets in one persistent launch per qubit
+    count (one CUDA-graph replay per round) against the same jobs launched
+    one target at a time, on identical work (the trajectories are
+    deterministic, and each arm runs every job for the same rounds).  The
+    rounds double until the batched arm takes at least min_seconds; each arm
+    is then timed `repeats` times on fresh copies of the jobs."""
     from paper_1606_07413_gb300 import autotune
 
     targets = W.batched_targets(n_targets)
@@ -272,41 +341,62 @@ def run_batched(Q, W, torch, stream, n_targets=256, rounds=12, mac_peak=None):
                                       steps_per_round=best["steps_per_round"], table_log2=18,
                                       queue_capacity=best["queue_capacity"])
 
-    probs = [mk(i, t) for i, t in enumerate(targets)]
-    with Q.Batch(bp(len(targets)), stream) as b:
-        ids = [b.add(p) for p in probs]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(rounds):
-            b.round()
-        batched_s = time.perf_counter() - t0
-        res = [b.poll(j) for j in ids]
-    for p in probs:
-        p.close()
-    one_s = 0.0
-    for i, t in enumerate(targets):
-        p = mk(i, t)
-        with Q.Batch(bp(1), stream) as b:
-            j = b.add(p)
+    def batched(rounds):
+        probs = [mk(i, t) for i, t in enumerate(targets)]
+        with Q.Batch(bp(len(targets)), stream) as b:
+            ids = [b.add(p) for p in probs]
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(rounds):
                 b.round()
-            one_s += time.perf_counter() - t0
-        p.close()
+            secs = time.perf_counter() - t0
+            res = [b.poll(j) for j in ids]
+        for p in probs:
+            p.close()
+        return secs, res
+
+    def one_at_a_time(rounds):
+        secs = 0.0
+        res = []
+        for i, t in enumerate(targets):
+            p = mk(i, t)
+            with Q.Batch(bp(1), stream) as b:
+                j = b.add(p)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(rounds):
+                    b.round()
+                secs += time.perf_counter() - t0
+                res.append(b.poll(j))
+            p.close()
+        return secs, res
+
+    rounds = 12
+    while True:
+        secs, res = batched(rounds)
+        if secs >= min_seconds or rounds >= 4096:
+            break
+        rounds *= 2
+    b_secs = [secs] + [batched(rounds)[0] for _ in range(repeats - 1)]
+    o_runs = [one_at_a_time(rounds) for _ in range(repeats)]
+    o_secs = [r[0] for r in o_runs]
     fev = sum(r["steps"] + r["rewalk_steps"] for r in res)
+    fev_one = sum(r["steps"] + r["rewalk_steps"] for r in o_runs[0][1])
     walk = sum(r["steps"] for r in res)
     imad = sum(r["w_steps"] * 2 * (4 ** t["n"] - 1) ** 2 for r, t in zip(res, targets))
     tts = sorted(r["seconds"] for r in res if r["status_name"] == "found")
     q = lambda f: tts[min(len(tts) - 1, int(f * len(tts)))] if tts else None
+    bs, os_ = statistics.median(b_secs), statistics.median(o_secs)
     return {
-        "workload": f"{n_targets} seeded targets, n~U{{2,3,4}}, T-count~U{{3..7}}, {rounds} rounds",
+        "workload": f"{n_targets} seeded targets, n~U{{2,3,4}}, T-count~U{{3..7}}, {rounds} rounds per job",
         "autotuned": best, "autotune_seconds": tune_s, "autotune_trials": len(trials),
-        "batched_fevals_per_s": fev / batched_s, "one_target_fevals_per_s": fev / one_s,
-        "batched_walk_steps_per_s": walk / batched_s, "one_target_walk_steps_per_s": walk / one_s,
-        "speedup": one_s / batched_s, "batched_s": batched_s, "one_target_s": one_s,
-        "contraction_ops_per_s_batched": imad / batched_s,
-        "contraction_alu_frac_batched": (imad / batched_s / mac_peak) if mac_peak else None,
+        "batched_fevals_per_s": fev / bs, "one_target_fevals_per_s": fev_one / os_,
+        "batched_walk_steps_per_s": walk / bs, "one_target_walk_steps_per_s": walk / os_,
+        "speedup": os_ / bs, "speedup_min_max": [min(o_secs) / max(b_secs), max(o_secs) / min(b_secs)],
+        "batched_s": b_secs, "one_target_s": o_secs, "repeats": repeats,
+        "identical_work": fev == fev_one,
+        "contraction_ops_per_s_batched": imad / bs,
+        "contraction_alu_frac_batched": (imad / bs / mac_peak) if mac_peak else None,
         "alu_peak_note": "contraction multiply-adds of all jobs against twice the measured dp4a rate",
         "found": len(tts), "time_to_tcount_p50_s": q(0.5), "time_to_tcount_p99_s": q(0.99),
         "graph": "each batched round is one CUDA-graph replay",
@@ -348,35 +438,41 @@ def table1_circuits(Q, W, stream, trials=10):
             p.close()
         out[name] = {"t_counts": sorted(set(tcs)), "mean_s": float(np.mean(secs)), "sd_s": float(np.std(secs)),
                      "trials": trials, "paper_mean_s_4096_bgq_cores": paper[name]}
-    out["adder"] = dict(n4_time_to_optimal(Q, W, stream, "exhaustive", unitary=perm_unitary(targets["adder"][1])),
+    out["adder"] = dict(time_to_optimal(Q, W, stream, 3, "exhaustive", unitary=perm_unitary(targets["adder"][1])),
                         paper_first_synthesis_s_4096_bgq_cores=12.5 * 3600)
     return out
 
 
-def config3_time_to_optimal(Q, W, stream, mode="exhaustive", table_log2=30, queue_log2=24, limit_s=900):
-    """Time to the optimal T-count of the n = 4, 7-factor seeded target (see
-    n4_time_to_optimal)."""
-    return n4_time_to_optimal(Q, W, stream, mode, table_log2, queue_log2, limit_s)
+# table of the collision walk for time-to-optimal runs per configuration:
+# (table_log2, queue_log2); the level-7 walk at n = 4 gets 16 GiB of table
+TTO_TABLES = {1: (16, 20), 2: (22, 20), 3: (30, 24)}
 
 
-def n4_time_to_optimal(Q, W, stream, mode="exhaustive", table_log2=30, queue_log2=24, limit_s=900, unitary=None):
-    """Time to the optimal T-count (at most 7) of an n = 4 target: the seeded
-    7-factor target, or the given unitary (Z[omega] coefficients over
-    sqrt2^0).  mode "exhaustive": the ladder settles each level by the
-    exhaustive pass alone (the key table of level 7 is 512 MiB); mode "walk":
-    the collision search alone with a 2^table_log2-slot table (16 bytes a
-    slot), theta policy 1, no exhaustive pass."""
-    c = W.CONFIGS[3]
-    gates, _ = W.config_target(3)
+def time_to_optimal(Q, W, stream, cfg, mode="walk", table_log2=None, queue_log2=None, limit_s=900, unitary=None,
+                    dp_bits=None):
+    """Time to the optimal T-count of a configuration's seeded target (or of
+    the given n-qubit unitary, Z[omega] coefficients over sqrt2^0), through
+    the public API (qcs_create_problem_circuit, qcs_run_walks, qcs_wait).
+    mode "walk": the collision search alone (no exhaustive pass) with a
+    2^table_log2-slot table (16 bytes a slot) and theta from the Appendix
+    policy (or fixed at 2^-dp_bits); mode "exhaustive": every level settled
+    by the exhaustive pass alone."""
+    c = W.CONFIGS[cfg]
+    n = c["n"]
+    gates, _ = W.config_target(cfg)
+    tl, ql = TTO_TABLES[cfg]
+    table_log2 = table_log2 or tl
+    queue_log2 = queue_log2 or ql
     if mode == "exhaustive":
-        p = Q.default_params(4, exhaustive_first=1, exhaustive_log2=34)
+        p = Q.default_params(n, exhaustive_first=1, exhaustive_log2=34)
     else:
-        p = Q.default_params(4, table_log2=table_log2, queue_capacity=1 << queue_log2, exhaustive_log2=0)
+        extra = {"theta_policy": 0, "dp_bits": dp_bits} if dp_bits else {}
+        p = Q.default_params(n, table_log2=table_log2, queue_capacity=1 << queue_log2, exhaustive_log2=0, **extra)
     t0 = time.perf_counter()
     if unitary is None:
-        prob = Q.Problem.from_circuit(4, gates, c["k_max"], p)
+        prob = Q.Problem.from_circuit(n, gates, c["k_max"], p)
     else:
-        prob = Q.Problem.from_unitary(4, unitary, 0, c["k_max"], p)
+        prob = Q.Problem.from_unitary(n, unitary, 0, c["k_max"], p)
     prob.run_walks(stream=stream)
     r = prob.wait(int(limit_s * 1000))
     if r["timed_out"]:
@@ -384,11 +480,21 @@ def n4_time_to_optimal(Q, W, stream, mode="exhaustive", table_log2=30, queue_log
         r = prob.wait(60_000)
         r["status_name"] = "time_limit"
     secs = time.perf_counter() - t0
+    sde = prob.sde
     prob.close()
-    return {"mode": mode, "seconds": secs, "status": r["status_name"], "t_count": r["t_count"],
-            "sde": r["sde"], "walk_steps": r["steps"], "exhaustive_points": r["cert_points"],
-            "certified_levels": r["certified_levels"], "merges": r["merges"], "claws": r["claws"],
-            "table_log2": None if mode == "exhaustive" else table_log2}
+    out = {"mode": mode, "seconds": secs, "status": r["status_name"], "t_count": r["t_count"], "sde": r["sde"],
+           "walk_steps": r["steps"], "rewalk_steps": r["rewalk_steps"], "merges": r["merges"],
+           "claws": r["claws"], "false_hash": r["false_hash"], "exhaustive_points": r["cert_points"],
+           "certified_levels": r["certified_levels"]}
+    if mode == "walk":
+        k = r["t_count"] if r["t_count"] > 0 else c["k_max"]
+        plan = Q.plan_level(n, k, p)
+        out.update(table_slots=1 << table_log2, dp_bits=plan["dp_bits"], theta=2.0 ** -plan["dp_bits"],
+                   walks=plan["walks"], steps_per_launch=plan["steps"], level_points=plan["points"],
+                   walk_steps_over_level_points=r["steps"] / plan["points"],
+                   levels=f"{sde}..{k}", theta_rule="fixed" if dp_bits else "Appendix optimum sqrt(2w/N), "
+                                                                          "at most 1/2")
+    return out
 
 
 def exhaustive_level_pass(Q, W, stream, n=4, k=7, t=9, seed=4009):
@@ -407,41 +513,132 @@ def exhaustive_level_pass(Q, W, stream, n=4, k=7, t=9, seed=4009):
             "has_claw": bool(has), "certified_levels": r["certified_levels"]}
 
 
+def serving_stats(polls, deadline_s):
+    """Latency over every request of the stream: a request answered in time
+    counts with its latency, one that missed its deadline (dropped in the
+    queue, or stopped while running) counts at the deadline and is censored
+    (its true time to an answer is longer)."""
+    lat = []
+    for p in polls:
+        if p["status"] == "found":
+            lat.append((p["latency"], False))
+        else:
+            lat.append((deadline_s, True))
+    lat.sort()
+    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else (None, False)
+    answered = sorted(v for v, cens in lat if not cens)
+    qa = lambda f: answered[min(len(answered) - 1, int(f * len(answered)))] if answered else None
+    misses = {}
+    for p in polls:
+        if p["status"] != "found":
+            key = f"n{p['n']}_t{p['k_max']}"
+            misses[key] = misses.get(key, 0) + 1
+    return {"p50_all_s": q(0.5)[0], "p50_all_censored": q(0.5)[1], "p99_all_s": q(0.99)[0],
+            "p99_all_censored": q(0.99)[1], "miss_rate": sum(c for _, c in lat) / max(1, len(lat)),
+            "misses_by_class": dict(sorted(misses.items())), "answered_p50_s": qa(0.5), "answered_p99_s": qa(0.99),
+            "note": "p50/p99 over all requests; a missed request counts at the deadline (censored)"}
+
+
 def run_serving(Q, W, torch, stream, tuned, n_requests=2000, rate=50.0, budget_bytes=2 << 30,
                 deadline_s=10.0, drain_s=15.0):
-    """The serving workload: a Poisson stream of seeded targets replayed in real time into
-    the continuous-batching server; latency is arrival to answer."""
+    """The serving workload: a Poisson stream of seeded targets replayed in real time
+    into the continuous-batching server; latency is arrival to answer, and
+    the deadline counts from arrival too."""
     from paper_1606_07413_gb300 import serve
 
     times, targets = W.poisson_arrivals(n_requests, rate)
     bp = Q.default_batch_params(max_jobs=512, walks_per_job=tuned["walks_per_job"],
                                 steps_per_round=tuned["steps_per_round"], table_log2=18,
                                 queue_capacity=tuned["queue_capacity"])
-    # serving policy: levels of at most 2^26 V + W points are settled by the
-    # exact pass first, larger ones are walked
-    policy = {"theta_min_bits": tuned["theta_min_bits"], "exhaustive_first": 1, "exhaustive_log2": 26}
+    # serving policy: every level of at most 2^32 V + W points (all levels of
+    # this stream, n = 4 level 7 included) is settled by the exact pass
+    policy = {"theta_min_bits": tuned["theta_min_bits"], "exhaustive_first": 1, "exhaustive_log2": 32}
     with serve.Server(bp, budget_bytes, stream=stream, deadline_s=deadline_s,
                       params_for=lambda n: Q.default_params(n, **policy)) as srv:
         rids, wall = serve.replay_stream(srv, times, targets, time_limit_s=float(times[-1]) + drain_s)
         polls = [srv.poll(r) for r in rids]
         fevals, rounds, peak = srv.fevals, srv.rounds, srv.peak_used
-    lat = sorted(p["latency"] for p in polls if p["status"] == "found")
-    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None
     status = {}
     for p in polls:
         status[p["status"]] = status.get(p["status"], 0) + 1
+    offered = {}
+    for t in targets:
+        key = f"n{t['n']}_t{t['t']}"
+        offered[key] = offered.get(key, 0) + 1
+    span = float(times[-1])
     return {
         "workload": f"{n_requests} seeded targets, Poisson arrivals at {rate}/s, n~U{{2,3,4}}, T-count~U{{3..7}}",
-        "answered_p50_s": q(0.5), "answered_p99_s": q(0.99), "status_counts": status,
+        **serving_stats(polls, deadline_s), "status_counts": status,
+        "offered_per_s_by_class": {k: v / span for k, v in sorted(offered.items())},
         "fevals_per_s": fevals / wall, "wall_s": wall, "rounds": rounds, "memory_budget_bytes": budget_bytes,
         "peak_admitted_bytes": peak, "deadline_s": deadline_s,
-        "policy": dict(policy, note="exhaustive pass first on levels of at most 2^26 V + W points, the walk "
-                                    "above; the pass's key table (up to 512 MiB) is allocated for its call and "
-                                    "is not part of the admitted bytes"),
+        "policy": dict(policy, note="exhaustive pass first on every level of at most 2^32 V + W points (n = 4 "
+                                    "level 7: 4.2e9 points, a 512 MiB key table reserved at admission); a "
+                                    "request still queued at its deadline is dropped unanswered"),
     }
 
 
 # ------------------------------------------------------------------ GPU arm
+def timed_level(Q, torch, prob, stream, k, dp_bits, steps, warmup, launches, flush):
+    """`warmup` untimed then `launches` timed bench steps of one level: the
+    walk launch, the re-walk and the host collect, each step bracketed by
+    CUDA events on the launching stream (L2 flushed before each step,
+    outside the events).  Returns (step ms list, walk-kernel ms list, result
+    before, result after)."""
+    with torch.cuda.stream(stream):
+        prob.level_begin(k, version=0, dp_bits=dp_bits, stream=stream)
+        for _ in range(warmup):
+            prob.level_walk(steps, stream)
+            prob.level_rewalk(stream)
+            prob.level_collect(stream)
+    torch.cuda.synchronize()
+    r0 = prob.poll()
+    step_ms, walk_ms = [], []
+    with torch.cuda.stream(stream):
+        for _ in range(launches):
+            flush.zero_()  # evict L2 between steps (outside the timed events)
+            e0, e1, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            prob.level_walk(steps, stream)
+            e1.record(stream)
+            prob.level_rewalk(stream)
+            prob.level_collect(stream)  # synchronizes and checks claw candidates on the host
+            e3.record(stream)
+            e3.synchronize()
+            step_ms.append(e0.elapsed_time(e3))
+            walk_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    return step_ms, walk_ms, r0, prob.poll()
+
+
+def e2e_run(Q, torch, cfg_c, gates, k, steps_per_launch, launches, stream, seed):
+    """The headline metric through the public API: problem creation from the
+    host gate list (uploads C^ and its tables), qcs_run_walks with a step
+    budget of `launches` bench steps, and the per-launch reads of the
+    counters and queued candidates; the byte counts are the ones the library
+    reports it copied."""
+    c = cfg_c
+    budget = launches * c["walks"] * steps_per_launch
+    pe = Q.default_params(c["n"], walks=c["walks"], state_bits=c["L"], dp_bits=c["dtheta"],
+                          table_log2=c["table_log2"], theta_policy=0, version_factor=0,
+                          steps_per_launch=steps_per_launch, budget_factor=1 << 20, stop_on_claw=0,
+                          exhaustive_log2=0, seed=seed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pb = Q.Problem.from_circuit(c["n"], gates, k, pe)
+    pb.run_walks(step_budget=budget, stream=stream)
+    re = pb.wait(600_000)
+    t_e2e = time.perf_counter() - t0
+    pb.close()
+    n_launch = max(re["launches"], 1)
+    return {"value": re["steps"] / t_e2e, "unit": "walk_steps/s",
+            "h2d_bytes_per_step": re["h2d_bytes"] / n_launch, "d2h_bytes_per_step": re["d2h_bytes"] / n_launch,
+            "h2d_bytes": re["h2d_bytes"], "d2h_bytes": re["d2h_bytes"], "steps": re["steps"],
+            "seconds": t_e2e, "launches": n_launch,
+            "path": "qcs_create_problem_circuit + qcs_run_walks + qcs_poll_collisions/qcs_wait; bytes as counted "
+                    "by the library (C^ and its tables up, counters and queued candidates down)"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -469,142 +666,94 @@ def run_ours(args):
                               table_log2=c["table_log2"], seed=rank_seed(rank))
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # measured integer-ALU peaks: IMAD (the 32-bit contraction, n <= 2) and
-    # dp4a (the byte-plane contraction, n >= 3 with C^ in int8)
+    # measured integer-ALU peaks: IMAD (the 32-bit contraction) and dp4a
+    # (the byte-plane contraction, n >= 3 with C^ in int8)
     Q.measure_int_peak("imad", 8, 512)
     imad_per_s, _ = Q.measure_int_peak("imad", 8, 4096)
     dp4a_per_s, _ = Q.measure_int_peak("idp4a", 8, 4096)
 
     prob = Q.Problem.from_circuit(c["n"], gates, K_LEVEL, params)
-    with torch.cuda.stream(stream):
-        prob.level_begin(K_LEVEL, version=0, dp_bits=c["dtheta"], stream=stream)
-        for _ in range(args.warmup):
-            prob.level_walk(STEPS_PER_LAUNCH, stream)
-            prob.level_rewalk(stream)
-            prob.level_collect(stream)
     barrier()
-    r0 = prob.poll()
     clocks = ClockSampler(local)
     clocks.start()
-    step_ms, walk_ms = [], []
     barrier()
     t_wall = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for _ in range(args.steps):
-            flush.zero_()  # evict L2 between steps (outside the timed events)
-            e0, e1, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            e0.record(stream)
-            prob.level_walk(STEPS_PER_LAUNCH, stream)
-            e1.record(stream)
-            prob.level_rewalk(stream)
-            prob.level_collect(stream)  # synchronizes and checks claw candidates on the host
-            e3.record(stream)
-            e3.synchronize()
-            step_ms.append(e0.elapsed_time(e3))
-            walk_ms.append(e0.elapsed_time(e1))
+    step_ms, walk_ms, r0, r1 = timed_level(Q, torch, prob, stream, K_LEVEL, c["dtheta"], STEPS_PER_LAUNCH,
+                                           args.warmup, args.steps, flush)
     barrier()
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
-    r1 = prob.poll()
+    prob.close()
     steps_done = r1["steps"] - r0["steps"]
     w_steps = r1["w_steps"] - r0["w_steps"]
     t_local = sum(step_ms) / 1e3
     t_all, steps_all = combine_ranks(t_local, float(steps_done), world, dist if world > 1 else None, dev)
     value = steps_all / t_all
-
-    # roofline of the walk kernel: algorithmic multiply-adds = W-side steps x
-    # 2 d^2 (16-bit fingerprint weights times C^).  A dp4a makes four byte
-    # products and a multiply-add needs two (one per weight byte), so the
-    # peak is twice the measured dp4a rate.
-    d = 4 ** c["n"] - 1
     walk_s = sum(walk_ms) / 1e3
-    achieved = w_steps * 2 * d * d / walk_s
-    peak = 2 * dp4a_per_s
-    traffic = walk_traffic()
-    hbm_peak, hbm_src = measured_hbm_gbs()
-    hbm = None
-    if traffic is not None:
-        per_launch_s = walk_s / max(1, args.steps)
-        hbm = {"achieved_gbs": traffic / per_launch_s / 1e9, "peak_gbs": hbm_peak,
-               "frac": traffic / per_launch_s / 1e9 / hbm_peak, "peak_source": hbm_src}
-    roof = {"bound": "alu", "unit": "Gop/s", "kernel": "k_walks<3>",
-            "achieved": achieved / 1e9, "peak": peak / 1e9, "frac": achieved / peak,
-            "traffic": traffic, "traffic_unit": "bytes per launch", "hbm": hbm,
-            "peak_source": "2 x measured dp4a rate (qcs_peak_idp4a, this run: "
-                           f"{dp4a_per_s / 1e9:.0f} G dp4a/s); IMAD measured {imad_per_s / 1e9:.0f} Gop/s",
-            "algorithmic_ops": f"2*d^2 = {2 * d * d} 16-bit-weight multiply-adds per W-side walk step "
-                               "(executed as two byte-plane dp4a per four multiply-adds)",
-            "walk_kernel_share": walk_s / t_local}
+    roof = walk_roofline(f"k_walks<{c['n']}>", c["n"], w_steps, steps_done, walk_s, args.steps, dp4a_per_s,
+                         clk.get("sm_mhz"), num_sms)
+    roof["walk_kernel_share"] = walk_s / t_local
+    roof["imad_measured_gops"] = imad_per_s / 1e9
 
-    # e2e through the public API: create from the host gate list, search
-    # launches with per-launch host reads, same throughput setting
     e2e = None
-    tts = None
-    extra = None
+    extra = {}
     if rank == 0:
-        budget = args.steps * c["walks"] * STEPS_PER_LAUNCH
-        pe = Q.default_params(c["n"], walks=c["walks"], state_bits=c["L"], dp_bits=c["dtheta"],
-                              table_log2=c["table_log2"], theta_policy=0, version_factor=0,
-                              steps_per_launch=STEPS_PER_LAUNCH, budget_factor=1 << 20, stop_on_claw=0,
-                              seed=0xE2E)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pb = Q.Problem.from_circuit(c["n"], gates, K_LEVEL, pe)
-        pb.run_walks(step_budget=budget, stream=stream)
-        re = pb.wait(600_000)
-        t_e2e = time.perf_counter() - t0
-        pb.close()
-        launches = max(re["launches"], 1)
-        D = 4 ** c["n"]
-        h2d = (D * D * 8 + D * 8) / launches
-        d2h = 16 * 8 + 4 + 4096 * 24
-        e2e = {"value": re["steps"] / t_e2e, "unit": "walk_steps/s", "h2d_bytes_per_step": round(h2d),
-               "d2h_bytes_per_step": d2h, "steps": re["steps"], "seconds": t_e2e, "launches": launches}
+        e2e = e2e_run(Q, torch, c, gates, K_LEVEL, STEPS_PER_LAUNCH, args.steps, stream, 0xE2E)
         if not args.no_tts:
-            t0 = time.perf_counter()
-            pt = Q.Problem.from_circuit(c["n"], gates, c["k_max"], Q.default_params(c["n"]))
-            pt.run_walks(stream=stream)
-            rt = pt.wait(600_000)
-            tts = {"seconds": time.perf_counter() - t0, "t_count": rt["t_count"], "status": rt["status_name"],
-                   "steps": rt["steps"], "levels": f"{pt.sde}..{c['k_max']}",
-                   "decomposition_verified_exactly": rt["status_name"] == "found",
-                   "note": "full ladder from the sde bound, theta policy 1; the library reports FOUND "
-                           "only after its exact host verification of the decomposition"}
-            pt.close()
+            extra["tto_walk_cfg1"] = time_to_optimal(Q, W, stream, 1, "walk")
+            extra["tto_walk_cfg2"] = time_to_optimal(Q, W, stream, 2, "walk")
+            extra["tto_walk_cfg3"] = time_to_optimal(Q, W, stream, 3, "walk", limit_s=300)
+            extra["tto_exhaustive_cfg2"] = time_to_optimal(Q, W, stream, 2, "exhaustive")
+            extra["tto_exhaustive_cfg3"] = time_to_optimal(Q, W, stream, 3, "exhaustive")
         if not args.no_extra:
+            c2 = W.CONFIGS[2]
+            g2, _ = W.config_target(2)
+            p2 = Q.default_params(c2["n"], walks=c2["walks"], state_bits=c2["L"], dp_bits=c2["dtheta"],
+                                  table_log2=c2["table_log2"], seed=rank_seed(rank))
+            prob2 = Q.Problem.from_circuit(c2["n"], g2, 5, p2)
+            s2, w2, q0, q1 = timed_level(Q, torch, prob2, stream, 5, c2["dtheta"], 512, 3, 20, flush)
+            prob2.close()
+            st2 = q1["steps"] - q0["steps"]
+            extra["n3_level5"] = {
+                "config": workload_config(c2, 5, 512), "walk_steps_per_s": st2 / (sum(s2) / 1e3),
+                "ms_per_step": sum(s2) / len(s2),
+                "roofline": walk_roofline("k_walks<3>", 3, q1["w_steps"] - q0["w_steps"], st2, sum(w2) / 1e3, 20,
+                                          dp4a_per_s, clk.get("sm_mhz"), num_sms)}
             batched = run_batched(Q, W, torch, stream, mac_peak=2 * dp4a_per_s)
-            extra = {
+            extra.update({
                 "batched": batched,
                 "serving": run_serving(Q, W, torch, stream, batched["autotuned"]),
                 "table1_circuits": table1_circuits(Q, W, stream),
-                "config3_time_to_optimal": config3_time_to_optimal(Q, W, stream, "exhaustive"),
                 "n4_level7_exhaustive_pass": exhaustive_level_pass(Q, W, stream),
                 "n2_level3": level_throughput(Q, W, torch, 1, 3, 512, stream, alu_per_s=imad_per_s),
-                "n4_level7": level_throughput(Q, W, torch, 3, 7, 16, stream, alu_per_s=2 * dp4a_per_s),
                 # the table at its busiest: half the points distinguished
                 "n3_level5_theta_half": level_throughput(Q, W, torch, 2, 5, 64, stream, alu_per_s=2 * dp4a_per_s,
                                                          dp_bits=1, table_log2=26),
-            }
-    prob.close()
+                # targets whose reduced C^ leaves int8: the 32-bit word contraction (IMAD; n = 4 reads C^
+                # through L2), against the measured IMAD rate
+                "c32_n3_level5": level_throughput(Q, W, torch, 2, 5, 512, stream, alu_per_s=imad_per_s,
+                                                  target=(3, 19, 4019)),
+                "c32_n4_level7": level_throughput(Q, W, torch, 3, 7, 16, stream, alu_per_s=imad_per_s,
+                                                  target=(4, 15, 4015)),
+            })
 
     if rank == 0:
         line = {
             "metric": "walk_steps_per_sec", "value": value, "unit": "walk_steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_all * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic (seeded target C0.R(P5)..R(P1), n=3)", "config": workload_config(c),
+            "data": "synthetic (seeded target C0.R(P7)..R(P1), n=4)", "config": workload_config(c),
             "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e, "clocks": clk,
-            "gpu_launches": 2 * args.steps, "time_to_optimal_t_count": tts,
-            "wall_s": wall,
+            "gpu_launches": 2 * args.steps, "wall_s": wall,
         }
-        if extra:
-            line.update(extra)
+        line.update(extra)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -630,7 +779,7 @@ def run_reference(args):
     line = {"metric": "walk_steps_per_sec", "value": value, "unit": "walk_steps/s", "impl": "reference",
             "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic (seeded target C0.R(P5)..R(P1), n=3)", "config": workload_config(c),
+            "data": "synthetic (seeded target C0.R(P7)..R(P1), n=4)", "config": workload_config(c),
             "cpu_baseline": base,
             "e2e": {"value": value, "unit": "walk_steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -645,7 +794,7 @@ def run_level_only(args):
 
     B.build()
     stream = torch.cuda.Stream()
-    cfg, k, steps = {"n2_level3": (1, 3, 512), "n4_level7": (3, 7, 16)}[args.level_only]
+    cfg, k, steps = {"n2_level3": (1, 3, 512), "n3_level5": (2, 5, 512), "n4_level7": (3, 7, 16)}[args.level_only]
     Q.measure_int_peak("imad", 8, 512)
     peak = Q.measure_int_peak("imad" if cfg == 1 else "idp4a", 8, 4096)[0] * (1 if cfg == 1 else 2)
     print(json.dumps({args.level_only: level_throughput(Q, W, torch, cfg, k, steps, stream, launches=args.steps,
@@ -676,11 +825,30 @@ def run_config3_walk(args):
     stream = torch.cuda.Stream()
     if args.adder_walk:
         u = perm_unitary(W.permutation_targets()["adder"][1])
-        print(json.dumps({"adder_time_to_optimal": n4_time_to_optimal(Q, W, stream, "walk", args.adder_walk,
-                                                                     unitary=u)}))
+        print(json.dumps({"adder_time_to_optimal": time_to_optimal(Q, W, stream, 3, "walk", args.adder_walk,
+                                                                  unitary=u)}))
     else:
-        print(json.dumps({"config3_time_to_optimal": config3_time_to_optimal(Q, W, stream, "walk",
-                                                                             args.config3_walk)}))
+        print(json.dumps({"tto_walk_cfg3": time_to_optimal(Q, W, stream, 3, "walk", args.config3_walk)}))
+
+
+def run_tto_sweep(args):
+    """The n = 4 seeded target's collision walk over table sizes w and
+    distinguished fractions theta (the Appendix's steps per collision,
+    N theta / w + 2 / theta, against measured time)."""
+    import torch
+
+    import paper_1606_07413_gb300 as Q
+    from paper_1606_07413_gb300 import build as B
+    from paper_1606_07413_gb300 import workloads as W
+
+    B.build()
+    stream = torch.cuda.Stream()
+    out = []
+    for table_log2, dp_bits in ((30, None), (30, 2), (30, 3), (28, None), (32, None), (33, None)):
+        r = time_to_optimal(Q, W, stream, 3, "walk", table_log2, limit_s=240, dp_bits=dp_bits)
+        out.append(r)
+        print(json.dumps(r), file=sys.stderr)
+    print(json.dumps({"tto_walk_cfg3_sweep": out}))
 
 
 def run_exhaustive_only(args):
@@ -700,6 +868,8 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.exhaustive_only:
         run_exhaustive_only(a)
+    elif a.tto_sweep:
+        run_tto_sweep(a)
     elif a.config3_walk or a.adder_walk:
         run_config3_walk(a)
     elif a.level_only:

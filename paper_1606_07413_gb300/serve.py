@@ -10,7 +10,9 @@ a key table for the call; the budget keeps room for the largest such table
 among the admitted jobs.  A job
 leaves the batch as soon as it has its answer (or passes its deadline) and
 its memory is released for the next request.  Times are measured from each
-request's arrival to its answer.
+request's arrival to its answer, and so is the deadline: a request still
+waiting when its deadline passes is dropped without running, so that the
+GPU's time goes to requests that can still be answered in time.
 """
 from __future__ import annotations
 
@@ -24,13 +26,29 @@ import numpy as np
 import paper_1606_07413_gb300 as Q
 
 
-def exhaustive_table_bytes(params) -> int:
-    """Upper bound on the key table of one exhaustive level pass under these
-    search parameters: a level of at most 2^exhaustive_log2 points stores at
-    most half of them, in a power-of-two table of at least twice as many
-    slots (and at least 1024), 16 bytes a slot."""
+def exhaustive_table_bytes(params, n: int | None = None, k_max: int | None = None) -> int:
+    """Key table of the largest exhaustive level pass a request may run under
+    these search parameters (16 bytes a slot).  The pass stores the xi^h
+    points of its smaller side (xi = 4^n - 1, h = floor(k/2)) in a power-of-two
+    table of at least twice as many slots and at least 1024, and runs only on
+    levels 2..k_max of at most 2^exhaustive_log2 V + W points.  Without n and
+    k_max: the bound 16 x 2^exhaustive_log2 over every level size."""
     e = int(getattr(params, "exhaustive_log2", 0) or 0)
-    return 16 << max(e, 10) if e > 0 else 0
+    if e <= 0:
+        return 0
+    if n is None or k_max is None:
+        return 16 << max(e, 10)
+    xi = 4 ** int(n) - 1
+    most = 0
+    for k in range(2, int(k_max) + 1):
+        stored = xi ** (k // 2)
+        if stored + stored * (xi if k & 1 else 1) > 1 << e:
+            continue
+        slots = 1024
+        while slots < 2 * stored:
+            slots <<= 1
+        most = max(most, 16 * slots)
+    return most
 
 
 class Request:
@@ -73,7 +91,7 @@ class Server:
         r = Request(rid, n, np.asarray(gates, np.int32), k_max, params,
                     self.clock() if t_arrival is None else t_arrival)
         p = params or self.params_for(n)
-        r.table_bytes = exhaustive_table_bytes(p)
+        r.table_bytes = exhaustive_table_bytes(p, n, k_max) if p is not None else 0
         r.future = self.pool.submit(Q.Problem.from_circuit, n, r.gates, k_max, p)
         self.requests[rid] = r
         self.waiting.append(r)
@@ -81,14 +99,31 @@ class Server:
 
     def poll(self, rid: int) -> dict:
         r = self.requests[rid]
-        out = {"status": r.status, "t_arrival": r.t_arrival, "t_admit": r.t_admit, "t_done": r.t_done}
+        out = {"status": r.status, "n": r.n, "k_max": r.k_max, "t_arrival": r.t_arrival, "t_admit": r.t_admit,
+               "t_done": r.t_done}
         if r.result is not None:
             out.update(t_count=r.result["t_count"], paulis=r.result["paulis"], steps=r.result["steps"],
                        latency=r.t_done - r.t_arrival)
         return out
 
     # ---- server side ----------------------------------------------------
+    def _expired(self, r, now) -> bool:
+        return self.deadline is not None and now - r.t_arrival > self.deadline
+
+    def _drop_expired(self):
+        """Requests whose deadline passed while they waited leave unanswered."""
+        now = self.clock()
+        keep = collections.deque()
+        for r in self.waiting:
+            if self._expired(r, now):
+                r.status, r.t_done = "deadline", now
+                r.future.add_done_callback(lambda f: f.result().close())
+            else:
+                keep.append(r)
+        self.waiting = keep
+
     def _admit(self, block: bool = False):
+        self._drop_expired()
         while self.waiting and len(self.running) < self.slots:
             r = self.waiting[0]
             if not r.future.done() and not (block and not self.running):
@@ -133,7 +168,7 @@ class Server:
             res = self.batch.poll(slot)
             if res["status_name"] != "searching":
                 self._finish(r, res["status_name"], res)
-            elif self.deadline is not None and now - r.t_admit > self.deadline:
+            elif self._expired(r, now):
                 self._finish(r, "deadline", res)
         return len(self.running)
 

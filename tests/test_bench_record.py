@@ -38,8 +38,9 @@ def test_roofline_and_timing_are_consistent():
     # steps per bench step / seconds per bench step = the headline value
     steps_per_step = r["config"]["walks"] * r["config"]["steps_per_walk_per_step"]
     assert abs(r["value"] - steps_per_step / (r["ms_per_step"] / 1e3)) / r["value"] < 0.02
-    if roof["traffic"] is not None:
-        assert roof["traffic"] == bench.WALK_TRAFFIC["bytes_per_launch"]
+    rec = bench.WALK_NCU.get(roof["kernel"])
+    if roof["traffic"] is not None and rec and rec["dram_bytes_per_launch"] is not None:
+        assert roof["traffic"] == rec["dram_bytes_per_launch"]
 
 
 def test_clocks_and_e2e():

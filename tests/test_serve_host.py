@@ -112,6 +112,8 @@ def test_deadline_ends_a_job_and_frees_its_memory(fake):
     with serve.Server(bparams(2), memory_budget=10_000, deadline_s=1.0, clock=clock) as srv:
         slow = srv.submit(3, [[1000, 0, 0]], 5)
         fast = srv.submit(2, [[2, 0, 0]], 3)
+        for r in srv.requests.values():  # both set-ups done before the simulated clock runs
+            r.future.result()
         for _ in range(30):
             clock.t += 0.1
             srv.step()
@@ -157,3 +159,34 @@ def test_admission_keeps_room_for_one_exhaustive_key_table(fake):
             assert srv.idle() and peak == most
             assert all(srv.poll(r)["status"] == "found" for r in rids)
 
+
+
+def test_a_request_whose_deadline_passes_in_the_queue_never_runs(fake):
+    """The deadline counts from arrival: a request still queued behind a long
+    job when its deadline passes is dropped without being added to the batch."""
+    clock = Clock()
+    with serve.Server(bparams(1), memory_budget=10_000, deadline_s=1.0, clock=clock) as srv:
+        long_job = srv.submit(3, [[1000, 0, 0]], 5)
+        queued = srv.submit(2, [[2, 0, 0]], 3)
+        for r in srv.requests.values():
+            r.future.result()
+        for _ in range(30):
+            clock.t += 0.1
+            srv.step()
+        assert srv.poll(long_job)["status"] == "deadline"
+        assert srv.poll(queued)["status"] == "deadline" and srv.poll(queued)["t_admit"] is None
+        assert len(srv.batch.added) == 1 and srv.idle()
+
+
+def test_exhaustive_table_is_sized_for_the_requests_largest_eligible_level():
+    """xi^h stored points in a power-of-two table of at least twice as many
+    slots: n = 4 level 7 stores 255^3 points in 2^25 slots (512 MiB); a level
+    beyond 2^exhaustive_log2 points does not count."""
+    from types import SimpleNamespace
+
+    p32, p26 = SimpleNamespace(exhaustive_log2=32), SimpleNamespace(exhaustive_log2=26)
+    assert serve.exhaustive_table_bytes(p32, 4, 7) == 16 << 25
+    assert serve.exhaustive_table_bytes(p26, 4, 7) == 16 << 25  # level 6: 2 x 255^3 points, same table
+    assert serve.exhaustive_table_bytes(p26, 4, 5) == 16 << 17  # level 5: 255^2 stored
+    assert serve.exhaustive_table_bytes(p32, 2, 3) == 16 << 10
+    assert serve.exhaustive_table_bytes(SimpleNamespace(exhaustive_log2=0), 4, 7) == 0
