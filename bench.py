@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--adder-walk", type=int, default=0, metavar="TABLE_LOG2",
                     help="only time the 4-qubit full adder's search by the collision walk alone with a "
                          "2^TABLE_LOG2-slot table, print its JSON and exit")
+    ap.add_argument("--shape", type=int, default=0, help="launch shape of the --level-only walk kernel")
+    ap.add_argument("--c-layout", type=int, default=0, help="C^ layout of the --level-only walk (0 int8, 1 words)")
     ap.add_argument("--tto-sweep", action="store_true",
                     help="only time the n = 4 seeded target's collision walk over a grid of table sizes and "
                          "distinguished fractions, print its JSON and exit")
@@ -95,8 +97,8 @@ def workload_config(c, k=None, steps=None):
 # kernel's source files, comments and layout removed); otherwise its figures
 # are reported as null.
 WALK_NCU = {
-    "k_walks<4>": {"source_sha256_16": None, "dram_bytes_per_launch": None, "warp_inst_per_step": None},
-    "k_walks<3>": {"source_sha256_16": None, "dram_bytes_per_launch": None, "warp_inst_per_step": None},
+    "k_walks<4,0>": {"source_sha256_16": None, "dram_bytes_per_launch": None, "warp_inst_per_step": None},
+    "k_walks<3,0>": {"source_sha256_16": None, "dram_bytes_per_launch": None, "warp_inst_per_step": None},
 }
 
 
@@ -272,7 +274,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ other workloads
 def level_throughput(Q, W, torch, cfg, k, steps, stream, launches=3, alu_per_s=None, dp_bits=None, table_log2=None,
-                     target=None):
+                     target=None, shape=0, c_layout=0):
     """Walk steps/s of one single-target level launch at a configured size
     (dp_bits / table_log2 override the configuration's theta and table;
     target = (n, t, seed) takes another seeded target of that size class),
@@ -285,10 +287,10 @@ def level_throughput(Q, W, torch, cfg, k, steps, stream, launches=3, alu_per_s=N
         k_max = c["k_max"]
     else:
         gates, _ = W.seeded_target(*target)
-        k_max = max(k, target[1])
+        k_max = k
     dpb = dp_bits or c["dtheta"]
     p = Q.default_params(c["n"], walks=c["walks"], state_bits=c["L"], dp_bits=dpb,
-                         table_log2=table_log2 or min(c["table_log2"], 24))
+                         table_log2=table_log2 or min(c["table_log2"], 24), launch_shape=shape, c_layout=c_layout)
     prob = Q.Problem.from_circuit(c["n"], gates, k_max, p)
     prob.level_begin(k, 0, dpb, stream=stream)
     prob.level_walk(steps, stream); prob.level_rewalk(stream); prob.level_collect(stream)
@@ -334,12 +336,13 @@ def run_batched(Q, W, torch, stream, n_targets=256, mac_peak=None, min_seconds=1
 
     def mk(i, t):
         return Q.Problem.from_circuit(t["n"], t["gates"], t["t"],
-                                      Q.default_params(t["n"], theta_min_bits=best["theta_min_bits"], seed=1000 + i))
+                                      Q.default_params(t["n"], theta_min_bits=best["theta_min_bits"], seed=1000 + i,
+                                                       c_layout=best["c_layout"].get(t["n"], 0)))
 
     def bp(J):
         return Q.default_batch_params(max_jobs=J, walks_per_job=best["walks_per_job"],
                                       steps_per_round=best["steps_per_round"], table_log2=18,
-                                      queue_capacity=best["queue_capacity"])
+                                      queue_capacity=best["queue_capacity"], launch_shape=best["launch_shape"])
 
     def batched(rounds):
         probs = [mk(i, t) for i, t in enumerate(targets)]
@@ -389,7 +392,9 @@ def run_batched(Q, W, torch, stream, n_targets=256, mac_peak=None, min_seconds=1
     bs, os_ = statistics.median(b_secs), statistics.median(o_secs)
     return {
         "workload": f"{n_targets} seeded targets, n~U{{2,3,4}}, T-count~U{{3..7}}, {rounds} rounds per job",
-        "autotuned": best, "autotune_seconds": tune_s, "autotune_trials": len(trials),
+        "autotuned": {**best, "launch_shape": {str(k): v for k, v in best["launch_shape"].items()},
+                      "c_layout": {str(k): v for k, v in best["c_layout"].items()}},
+        "autotune_seconds": tune_s, "autotune_trials": len(trials),
         "batched_fevals_per_s": fev / bs, "one_target_fevals_per_s": fev_one / os_,
         "batched_walk_steps_per_s": walk / bs, "one_target_walk_steps_per_s": walk / os_,
         "speedup": os_ / bs, "speedup_min_max": [min(o_secs) / max(b_secs), max(o_secs) / min(b_secs)],
@@ -549,12 +554,14 @@ def run_serving(Q, W, torch, stream, tuned, n_requests=2000, rate=50.0, budget_b
     times, targets = W.poisson_arrivals(n_requests, rate)
     bp = Q.default_batch_params(max_jobs=512, walks_per_job=tuned["walks_per_job"],
                                 steps_per_round=tuned["steps_per_round"], table_log2=18,
-                                queue_capacity=tuned["queue_capacity"])
+                                queue_capacity=tuned["queue_capacity"],
+                                launch_shape={int(k): v for k, v in tuned.get("launch_shape", {}).items()})
+    layouts = {int(k): v for k, v in tuned.get("c_layout", {}).items()}
     # serving policy: every level of at most 2^32 V + W points (all levels of
     # this stream, n = 4 level 7 included) is settled by the exact pass
     policy = {"theta_min_bits": tuned["theta_min_bits"], "exhaustive_first": 1, "exhaustive_log2": 32}
     with serve.Server(bp, budget_bytes, stream=stream, deadline_s=deadline_s,
-                      params_for=lambda n: Q.default_params(n, **policy)) as srv:
+                      params_for=lambda n: Q.default_params(n, c_layout=layouts.get(n, 0), **policy)) as srv:
         rids, wall = serve.replay_stream(srv, times, targets, time_limit_s=float(times[-1]) + drain_s)
         polls = [srv.poll(r) for r in rids]
         fevals, rounds, peak = srv.fevals, srv.rounds, srv.peak_used
@@ -611,7 +618,7 @@ def timed_level(Q, torch, prob, stream, k, dp_bits, steps, warmup, launches, flu
     return step_ms, walk_ms, r0, prob.poll()
 
 
-def e2e_run(Q, torch, cfg_c, gates, k, steps_per_launch, launches, stream, seed):
+def e2e_run(Q, torch, cfg_c, gates, k, steps_per_launch, launches, stream, seed, shape):
     """The headline metric through the public API: problem creation from the
     host gate list (uploads C^ and its tables), qcs_run_walks with a step
     budget of `launches` bench steps, and the per-launch reads of the
@@ -622,7 +629,8 @@ def e2e_run(Q, torch, cfg_c, gates, k, steps_per_launch, launches, stream, seed)
     pe = Q.default_params(c["n"], walks=c["walks"], state_bits=c["L"], dp_bits=c["dtheta"],
                           table_log2=c["table_log2"], theta_policy=0, version_factor=0,
                           steps_per_launch=steps_per_launch, budget_factor=1 << 20, stop_on_claw=0,
-                          exhaustive_log2=0, seed=seed)
+                          exhaustive_log2=0, seed=seed, launch_shape=shape["launch_shape"],
+                          c_layout=shape["c_layout"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     pb = Q.Problem.from_circuit(c["n"], gates, k, pe)
@@ -679,6 +687,17 @@ def run_ours(args):
     imad_per_s, _ = Q.measure_int_peak("imad", 8, 4096)
     dp4a_per_s, _ = Q.measure_int_peak("idp4a", 8, 4096)
 
+    # launch shape and C^ layout of the level walk, chosen by the autotuner on
+    # this level (the walks are the same under every choice)
+    from paper_1606_07413_gb300 import autotune
+
+    def tune_problem(**kw):
+        pt = Q.default_params(c["n"], walks=c["walks"], state_bits=c["L"], dp_bits=c["dtheta"], table_log2=24,
+                              seed=rank_seed(rank), **kw)
+        return Q.Problem.from_circuit(c["n"], gates, K_LEVEL, pt)
+
+    shape, shape_trials = autotune.tune_level_shape(c["n"], tune_problem, K_LEVEL, 16, stream)
+    params.launch_shape, params.c_layout = shape["launch_shape"], shape["c_layout"]
     prob = Q.Problem.from_circuit(c["n"], gates, K_LEVEL, params)
     barrier()
     clocks = ClockSampler(local)
@@ -697,15 +716,15 @@ def run_ours(args):
     t_all, steps_all = combine_ranks(t_local, float(steps_done), world, dist if world > 1 else None, dev)
     value = steps_all / t_all
     walk_s = sum(walk_ms) / 1e3
-    roof = walk_roofline(f"k_walks<{c['n']}>", c["n"], w_steps, steps_done, walk_s, args.steps, dp4a_per_s,
-                         clk.get("sm_mhz"), num_sms)
+    roof = walk_roofline(f"k_walks<{c['n']},{shape['launch_shape']}>", c["n"], w_steps, steps_done, walk_s,
+                         args.steps, dp4a_per_s, clk.get("sm_mhz"), num_sms)
     roof["walk_kernel_share"] = walk_s / t_local
     roof["imad_measured_gops"] = imad_per_s / 1e9
 
     e2e = None
     extra = {}
     if rank == 0:
-        e2e = e2e_run(Q, torch, c, gates, K_LEVEL, STEPS_PER_LAUNCH, args.steps, stream, 0xE2E)
+        e2e = e2e_run(Q, torch, c, gates, K_LEVEL, STEPS_PER_LAUNCH, args.steps, stream, 0xE2E, shape)
         if not args.no_tts:
             extra["tto_walk_cfg1"] = time_to_optimal(Q, W, stream, 1, "walk")
             extra["tto_walk_cfg2"] = time_to_optimal(Q, W, stream, 2, "walk")
@@ -724,7 +743,7 @@ def run_ours(args):
             extra["n3_level5"] = {
                 "config": workload_config(c2, 5, 512), "walk_steps_per_s": st2 / (sum(s2) / 1e3),
                 "ms_per_step": sum(s2) / len(s2),
-                "roofline": walk_roofline("k_walks<3>", 3, q1["w_steps"] - q0["w_steps"], st2, sum(w2) / 1e3, 20,
+                "roofline": walk_roofline("k_walks<3,0>", 3, q1["w_steps"] - q0["w_steps"], st2, sum(w2) / 1e3, 20,
                                           dp4a_per_s, clk.get("sm_mhz"), num_sms)}
             batched = run_batched(Q, W, torch, stream, mac_peak=2 * dp4a_per_s)
             extra.update({
@@ -749,8 +768,10 @@ def run_ours(args):
             "metric": "walk_steps_per_sec", "value": value, "unit": "walk_steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_all * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic (seeded target C0.R(P7)..R(P1), n=4)", "config": workload_config(c),
-            "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e, "clocks": clk,
+            "data": "synthetic (seeded target C0.R(P7)..R(P1), n=4)",
+            "config": dict(workload_config(c), launch_shape=Q.launch_shapes(c["n"])[shape["launch_shape"]],
+                           c_layout=["int8 byte quads (dp4a)", "32-bit words (IMAD)"][shape["c_layout"]]),
+            "autotuned_level_shape": shape_trials, "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e, "clocks": clk,
             "gpu_launches": 2 * args.steps, "wall_s": wall,
         }
         line.update(extra)
@@ -798,7 +819,7 @@ def run_level_only(args):
     Q.measure_int_peak("imad", 8, 512)
     peak = Q.measure_int_peak("imad" if cfg == 1 else "idp4a", 8, 4096)[0] * (1 if cfg == 1 else 2)
     print(json.dumps({args.level_only: level_throughput(Q, W, torch, cfg, k, steps, stream, launches=args.steps,
-                                                        alu_per_s=peak)}))
+                                                        alu_per_s=peak, shape=args.shape, c_layout=args.c_layout)}))
 
 
 def run_batched_only(args):

@@ -113,6 +113,11 @@ typedef struct qcs_params {
                                  claw (0: never; at most 40) */
     int32_t exhaustive_first; /* 1: qcs_run_walks settles such levels by qcs_certify_level alone,
                                  without walking them (0: walk first) */
+    int32_t launch_shape;     /* launch shape of the level-walk kernel, 0 .. qcs_launch_shapes(n) - 1
+                                 (0 = default); the walks and results do not depend on it */
+    int32_t c_layout;         /* device layout of C^ for the W side's contraction (n >= 3): 0 = signed
+                                 byte quads when every entry fits in int8 (dp4a), else 32-bit words;
+                                 1 = 32-bit words always (IMAD).  Results do not depend on it */
     uint64_t seed;            /* seed of trail starting points */
 } qcs_params;
 
@@ -137,7 +142,8 @@ typedef struct qcs_result {
     int64_t rewalk_steps; /* evaluations of f made by the re-walk (Fig. 2 trace-back) */
     int64_t certified_levels; /* levels proved claw-free by the exhaustive pass */
     int64_t cert_points;      /* points (V and W) evaluated by the exhaustive pass */
-    int64_t h2d_bytes;        /* bytes this problem copied host to device: the upload of C^, its
+    int64_t h2d_bytes;        /* since the problem's creation (searches do not reset these two):
+                                 bytes this problem copied host to device: the upload of C^, its
                                  weights and rotation tables at creation (and the shared stage tables
                                  when this creation uploaded them); device-side resets not counted */
     int64_t d2h_bytes;        /* bytes copied device to host for this problem: per launch the
@@ -146,6 +152,15 @@ typedef struct qcs_result {
 } qcs_result;
 
 typedef struct qcs_problem qcs_problem;
+
+/* Launch shapes of the walk kernels for n qubits (the autotuner's space; not
+ * a passage of the paper: how walks map onto the GPU).  Returns the number
+ * of shapes (>= 1) and fills, for shape i < max_shapes, warps[i] (warps per
+ * CTA, each warp evaluating 32 / min(32, 4^n) walks) and min_blocks[i] (the
+ * resident CTAs per SM the kernel is compiled for, capping its registers at
+ * 65536 / (32 warps[i] min_blocks[i])).  Either pointer may be NULL.
+ * QCS_ERR_ARG if n is not in 1..4. */
+QCS_API int qcs_launch_shapes(int n_qubits, int32_t *warps, int32_t *min_blocks, int max_shapes);
 
 /* Fill *p with the defaults for n qubits (L = 32/48/64, d_theta = 6/10/12 ...). */
 QCS_API void qcs_default_params(int n_qubits, qcs_params *p);
@@ -312,6 +327,8 @@ typedef struct qcs_batch_params {
     int32_t use_graph;       /* 1: each round is one CUDA-graph replay */
     int32_t rewalk_budget;   /* evaluations of f one re-walk may take per round; an unfinished
                                 re-walk resumes in the next round (0: no bound) */
+    int32_t launch_shape[4];  /* launch shape of the batched walk kernel for n = 1..4 qubits
+                                 (index n - 1; 0 = default; see qcs_launch_shapes) */
     int32_t reserved;
 } qcs_batch_params;
 

@@ -18,7 +18,7 @@ from . import build as _build_mod
 
 __all__ = ["lib", "Params", "Result", "Problem", "Batch", "BatchParams", "default_params",
            "default_batch_params", "verify_decomposition", "channel_from_unitary", "strerror", "QcsError",
-           "plan_level"]
+           "plan_level", "launch_shapes"]
 
 OK = 0
 ERR_ARG, ERR_NOT_UNITARY, ERR_NOMEM, ERR_CUDA, ERR_MISMATCH, ERR_OVERFLOW, ERR_BUSY, ERR_TIMEOUT, ERR_DEVICE = \
@@ -36,7 +36,7 @@ class Params(ctypes.Structure):
                 ("budget_factor", ctypes.c_int32), ("theta_policy", ctypes.c_int32),
                 ("version_factor", ctypes.c_int32), ("stop_on_claw", ctypes.c_int32), ("theta_min_bits", ctypes.c_int32),
                 ("exhaustive_log2", ctypes.c_int32), ("exhaustive_first", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("launch_shape", ctypes.c_int32), ("c_layout", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -74,10 +74,13 @@ class BatchParams(ctypes.Structure):
     _fields_ = [("max_jobs", ctypes.c_int32), ("walks_per_job", ctypes.c_int32),
                 ("steps_per_round", ctypes.c_int32), ("table_log2", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("rewalk_budget", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("rewalk_budget", ctypes.c_int32), ("launch_shape", ctypes.c_int32 * 4),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+        d["launch_shape"] = list(self.launch_shape)
+        return d
 
 
 class QcsError(RuntimeError):
@@ -129,6 +132,7 @@ def lib():
             "qcs_level_walk_static": (ctypes.c_int, [_vp, ctypes.c_int, _u32, ctypes.c_int, ctypes.c_int, _vp, _u32,
                                                      _u32, _vp, _u32, _vp, _vp]),
             "qcs_batch_default_params": (None, [ctypes.POINTER(BatchParams)]),
+            "qcs_launch_shapes": (ctypes.c_int, [ctypes.c_int, _vp, _vp, ctypes.c_int]),
             "qcs_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchParams), _vp, ctypes.POINTER(_vp)]),
             "qcs_batch_job_bytes": (_u64, [_vp, _vp]),
             "qcs_batch_add": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_int)]),
@@ -170,6 +174,17 @@ def default_params(n: int, **overrides) -> Params:
             raise TypeError(f"unknown search parameter {k!r}")
         setattr(p, k, v)
     return p
+
+
+def launch_shapes(n: int) -> list[dict]:
+    """qcs_launch_shapes: the walk kernel's launch shapes for n qubits, as
+    [{"shape": i, "warps": .., "min_blocks": ..}] (shape 0 is the default)."""
+    warps = np.zeros(8, np.int32)
+    minb = np.zeros(8, np.int32)
+    cnt = lib().qcs_launch_shapes(int(n), warps.ctypes.data_as(_vp), minb.ctypes.data_as(_vp), 8)
+    if cnt < 0:
+        _check(cnt, "qcs_launch_shapes")
+    return [{"shape": i, "warps": int(warps[i]), "min_blocks": int(minb[i])} for i in range(cnt)]
 
 
 def plan_level(n: int, k: int, params: Params) -> dict:
@@ -349,12 +364,19 @@ class Problem:
 
 
 def default_batch_params(**overrides) -> BatchParams:
+    """Batch parameters; launch_shape may be given as a list of 4 shapes
+    (n = 1..4) or as a dict {n: shape}."""
     p = BatchParams()
     lib().qcs_batch_default_params(ctypes.byref(p))
     names = {name for name, _ in BatchParams._fields_}
     for k, v in overrides.items():
         if k not in names or k == "reserved":
             raise TypeError(f"unknown batch parameter {k!r}")
+        if k == "launch_shape":
+            items = v.items() if isinstance(v, dict) else enumerate(v, start=1)
+            for n, sh in items:
+                p.launch_shape[int(n) - 1] = int(sh)
+            continue
         setattr(p, k, v)
     return p
 

@@ -85,6 +85,7 @@ bool params_ok(int n, int k_max, const qcs_params &p)
     if (p.steps_per_launch < 1 || p.max_trail_factor < 1 || p.queue_capacity < 1) return false;
     if (p.budget_factor < 0 || p.version_factor < 0 || p.theta_min_bits < 0) return false;
     if (p.exhaustive_log2 < 0 || p.exhaustive_log2 > 40) return false;
+    if (p.launch_shape < 0 || p.launch_shape >= launch_shapes(n) || p.c_layout < 0 || p.c_layout > 1) return false;
     // every rotation field must reach all 4^n - 1 Paulis: 2^ell > xi
     const int h = k_max / 2;
     return h == 0 || field_bits(p.state_bits, h) >= 2 * n;
@@ -221,7 +222,7 @@ int upload_problem(qcs_problem *P)
     // one word) when every entry fits in int8, laid out for the walk
     // kernel's byte-plane contraction (LevelCtx::Cq)
     std::vector<uint32_t> cq;
-    if (n >= 3) {
+    if (n >= 3 && P->p.c_layout == 0) {
         bool fits = true;
         for (size_t i = 0; i < P->C.a.size() && fits; i++)
             fits = P->C.a[i] >= -128 && P->C.a[i] <= 127 && P->C.b[i] >= -128 && P->C.b[i] <= 127;
@@ -393,6 +394,7 @@ int level_begin(qcs_problem *P, int k, uint32_t version, int dp_bits, uint32_t n
     w.ccount = P->dQhead + 1;
     w.ccap = kCandCap;
     w.counters = P->dCounters;
+    w.shape = P->p.launch_shape;
     CK(cudaMemsetAsync(P->dTable, 0xFF, sizeof(Slot) << P->p.table_log2, s));
     CK(cudaMemsetAsync(P->dQhead, 0, 2 * sizeof(uint32_t), s));
     CK(launch_init_walks(w, s));
@@ -807,6 +809,17 @@ int qcs::record_cuda_error(cudaError_t e) { return cuda_fail(e); }
 
 extern "C" {
 
+int qcs_launch_shapes(int n_qubits, int32_t *warps, int32_t *min_blocks, int max_shapes)
+{
+    if (n_qubits < 1 || n_qubits > 4) return QCS_ERR_ARG;
+    const int cnt = launch_shapes(n_qubits);
+    for (int i = 0; i < cnt && i < max_shapes; i++) {
+        if (warps) warps[i] = shape_warps_of(n_qubits, i);
+        if (min_blocks) min_blocks[i] = shape_min_blocks_of(n_qubits, i);
+    }
+    return cnt;
+}
+
 void qcs_default_params(int n_qubits, qcs_params *p)
 {
     if (!p) return;
@@ -889,7 +902,10 @@ int qcs_run_walks(qcs_problem *P, uint64_t step_budget, void *stream)
     P->running = true;
     P->cancel = false;
     const int sde = P->res.sde;
+    const int64_t h2d = P->res.h2d_bytes, d2h = P->res.d2h_bytes; // kept for the problem's lifetime
     memset(&P->res, 0, sizeof P->res);
+    P->res.h2d_bytes = h2d;
+    P->res.d2h_bytes = d2h;
     P->res.status = QCS_SEARCHING;
     P->res.t_count = -1;
     P->res.sde = sde;
@@ -967,7 +983,10 @@ int qcs_level_begin(qcs_problem *P, int k, uint32_t version, int dp_bits, void *
         std::lock_guard<std::mutex> g(P->mu);
         if (P->res.status != QCS_SEARCHING) {
             const int sde = P->res.sde;
+            const int64_t h2d = P->res.h2d_bytes, d2h = P->res.d2h_bytes; // kept for the problem's lifetime
             memset(&P->res, 0, sizeof P->res);
+            P->res.h2d_bytes = h2d;
+            P->res.d2h_bytes = d2h;
             P->res.sde = sde;
             P->res.t_count = -1;
             P->res.status = QCS_SEARCHING;

@@ -196,7 +196,7 @@ void build_tasks(qcs_batch *B)
         if (!j.active) continue;
         const int c = j.P->n;
         B->hIds[(size_t)c * B->bp.max_jobs + nj[c]++] = (uint32_t)slot;
-        const int per = walks_per_task(c);
+        const int per = walks_per_task(c, B->bp.launch_shape[c - 1]);
         for (int first = 0; first < j.w.n_walks; first += per) {
             uint32_t *t = B->hTasks + (size_t)c * 2 * B->max_tasks + 2 * nt[c]++;
             t[0] = (uint32_t)slot;
@@ -226,7 +226,7 @@ int enqueue_round(qcs_batch *B)
         BatchArgs a{B->dJobs, B->dTasks + (size_t)c * 2 * B->max_tasks, B->dCounts + 2 * c, B->dIds + (size_t)c * J,
                     B->dCounts + 2 * c + 1};
         e = cudaStreamWaitEvent(B->cs[c], B->fork, 0);
-        if (!e) e = launch_walks_batch(c, a, B->cs[c]);
+        if (!e) e = launch_walks_batch(c, B->bp.launch_shape[c - 1], a, B->cs[c]);
         if (!e) e = launch_rewalk_batch(c, a, B->cs[c]);
         if (!e) e = cudaEventRecord(B->join[c], B->cs[c]);
         if (!e) e = cudaStreamWaitEvent(s, B->join[c], 0);
@@ -361,6 +361,8 @@ int qcs_batch_create(const qcs_batch_params *pin, void *stream, qcs_batch **out)
         (uint32_t)bp.walks_per_job > kMaxWalks || bp.walks_per_job % 16 || bp.steps_per_round < 1 ||
         bp.table_log2 < 4 || bp.table_log2 > 30 || bp.queue_capacity < 16 || bp.rewalk_budget < 0)
         return QCS_ERR_ARG;
+    for (int n = 1; n <= 4; n++)
+        if (bp.launch_shape[n - 1] < 0 || bp.launch_shape[n - 1] >= launch_shapes(n)) return QCS_ERR_ARG;
     qcs_batch *B = new (std::nothrow) qcs_batch();
     if (!B) return QCS_ERR_NOMEM;
     B->bp = bp;
@@ -433,7 +435,10 @@ int qcs_batch_add(qcs_batch *B, qcs_problem *P, int *job)
         std::lock_guard<std::mutex> g(P->mu);
         if (P->running) return QCS_ERR_BUSY;
         const int sde = P->res.sde;
+        const int64_t h2d = P->res.h2d_bytes, d2h = P->res.d2h_bytes; // kept for the problem's lifetime
         memset(&P->res, 0, sizeof P->res);
+        P->res.h2d_bytes = h2d;
+        P->res.d2h_bytes = d2h;
         P->res.sde = sde;
         P->res.t_count = -1;
         P->res.status = QCS_SEARCHING;

@@ -145,6 +145,7 @@ struct WalkLaunch {
     const Pending *pend_in;
     Pending *pend_out;
     uint32_t *pend_out_n;
+    int32_t shape;       // launch shape of k_walks (host-side choice; see launch_shapes)
 };
 
 // Many jobs in one launch: per qubit count, the device list of tasks
@@ -188,11 +189,14 @@ int certify_level(::qcs_problem *P, int k, cudaStream_t s, bool *got);
 uint64_t exhaustive_points(const ::qcs_problem *P, int k); // V + W points of level k
 bool exhaustive_eligible(const ::qcs_problem *P, int k);   // within exhaustive_log2 and device memory
 
-int walks_per_task(int n); // walks (lane groups) per CTA of the walk kernels for n qubits
+int walks_per_task(int n, int shape); // walks (lane groups) per CTA of the walk kernels of that launch shape
 int lanes_per_walk(int n); // lanes of a warp that evaluate one walk (the device layouts follow it)
+int launch_shapes(int n);                    // launch shapes of the walk kernels for n qubits
+int shape_warps_of(int n, int shape);        // warps per CTA of a launch shape
+int shape_min_blocks_of(int n, int shape);   // minimum resident CTAs per SM (the register cap) of a shape
 
 // ---- kernel launchers (qcs_walk.cu); all return cudaError_t of the launch ----
-cudaError_t launch_walks_batch(int n, const BatchArgs &a, cudaStream_t s);
+cudaError_t launch_walks_batch(int n, int shape, const BatchArgs &a, cudaStream_t s);
 cudaError_t launch_rewalk_batch(int n, const BatchArgs &a, cudaStream_t s);
 cudaError_t launch_walk_step(const LevelCtx &lv, int chunk, const uint64_t *in, uint64_t *out,
                              uint8_t *is_dp, size_t count, cudaStream_t s);

@@ -60,6 +60,25 @@ namespace {
 constexpr int kWarps = QCS_WARPS;
 constexpr int kWarps3 = QCS_WARPS3;
 constexpr int kGemvUnroll = QCS_GEMV_UNROLL;
+
+// Launch shapes of the walk kernels k_walks and k_walks_batch: warps per CTA
+// and the minimum resident CTAs per SM, which caps the registers at 65536 /
+// (threads x CTAs).  Shape 0 is the default; the others are chosen at run
+// time (qcs_params.launch_shape, qcs_batch_params.launch_shape[n - 1]),
+// e.g. by the autotuner.  Every shape evaluates the same walks with the
+// same per-walk arithmetic, so the trajectories do not depend on it.
+//   n <= 2: 8 warps
+//   n = 3 : (16, 2) (8, 4) (32, 1) (16, 1)
+//   n = 4 : (16, 1) (24, 1) (32, 1)   (one CTA per SM: C^ takes 128 KB)
+__host__ __device__ constexpr int shape_count(int nq) { return nq <= 2 ? 1 : nq == 3 ? 4 : 3; }
+__host__ __device__ constexpr int shape_warps(int nq, int s)
+{
+    return nq <= 2 ? kWarps : nq == 3 ? (s == 1 ? 8 : s == 2 ? 32 : kWarps3) : (s == 1 ? 24 : s == 2 ? 32 : 16);
+}
+__host__ __device__ constexpr int shape_min_blocks(int nq, int s)
+{
+    return nq <= 2 ? 1 : nq == 3 ? (s == 1 ? 4 : s >= 2 ? 1 : QCS_MIN_BLOCKS3) : 1;
+}
 constexpr uint32_t kMaxRewalkLen = 1u << 20; // longer trails are reported as no merge
 
 __device__ __forceinline__ uint64_t smix(uint64_t z)
@@ -103,6 +122,18 @@ struct Geo {
     static constexpr size_t off_base_v = off_coef_v + sizeof(uint32_t) * COEF_WORDS;
     static constexpr size_t off_xchg_v = off_base_v + sizeof(uint64_t) * MAX_CHUNKS;
     static constexpr size_t smem_bytes_v = off_xchg_v + sizeof(uint2) * WALKS * DIM;
+};
+
+// One launch shape of the walk kernels (see shape_warps): the CTA's warps,
+// its lane groups (walks) and its shared memory, whose exchange buffers
+// grow with the walks.
+template <int NQ, int S>
+struct Shape {
+    static constexpr int WARPS = shape_warps(NQ, S);
+    static constexpr int THREADS = WARPS * 32;
+    static constexpr int WALKS = WARPS * Geo<NQ>::GROUPS;
+    static constexpr int MIN_BLOCKS = shape_min_blocks(NQ, S);
+    static constexpr size_t smem_bytes = Geo<NQ>::off_xchg + sizeof(uint2) * WALKS * Geo<NQ>::DIM;
 };
 
 // Shared-memory views of one CTA (C may point to global memory for n = 4).
@@ -583,15 +614,15 @@ __device__ __forceinline__ void walk_one(const WL &w, const Smem<NQ> &sm, int wa
     if (g.sub == 0) w.walks[walk] = st;
 }
 
-template <int NQ>
-__global__ void __launch_bounds__(Geo<NQ>::THREADS, Geo<NQ>::MIN_BLOCKS) k_walks(WalkLaunch w)
+template <int NQ, int S>
+__global__ void __launch_bounds__(Shape<NQ, S>::THREADS, Shape<NQ, S>::MIN_BLOCKS) k_walks(WalkLaunch w)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Smem<NQ> sm = stage<NQ>(w.lv, smem_raw);
     const Lanes g = thread_lanes<NQ>();
     Tally t;
-    for (int walk = blockIdx.x * Geo<NQ>::WALKS + group_in_cta<NQ>(); walk < w.n_walks;
-         walk += gridDim.x * Geo<NQ>::WALKS)
+    for (int walk = blockIdx.x * Shape<NQ, S>::WALKS + group_in_cta<NQ>(); walk < w.n_walks;
+         walk += gridDim.x * Shape<NQ, S>::WALKS)
         walk_one<NQ>(w, sm, walk, g, t);
     flush_tally(w.counters, t, g);
 }
@@ -599,10 +630,10 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS, Geo<NQ>::MIN_BLOCKS) k_walks
 // Many jobs (targets, each at its own level) in one persistent launch: the
 // CTA takes a contiguous range of tasks (job, first walk) of this qubit
 // count, restages the job's data when the job changes, and each lane group
-// walks one of the task's WALKS walks.  The job's launch record is copied to
+// walks one of the task's Shape<NQ, S>::WALKS walks.  The job's launch record is copied to
 // shared memory.
-template <int NQ>
-__global__ void __launch_bounds__(Geo<NQ>::THREADS, Geo<NQ>::MIN_BLOCKS) k_walks_batch(BatchArgs a)
+template <int NQ, int S>
+__global__ void __launch_bounds__(Shape<NQ, S>::THREADS, Shape<NQ, S>::MIN_BLOCKS) k_walks_batch(BatchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ WalkLaunch sw;
@@ -973,24 +1004,26 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_certify(CertArgs a)
 
 int g_num_sms = 0;
 
-template <int NQ>
+// resident CTAs per SM of k_walks<NQ, S> (occupancy, cached)
+template <int NQ, int S = 0>
 int blocks_per_sm()
 {
     static int cached = 0;
     if (!cached) {
-        cudaFuncSetAttribute(k_walks<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<NQ>::smem_bytes);
+        using L = Shape<NQ, S>;
+        cudaFuncSetAttribute(k_walks<NQ, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::smem_bytes);
         int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walks<NQ>, Geo<NQ>::THREADS, Geo<NQ>::smem_bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walks<NQ, S>, L::THREADS, L::smem_bytes);
         cached = b > 0 ? b : 1;
     }
     return cached;
 }
 
-template <int NQ>
+template <int NQ, int S = 0>
 unsigned grid_for(size_t units)
 {
-    const size_t cap = (size_t)num_sms() * (size_t)blocks_per_sm<NQ>();
-    size_t g = (units + Geo<NQ>::WALKS - 1) / Geo<NQ>::WALKS;
+    const size_t cap = (size_t)num_sms() * (size_t)blocks_per_sm<NQ, S>();
+    size_t g = (units + Shape<NQ, S>::WALKS - 1) / Shape<NQ, S>::WALKS;
     if (g > cap) g = cap;
     if (g == 0) g = 1;
     return (unsigned)g;
@@ -1006,39 +1039,73 @@ cudaError_t walk_step_n(const LevelCtx &lv, int chunk, const uint64_t *in, uint6
     return cudaGetLastError();
 }
 
-template <int NQ>
-cudaError_t walks_n(const WalkLaunch &w, cudaStream_t s)
+template <int NQ, int S>
+cudaError_t walks_ns(const WalkLaunch &w, cudaStream_t s)
 {
-    k_walks<NQ><<<grid_for<NQ>((size_t)w.n_walks), Geo<NQ>::THREADS, Geo<NQ>::smem_bytes, s>>>(w);
+    using L = Shape<NQ, S>;
+    k_walks<NQ, S><<<grid_for<NQ, S>((size_t)w.n_walks), L::THREADS, L::smem_bytes, s>>>(w);
     return cudaGetLastError();
 }
 
 template <int NQ>
+cudaError_t walks_n(const WalkLaunch &w, cudaStream_t s)
+{
+    switch (w.shape) {
+    case 0: return walks_ns<NQ, 0>(w, s);
+    case 1: if constexpr (shape_count(NQ) > 1) return walks_ns<NQ, 1>(w, s); break;
+    case 2: if constexpr (shape_count(NQ) > 2) return walks_ns<NQ, 2>(w, s); break;
+    case 3: if constexpr (shape_count(NQ) > 3) return walks_ns<NQ, 3>(w, s); break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+// CTAs of the persistent batch walk kernel: every SM x its resident CTAs
+template <int NQ, int S>
 int batch_grid()
 {
     static int g = 0;
     if (!g) {
-        cudaFuncSetAttribute(k_walks_batch<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<NQ>::smem_bytes);
-        cudaFuncSetAttribute(k_rewalk_batch<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Geo<NQ>::smem_bytes);
+        using L = Shape<NQ, S>;
+        cudaFuncSetAttribute(k_walks_batch<NQ, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::smem_bytes);
         int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walks_batch<NQ>, Geo<NQ>::THREADS, Geo<NQ>::smem_bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walks_batch<NQ, S>, L::THREADS, L::smem_bytes);
         g = num_sms() * (b > 0 ? b : 1);
     }
     return g;
 }
 
-template <int NQ>
-cudaError_t walks_batch_n(const BatchArgs &a, cudaStream_t s)
+template <int NQ, int S>
+cudaError_t walks_batch_ns(const BatchArgs &a, cudaStream_t s)
 {
-    k_walks_batch<NQ><<<batch_grid<NQ>(), Geo<NQ>::THREADS, Geo<NQ>::smem_bytes, s>>>(a);
+    using L = Shape<NQ, S>;
+    k_walks_batch<NQ, S><<<batch_grid<NQ, S>(), L::THREADS, L::smem_bytes, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int NQ>
+cudaError_t walks_batch_n(int shape, const BatchArgs &a, cudaStream_t s)
+{
+    switch (shape) {
+    case 0: return walks_batch_ns<NQ, 0>(a, s);
+    case 1: if constexpr (shape_count(NQ) > 1) return walks_batch_ns<NQ, 1>(a, s); break;
+    case 2: if constexpr (shape_count(NQ) > 2) return walks_batch_ns<NQ, 2>(a, s); break;
+    case 3: if constexpr (shape_count(NQ) > 3) return walks_batch_ns<NQ, 3>(a, s); break;
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int NQ>
 cudaError_t rewalk_batch_n(const BatchArgs &a, cudaStream_t s)
 {
-    k_rewalk_batch<NQ><<<batch_grid<NQ>(), Geo<NQ>::THREADS, Geo<NQ>::smem_bytes, s>>>(a);
+    static int g = 0;
+    if (!g) {
+        cudaFuncSetAttribute(k_rewalk_batch<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Geo<NQ>::smem_bytes);
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_rewalk_batch<NQ>, Geo<NQ>::THREADS, Geo<NQ>::smem_bytes);
+        g = num_sms() * (b > 0 ? b : 1);
+    }
+    k_rewalk_batch<NQ><<<g, Geo<NQ>::THREADS, Geo<NQ>::smem_bytes, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1114,7 +1181,13 @@ int num_sms()
 
 int lanes_per_walk(int n) { return n == 4 ? Geo<4>::LPW : n == 3 ? Geo<3>::LPW : n == 2 ? Geo<2>::LPW : Geo<1>::LPW; }
 
-int walks_per_task(int n) { return n == 4 ? Geo<4>::WALKS : n == 3 ? Geo<3>::WALKS : n == 2 ? Geo<2>::WALKS : Geo<1>::WALKS; }
+int launch_shapes(int n) { return n == 4 ? shape_count(4) : n == 3 ? shape_count(3) : shape_count(2); }
+
+int shape_warps_of(int n, int shape) { return shape_warps(n, shape); }
+
+int shape_min_blocks_of(int n, int shape) { return shape_min_blocks(n, shape); }
+
+int walks_per_task(int n, int shape) { return shape_warps(n, shape) * (32 / lanes_per_walk(n)); }
 
 int walk_blocks_per_sm(int n)
 {
@@ -1167,13 +1240,13 @@ cudaError_t launch_rewalk_pairs(const WalkLaunch &w, cudaStream_t s)
     }
 }
 
-cudaError_t launch_walks_batch(int n, const BatchArgs &a, cudaStream_t s)
+cudaError_t launch_walks_batch(int n, int shape, const BatchArgs &a, cudaStream_t s)
 {
     switch (n) {
-    case 1: return walks_batch_n<1>(a, s);
-    case 2: return walks_batch_n<2>(a, s);
-    case 3: return walks_batch_n<3>(a, s);
-    case 4: return walks_batch_n<4>(a, s);
+    case 1: return walks_batch_n<1>(shape, a, s);
+    case 2: return walks_batch_n<2>(shape, a, s);
+    case 3: return walks_batch_n<3>(shape, a, s);
+    case 4: return walks_batch_n<4>(shape, a, s);
     default: return cudaErrorInvalidValue;
     }
 }

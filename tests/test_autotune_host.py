@@ -73,7 +73,7 @@ def test_tuner_times_every_setting_and_keeps_the_fastest(fake):
     targets = [{"n": 2, "t": 3, "gates": [[0, 0, 0]]} for _ in range(4)]
     grid = {"walks_per_job": (512, 2048), "steps_per_round": (16, 64), "theta_min_bits": (1,),
             "queue_capacity": (4096,)}
-    best, trials = autotune.tune_batch(targets, rounds=8, grid=grid)
+    best, trials = autotune.tune_batch(targets, rounds=8, grid=grid, shapes=False)
     assert len(trials) == 4
     seen = {(t["walks_per_job"], t["steps_per_round"]) for t in trials}
     assert seen == set(itertools.product((512, 2048), (16, 64)))
@@ -84,3 +84,42 @@ def test_tuner_times_every_setting_and_keeps_the_fastest(fake):
     for t in trials:
         need = max(1, 40000 // (t["walks_per_job"] * t["steps_per_round"]))
         assert (t["found"] > 0) == (need <= 8)
+
+
+class ShapedBatch(FakeBatch):
+    """Round time depends on the launch shape of each qubit count present and
+    on the C^ layout of its jobs: n = 3 is fastest with shape 2 and int8
+    quads, n = 4 with shape 1 and 32-bit words."""
+
+    COST = {2: [1.0], 3: [3.0, 2.5, 1.0, 4.0], 4: [5.0, 4.0, 6.0]}
+
+    def add(self, p):
+        p.layout = p.params_layout
+        return super().add(p)
+
+    def round(self):
+        self.rounds += 1
+        for p in self.jobs:
+            shape = self.bp.launch_shape[p.n - 1]
+            base = self.COST[p.n][shape]
+            fast_layout = 0 if p.n == 3 else 1
+            CLOCK.t += 1e-3 * base * (1.0 if p.layout == fast_layout else 1.5)
+        return len(self.jobs)
+
+
+def test_tuner_picks_each_qubit_counts_fastest_shape_and_layout(monkeypatch):
+    class P(FakeProblem):
+        def __init__(self, n, gates, k, params):
+            super().__init__(n, gates, k, params)
+            self.params_layout = params.c_layout
+
+    monkeypatch.setattr(Q, "Batch", ShapedBatch)
+    monkeypatch.setattr(Q.Problem, "from_circuit", classmethod(lambda cls, *a: P(*a)))
+    monkeypatch.setattr(autotune.time, "perf_counter", CLOCK)
+    targets = [{"n": n, "t": 3, "gates": [[0, 0, 0]]} for n in (2, 3, 4, 3)]
+    grid = {"walks_per_job": (512,), "steps_per_round": (16,), "theta_min_bits": (1,), "queue_capacity": (4096,)}
+    best, trials = autotune.tune_batch(targets, rounds=4, grid=grid)
+    assert best["launch_shape"] == {3: 2, 4: 1} and best["c_layout"] == {3: 0, 4: 1}
+    # one host trial, then every (shape, layout) pair of n = 3 (4 x 2) and n = 4 (3 x 2)
+    assert len(trials) == 1 + 8 + 6
+    assert [s["shape"] for s in Q.launch_shapes(3)] == [0, 1, 2, 3]
