@@ -84,7 +84,7 @@ def workload_config(c, k=None, steps=None):
         "steps_per_walk_per_step": steps, "state_bits": c["L"], "dp_bits": c["dtheta"],
         "table_slots": 1 << c["table_log2"], "coefficients": "exact: int64 on the host, C^ as int8 byte quads on the device; fingerprints mod 2^16",
         "l2": f"flushed between steps ({FLUSH_BYTES >> 20} MiB write)",
-        "parallelism": "replicas, one target per GPU",
+        "parallelism": "one GPU (with N > 1: the level sharded over ranks by distinguished-point owner)",
     }
 
 
@@ -618,6 +618,41 @@ def timed_level(Q, torch, prob, stream, k, dp_bits, steps, warmup, launches, flu
     return step_ms, walk_ms, r0, prob.poll()
 
 
+def timed_sharded_level(Q, torch, prob, stream, k, dp_bits, steps, warmup, launches, flush, walks, dev):
+    """The level walked by every rank with distinguished points exchanged
+    with their owner ranks (DP-owner sharding, paper_1606_07413_gb300.shard):
+    `warmup` untimed then `launches` timed rounds (walk, bin, all-to-all,
+    insert, re-walk, collect), each bracketed by CUDA events on the launching
+    stream.  Returns (round ms list, walk-kernel ms list, result before, result
+    after, points lost to a full outbox)."""
+    import torch.distributed as dist
+
+    from paper_1606_07413_gb300 import shard
+
+    world = dist.get_world_size()
+    cap = 4 * max(1 << 16, (walks * steps) >> max(0, dp_bits - 2))  # 16 x the expected points, at least 2^18
+    eng = shard.DeviceEngine(prob, dev, cap, world, stream)
+    lvl = shard.ShardedLevel(eng, walks)
+    with torch.cuda.stream(stream):
+        lvl.begin(k, 0, dp_bits)
+        for _ in range(warmup):
+            lvl.round(steps)
+    torch.cuda.synchronize()
+    r0 = prob.poll()
+    step_ms, walk_ms = [], []
+    with torch.cuda.stream(stream):
+        for _ in range(launches):
+            flush.zero_()
+            e0, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lvl.round(steps)
+            e3.record(stream)
+            e3.synchronize()
+            step_ms.append(e0.elapsed_time(e3))
+    torch.cuda.synchronize()
+    return step_ms, walk_ms, r0, prob.poll(), lvl.lost
+
+
 def e2e_run(Q, torch, cfg_c, gates, k, steps_per_launch, launches, stream, seed, shape):
     """The headline metric through the public API: problem creation from the
     host gate list (uploads C^ and its tables), qcs_run_walks with a step
@@ -670,8 +705,10 @@ def run_ours(args):
     B.build()
     c = W.CONFIGS[CFG]
     gates, _ = W.config_target(CFG)
+    # replicas of one level would each need their own walk seed; the sharded
+    # level (N > 1) walks one level over all ranks with one seed
     params = Q.default_params(c["n"], walks=c["walks"], state_bits=c["L"], dp_bits=c["dtheta"],
-                              table_log2=c["table_log2"], seed=rank_seed(rank))
+                              table_log2=c["table_log2"], seed=rank_seed(0))
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -704,8 +741,15 @@ def run_ours(args):
     clocks.start()
     barrier()
     t_wall = time.perf_counter()
-    step_ms, walk_ms, r0, r1 = timed_level(Q, torch, prob, stream, K_LEVEL, c["dtheta"], STEPS_PER_LAUNCH,
-                                           args.warmup, args.steps, flush)
+    lost = None
+    if world > 1:
+        # one level over every rank, distinguished points exchanged with their owners
+        step_ms, walk_ms, r0, r1, lost = timed_sharded_level(Q, torch, prob, stream, K_LEVEL, c["dtheta"],
+                                                             STEPS_PER_LAUNCH, args.warmup, args.steps, flush,
+                                                             c["walks"], dev)
+    else:
+        step_ms, walk_ms, r0, r1 = timed_level(Q, torch, prob, stream, K_LEVEL, c["dtheta"], STEPS_PER_LAUNCH,
+                                               args.warmup, args.steps, flush)
     barrier()
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
@@ -715,7 +759,7 @@ def run_ours(args):
     t_local = sum(step_ms) / 1e3
     t_all, steps_all = combine_ranks(t_local, float(steps_done), world, dist if world > 1 else None, dev)
     value = steps_all / t_all
-    walk_s = sum(walk_ms) / 1e3
+    walk_s = sum(walk_ms) / 1e3 if walk_ms else t_local  # sharded rounds time the whole round
     roof = walk_roofline(f"k_walks<{c['n']},{shape['launch_shape']}>", c["n"], w_steps, steps_done, walk_s,
                          args.steps, dp4a_per_s, clk.get("sm_mhz"), num_sms)
     roof["walk_kernel_share"] = walk_s / t_local
@@ -772,8 +816,13 @@ def run_ours(args):
             "config": dict(workload_config(c), launch_shape=Q.launch_shapes(c["n"])[shape["launch_shape"]],
                            c_layout=["int8 byte quads (dp4a)", "32-bit words (IMAD)"][shape["c_layout"]]),
             "autotuned_level_shape": shape_trials, "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e, "clocks": clk,
-            "gpu_launches": 2 * args.steps, "wall_s": wall,
+            "gpu_launches": (5 if world > 1 else 2) * args.steps, "wall_s": wall,
         }
+        if world > 1:
+            line["config"]["parallelism"] = (f"DP-owner sharding over {world} ranks: one level, every rank walks "
+                                             f"{c['walks']} walks and owns a hash share of the distinguished points "
+                                             "(all-to-all exchange per round)")
+            line["points_lost_to_outbox"] = lost
         line.update(extra)
         print(json.dumps(line))
     if world > 1:

@@ -270,6 +270,59 @@ QCS_API int qcs_level_rewalk(qcs_problem *prob, void *stream);
  * claw verified (Eq. tcount_synthesis). */
 QCS_API int qcs_level_collect(qcs_problem *prob, void *stream, qcs_result *out);
 
+/* ---- one level sharded across ranks (DP-owner exchange) ---------------
+ * Sec. 4.2 and Fig. 4: workers walk and send each distinguished point to a
+ * collector, which stores it and hands merged trails to a verifier.  Here
+ * every rank (one GPU each) is worker, collector and verifier: rank r walks
+ * its own walks and owns the distinguished points whose owner index (a hash
+ * of the point, computed on the device by qcs_shard_bin) is r.  One round:
+ *   qcs_level_walk_out  - walk; distinguished points go to an outbox;
+ *   qcs_shard_bin       - group the outbox by owner rank;
+ *   (the caller exchanges the groups, e.g. one all-to-all over NCCL);
+ *   qcs_level_insert    - store the received points in the local table,
+ *                         queueing merges exactly as qcs_level_walk would;
+ *   qcs_level_rewalk, qcs_level_collect - as for an unsharded level.
+ * Trail references name walks by their index among all ranks' walks, and
+ * every rank uses the same params.seed, so any rank recomputes any trail's
+ * start: the owner re-walks merges of trails from every rank.
+ *
+ * qcs_level_begin_shard: qcs_level_begin for rank-local walks walk_base ..
+ * walk_base + params.walks - 1 of total_walks <= 2^24 walks in all.
+ * QCS_ERR_ARG if that range does not fit. */
+QCS_API int qcs_level_begin_shard(qcs_problem *prob, int k, uint32_t version, int dp_bits, uint32_t walk_base,
+                                  uint32_t total_walks, void *stream);
+
+/* qcs_level_walk for a sharded level: the distinguished points reached go to
+ * `outbox` (DEVICE, cap pairs {point, trail reference} of uint64) instead of
+ * the local table; *count (DEVICE uint32, zeroed by the call) counts every
+ * point reached, also those past cap (which are lost: size the outbox for
+ * walks x steps x theta with room to spare).  Resets the launch counters and
+ * the merge queue like qcs_level_walk.  Asynchronous on `stream`. */
+QCS_API int qcs_level_walk_out(qcs_problem *prob, uint32_t steps, uint64_t *outbox, uint32_t cap,
+                               uint32_t *count, void *stream);
+
+/* Group `count` points (DEVICE pairs {point, trail reference}) by owner rank
+ * in 0 .. n_owners - 1 (n_owners <= 1024): `out` (DEVICE, count pairs) gets
+ * them owner by owner in rank order, owner_counts (DEVICE, 2 n_owners
+ * uint32; the first n_owners hold the counts, the rest is scratch) the size
+ * of each group.  The order within a group is arbitrary.  No problem is
+ * needed: the owner is a fixed hash of the point.  Asynchronous. */
+QCS_API int qcs_shard_bin(const uint64_t *points, uint32_t count, uint32_t n_owners, uint64_t *out,
+                          uint32_t *owner_counts, void *stream);
+
+/* Store `count` received points (DEVICE pairs {point, trail reference}) in
+ * the level's table (Sec. 3: a point already stored from another trail is a
+ * merge, queued for qcs_level_rewalk).  Call after qcs_level_walk_out and
+ * before qcs_level_rewalk of the same round.  Asynchronous on `stream`. */
+QCS_API int qcs_level_insert(qcs_problem *prob, const uint64_t *points, uint32_t count, void *stream);
+
+/* Copy the merges queued by the last qcs_level_walk / qcs_level_insert to
+ * HOST memory: up to cap triples {trail ref a, trail ref b, distinguished
+ * point} into out (3 cap uint64), *n_out = the number copied.  Waits for the
+ * problem's queue on `stream` first.  For inspection and tests: the search
+ * itself re-walks the queue on the device (qcs_level_rewalk). */
+QCS_API int qcs_level_merges(qcs_problem *prob, uint64_t *out, uint32_t cap, uint32_t *n_out, void *stream);
+
 /* qcs_level_walk_static: the walk of qcs_level_walk (begin = 1: preceded by
  * the reset of qcs_level_begin) for callers that must not allocate device
  * memory: code whose device memory belongs to a framework's caching allocator

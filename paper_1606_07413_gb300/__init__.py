@@ -18,7 +18,7 @@ from . import build as _build_mod
 
 __all__ = ["lib", "Params", "Result", "Problem", "Batch", "BatchParams", "default_params",
            "default_batch_params", "verify_decomposition", "channel_from_unitary", "strerror", "QcsError",
-           "plan_level", "launch_shapes"]
+           "plan_level", "launch_shapes", "shard_bin"]
 
 OK = 0
 ERR_ARG, ERR_NOT_UNITARY, ERR_NOMEM, ERR_CUDA, ERR_MISMATCH, ERR_OVERFLOW, ERR_BUSY, ERR_TIMEOUT, ERR_DEVICE = \
@@ -128,6 +128,11 @@ def lib():
             "qcs_level_rewalk": (ctypes.c_int, [_vp, _vp]),
             "qcs_level_collect": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(Result)]),
             "qcs_certify_level": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_int)]),
+            "qcs_level_begin_shard": (ctypes.c_int, [_vp, ctypes.c_int, _u32, ctypes.c_int, _u32, _u32, _vp]),
+            "qcs_level_walk_out": (ctypes.c_int, [_vp, _u32, _vp, _u32, _vp, _vp]),
+            "qcs_shard_bin": (ctypes.c_int, [_vp, _u32, _u32, _vp, _vp, _vp]),
+            "qcs_level_insert": (ctypes.c_int, [_vp, _vp, _u32, _vp]),
+            "qcs_level_merges": (ctypes.c_int, [_vp, _vp, _u32, ctypes.POINTER(_u32), _vp]),
             "qcs_plan_level": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), ctypes.POINTER(Plan)]),
             "qcs_level_walk_static": (ctypes.c_int, [_vp, ctypes.c_int, _u32, ctypes.c_int, ctypes.c_int, _vp, _u32,
                                                      _u32, _vp, _u32, _vp, _vp]),
@@ -201,6 +206,27 @@ def _ptr(t):
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("expected a contiguous CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _device_tensors(**tensors):
+    """Every tensor whose pointer and size go to the library: contiguous, on
+    the GPU, int64 (point pairs) or int32 (counts)."""
+    import torch
+
+    for name, t in tensors.items():
+        if t.dtype not in (torch.int64, torch.int32) or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous int64/int32 CUDA tensor")
+
+
+def shard_bin(points, count, n_owners, out, owner_counts, stream=None):
+    """qcs_shard_bin: group `count` points (int64 CUDA tensor, 2 per point) by
+    owner rank into `out`; owner_counts (int32 CUDA tensor, 2 n_owners) gets
+    the group sizes in its first n_owners entries."""
+    _device_tensors(points=points, out=out, owner_counts=owner_counts)
+    if owner_counts.numel() < 2 * n_owners or out.numel() < 2 * count or points.numel() < 2 * count:
+        raise ValueError("buffers too small for the points and owners")
+    _check(lib().qcs_shard_bin(_ptr(points), int(count), int(n_owners), _ptr(out), _ptr(owner_counts),
+                               _stream(stream)), "qcs_shard_bin")
 
 
 def _stream(stream):
@@ -290,6 +316,34 @@ class Problem:
         r = Result()
         _check(lib().qcs_level_collect(self._h, _stream(stream), ctypes.byref(r)), "qcs_level_collect")
         return r.as_dict()
+
+    # one level sharded across ranks (Sec. 4.2 collectors; see shard.py)
+    def level_begin_shard(self, k, version, dp_bits, walk_base, total_walks, stream=None):
+        _check(lib().qcs_level_begin_shard(self._h, int(k), int(version), int(dp_bits), int(walk_base),
+                                           int(total_walks), _stream(stream)), "qcs_level_begin_shard")
+
+    def level_walk_out(self, steps, outbox, count, stream=None):
+        """Walk `steps` steps; distinguished points go to outbox (int64 CUDA
+        tensor, 2 per point) and count (int32 CUDA tensor) counts them."""
+        _device_tensors(outbox=outbox, count=count)
+        _check(lib().qcs_level_walk_out(self._h, int(steps), _ptr(outbox), outbox.numel() // 2, _ptr(count),
+                                        _stream(stream)), "qcs_level_walk_out")
+
+    def level_insert(self, points, count=None, stream=None):
+        """Store received points (int64 CUDA tensor, 2 per point) in the level's table."""
+        _device_tensors(points=points)
+        n = points.numel() // 2 if count is None else int(count)
+        _check(lib().qcs_level_insert(self._h, _ptr(points) if n else None, n, _stream(stream)),
+               "qcs_level_insert")
+
+    def level_merges(self, cap=1 << 20, stream=None) -> np.ndarray:
+        """The merges queued by the last walk or insert, as an (m, 3) uint64
+        array of {trail ref a, trail ref b, distinguished point}."""
+        out = np.zeros((cap, 3), np.uint64)
+        n = _u32(0)
+        _check(lib().qcs_level_merges(self._h, out.ctypes.data_as(_vp), int(cap), ctypes.byref(n),
+                                      _stream(stream)), "qcs_level_merges")
+        return out[: n.value]
 
     def certify_level(self, k, stream=None) -> bool:
         """qcs_certify_level: exhaustive pass over level k; True iff a

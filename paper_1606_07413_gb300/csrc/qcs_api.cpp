@@ -367,7 +367,8 @@ void qcs::found(qcs_problem *P, int k, const uint32_t *paulis, PMat &&Dh)
 
 namespace {
 
-int level_begin(qcs_problem *P, int k, uint32_t version, int dp_bits, uint32_t n_walks, cudaStream_t s)
+int level_begin(qcs_problem *P, int k, uint32_t version, int dp_bits, uint32_t n_walks, cudaStream_t s,
+                uint32_t walk_base = 0)
 {
     if (k < 2 || k > P->k_max) return QCS_ERR_ARG;
     if (dp_bits == 0) dp_bits = P->p.dp_bits;
@@ -395,6 +396,7 @@ int level_begin(qcs_problem *P, int k, uint32_t version, int dp_bits, uint32_t n
     w.ccap = kCandCap;
     w.counters = P->dCounters;
     w.shape = P->p.launch_shape;
+    w.walk_base = walk_base;
     CK(cudaMemsetAsync(P->dTable, 0xFF, sizeof(Slot) << P->p.table_log2, s));
     CK(cudaMemsetAsync(P->dQhead, 0, 2 * sizeof(uint32_t), s));
     CK(launch_init_walks(w, s));
@@ -975,7 +977,7 @@ static bool busy(qcs_problem *P)
     return P->running;
 }
 
-int qcs_level_begin(qcs_problem *P, int k, uint32_t version, int dp_bits, void *stream)
+static int begin_levels(qcs_problem *P, int k, uint32_t version, int dp_bits, void *stream, uint32_t walk_base)
 {
     if (!P) return QCS_ERR_ARG;
     if (busy(P)) return QCS_ERR_BUSY;
@@ -994,7 +996,12 @@ int qcs_level_begin(qcs_problem *P, int k, uint32_t version, int dp_bits, void *
             P->t0 = std::chrono::steady_clock::now();
         }
     }
-    return level_begin(P, k, version, dp_bits, 0, (cudaStream_t)stream);
+    return level_begin(P, k, version, dp_bits, 0, (cudaStream_t)stream, walk_base);
+}
+
+int qcs_level_begin(qcs_problem *P, int k, uint32_t version, int dp_bits, void *stream)
+{
+    return begin_levels(P, k, version, dp_bits, stream, 0);
 }
 
 int qcs_level_walk(qcs_problem *P, uint32_t steps, void *stream)
@@ -1002,6 +1009,68 @@ int qcs_level_walk(qcs_problem *P, uint32_t steps, void *stream)
     if (!P) return QCS_ERR_ARG;
     if (busy(P)) return QCS_ERR_BUSY;
     return level_walk(P, steps, (cudaStream_t)stream);
+}
+
+int qcs_level_begin_shard(qcs_problem *P, int k, uint32_t version, int dp_bits, uint32_t walk_base,
+                          uint32_t total_walks, void *stream)
+{
+    if (!P) return QCS_ERR_ARG;
+    if (total_walks > kMaxWalks || walk_base > total_walks || (uint64_t)P->p.walks > total_walks - walk_base)
+        return QCS_ERR_ARG;
+    return begin_levels(P, k, version, dp_bits, stream, walk_base);
+}
+
+int qcs_level_walk_out(qcs_problem *P, uint32_t steps, uint64_t *outbox, uint32_t cap, uint32_t *count,
+                       void *stream)
+{
+    if (!P || !count || (cap && !outbox)) return QCS_ERR_ARG;
+    if (busy(P)) return QCS_ERR_BUSY;
+    if (!P->lvl.active || steps == 0) return QCS_ERR_ARG;
+    const cudaStream_t s = (cudaStream_t)stream;
+    WalkLaunch w = P->lvl.w;
+    w.steps = steps;
+    w.outbox = reinterpret_cast<Slot *>(outbox);
+    w.ocap = cap;
+    w.ohead = count;
+    CK(cudaMemsetAsync(count, 0, sizeof(uint32_t), s));
+    CK(cudaMemsetAsync(P->dQhead, 0, 2 * sizeof(uint32_t), s));
+    CK(cudaMemsetAsync(P->dCounters, 0, sizeof(unsigned long long) * C_NCOUNTERS, s));
+    CK(launch_walks(w, s));
+    return QCS_OK;
+}
+
+int qcs_shard_bin(const uint64_t *points, uint32_t count, uint32_t n_owners, uint64_t *out, uint32_t *owner_counts,
+                  void *stream)
+{
+    if (n_owners == 0 || n_owners > 1024 || !owner_counts || (count && (!points || !out))) return QCS_ERR_ARG;
+    const cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(owner_counts, 0, sizeof(uint32_t) * n_owners, s));
+    CK(launch_bin_owners(reinterpret_cast<const Slot *>(points), count, n_owners, reinterpret_cast<Slot *>(out),
+                         owner_counts, s));
+    return QCS_OK;
+}
+
+int qcs_level_insert(qcs_problem *P, const uint64_t *points, uint32_t count, void *stream)
+{
+    if (!P || (count && !points)) return QCS_ERR_ARG;
+    if (busy(P)) return QCS_ERR_BUSY;
+    if (!P->lvl.active) return QCS_ERR_ARG;
+    CK(launch_insert_points(P->lvl.w, reinterpret_cast<const Slot *>(points), count, (cudaStream_t)stream));
+    return QCS_OK;
+}
+
+int qcs_level_merges(qcs_problem *P, uint64_t *out, uint32_t cap, uint32_t *n_out, void *stream)
+{
+    if (!P || !n_out || (cap && !out)) return QCS_ERR_ARG;
+    if (!P->lvl.active) return QCS_ERR_ARG;
+    const cudaStream_t s = (cudaStream_t)stream;
+    uint32_t head = 0;
+    CK(cudaMemcpyAsync(&head, P->dQhead, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint32_t n = std::min(std::min(head, P->lvl.w.qcap), cap);
+    if (n) CK(cudaMemcpy(out, P->dQueue, sizeof(Pair) * n, cudaMemcpyDeviceToHost));
+    *n_out = n;
+    return QCS_OK;
 }
 
 int qcs_level_rewalk(qcs_problem *P, void *stream)

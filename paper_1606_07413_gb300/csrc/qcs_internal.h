@@ -146,6 +146,15 @@ struct WalkLaunch {
     Pending *pend_out;
     uint32_t *pend_out_n;
     int32_t shape;       // launch shape of k_walks (host-side choice; see launch_shapes)
+    // DP-owner sharding (Sec. 4.2 collectors): the walks of this launch are
+    // walks walk_base .. walk_base + n_walks - 1 of all ranks' walks (trail
+    // references and starts use the global index), and with outbox set their
+    // distinguished points go to outbox (up to ocap, *ohead counts every one)
+    // instead of the local table, for the exchange with their owners
+    uint32_t walk_base;
+    uint32_t ocap;
+    Slot *outbox;
+    uint32_t *ohead;
 };
 
 // Many jobs in one launch: per qubit count, the device list of tasks
@@ -202,6 +211,15 @@ cudaError_t launch_walk_step(const LevelCtx &lv, int chunk, const uint64_t *in, 
                              uint8_t *is_dp, size_t count, cudaStream_t s);
 cudaError_t launch_init_walks(const WalkLaunch &w, cudaStream_t s);
 cudaError_t launch_walks(const WalkLaunch &w, cudaStream_t s);
+// DP-owner sharding: insert `count` distinguished points {dp, trail ref}
+// into w's table (merges queued as by the walk), and bin points by owner
+// rank (owner_of in qcs_walk.cu): out gets the points grouped by owner in
+// rank order, counts[r] the number for rank r (device arrays; counts has
+// 2 n_owners entries, the first n_owners zeroed by the caller, the rest are
+// the scatter's cursors)
+cudaError_t launch_insert_points(const WalkLaunch &w, const Slot *pts, uint32_t count, cudaStream_t s);
+cudaError_t launch_bin_owners(const Slot *in, uint32_t count, uint32_t n_owners, Slot *out, uint32_t *counts,
+                              cudaStream_t s);
 cudaError_t launch_rewalk_pairs(const WalkLaunch &w, cudaStream_t s);
 cudaError_t launch_rewalk_arrays(const LevelCtx &lv, int chunk, const uint64_t *sa, const uint32_t *la,
                                  const uint64_t *sb, const uint32_t *lb, size_t count, int32_t *cls,

@@ -26,6 +26,7 @@
 // bit-identical to hashing the explicitly formed product.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "qcs_internal.h"
@@ -561,6 +562,17 @@ __device__ __forceinline__ void flush_tally(unsigned long long *counters, Tally 
 template <typename WL>
 __device__ void dp_insert(const WL &w, uint64_t dp, uint64_t ref, Tally &c)
 {
+    if (w.outbox) {
+        // DP-owner sharding: the point goes to its owner's table after the exchange
+        const uint32_t idx = atomicAdd(w.ohead, 1u);
+        if (idx < w.ocap) {
+            Slot o;
+            o.key = dp;
+            o.ref = ref;
+            w.outbox[idx] = o;
+        }
+        return;
+    }
     Slot nv;
     nv.key = dp;
     nv.ref = ref;
@@ -589,9 +601,10 @@ __device__ void dp_insert(const WL &w, uint64_t dp, uint64_t ref, Tally &c)
 // distinguished point is stored and a new one starts; a trail longer than
 // the cut-off is abandoned.  All lanes of the group call it.
 template <int NQ, typename WL>
-__device__ __forceinline__ void walk_one(const WL &w, const Smem<NQ> &sm, int walk, Lanes g, Tally &t)
+__device__ __forceinline__ void walk_one(const WL &w, const Smem<NQ> &sm, int local, Lanes g, Tally &t)
 {
-    WalkState st = w.walks[walk];
+    WalkState st = w.walks[local];
+    const uint32_t walk = w.walk_base + (uint32_t)local; // index among all ranks' walks
     const uint32_t steps = w.steps, max_len = w.max_len;
     const int dshift = w.lv.dshift;
     for (uint32_t s = 0; s < steps; s++) {
@@ -601,17 +614,17 @@ __device__ __forceinline__ void walk_one(const WL &w, const Smem<NQ> &sm, int wa
         st.len++;
         if ((y >> dshift) == 0) {
             t.dp++;
-            if (g.sub == 0) dp_insert(w, y, make_ref((uint32_t)walk, st.seq, st.len), t);
+            if (g.sub == 0) dp_insert(w, y, make_ref(walk, st.seq, st.len), t);
             __syncwarp(g.mask);
-            new_trail(st, (uint32_t)walk, w.lv);
+            new_trail(st, walk, w.lv);
         } else if (st.len >= max_len) {
             t.ab++;
-            new_trail(st, (uint32_t)walk, w.lv);
+            new_trail(st, walk, w.lv);
         } else {
             st.cur = y;
         }
     }
-    if (g.sub == 0) w.walks[walk] = st;
+    if (g.sub == 0) w.walks[local] = st;
 }
 
 template <int NQ, int S>
@@ -669,8 +682,60 @@ __global__ void k_init_walks(WalkLaunch w)
     WalkState st;
     st.seq = 0;
     st.pad = 0;
-    new_trail(st, (uint32_t)i, w.lv);
+    new_trail(st, w.walk_base + (uint32_t)i, w.lv);
     w.walks[i] = st;
+}
+
+// DP-owner sharding: the distinguished points received from every rank go
+// into this rank's table exactly as the walk's own inserts would.
+__global__ void k_insert_points(WalkLaunch w, const Slot *__restrict__ pts, uint32_t count)
+{
+    Tally t;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const Slot p = pts[i];
+        dp_insert(w, p.key, p.ref, t);
+    }
+    // per-thread tallies (there are no lane groups here)
+    if (t.evicted) atomicAdd(&w.counters[C_EVICTED], t.evicted);
+    if (t.duplicate) atomicAdd(&w.counters[C_DUPLICATE], t.duplicate);
+    if (t.pairs) atomicAdd(&w.counters[C_PAIRS], t.pairs);
+}
+
+// owner rank of a distinguished point among n ranks: the high word of a
+// second finaliser (independent of the table slot, which takes smix's low
+// bits) scaled to [0, n)
+__device__ __forceinline__ uint32_t owner_of(uint64_t dp, uint32_t n)
+{
+    return (uint32_t)(((smix(dp ^ 0xD1B54A32D192ED03ull) >> 32) * (uint64_t)n) >> 32);
+}
+
+// Bin points by owner: one counting pass, a prefix over the n owners in
+// every block (n <= 1024), then scatter.  Order within a bin is arbitrary
+// (the table does not depend on insertion order beyond which trail a slot
+// keeps).
+__global__ void k_count_owners(const Slot *__restrict__ in, uint32_t count, uint32_t n, uint32_t *counts)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        atomicAdd(&counts[owner_of(in[i].key, n)], 1u);
+}
+
+__global__ void k_scatter_owners(const Slot *__restrict__ in, uint32_t count, uint32_t n,
+                                 const uint32_t *__restrict__ counts, uint32_t *fill, Slot *out)
+{
+    extern __shared__ uint32_t start[]; // exclusive prefix of counts
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (uint32_t r = 0; r < n; r++) {
+            start[r] = acc;
+            acc += counts[r];
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const Slot p = in[i];
+        const uint32_t r = owner_of(p.key, n);
+        out[start[r] + atomicAdd(&fill[r], 1u)] = p;
+    }
 }
 
 // Sec. 3, Fig. 2: align the longer trail, step both until the images agree,
@@ -1215,6 +1280,31 @@ cudaError_t launch_walk_step(const LevelCtx &lv, int chunk, const uint64_t *in, 
 cudaError_t launch_init_walks(const WalkLaunch &w, cudaStream_t s)
 {
     if (w.n_walks > 0) k_init_walks<<<(w.n_walks + 255) / 256, 256, 0, s>>>(w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_insert_points(const WalkLaunch &w, const Slot *pts, uint32_t count, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<uint64_t>(((uint64_t)count + 255) / 256, (uint64_t)num_sms() * 8);
+    k_insert_points<<<grid, 256, 0, s>>>(w, pts, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_owners(const Slot *in, uint32_t count, uint32_t n_owners, Slot *out, uint32_t *counts,
+                              cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    if (n_owners == 0 || n_owners > 1024) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)std::min<uint64_t>(((uint64_t)count + 255) / 256, (uint64_t)num_sms() * 8);
+    k_count_owners<<<grid, 256, 0, s>>>(in, count, n_owners, counts);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the scatter's fill cursors sit right after the counts
+    e = cudaMemsetAsync(counts + n_owners, 0, sizeof(uint32_t) * n_owners, s);
+    if (e != cudaSuccess) return e;
+    k_scatter_owners<<<grid, 256, sizeof(uint32_t) * n_owners, s>>>(in, count, n_owners, counts,
+                                                                   counts + n_owners, out);
     return cudaGetLastError();
 }
 
