@@ -40,6 +40,10 @@ sys.path.insert(0, ROOT)
 CFG = 3
 K_LEVEL = 7
 STEPS_PER_LAUNCH = 64
+# evaluations of f one merge's re-walk may take per bench step; longer
+# re-walks continue in the next step (the level walk's pipeline), so a step
+# is not held up by the one longest trail pair
+REWALK_BUDGET = 1024
 FLUSH_BYTES = 256 << 20
 LEVELS = {1: 3, 2: 5, 3: 7}  # the level each configuration's construction T-count puts its claw on
 
@@ -74,14 +78,16 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(c, k=None, steps=None):
+def workload_config(c, k=None, steps=None, rewalk_budget=None):
     k = K_LEVEL if k is None else k
+    rewalk_budget = REWALK_BUDGET if rewalk_budget is None else rewalk_budget
     steps = STEPS_PER_LAUNCH if steps is None else steps
     return {
         "workload": f"n{c['n']}_t{c['t']}_level{k}_walks{c['walks']}_L{c['L']}_theta2^-{c['dtheta']}",
         "n_qubits": c["n"], "level_k": k, "chunks": 4 ** c["n"] - 1, "walks": c["walks"],
         "level_points": 2 * (4 ** c["n"] - 1) ** (k // 2) * ((4 ** c["n"] - 1) if k & 1 else 1),
         "steps_per_walk_per_step": steps, "state_bits": c["L"], "dp_bits": c["dtheta"],
+        "rewalk_budget_per_step": rewalk_budget or "none (every merge re-walked in its own step)",
         "table_slots": 1 << c["table_log2"], "coefficients": "exact: int64 on the host, C^ as int8 byte quads on the device; fingerprints mod 2^16",
         "l2": f"flushed between steps ({FLUSH_BYTES >> 20} MiB write)",
         "parallelism": "one GPU (with N > 1: the level sharded over ranks by distinguished-point owner)",
@@ -665,7 +671,7 @@ def e2e_run(Q, torch, cfg_c, gates, k, steps_per_launch, launches, stream, seed,
                           table_log2=c["table_log2"], theta_policy=0, version_factor=0,
                           steps_per_launch=steps_per_launch, budget_factor=1 << 20, stop_on_claw=0,
                           exhaustive_log2=0, seed=seed, launch_shape=shape["launch_shape"],
-                          c_layout=shape["c_layout"])
+                          c_layout=shape["c_layout"], rewalk_budget=REWALK_BUDGET)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     pb = Q.Problem.from_circuit(c["n"], gates, k, pe)
@@ -708,7 +714,7 @@ def run_ours(args):
     # replicas of one level would each need their own walk seed; the sharded
     # level (N > 1) walks one level over all ranks with one seed
     params = Q.default_params(c["n"], walks=c["walks"], state_bits=c["L"], dp_bits=c["dtheta"],
-                              table_log2=c["table_log2"], seed=rank_seed(0))
+                              table_log2=c["table_log2"], seed=rank_seed(0), rewalk_budget=REWALK_BUDGET)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -785,7 +791,7 @@ def run_ours(args):
             prob2.close()
             st2 = q1["steps"] - q0["steps"]
             extra["n3_level5"] = {
-                "config": workload_config(c2, 5, 512), "walk_steps_per_s": st2 / (sum(s2) / 1e3),
+                "config": workload_config(c2, 5, 512, 0), "walk_steps_per_s": st2 / (sum(s2) / 1e3),
                 "ms_per_step": sum(s2) / len(s2),
                 "roofline": walk_roofline("k_walks<3,0>", 3, q1["w_steps"] - q0["w_steps"], st2, sum(w2) / 1e3, 20,
                                           dp4a_per_s, clk.get("sm_mhz"), num_sms)}

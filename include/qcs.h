@@ -118,6 +118,12 @@ typedef struct qcs_params {
     int32_t c_layout;         /* device layout of C^ for the W side's contraction (n >= 3): 0 = signed
                                  byte quads when every entry fits in int8 (dp4a), else 32-bit words;
                                  1 = 32-bit words always (IMAD).  Results do not depend on it */
+    int32_t rewalk_budget;    /* evaluations of f one re-walk of a merge (Sec. 3, Fig. 2) may take per
+                                 launch; an unfinished re-walk is carried to the next launch of the same
+                                 level and function version (up to queue_capacity of them; more are
+                                 dropped and counted in queue_overflow).  0: no bound, every merge is
+                                 re-walked to its end in its own launch */
+    int32_t reserved;
     uint64_t seed;            /* seed of trail starting points */
 } qcs_params;
 
@@ -149,6 +155,8 @@ typedef struct qcs_result {
     int64_t d2h_bytes;        /* bytes copied device to host for this problem: per launch the
                                  counters and queue heads, plus the claw candidates and exhaustive-pass
                                  matches actually queued (batch jobs: 0, the batch copies per round) */
+    int64_t rewalk_carried;   /* re-walks carried into the next launch (params.rewalk_budget > 0):
+                                 merges queued so far = the re-walk classes + this + queue_overflow */
 } qcs_result;
 
 typedef struct qcs_problem qcs_problem;

@@ -36,7 +36,8 @@ class Params(ctypes.Structure):
                 ("budget_factor", ctypes.c_int32), ("theta_policy", ctypes.c_int32),
                 ("version_factor", ctypes.c_int32), ("stop_on_claw", ctypes.c_int32), ("theta_min_bits", ctypes.c_int32),
                 ("exhaustive_log2", ctypes.c_int32), ("exhaustive_first", ctypes.c_int32),
-                ("launch_shape", ctypes.c_int32), ("c_layout", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("launch_shape", ctypes.c_int32), ("c_layout", ctypes.c_int32),
+                ("rewalk_budget", ctypes.c_int32), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -52,7 +53,7 @@ class Result(ctypes.Structure):
                 ("queue_overflow", ctypes.c_int64), ("launches", ctypes.c_int64), ("seconds", ctypes.c_double),
                 ("w_steps", ctypes.c_int64), ("rewalk_steps", ctypes.c_int64),
                 ("certified_levels", ctypes.c_int64), ("cert_points", ctypes.c_int64),
-                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64), ("rewalk_carried", ctypes.c_int64)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}

@@ -271,20 +271,22 @@ int ensure_search_buffers(qcs_problem *P)
     const size_t slots = (size_t)1 << P->p.table_log2;
     CK(cudaMalloc(&P->dTable, sizeof(Slot) * slots));
     CK(cudaMalloc(&P->dQueue, sizeof(Pair) * (size_t)P->p.queue_capacity));
-    CK(cudaMalloc(&P->dQhead, 2 * sizeof(uint32_t)));
+    CK(cudaMalloc(&P->dQhead, 3 * sizeof(uint32_t)));
+    if (P->p.rewalk_budget > 0)
+        for (int i = 0; i < 2; i++) CK(cudaMalloc(&P->dPend[i], sizeof(Pending) * (size_t)P->p.queue_capacity));
     CK(cudaMalloc(&P->dCands, sizeof(Cand) * kCandCap));
     CK(cudaMalloc(&P->dWalks, sizeof(WalkState) * (size_t)P->p.walks));
     CK(cudaMalloc(&P->dCounters, sizeof(unsigned long long) * C_NCOUNTERS));
     CK(cudaMallocHost(&P->hCounters, sizeof(unsigned long long) * C_NCOUNTERS));
     CK(cudaMallocHost(&P->hCands, sizeof(Cand) * kCandCap));
-    CK(cudaMallocHost(&P->hQhead, 2 * sizeof(uint32_t)));
+    CK(cudaMallocHost(&P->hQhead, 3 * sizeof(uint32_t)));
     return QCS_OK;
 }
 
 void free_problem_memory(qcs_problem *P)
 {
     cudaFree(P->dC32); cudaFree(P->dCq); cudaFree(P->dU); cudaFree(P->dCoef); cudaFree(P->dTable); cudaFree(P->dQueue); cudaFree(P->dQhead);
-    cudaFree(P->dCands); cudaFree(P->dWalks); cudaFree(P->dCounters);
+    cudaFree(P->dCands); cudaFree(P->dWalks); cudaFree(P->dCounters); cudaFree(P->dPend[0]); cudaFree(P->dPend[1]);
     cudaFreeHost(P->hCounters); cudaFreeHost(P->hCands); cudaFreeHost(P->hQhead);
 }
 
@@ -397,6 +399,8 @@ int level_begin(qcs_problem *P, int k, uint32_t version, int dp_bits, uint32_t n
     w.counters = P->dCounters;
     w.shape = P->p.launch_shape;
     w.walk_base = walk_base;
+    L.pp = 0;
+    L.pend_n = 0; // a new level or function version drops carried re-walks
     CK(cudaMemsetAsync(P->dTable, 0xFF, sizeof(Slot) << P->p.table_log2, s));
     CK(cudaMemsetAsync(P->dQhead, 0, 2 * sizeof(uint32_t), s));
     CK(launch_init_walks(w, s));
@@ -420,11 +424,23 @@ int level_walk(qcs_problem *P, uint32_t steps, cudaStream_t s)
 int level_rewalk(qcs_problem *P, cudaStream_t s)
 {
     if (!P->lvl.active) return QCS_ERR_ARG;
-    const WalkLaunch &w = P->lvl.w;
+    auto &L = P->lvl;
+    WalkLaunch w = L.w;
+    if (P->p.rewalk_budget > 0) {
+        // the re-walks carried from the previous launch first, then this
+        // launch's merges; unfinished ones go to the other buffer
+        w.rewalk_budget = (uint32_t)P->p.rewalk_budget;
+        w.pend_in = P->dPend[L.pp];
+        w.pend_in_n = L.pend_n;
+        w.pend_out = P->dPend[L.pp ^ 1];
+        w.pend_out_n = P->dQhead + 2;
+        w.pend_cap = (uint32_t)P->p.queue_capacity;
+        CK(cudaMemsetAsync(P->dQhead + 2, 0, sizeof(uint32_t), s));
+    }
     CK(launch_rewalk_pairs(w, s));
     CK(cudaMemcpyAsync(P->hCounters, P->dCounters, sizeof(unsigned long long) * C_NCOUNTERS,
                        cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(P->hQhead, P->dQhead, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(P->hQhead, P->dQhead, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     return QCS_OK;
 }
 
@@ -439,7 +455,16 @@ int level_collect(qcs_problem *P, cudaStream_t s, bool *got, uint64_t *steps)
     const unsigned long long *c = P->hCounters;
     const uint32_t npairs = std::min(P->hQhead[0], L.w.qcap);
     const uint32_t ncand = std::min(P->hQhead[1], kCandCap);
-    int64_t d2h = (int64_t)(sizeof(unsigned long long) * C_NCOUNTERS + 2 * sizeof(uint32_t));
+    int64_t d2h = (int64_t)(sizeof(unsigned long long) * C_NCOUNTERS + 3 * sizeof(uint32_t));
+    int64_t carried_lost = 0;
+    if (P->p.rewalk_budget > 0) {
+        // re-walks carried into the next launch (those past the buffer are lost)
+        auto &Lm = P->lvl;
+        const uint32_t cap = (uint32_t)P->p.queue_capacity;
+        carried_lost = P->hQhead[2] > cap ? (int64_t)(P->hQhead[2] - cap) : 0;
+        Lm.pend_n = std::min(P->hQhead[2], cap);
+        Lm.pp ^= 1;
+    }
     if (ncand > 0) {
         // read back only the candidates the re-walk queued
         CK(cudaMemcpyAsync(P->hCands, P->dCands, sizeof(Cand) * ncand, cudaMemcpyDeviceToHost, s));
@@ -476,7 +501,8 @@ int level_collect(qcs_problem *P, cudaStream_t s, bool *got, uint64_t *steps)
         R.abandoned += (int64_t)c[C_ABANDONED];
         R.dropped += (int64_t)c[C_EVICTED];
         R.merges += (int64_t)npairs;
-        R.queue_overflow += (int64_t)(c[C_PAIRS] - npairs);
+        R.queue_overflow += (int64_t)(c[C_PAIRS] - npairs) + carried_lost;
+        R.rewalk_carried = (int64_t)P->lvl.pend_n;
         R.robin_hood += (int64_t)c[C_CLS0 + QCS_MERGE_ROBIN_HOOD];
         R.trivial += (int64_t)c[C_CLS0 + QCS_MERGE_TRIVIAL];
         R.same_side += (int64_t)c[C_CLS0 + QCS_MERGE_SAME_SIDE];

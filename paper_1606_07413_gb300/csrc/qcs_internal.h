@@ -297,14 +297,15 @@ struct qcs_problem {
     uint32_t *dCoef = nullptr;
     qcs::Slot *dTable = nullptr;
     qcs::Pair *dQueue = nullptr;
-    uint32_t *dQhead = nullptr; // [0] queued merges, [1] claw candidates
+    uint32_t *dQhead = nullptr; // [0] queued merges, [1] claw candidates, [2] carried re-walks
+    qcs::Pending *dPend[2] = {nullptr, nullptr}; // carried re-walks (params.rewalk_budget > 0)
     qcs::Cand *dCands = nullptr;
     qcs::WalkState *dWalks = nullptr;
     unsigned long long *dCounters = nullptr;
     // pinned host mirrors
     unsigned long long *hCounters = nullptr;
     qcs::Cand *hCands = nullptr;
-    uint32_t *hQhead = nullptr;
+    uint32_t *hQhead = nullptr; // mirrors dQhead
     // search state
     std::thread driver;
     std::mutex mu;
@@ -320,5 +321,7 @@ struct qcs_problem {
         bool active = false;
         int k = 0, h = 0, dp_bits = 0;
         qcs::WalkLaunch w{};
+        int pp = 0;          // dPend[pp] holds the re-walks carried into the next launch
+        uint32_t pend_n = 0; // how many
     } lvl;
 };

@@ -63,7 +63,7 @@ def test_reported_copies_match_the_uploads_and_reads():
     device) uploads C^ as 64 x 64 (a, b) words, the 64 fingerprint weights,
     the 64 x 2R rotation masks (R = 64 / 32 lanes) and, with every entry in
     int8, the byte quads; each walk launch reads back the 15 counters and
-    two queue heads, plus 24 bytes per claw candidate."""
+    three queue heads, plus 24 bytes per claw candidate."""
     from paper_1606_07413_gb300 import build
 
     build.build()
@@ -83,7 +83,40 @@ def test_reported_copies_match_the_uploads_and_reads():
             r = prob.level_collect()
         checked = r["claws"] + r["false_hash"]  # the host stops checking a launch's list at its first claw
         assert r["h2d_bytes"] == want_up
-        read_cands = r["d2h_bytes"] - launches * (15 * 8 + 2 * 4)
+        read_cands = r["d2h_bytes"] - launches * (15 * 8 + 3 * 4)
         assert read_cands % 24 == 0 and read_cands // 24 >= checked
     with Q.Problem.from_circuit(3, gates, 5, Q.default_params(3, walks=4096, c_layout=1)) as wide:
         assert wide.poll()["h2d_bytes"] == want_up - D * D // 2 * 4  # no byte quads
+
+
+def test_carried_rewalks_account_for_every_merge():
+    """With a per-launch re-walk budget (params.rewalk_budget), a merge whose
+    re-walk (Sec. 3, Fig. 2) does not finish in its launch resumes in the
+    next one: after every launch, the merges queued so far are exactly the
+    ones classified plus the ones carried (level 4 of the n = 3 seeded
+    target has no claw, so every candidate is checked and counted), and the
+    walk itself is the same as without the budget."""
+    from paper_1606_07413_gb300 import build
+
+    build.build()
+    gates, _ = W.config_target(2)
+    runs = {}
+    for budget in (0, 4):
+        p = Q.default_params(3, walks=4096, rewalk_budget=budget)
+        with Q.Problem.from_circuit(3, gates, 5, p) as prob:
+            prob.level_begin(4, 2, 4)
+            seen_carried = 0
+            hist = []
+            for _ in range(5):
+                prob.level_walk(48)
+                prob.level_rewalk()
+                r = prob.level_collect()
+                classified = r["robin_hood"] + r["trivial"] + r["same_side"] + r["claws"] + r["false_hash"] + \
+                    r["no_merge"]
+                assert r["queue_overflow"] == 0 and r["claws"] == 0
+                assert classified + r["rewalk_carried"] == r["merges"], (budget, r)
+                seen_carried = max(seen_carried, r["rewalk_carried"])
+                hist.append((r["steps"], r["dps"], r["merges"]))
+            runs[budget] = (hist, seen_carried)
+    assert runs[0][1] == 0 and runs[4][1] > 0
+    assert runs[0][0] == runs[4][0]  # same walks, distinguished points and merges
