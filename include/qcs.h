@@ -374,9 +374,11 @@ QCS_API int qcs_level_walk_static(qcs_problem *prob, int k, uint32_t version, in
  * in one persistent walk kernel and one persistent re-walk kernel.  With
  * use_graph = 1 a round is one replay of a CUDA graph captured at the first
  * round.  Jobs may be added and removed between rounds.  A job's levels are
- * settled by the exhaustive pass (qcs_certify_level, synchronously within
- * the round) as its problem's exhaustive_log2 / exhaustive_first ask: before
- * the level's walk (exhaustive_first) or when its walk budget ends. */
+ * settled by the exhaustive pass (the work of qcs_certify_level, run in
+ * shares of cert_points_log2 per round, each job holding its own key table
+ * until its pass ends) as its problem's exhaustive_log2 / exhaustive_first
+ * ask: before the level's walk (exhaustive_first) or when its walk budget
+ * ends. */
 typedef struct qcs_batch qcs_batch;
 
 typedef struct qcs_batch_params {
@@ -390,7 +392,10 @@ typedef struct qcs_batch_params {
                                 re-walk resumes in the next round (0: no bound) */
     int32_t launch_shape[4];  /* launch shape of the batched walk kernel for n = 1..4 qubits
                                  (index n - 1; 0 = default; see qcs_launch_shapes) */
-    int32_t reserved;
+    int32_t cert_points_log2; /* a round runs at most 2^cert_points_log2 points' worth of exhaustive-pass
+                                 work (a point with the contraction against C^ counts four), oldest job
+                                 first; a job whose pass is unfinished keeps it and is not walked that
+                                 round.  0: every pass a round starts runs to its end in that round */
 } qcs_batch_params;
 
 QCS_API void qcs_batch_default_params(qcs_batch_params *p);

@@ -76,10 +76,10 @@ class BatchParams(ctypes.Structure):
                 ("steps_per_round", ctypes.c_int32), ("table_log2", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("rewalk_budget", ctypes.c_int32), ("launch_shape", ctypes.c_int32 * 4),
-                ("reserved", ctypes.c_int32)]
+                ("cert_points_log2", ctypes.c_int32)]
 
     def as_dict(self):
-        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+        d = {name: getattr(self, name) for name, _ in self._fields_}
         d["launch_shape"] = list(self.launch_shape)
         return d
 
@@ -425,7 +425,7 @@ def default_batch_params(**overrides) -> BatchParams:
     lib().qcs_batch_default_params(ctypes.byref(p))
     names = {name for name, _ in BatchParams._fields_}
     for k, v in overrides.items():
-        if k not in names or k == "reserved":
+        if k not in names:
             raise TypeError(f"unknown batch parameter {k!r}")
         if k == "launch_shape":
             items = v.items() if isinstance(v, dict) else enumerate(v, start=1)

@@ -591,11 +591,13 @@ bool qcs::exhaustive_eligible(const qcs_problem *P, int k)
     return sizeof(CertSlot) * slots <= free_b / 2;
 }
 
-int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
+int qcs::cert_begin(qcs_problem *P, int k, cudaStream_t s, CertPass *c)
 {
-    *got = false;
-    const int h = k / 2;
-    const uint64_t xi = (uint64_t)(P->D - 1), xi_h = upow(xi, h);
+    *c = CertPass();
+    c->k = k;
+    c->h = k / 2;
+    c->xi = (uint64_t)(P->D - 1);
+    c->xi_h = upow(c->xi, c->h);
     // Odd k puts 2h + 1 rotations into two products, so one side gets h + 1
     // and has xi times the points of the other.  With a denominator in C^
     // (E >= 1) the extra rotation goes on V: the xi^(h+1) streamed points are
@@ -604,98 +606,120 @@ int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
     // E + h (V' raised from h + 1 by sqrt2^(E-1)).  A claw V' ~ W' is
     // C^ ~ R(s_h)..R(s_1) R(r_(h+1))..R(r_1).  Otherwise (even k, or E = 0)
     // V = h rotations is stored and W (with the chunk rotation) streamed.
-    const bool v_heavy = (k & 1) && P->C.E >= 1;
-    const uint64_t n_probe = xi_h * ((k & 1) ? xi : 1);
+    c->v_heavy = (k & 1) && P->C.E >= 1;
+    c->n_probe = c->xi_h * ((k & 1) ? c->xi : 1);
     uint64_t slots = 1024;
-    while (slots < 2 * xi_h) slots <<= 1;
+    while (slots < 2 * c->xi_h) slots <<= 1;
     {
         // the key table must fit: refuse before allocating
         size_t free_b = 0, total_b = 0;
         CK(cudaMemGetInfo(&free_b, &total_b));
         if (sizeof(CertSlot) * slots > free_b) return QCS_ERR_NOMEM;
     }
-    constexpr uint32_t kCap = 1u << 16;
-    // probing points per launch: slices start small, so that a claw early in
-    // the stream ends the pass soon, and double up to 2^24 (about 25 ms at
-    // n = 4), so that a long pass pays little per-slice overhead
-    constexpr uint64_t kSliceMin = 1ull << 20, kSliceMax = 1ull << 24;
-    LevelCtx lv_store = make_level(P, v_heavy ? 2 * h : k, 0, P->p.dp_bits);
-    LevelCtx lv_probe = make_level(P, v_heavy ? 2 * h + 2 : k, 0, P->p.dp_bits);
-    if (v_heavy) {
-        lv_probe.K = lv_store.K; // E + h
-        lv_probe.ev = P->C.E - 1;
+    c->lv_store = make_level(P, c->v_heavy ? 2 * c->h : k, 0, P->p.dp_bits);
+    c->lv_probe = make_level(P, c->v_heavy ? 2 * c->h + 2 : k, 0, P->p.dp_bits);
+    if (c->v_heavy) {
+        c->lv_probe.K = c->lv_store.K; // E + h
+        c->lv_probe.ev = P->C.E - 1;
     }
-    CertArgs a{};
-    a.xi_h = xi_h;
+    CertArgs &a = c->a;
+    a.xi_h = c->xi_h;
     a.mask = slots - 1;
-    a.cap = kCap;
+    a.cap = CertPass::kCap;
     // one hash base for every chunk, so the keys of a coset agree on both sides
     const uint64_t tag =
-        (uint64_t)P->n | ((uint64_t)k << 8) | (0xFFFFull << 16) | ((uint64_t)(uint32_t)lv_store.K << 32);
+        (uint64_t)P->n | ((uint64_t)k << 8) | (0xFFFFull << 16) | ((uint64_t)(uint32_t)c->lv_store.K << 32);
     a.base = smix_host(smix_host(kSeedH ^ 0xCE27u) ^ tag);
-    uint32_t *hN = nullptr;
-    uint64_t *hPairs = nullptr;
+    c->slice = CertPass::kSliceMin;
     cudaError_t e = cudaMalloc(&a.table, sizeof(CertSlot) * slots);
-    if (e == cudaSuccess) e = cudaMalloc(&a.pairs, sizeof(uint64_t) * 2 * kCap);
+    if (e == cudaSuccess) e = cudaMalloc(&a.pairs, sizeof(uint64_t) * 2 * CertPass::kCap);
     if (e == cudaSuccess) e = cudaMalloc(&a.n_pairs, sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMallocHost(&hN, sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMallocHost(&hPairs, sizeof(uint64_t) * 2 * kCap);
-    int rc = QCS_OK;
-    bool overflow = false;
-    uint64_t done_probe = 0;
-    int64_t d2h = 0;
+    if (e == cudaSuccess) e = cudaMallocHost(&c->hN, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->hPairs, sizeof(uint64_t) * 2 * CertPass::kCap);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.table, 0xFF, sizeof(CertSlot) * slots, s);
-    if (e == cudaSuccess) {
-        a.lv = lv_store;
-        a.side = v_heavy ? 1 : 0;
-        a.insert = 1;
-        a.first = 0;
-        a.count = xi_h;
-        e = launch_certify(a, s);
+    if (e != cudaSuccess) {
+        cert_end(P, c, s);
+        return e == cudaErrorMemoryAllocation ? QCS_ERR_NOMEM : cuda_fail(e);
     }
-    a.lv = lv_probe;
-    a.side = v_heavy ? 0 : 1;
-    a.insert = 0;
-    uint64_t slice = kSliceMin;
-    for (uint64_t first = 0; e == cudaSuccess && first < n_probe && !*got;
-         first += slice, slice = std::min(2 * slice, kSliceMax)) {
-        if (P->cancel.load()) {
-            rc = QCS_ERR_BUSY;
+    c->table_bytes = sizeof(CertSlot) * slots;
+    return QCS_OK;
+}
+
+int qcs::cert_advance(qcs_problem *P, CertPass *c, cudaStream_t s, uint64_t budget, uint64_t *used)
+{
+    // A stored point with the contraction against C^ costs about four
+    // streamed ones without it; `budget` and *used count in streamed points.
+    constexpr uint64_t kStoreCost = 4;
+    *used = 0;
+    CertArgs &a = c->a;
+    cudaError_t e = cudaSuccess;
+    while (!c->done && *used < budget) {
+        if (P->cancel.load()) return QCS_ERR_BUSY;
+        if (c->stored < c->xi_h) {
+            // the smaller side into the key table, in slices (W' carries the
+            // contraction with C^ when the extra rotation went on V)
+            const uint64_t cost = c->v_heavy ? kStoreCost : 1;
+            uint64_t n = std::min<uint64_t>(c->xi_h - c->stored, CertPass::kSliceMax);
+            n = std::max<uint64_t>(1, std::min<uint64_t>(n, (budget - *used + cost - 1) / cost));
+            a.lv = c->lv_store;
+            a.side = c->v_heavy ? 1 : 0;
+            a.insert = 1;
+            a.first = c->stored;
+            a.count = n;
+            if ((e = launch_certify(a, s)) != cudaSuccess) break;
+            c->stored += n;
+            *used += n * cost;
+            continue;
+        }
+        if (c->probed >= c->n_probe) {
+            c->done = true;
             break;
         }
-        a.first = first;
-        a.count = std::min(slice, n_probe - first);
+        // the other side probes the table, one slice at a time; the key
+        // matches of each slice are checked exactly on the host
+        const uint64_t cost = c->v_heavy ? 1 : kStoreCost;
+        uint64_t n = std::min(c->slice, c->n_probe - c->probed);
+        n = std::max<uint64_t>(1, std::min<uint64_t>(n, (budget - *used + cost - 1) / cost));
+        a.lv = c->lv_probe;
+        a.side = c->v_heavy ? 0 : 1;
+        a.insert = 0;
+        a.first = c->probed;
+        a.count = n;
         if ((e = cudaMemsetAsync(a.n_pairs, 0, sizeof(uint32_t), s)) != cudaSuccess) break;
         if ((e = launch_certify(a, s)) != cudaSuccess) break;
-        if ((e = cudaMemcpyAsync(hN, a.n_pairs, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(c->hN, a.n_pairs, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
-        d2h += (int64_t)sizeof(uint32_t);
-        done_probe += a.count;
-        const uint32_t n = std::min(*hN, kCap);
-        if (*hN > kCap) overflow = true;
-        if (n > 0) {
+        c->d2h += (int64_t)sizeof(uint32_t);
+        c->probed += n;
+        *used += n * cost;
+        if (n == c->slice) c->slice = std::min(2 * c->slice, CertPass::kSliceMax);
+        const uint32_t m = std::min(*c->hN, CertPass::kCap);
+        if (*c->hN > CertPass::kCap) c->overflow = true;
+        if (m > 0) {
             // read back only the matches the slice queued
-            if ((e = cudaMemcpyAsync(hPairs, a.pairs, sizeof(uint64_t) * 2 * n, cudaMemcpyDeviceToHost, s)) !=
+            if ((e = cudaMemcpyAsync(c->hPairs, a.pairs, sizeof(uint64_t) * 2 * m, cudaMemcpyDeviceToHost, s)) !=
                 cudaSuccess)
                 break;
             if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
-            d2h += (int64_t)(sizeof(uint64_t) * 2 * n);
+            c->d2h += (int64_t)(sizeof(uint64_t) * 2 * m);
         }
-        for (uint32_t i = 0; i < n && !*got; i++) {
+        const int k = c->k, h = c->h;
+        const uint64_t xi = c->xi;
+        for (uint32_t i = 0; i < m && !c->got; i++) {
             // exact check of the key match: rotations from the point indices
             uint32_t paulis[16] = {0};
-            uint64_t st = hPairs[2 * i], pr = hPairs[2 * i + 1];
+            uint64_t st = c->hPairs[2 * i], pr = c->hPairs[2 * i + 1];
             PMat Dh;
             bool ok;
-            if (v_heavy) {
+            if (c->v_heavy) {
                 // P_1..P_(h+1) = r_1..r_(h+1) (probing V'), P_(h+2)..P_k = s_1..s_h (stored W')
                 for (int j = 0; j <= h; j++, pr /= xi) paulis[j] = (uint32_t)(pr % xi) + 1;
                 for (int j = 0; j < h; j++, st /= xi) paulis[h + 1 + j] = (uint32_t)(st % xi) + 1;
                 ok = exact_verify(P->n, P->C, paulis, k, &Dh) == QCS_OK;
             } else {
                 uint32_t qv[kMaxH], qw[kMaxH];
-                const int chunk = (k & 1) ? (int)(pr / xi_h) + 1 : 0;
-                pr %= xi_h;
+                const int chunk = (k & 1) ? (int)(pr / c->xi_h) + 1 : 0;
+                pr %= c->xi_h;
                 for (int j = 0; j < h; j++) {
                     qv[j] = (uint32_t)(st % xi) + 1;
                     qw[j] = (uint32_t)(pr % xi) + 1;
@@ -706,25 +730,48 @@ int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
             }
             if (ok) {
                 found(P, k, paulis, std::move(Dh));
-                *got = true;
+                c->got = true;
             }
         }
+        if (c->got) c->done = true;
     }
-    if (e != cudaSuccess) rc = cuda_fail(e);
+    return e == cudaSuccess ? QCS_OK : cuda_fail(e);
+}
+
+int qcs::cert_end(qcs_problem *P, CertPass *c, cudaStream_t s)
+{
     cudaStreamSynchronize(s);
-    cudaFree(a.table);
-    cudaFree(a.pairs);
-    cudaFree(a.n_pairs);
-    cudaFreeHost(hN);
-    cudaFreeHost(hPairs);
+    cudaFree(c->a.table);
+    cudaFree(c->a.pairs);
+    cudaFree(c->a.n_pairs);
+    cudaFreeHost(c->hN);
+    cudaFreeHost(c->hPairs);
+    c->a.table = nullptr;
+    c->a.pairs = nullptr;
+    c->a.n_pairs = nullptr;
+    c->hN = nullptr;
+    c->hPairs = nullptr;
     {
         std::lock_guard<std::mutex> g(P->mu);
-        P->res.cert_points += (int64_t)(xi_h + done_probe);
-        P->res.d2h_bytes += d2h;
-        if (rc == QCS_OK && !*got && !overflow) P->res.certified_levels += 1;
+        P->res.cert_points += (int64_t)(c->stored + c->probed);
+        P->res.d2h_bytes += c->d2h;
+        if (c->done && !c->got && !c->overflow) P->res.certified_levels += 1;
     }
-    if (rc == QCS_OK && !*got && overflow) rc = QCS_ERR_OVERFLOW;
-    return rc;
+    c->d2h = 0;
+    return (c->done && !c->got && c->overflow) ? QCS_ERR_OVERFLOW : QCS_OK;
+}
+
+int qcs::certify_level(qcs_problem *P, int k, cudaStream_t s, bool *got)
+{
+    *got = false;
+    CertPass c;
+    int rc = cert_begin(P, k, s, &c);
+    if (rc != QCS_OK) return rc;
+    uint64_t used = 0;
+    while (rc == QCS_OK && !c.done) rc = cert_advance(P, &c, s, ~0ull, &used);
+    const int rc_end = cert_end(P, &c, s);
+    *got = c.got;
+    return rc != QCS_OK ? rc : rc_end;
 }
 
 namespace {

@@ -44,6 +44,12 @@ struct Job {
     int pp = 0;                            // pend[pp] feeds the next round
     uint32_t pend_n = 0;
     std::chrono::steady_clock::time_point t0;
+    // the exhaustive pass of the job's level, run a share per round
+    CertPass *cert = nullptr;
+    bool cert_after_walk = false; // the level's walk budget ended: settle it exactly next
+    int cert_skip_k = -1;         // a level whose pass was inconclusive is walked instead
+    bool parked = false;          // busy with its pass this round: not walked
+    uint64_t seq = 0;             // order of arrival (the passes' share goes to the oldest first)
 };
 
 int fail(cudaError_t e) { return record_cuda_error(e); }
@@ -72,6 +78,7 @@ struct qcs_batch {
     // (and the long tail of one class's re-walks) overlap
     cudaStream_t cs[kClasses] = {};
     cudaEvent_t fork = nullptr, join[kClasses] = {};
+    uint64_t next_seq = 0;
 };
 
 namespace {
@@ -82,8 +89,12 @@ size_t job_bytes(const qcs_batch_params &bp)
            (sizeof(Pair) + 2 * sizeof(Pending)) * (size_t)bp.queue_capacity;
 }
 
-void free_job(Job &j)
+void free_job(Job &j, cudaStream_t s)
 {
+    if (j.cert) {
+        cert_end(j.P, j.cert, s);
+        delete j.cert;
+    }
     cudaFree(j.walks);
     cudaFree(j.table);
     cudaFree(j.queue);
@@ -121,34 +132,99 @@ void settle_small_levels(Job &j)
     }
 }
 
-// exhaustive_first: settle the job's levels that qualify by the exhaustive
-// pass alone, before any walk of theirs (returns a status code)
-int settle_exhaustive_levels(qcs_batch *B, Job &j)
+void job_error(Job &j, int rc)
+{
+    std::lock_guard<std::mutex> g(j.P->mu);
+    j.P->res.error = rc;
+    j.status = QCS_ERROR;
+    j.active = false;
+}
+
+void next_level(Job &j)
+{
+    j.k++;
+    j.version++;
+    j.launches = 0;
+    j.in_version = 0;
+    j.need_begin = true;
+    if (j.k > j.P->k_max) {
+        j.status = QCS_BUDGET_EXHAUSTED;
+        j.active = false;
+    }
+}
+
+// The job's exhaustive passes: exhaustive_first settles each qualifying level
+// by the pass alone, before any walk of it; a level whose walk budget ended
+// without a claw is settled by the pass before the next level.  A pass runs
+// for as much of *budget (streamed-point equivalents, see cert_advance) as
+// it needs; if the budget runs out first the job is parked: it keeps its
+// pass and is not walked this round.
+int cert_work(qcs_batch *B, Job &j, uint64_t *budget)
 {
     qcs_problem *P = j.P;
-    while (j.active && j.launches == 0 && P->p.exhaustive_first && exhaustive_eligible(P, j.k)) {
-        bool claw = false;
-        const int rc = certify_level(P, j.k, B->s, &claw);
-        if (rc == QCS_ERR_OVERFLOW) return QCS_OK; // inconclusive: walk the level
+    j.parked = false;
+    while (j.active) {
+        if (!j.cert) {
+            const bool first = P->p.exhaustive_first && j.need_begin && j.launches == 0 && j.k != j.cert_skip_k &&
+                               exhaustive_eligible(P, j.k);
+            if (!first && !j.cert_after_walk) return QCS_OK;
+            if (*budget == 0) {
+                j.parked = true;
+                return QCS_OK;
+            }
+            j.cert = new (std::nothrow) CertPass();
+            if (!j.cert) return QCS_ERR_NOMEM;
+            const int rc = cert_begin(P, j.k, B->s, j.cert);
+            if (rc != QCS_OK) {
+                delete j.cert;
+                j.cert = nullptr;
+                if (rc == QCS_ERR_NOMEM && !j.cert_after_walk) { // no room for the table now: walk the level
+                    j.cert_skip_k = j.k;
+                    return QCS_OK;
+                }
+                j.cert_after_walk = false;
+                if (rc == QCS_ERR_NOMEM) {
+                    next_level(j);
+                    continue;
+                }
+                job_error(j, rc);
+                return QCS_OK;
+            }
+        }
+        uint64_t used = 0;
+        int rc = cert_advance(P, j.cert, B->s, *budget, &used);
+        *budget -= std::min(used, *budget);
         if (rc != QCS_OK) {
-            std::lock_guard<std::mutex> g(P->mu);
-            P->res.error = rc;
-            j.status = QCS_ERROR;
-            j.active = false;
+            cert_end(P, j.cert, B->s);
+            delete j.cert;
+            j.cert = nullptr;
+            job_error(j, rc);
             return QCS_OK;
         }
+        if (!j.cert->done) {
+            j.parked = true;
+            return QCS_OK;
+        }
+        const bool claw = j.cert->got;
+        rc = cert_end(P, j.cert, B->s);
+        delete j.cert;
+        j.cert = nullptr;
+        const bool after_walk = j.cert_after_walk;
+        j.cert_after_walk = false;
         if (claw) {
             j.status = QCS_FOUND;
             j.active = false;
             return QCS_OK;
         }
-        j.k++;
-        j.version++;
-        j.need_begin = true;
-        if (j.k > P->k_max) {
-            j.status = QCS_BUDGET_EXHAUSTED;
-            j.active = false;
+        if (rc == QCS_ERR_OVERFLOW && !after_walk) { // inconclusive: walk the level
+            j.cert_skip_k = j.k;
+            return QCS_OK;
         }
+        if (rc != QCS_OK && rc != QCS_ERR_OVERFLOW) {
+            job_error(j, rc);
+            return QCS_OK;
+        }
+        next_level(j); // proved empty (or walked and inconclusive): the next level
     }
     return QCS_OK;
 }
@@ -193,7 +269,7 @@ void build_tasks(qcs_batch *B)
     uint32_t nt[kClasses] = {0}, nj[kClasses] = {0};
     for (size_t slot = 0; slot < B->jobs.size(); slot++) {
         const Job &j = B->jobs[slot];
-        if (!j.active) continue;
+        if (!j.active || j.parked) continue;
         const int c = j.P->n;
         B->hIds[(size_t)c * B->bp.max_jobs + nj[c]++] = (uint32_t)slot;
         const int per = walks_per_task(c, B->bp.launch_shape[c - 1]);
@@ -239,7 +315,7 @@ int enqueue_round(qcs_batch *B)
 }
 
 // fold one job's round into its result and advance its ladder
-void collect_job(Job &j, const unsigned long long *c, const uint32_t *heads, const Cand *cands, cudaStream_t s)
+void collect_job(Job &j, const unsigned long long *c, const uint32_t *heads, const Cand *cands)
 {
     qcs_problem *P = j.P;
     const int k = j.k, h = k / 2;
@@ -297,30 +373,12 @@ void collect_job(Job &j, const unsigned long long *c, const uint32_t *heads, con
     }
     if (j.launches >= j.pl.min_launches) { // level exhausted: the next one
         if (exhaustive_eligible(P, k)) {
-            // settle the level exactly before moving on (a claw the walk missed)
-            bool claw = false;
-            const int rc = certify_level(P, k, s, &claw);
-            if (rc != QCS_OK && rc != QCS_ERR_OVERFLOW) {
-                std::lock_guard<std::mutex> g(P->mu);
-                P->res.error = rc;
-                j.status = QCS_ERROR;
-                j.active = false;
-                return;
-            }
-            if (claw) {
-                j.status = QCS_FOUND;
-                j.active = false;
-                return;
-            }
+            // settle the level exactly before moving on (a claw the walk
+            // missed): the pass runs from the next round on (cert_work)
+            j.cert_after_walk = true;
+            return;
         }
-        j.k++;
-        j.version++;
-        j.launches = 0;
-        j.need_begin = true;
-        if (j.k > P->k_max) {
-            j.status = QCS_BUDGET_EXHAUSTED;
-            j.active = false;
-        }
+        next_level(j);
     } else if (j.in_version >= j.pl.launches_per_version) {
         j.version++;
         j.need_begin = true;
@@ -363,6 +421,7 @@ int qcs_batch_create(const qcs_batch_params *pin, void *stream, qcs_batch **out)
         return QCS_ERR_ARG;
     for (int n = 1; n <= 4; n++)
         if (bp.launch_shape[n - 1] < 0 || bp.launch_shape[n - 1] >= launch_shapes(n)) return QCS_ERR_ARG;
+    if (bp.cert_points_log2 < 0 || bp.cert_points_log2 > 40) return QCS_ERR_ARG;
     qcs_batch *B = new (std::nothrow) qcs_batch();
     if (!B) return QCS_ERR_NOMEM;
     B->bp = bp;
@@ -461,9 +520,10 @@ int qcs_batch_add(qcs_batch *B, qcs_problem *P, int *job)
     if (!e) e = cudaMalloc(&j.pend[0], sizeof(Pending) * (size_t)j.jp.queue_capacity);
     if (!e) e = cudaMalloc(&j.pend[1], sizeof(Pending) * (size_t)j.jp.queue_capacity);
     if (e) {
-        free_job(j);
+        free_job(j, B->s);
         return e == cudaErrorMemoryAllocation ? QCS_ERR_NOMEM : fail(e);
     }
+    j.seq = B->next_seq++;
     j.k = P->C.E;
     j.active = true;
     j.status = QCS_SEARCHING;
@@ -483,7 +543,7 @@ int qcs_batch_remove(qcs_batch *B, int job)
         publish_status(j);
     }
     memset(&B->hJobs[job], 0, sizeof(WalkLaunch));
-    free_job(j);
+    free_job(j, B->s);
     return e ? fail(e) : QCS_OK;
 }
 
@@ -491,13 +551,30 @@ int qcs_batch_round(qcs_batch *B, int *n_active)
 {
     if (!B) return QCS_ERR_ARG;
     int rc;
-    int active = 0;
+    int active = 0, parked = 0;
+    // 1. exhaustive passes, oldest job first, within the round's share
+    {
+        std::vector<size_t> order;
+        for (size_t slot = 0; slot < B->jobs.size(); slot++)
+            if (B->jobs[slot].active) order.push_back(slot);
+        std::sort(order.begin(), order.end(),
+                  [B](size_t x, size_t y) { return B->jobs[x].seq < B->jobs[y].seq; });
+        uint64_t budget = B->bp.cert_points_log2 > 0 ? (1ull << B->bp.cert_points_log2) : ~0ull;
+        for (size_t slot : order) {
+            Job &j = B->jobs[slot];
+            if ((rc = cert_work(B, j, &budget))) return rc;
+            if (!j.active) { // settled by its pass
+                publish_status(j);
+                memset(&B->hJobs[slot], 0, sizeof(WalkLaunch));
+            }
+        }
+    }
+    // 2. the walkers
     for (size_t slot = 0; slot < B->jobs.size(); slot++) {
         Job &j = B->jobs[slot];
         if (!j.active) continue;
-        if (j.need_begin && (rc = settle_exhaustive_levels(B, j))) return rc;
-        if (!j.active) {
-            publish_status(j);
+        if (j.parked) {
+            parked++;
             memset(&B->hJobs[slot], 0, sizeof(WalkLaunch));
             continue;
         }
@@ -512,7 +589,7 @@ int qcs_batch_round(qcs_batch *B, int *n_active)
         w.pend_out_n = B->dHeads + kHeads * slot + 2;
         active++;
     }
-    if (n_active) *n_active = active;
+    if (n_active) *n_active = active + parked;
     if (!active) return QCS_OK;
     build_tasks(B);
     if (B->bp.use_graph) {
@@ -539,9 +616,9 @@ int qcs_batch_round(qcs_batch *B, int *n_active)
     active = 0;
     for (size_t slot = 0; slot < B->jobs.size(); slot++) {
         Job &j = B->jobs[slot];
-        if (!j.active) continue;
+        if (!j.active || j.parked) continue;
         collect_job(j, B->hCounters + slot * C_NCOUNTERS, B->hHeads + kHeads * slot,
-                    B->hCands + slot * kBatchCandCap, B->s);
+                    B->hCands + slot * kBatchCandCap);
         if (!j.active) {
             publish_status(j);
             memset(&B->hJobs[slot], 0, sizeof(WalkLaunch));
@@ -549,7 +626,7 @@ int qcs_batch_round(qcs_batch *B, int *n_active)
             active++;
         }
     }
-    if (n_active) *n_active = active;
+    if (n_active) *n_active = active + parked;
     return QCS_OK;
 }
 
@@ -568,7 +645,7 @@ void qcs_batch_destroy(qcs_batch *B)
     if (!B) return;
     if (B->s) cudaStreamSynchronize(B->s);
     for (Job &j : B->jobs)
-        if (j.used) free_job(j);
+        if (j.used) free_job(j, B->s);
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->graph) cudaGraphDestroy(B->graph);
     cudaFree(B->dJobs); cudaFreeHost(B->hJobs);

@@ -195,6 +195,31 @@ struct CertArgs {
 cudaError_t launch_certify(const CertArgs &a, cudaStream_t s);
 // Host driver of the exhaustive pass (qcs_certify_level); *got = verified claw.
 int certify_level(::qcs_problem *P, int k, cudaStream_t s, bool *got);
+
+// The exhaustive pass as a resumable job (the batch engine runs a bounded
+// share of it per round): cert_begin allocates and clears the key table,
+// cert_advance evaluates points (stored side first, then probing slices,
+// each slice's key matches checked exactly) until the pass is done or
+// `budget` streamed-point equivalents are spent (*used), and cert_end frees
+// the table and folds the pass into the problem's result (QCS_ERR_OVERFLOW:
+// done without a claw but inconclusive).  certify_level is the three in a row.
+struct CertPass {
+    static constexpr uint32_t kCap = 1u << 16;          // key matches read back per slice
+    static constexpr uint64_t kSliceMin = 1ull << 20;   // probing points of the first slice
+    static constexpr uint64_t kSliceMax = 1ull << 24;   // slices double up to this
+    int k = 0, h = 0;
+    bool v_heavy = false, done = false, got = false, overflow = false;
+    uint64_t xi = 0, xi_h = 0, n_probe = 0, stored = 0, probed = 0, slice = 0;
+    uint64_t table_bytes = 0;
+    int64_t d2h = 0;
+    LevelCtx lv_store{}, lv_probe{};
+    CertArgs a{};
+    uint32_t *hN = nullptr;
+    uint64_t *hPairs = nullptr;
+};
+int cert_begin(::qcs_problem *P, int k, cudaStream_t s, CertPass *c);
+int cert_advance(::qcs_problem *P, CertPass *c, cudaStream_t s, uint64_t budget, uint64_t *used);
+int cert_end(::qcs_problem *P, CertPass *c, cudaStream_t s);
 uint64_t exhaustive_points(const ::qcs_problem *P, int k); // V + W points of level k
 bool exhaustive_eligible(const ::qcs_problem *P, int k);   // within exhaustive_log2 and device memory
 

@@ -4,10 +4,10 @@ Requests (a target and its k_max) arrive at any time.  Between two rounds of
 the batched search (qcs_batch_*) the server admits waiting requests while a
 job slot and enough device memory for the job's walk states, distinguished-
 point table and merge queue are free, then runs one round for every admitted
-job, so new work overlaps on the device with the work already there.  The
-exhaustive level pass that a round may run for one job at a time allocates
-a key table for the call; the budget keeps room for the largest such table
-among the admitted jobs.  A job
+job, so new work overlaps on the device with the work already there.  A job
+may settle a level by the exhaustive pass, which holds a key table until the
+pass ends (a round runs a bounded share of the passes, oldest job first), so
+each job is admitted with room for its largest such table.  A job
 leaves the batch as soon as it has its answer (or passes its deadline) and
 its memory is released for the next request.  Times are measured from each
 request's arrival to its answer, and so is the deadline: a request still
@@ -129,9 +129,8 @@ class Server:
             if not r.future.done() and not (block and not self.running):
                 break  # arrival order: wait for the head's set-up
             prob = r.future.result()
-            need = self.batch.job_bytes(prob)
-            table = max([r.table_bytes] + [o.table_bytes for o in self.running.values()])
-            if self.used + need + table > self.budget and self.running:
+            need = self.batch.job_bytes(prob) + r.table_bytes
+            if self.used + need > self.budget and self.running:
                 break  # memory is full: wait for a job to leave
             try:
                 slot = self.batch.add(prob)

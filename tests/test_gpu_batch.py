@@ -134,16 +134,24 @@ def test_jobs_join_and_leave_between_rounds(orc, dev):
         p_fast.close()
 
 
-def test_batch_exhaustive_first_settles_levels_without_walking(orc, dev):
+@pytest.mark.parametrize("share", [0, 10])
+def test_batch_exhaustive_first_settles_levels_without_walking(orc, dev, share):
+    # share: log2 of the exhaustive-pass points a round may run (0: every
+    # pass to its end in its round); with 2^10 a pass spans many rounds, its
+    # job parked (not walked) meanwhile, and the answers are the same
     cases = [(2, W.seeded_target(2, t, 400 + t)[0], t) for t in (3, 4, 5)]
     cases.append((3, W.seeded_target(3, 4, 404)[0], 4))
     probs, jobs = [], []
-    with Q.Batch(small_params(), torch.cuda.Stream()) as batch:
+    with Q.Batch(small_params(cert_points_log2=share), torch.cuda.Stream()) as batch:
         for n, gates, kmax in cases:
             p = Q.Problem.from_circuit(n, gates, kmax, Q.default_params(n, exhaustive_first=1))
             probs.append(p)
             jobs.append(batch.add(p))
-        assert run_to_end(batch, 4)
+        rounds = 0
+        while batch.round() > 0:
+            rounds += 1
+            assert rounds < 2000
+        assert rounds == 0 if share == 0 else rounds > 4
         for (n, gates, kmax), j in zip(cases, jobs):
             r = batch.poll(j)
             C = orc.channel_from_circuit(n, gates)

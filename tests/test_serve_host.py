@@ -133,17 +133,17 @@ def test_a_full_batch_leaves_the_request_queued(fake):
         assert srv.poll(rid)["status"] == "found"
 
 
-def test_admission_keeps_room_for_one_exhaustive_key_table(fake):
-    """A round may run the exhaustive pass for one job, whose key table is
-    allocated for the call: admission keeps room for the largest such table
-    among the admitted jobs (16 bytes x 2^exhaustive_log2 at most)."""
+def test_admission_keeps_room_for_each_jobs_exhaustive_key_table(fake):
+    """A job may hold the key table of an exhaustive pass across rounds:
+    admission counts each admitted job with its largest such table (16 bytes
+    x 2^exhaustive_log2 at most without the request's qubit count)."""
     from types import SimpleNamespace
 
     assert serve.exhaustive_table_bytes(SimpleNamespace(exhaustive_log2=10)) == 16 << 10
     assert serve.exhaustive_table_bytes(SimpleNamespace(exhaustive_log2=0)) == 0
     assert serve.exhaustive_table_bytes(None) == 0
     table = 16 << 10
-    for budget, most in ((table + 450, 2), (table + 250, 1)):
+    for budget, most in ((2 * table + 450, 2), (table + 250, 1)):
         clock = Clock()
         with serve.Server(bparams(4), memory_budget=budget, clock=clock,
                           params_for=lambda n: SimpleNamespace(exhaustive_log2=10)) as srv:
@@ -153,7 +153,7 @@ def test_admission_keeps_room_for_one_exhaustive_key_table(fake):
                 clock.t += 0.01
                 srv.step()
                 peak = max(peak, len(srv.running))
-                assert not srv.running or srv.used + table <= budget or len(srv.running) == 1
+                assert not srv.running or srv.used <= budget or len(srv.running) == 1
                 if srv.idle():
                     break
             assert srv.idle() and peak == most
