@@ -550,8 +550,8 @@ def serving_stats(polls, deadline_s):
             "note": "p50/p99 over all requests; a missed request counts at the deadline (censored)"}
 
 
-def run_serving(Q, W, torch, stream, tuned, n_requests=2000, rate=50.0, budget_bytes=2 << 30,
-                deadline_s=10.0, drain_s=15.0):
+def run_serving(Q, W, torch, stream, tuned, n_requests=2000, rate=50.0, budget_bytes=16 << 30,
+                deadline_s=10.0, drain_s=15.0, cert_points_log2=24):
     """The serving workload: a Poisson stream of seeded targets replayed in real time
     into the continuous-batching server; latency is arrival to answer, and
     the deadline counts from arrival too."""
@@ -561,7 +561,8 @@ def run_serving(Q, W, torch, stream, tuned, n_requests=2000, rate=50.0, budget_b
     bp = Q.default_batch_params(max_jobs=512, walks_per_job=tuned["walks_per_job"],
                                 steps_per_round=tuned["steps_per_round"], table_log2=18,
                                 queue_capacity=tuned["queue_capacity"],
-                                launch_shape={int(k): v for k, v in tuned.get("launch_shape", {}).items()})
+                                launch_shape={int(k): v for k, v in tuned.get("launch_shape", {}).items()},
+                                cert_points_log2=cert_points_log2)
     layouts = {int(k): v for k, v in tuned.get("c_layout", {}).items()}
     # serving policy: every level of at most 2^32 V + W points (all levels of
     # this stream, n = 4 level 7 included) is settled by the exact pass
@@ -570,7 +571,7 @@ def run_serving(Q, W, torch, stream, tuned, n_requests=2000, rate=50.0, budget_b
                       params_for=lambda n: Q.default_params(n, c_layout=layouts.get(n, 0), **policy)) as srv:
         rids, wall = serve.replay_stream(srv, times, targets, time_limit_s=float(times[-1]) + drain_s)
         polls = [srv.poll(r) for r in rids]
-        fevals, rounds, peak = srv.fevals, srv.rounds, srv.peak_used
+        fevals, rounds, peak, cert_points = srv.fevals, srv.rounds, srv.peak_used, srv.cert_points
     status = {}
     for p in polls:
         status[p["status"]] = status.get(p["status"], 0) + 1
@@ -583,11 +584,13 @@ def run_serving(Q, W, torch, stream, tuned, n_requests=2000, rate=50.0, budget_b
         "workload": f"{n_requests} seeded targets, Poisson arrivals at {rate}/s, n~U{{2,3,4}}, T-count~U{{3..7}}",
         **serving_stats(polls, deadline_s), "status_counts": status,
         "offered_per_s_by_class": {k: v / span for k, v in sorted(offered.items())},
-        "fevals_per_s": fevals / wall, "wall_s": wall, "rounds": rounds, "memory_budget_bytes": budget_bytes,
+        "fevals_per_s": fevals / wall, "exhaustive_points_per_s": cert_points / wall, "wall_s": wall, "rounds": rounds, "memory_budget_bytes": budget_bytes,
         "peak_admitted_bytes": peak, "deadline_s": deadline_s,
-        "policy": dict(policy, note="exhaustive pass first on every level of at most 2^32 V + W points (n = 4 "
-                                    "level 7: 4.2e9 points, a 512 MiB key table reserved at admission); a "
-                                    "request still queued at its deadline is dropped unanswered"),
+        "policy": dict(policy, cert_points_log2=cert_points_log2,
+                       note="exhaustive pass first on every level of at most 2^32 V + W points (n = 4 level 7: "
+                            "4.2e9 points, a 512 MiB key table held by its job and reserved at admission); a round "
+                            f"runs at most 2^{cert_points_log2} points of the passes, oldest job first; a request "
+                            "still queued at its deadline is dropped unanswered"),
     }
 
 

@@ -78,6 +78,7 @@ class Server:
         self.requests = {}
         self.rounds = 0
         self.fevals = 0
+        self.cert_points = 0
         self.next_id = 0
         self.peak_used = 0
         # the exact host set-up of a target (channel representation, upload)
@@ -149,6 +150,7 @@ class Server:
     def _finish(self, r, status, result):
         r.status, r.result, r.t_done = status, result, self.clock()
         self.fevals += result["steps"] + result["rewalk_steps"]
+        self.cert_points += result.get("cert_points", 0)
         self.batch.remove(r.slot)
         r.prob.close()
         r.prob = None
