@@ -35,6 +35,13 @@ QCS_PEAK_API int qcs_peak_iadd(int blocks_per_sm, int iters, double *iadd_per_s,
  * contraction; reports dp4a instructions per second. */
 QCS_PEAK_API int qcs_peak_idp4a(int blocks_per_sm, int iters, double *dp4a_per_s, double *ms);
 
+/* Legacy warp-level tensor-core MMA rates (mma.sync), reported as
+ * multiply-adds per second: f16 x f16 with f32 accumulation (m16n8k16), the
+ * form an exact small-integer contraction could take, and u8 x s8 with s32
+ * accumulation (m16n8k32).  Same launch and return convention as above. */
+QCS_PEAK_API int qcs_peak_hmma(int blocks_per_sm, int iters, double *mac_per_s, double *ms);
+QCS_PEAK_API int qcs_peak_imma(int blocks_per_sm, int iters, double *mac_per_s, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

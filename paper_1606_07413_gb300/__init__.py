@@ -494,7 +494,7 @@ def peak_lib():
     if not os.path.exists(path):
         raise RuntimeError(f"libqcs_peak.so is missing at {path}; run __graft_entry__.build()")
     L = ctypes.CDLL(path)
-    for name in ("qcs_peak_imad", "qcs_peak_iadd", "qcs_peak_idp4a"):
+    for name in ("qcs_peak_imad", "qcs_peak_iadd", "qcs_peak_idp4a", "qcs_peak_hmma", "qcs_peak_imma"):
         f = getattr(L, name)
         f.restype = ctypes.c_int
         f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
@@ -502,7 +502,8 @@ def peak_lib():
 
 
 def measure_int_peak(kind: str = "imad", blocks_per_sm: int = 8, iters: int = 4096) -> tuple[float, float]:
-    """(ops per second, kernel ms) of the IMAD, IADD3 or dp4a microbenchmark."""
+    """(ops per second, kernel ms) of the IMAD, IADD3 or dp4a microbenchmark,
+    or (multiply-adds per second, ms) of the hmma / imma tensor-core ones."""
     ops, ms = ctypes.c_double(0), ctypes.c_double(0)
     rc = getattr(peak_lib(), f"qcs_peak_{kind}")(blocks_per_sm, iters, ctypes.byref(ops), ctypes.byref(ms))
     if rc != 0:

@@ -56,8 +56,57 @@ __global__ void __launch_bounds__(256) k_idp4a(uint32_t a, uint32_t b, int iters
     if (s == 0x9E3779B9u) sink[0] = s;
 }
 
+// Legacy warp-level tensor-core MMAs (mma.sync), eight independent
+// accumulator tiles per warp: f16 x f16 -> f32 (m16n8k16, 2048 multiply-adds
+// each) and u8 x s8 -> s32 (m16n8k32, 4096 each).  The operands are fixed
+// register values: the rate, not the result, is measured.
+__global__ void __launch_bounds__(256) k_hmma(uint32_t a, uint32_t b, int iters, uint32_t *sink)
+{
+    float d[8][4] = {};
+    const uint32_t a0 = a, a1 = a ^ 0x00010001u, a2 = b, a3 = b ^ 0x00010001u, b0 = a ^ b, b1 = a + b;
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int u = 0; u < 16; u++) {
+#pragma unroll
+            for (int t = 0; t < 8; t++)
+                asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                             "{%8,%9}, {%0,%1,%2,%3};"
+                             : "+f"(d[t][0]), "+f"(d[t][1]), "+f"(d[t][2]), "+f"(d[t][3])
+                             : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+    }
+    float s = 0;
+#pragma unroll
+    for (int t = 0; t < 8; t++) s += d[t][0] + d[t][1] + d[t][2] + d[t][3];
+    if (s == 1.2345f) sink[0] = 1;
+}
+
+__global__ void __launch_bounds__(256) k_imma(uint32_t a, uint32_t b, int iters, uint32_t *sink)
+{
+    int32_t d[8][4] = {};
+    const uint32_t a0 = a, a1 = a ^ 0x01010101u, a2 = b, a3 = b ^ 0x01010101u, b0 = a ^ b, b1 = a + b;
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int u = 0; u < 16; u++) {
+#pragma unroll
+            for (int t = 0; t < 8; t++)
+                asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.u8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                             "{%8,%9}, {%0,%1,%2,%3};"
+                             : "+r"(d[t][0]), "+r"(d[t][1]), "+r"(d[t][2]), "+r"(d[t][3])
+                             : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+    }
+    int32_t s = 0;
+#pragma unroll
+    for (int t = 0; t < 8; t++) s ^= d[t][0] ^ d[t][1] ^ d[t][2] ^ d[t][3];
+    if (s == 0x12345) sink[0] = 1;
+}
+
+// ops per thread per outer iteration: 128 for the ALU kernels (16 x 8
+// chains); for the MMA kernels each warp issues 128 MMAs per iteration, so a
+// thread's share is 128 x (multiply-adds per MMA) / 32
 template <typename K>
-int run(K kern, int blocks_per_sm, int iters, double *ops_per_s, double *ms)
+int run(K kern, int blocks_per_sm, int iters, double *ops_per_s, double *ms, double ops_per_iter = 128.0)
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -81,7 +130,7 @@ int run(K kern, int blocks_per_sm, int iters, double *ops_per_s, double *ms)
     cudaFree(sink);
     if (e != cudaSuccess) return -(int)e;
     *ms = t;
-    *ops_per_s = (double)grid * 256.0 * (double)iters * 128.0 / ((double)t * 1e-3);
+    *ops_per_s = (double)grid * 256.0 * (double)iters * ops_per_iter / ((double)t * 1e-3);
     return 0;
 }
 
@@ -100,4 +149,14 @@ extern "C" int qcs_peak_iadd(int blocks_per_sm, int iters, double *iadd_per_s, d
 extern "C" int qcs_peak_idp4a(int blocks_per_sm, int iters, double *dp4a_per_s, double *ms)
 {
     return run(k_idp4a, blocks_per_sm, iters, dp4a_per_s, ms);
+}
+
+extern "C" int qcs_peak_hmma(int blocks_per_sm, int iters, double *mac_per_s, double *ms)
+{
+    return run(k_hmma, blocks_per_sm, iters, mac_per_s, ms, 128.0 * 2048.0 / 32.0);
+}
+
+extern "C" int qcs_peak_imma(int blocks_per_sm, int iters, double *mac_per_s, double *ms)
+{
+    return run(k_imma, blocks_per_sm, iters, mac_per_s, ms, 128.0 * 4096.0 / 32.0);
 }
