@@ -102,8 +102,15 @@ def workload_config(c, k=None, steps=None, rewalk_budget=None):
 # holds only for the kernel source it was captured on (hash of the walk
 # kernel's source files, comments and layout removed); otherwise its figures
 # are reported as null.
+# k_walks<4,0>: `ncu --set full` of `bench.py --level-only n4_level7 --steps 2`
+# (2^20 walks x 16 steps: 3.2367e10 warp instructions, 34.57 MB read and
+# 0.47 MB written).  The launch's DRAM traffic is the walk states and the
+# staged tables, which do not grow with the steps, plus 32 bytes per
+# distinguished point (0.5 MB at the headline's 64 steps), so the figure
+# stands for the headline launch (profiles/k_walks_n4_level7_walks1048576.md).
 WALK_NCU = {
-    "k_walks<4,0>": {"source_sha256_16": None, "dram_bytes_per_launch": None, "warp_inst_per_step": None},
+    "k_walks<4,0>": {"source_sha256_16": "7fcffe814850e398", "dram_bytes_per_launch": 35037184,
+                     "warp_inst_per_step": 1929.2},
     "k_walks<3,0>": {"source_sha256_16": None, "dram_bytes_per_launch": None, "warp_inst_per_step": None},
 }
 
@@ -117,9 +124,13 @@ def walk_source_hash() -> str:
     h = hashlib.sha256()
     for f in ("qcs_walk.cu", "qcs_internal.h"):
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1606_07413_gb300", "csrc", f)) as fh:
-            code = re.sub(r"/\*.*?\*/", " ", fh.read(), flags=re.S)
-            code = re.sub(r"//[^\n]*", " ", code)
-            h.update(" ".join(code.split()).encode())
+            text = fh.read()
+        if f == "qcs_internal.h":
+            # only the structures the walk kernels read (the rest is host-only)
+            text = text[: text.index("// Exhaustive meet-in-the-middle pass over one level")]
+        code = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 
@@ -610,20 +621,26 @@ def timed_level(Q, torch, prob, stream, k, dp_bits, steps, warmup, launches, flu
     torch.cuda.synchronize()
     r0 = prob.poll()
     step_ms, walk_ms = [], []
+    split = {"walk_ms": 0.0, "rewalk_ms": 0.0, "collect_ms": 0.0}
     with torch.cuda.stream(stream):
         for _ in range(launches):
             flush.zero_()  # evict L2 between steps (outside the timed events)
-            e0, e1, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
             e0.record(stream)
             prob.level_walk(steps, stream)
             e1.record(stream)
             prob.level_rewalk(stream)
+            e2.record(stream)
             prob.level_collect(stream)  # synchronizes and checks claw candidates on the host
             e3.record(stream)
             e3.synchronize()
             step_ms.append(e0.elapsed_time(e3))
             walk_ms.append(e0.elapsed_time(e1))
+            split["walk_ms"] += e0.elapsed_time(e1)
+            split["rewalk_ms"] += e1.elapsed_time(e2)
+            split["collect_ms"] += e2.elapsed_time(e3)
     torch.cuda.synchronize()
+    timed_level.split = {k: v / max(1, launches) for k, v in split.items()}
     return step_ms, walk_ms, r0, prob.poll()
 
 
@@ -772,6 +789,7 @@ def run_ours(args):
     roof = walk_roofline(f"k_walks<{c['n']},{shape['launch_shape']}>", c["n"], w_steps, steps_done, walk_s,
                          args.steps, dp4a_per_s, clk.get("sm_mhz"), num_sms)
     roof["walk_kernel_share"] = walk_s / t_local
+    step_split = getattr(timed_level, "split", None) if world == 1 else None
     roof["imad_measured_gops"] = imad_per_s / 1e9
 
     e2e = None
@@ -826,6 +844,11 @@ def run_ours(args):
                            c_layout=["int8 byte quads (dp4a)", "32-bit words (IMAD)"][shape["c_layout"]]),
             "autotuned_level_shape": shape_trials, "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e, "clocks": clk,
             "gpu_launches": (5 if world > 1 else 2) * args.steps, "wall_s": wall,
+            "step_split_ms": dict(step_split or {}, note="per bench step: walk kernel; re-walk kernel and the "
+                                                         "reads of its results; host wait and exact checks of "
+                                                         "claw candidates"),
+            "headline_counts": {k: r1[k] - r0[k] for k in ("steps", "w_steps", "dps", "merges", "claws",
+                                                            "false_hash", "robin_hood", "rewalk_steps")},
         }
         if world > 1:
             line["config"]["parallelism"] = (f"DP-owner sharding over {world} ranks: one level, every rank walks "

@@ -393,9 +393,10 @@ typedef struct qcs_batch_params {
     int32_t launch_shape[4];  /* launch shape of the batched walk kernel for n = 1..4 qubits
                                  (index n - 1; 0 = default; see qcs_launch_shapes) */
     int32_t cert_points_log2; /* a round runs at most 2^cert_points_log2 points' worth of exhaustive-pass
-                                 work (a point with the contraction against C^ counts four), oldest job
-                                 first; a job whose pass is unfinished keeps it and is not walked that
-                                 round.  0: every pass a round starts runs to its end in that round */
+                                 work (a point with the contraction against C^ counts four), the job
+                                 with the least pass work left first (ties: the oldest); a job whose
+                                 pass is unfinished keeps it and is not walked that round.  0: every
+                                 pass a round starts runs to its end in that round */
 } qcs_batch_params;
 
 QCS_API void qcs_batch_default_params(qcs_batch_params *p);

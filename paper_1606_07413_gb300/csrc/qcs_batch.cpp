@@ -153,6 +153,23 @@ void next_level(Job &j)
     }
 }
 
+// Exhaustive-pass work the job still has at its current level, in the
+// streamed-point units of cert_advance (a point with the contraction against
+// C^ counts four); 0 when it runs no pass.
+uint64_t pass_work_left(const Job &j)
+{
+    const qcs_problem *P = j.P;
+    const int k = j.cert ? j.cert->k : j.k;
+    const uint64_t xi = (uint64_t)(P->D - 1), xi_h = upow(xi, k / 2);
+    const bool v_heavy = (k & 1) && P->C.E >= 1;
+    const uint64_t cs = v_heavy ? 4 : 1, cp = v_heavy ? 1 : 4;
+    if (j.cert) return (xi_h - j.cert->stored) * cs + (j.cert->n_probe - j.cert->probed) * cp;
+    const bool first =
+        P->p.exhaustive_first && j.need_begin && j.launches == 0 && j.k != j.cert_skip_k && exhaustive_eligible(P, k);
+    if (!first && !j.cert_after_walk) return 0;
+    return xi_h * cs + xi_h * ((k & 1) ? xi : 1) * cp;
+}
+
 // The job's exhaustive passes: exhaustive_first settles each qualifying level
 // by the pass alone, before any walk of it; a level whose walk budget ended
 // without a claw is settled by the pass before the next level.  A pass runs
@@ -552,15 +569,20 @@ int qcs_batch_round(qcs_batch *B, int *n_active)
     if (!B) return QCS_ERR_ARG;
     int rc;
     int active = 0, parked = 0;
-    // 1. exhaustive passes, oldest job first, within the round's share
+    // 1. exhaustive passes within the round's share, the job with the least
+    //    pass work left first (ties: the oldest), so that a long pass does
+    //    not hold back the short passes of jobs that arrived after it
     {
-        std::vector<size_t> order;
+        std::vector<std::pair<uint64_t, size_t>> order;
         for (size_t slot = 0; slot < B->jobs.size(); slot++)
-            if (B->jobs[slot].active) order.push_back(slot);
-        std::sort(order.begin(), order.end(),
-                  [B](size_t x, size_t y) { return B->jobs[x].seq < B->jobs[y].seq; });
+            if (B->jobs[slot].active) order.push_back({pass_work_left(B->jobs[slot]), slot});
+        std::sort(order.begin(), order.end(), [B](const std::pair<uint64_t, size_t> &x,
+                                                 const std::pair<uint64_t, size_t> &y) {
+            return x.first != y.first ? x.first < y.first : B->jobs[x.second].seq < B->jobs[y.second].seq;
+        });
         uint64_t budget = B->bp.cert_points_log2 > 0 ? (1ull << B->bp.cert_points_log2) : ~0ull;
-        for (size_t slot : order) {
+        for (const auto &o : order) {
+            const size_t slot = o.second;
             Job &j = B->jobs[slot];
             if ((rc = cert_work(B, j, &budget))) return rc;
             if (!j.active) { // settled by its pass

@@ -124,28 +124,38 @@ class Server:
         self.waiting = keep
 
     def _admit(self, block: bool = False):
+        """Admit waiting requests in arrival order while job slots are free.
+        A request that does not fit the free memory, or whose set-up is
+        still running, is passed over for now and later ones that fit are
+        admitted (backfilling), so one large job waiting for memory does not
+        hold back small ones; it keeps its place in the order."""
         self._drop_expired()
+        kept = collections.deque()
         while self.waiting and len(self.running) < self.slots:
-            r = self.waiting[0]
+            r = self.waiting.popleft()
             if not r.future.done() and not (block and not self.running):
-                break  # arrival order: wait for the head's set-up
+                kept.append(r)  # its set-up is still running
+                continue
             prob = r.future.result()
             need = self.batch.job_bytes(prob) + r.table_bytes
             if self.used + need > self.budget and self.running:
-                break  # memory is full: wait for a job to leave
+                kept.append(r)  # does not fit now: wait for memory, let later ones try
+                continue
             try:
                 slot = self.batch.add(prob)
             except Q.QcsError as e:
                 if e.code != Q.ERR_BUSY:
                     raise
+                kept.append(r)
                 break  # every job slot of the batch is taken (also by jobs added directly)
-            self.waiting.popleft()
             r.prob, r.bytes, r.slot = prob, need, slot
             r.t_admit = self.clock()
             r.status = "running"
             self.used += need
             self.peak_used = max(self.peak_used, self.used)
             self.running[r.slot] = r
+        kept.extend(self.waiting)
+        self.waiting = kept
 
     def _finish(self, r, status, result):
         r.status, r.result, r.t_done = status, result, self.clock()

@@ -190,3 +190,25 @@ def test_exhaustive_table_is_sized_for_the_requests_largest_eligible_level():
     assert serve.exhaustive_table_bytes(p26, 4, 5) == 16 << 17  # level 5: 255^2 stored
     assert serve.exhaustive_table_bytes(p32, 2, 3) == 16 << 10
     assert serve.exhaustive_table_bytes(SimpleNamespace(exhaustive_log2=0), 4, 7) == 0
+
+
+def test_a_request_waiting_for_memory_does_not_hold_back_smaller_ones(fake):
+    """Backfilling: with room for one n = 4 job (400 bytes) or two n = 2 jobs,
+    a second n = 4 request waits for memory while the n = 2 requests behind
+    it are admitted; it keeps its place and runs once memory frees."""
+    clock = Clock()
+    with serve.Server(bparams(4), memory_budget=650, clock=clock) as srv:
+        big1 = srv.submit(4, [[3, 0, 0]], 3)
+        big2 = srv.submit(4, [[3, 0, 0]], 3)
+        small = [srv.submit(2, [[1, 0, 0]], 2) for _ in range(2)]
+        for r in srv.requests.values():
+            r.future.result()
+        clock.t += 0.01
+        srv.step()
+        assert srv.poll(big1)["status"] == "running" and srv.poll(big2)["status"] == "queued"
+        assert all(srv.poll(r)["status"] in ("running", "found") for r in small[:1])
+        for _ in range(20):
+            clock.t += 0.01
+            srv.step()
+        assert all(srv.poll(r)["status"] == "found" for r in (big1, big2, *small))
+        assert srv.poll(small[0])["t_admit"] < srv.poll(big2)["t_admit"]
