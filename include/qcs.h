@@ -114,7 +114,10 @@ typedef struct qcs_params {
     int32_t exhaustive_first; /* 1: qcs_run_walks settles such levels by qcs_certify_level alone,
                                  without walking them (0: walk first) */
     int32_t launch_shape;     /* launch shape of the level-walk kernel, 0 .. qcs_launch_shapes(n) - 1
-                                 (0 = default); the walks and results do not depend on it */
+                                 (0 = default); the walks and results do not depend on it.  n = 4,
+                                 shape 3: the W side's contraction on the tensor cores (f16 byte
+                                 planes, exact f32 sums), two walks per warp, when C^ is held in int8
+                                 (c_layout 0); otherwise, and in a batch, it runs shape 0 */
     int32_t c_layout;         /* device layout of C^ for the W side's contraction (n >= 3): 0 = signed
                                  byte quads when every entry fits in int8 (dp4a), else 32-bit words;
                                  1 = 32-bit words always (IMAD).  Results do not depend on it */
@@ -164,7 +167,8 @@ typedef struct qcs_problem qcs_problem;
 /* Launch shapes of the walk kernels for n qubits (the autotuner's space; not
  * a passage of the paper: how walks map onto the GPU).  Returns the number
  * of shapes (>= 1) and fills, for shape i < max_shapes, warps[i] (warps per
- * CTA, each warp evaluating 32 / min(32, 4^n) walks) and min_blocks[i] (the
+ * CTA, each warp evaluating 32 / min(32, 4^n) walks; two at n = 4, shape 3)
+ * and min_blocks[i] (the
  * resident CTAs per SM the kernel is compiled for, capping its registers at
  * 65536 / (32 warps[i] min_blocks[i])).  Either pointer may be NULL.
  * QCS_ERR_ARG if n is not in 1..4. */

@@ -99,6 +99,7 @@ LevelCtx qcs::make_level(const qcs_problem *P, int k, uint32_t version, int dp_b
     LevelCtx lv{};
     lv.C32 = P->dC32;
     lv.Cq = reinterpret_cast<const uint4 *>(P->dCq);
+    lv.Cm = reinterpret_cast<const uint4 *>(P->dCm);
     lv.U = P->dU;
     for (int side = 0; side < 2; side++) lv.T1[side] = P->dT1[side];
     lv.coef = P->dCoef;
@@ -221,7 +222,7 @@ int upload_problem(qcs_problem *P)
     // n >= 3: also C^ as signed byte quads (rows 4q .. 4q+3 of a column in
     // one word) when every entry fits in int8, laid out for the walk
     // kernel's byte-plane contraction (LevelCtx::Cq)
-    std::vector<uint32_t> cq;
+    std::vector<uint32_t> cq, cm;
     if (n >= 3 && P->p.c_layout == 0) {
         bool fits = true;
         for (size_t i = 0; i < P->C.a.size() && fits; i++)
@@ -244,6 +245,23 @@ int upload_problem(qcs_problem *P)
                             cq[o] = wa;
                             cq[o + 1] = wb;
                         }
+            if (n == 4) {
+                // the tensor-core layout (LevelCtx::Cm): biased bytes, K-blocks of 16 rows
+                cm.assign((size_t)D * 2 * D / 4, 0);
+                auto entry = [&](int k, int col) -> uint32_t {
+                    const size_t src = (size_t)(k & (D - 1)) * D + col;
+                    return (uint32_t)(uint8_t)((k < D ? P->C.a[src] : P->C.b[src]) + 128);
+                };
+                for (int col = 0; col < D; col++)
+                    for (int kb = 0; kb < 2 * D / 16; kb++)
+                        for (int q = 0; q < 4; q++) {
+                            const int k0 = 16 * kb + 2 * q;
+                            const uint32_t w = entry(k0, col) | entry(k0 + 1, col) << 8 | entry(k0 + 8, col) << 16 |
+                                               entry(k0 + 9, col) << 24;
+                            const int chunk = (4 * (kb / 4) + q) ^ (4 * (col & 1));
+                            cm[(size_t)col * 128 + (size_t)chunk * 4 + (kb % 4)] = w;
+                        }
+            }
         }
     }
     CK(cudaGetDevice(&P->device));
@@ -253,6 +271,11 @@ int upload_problem(qcs_problem *P)
         CK(cudaMalloc(&P->dCq, sizeof(uint32_t) * cq.size()));
         CK(cudaMemcpy(P->dCq, cq.data(), sizeof(uint32_t) * cq.size(), cudaMemcpyHostToDevice));
         h2d += (int64_t)(sizeof(uint32_t) * cq.size());
+    }
+    if (!cm.empty()) {
+        CK(cudaMalloc(&P->dCm, sizeof(uint32_t) * cm.size()));
+        CK(cudaMemcpy(P->dCm, cm.data(), sizeof(uint32_t) * cm.size(), cudaMemcpyHostToDevice));
+        h2d += (int64_t)(sizeof(uint32_t) * cm.size());
     }
     CK(cudaMalloc(&P->dC32, sizeof(uint2) * c32.size()));
     CK(cudaMalloc(&P->dU, sizeof(uint2) * D));
@@ -285,7 +308,7 @@ int ensure_search_buffers(qcs_problem *P)
 
 void free_problem_memory(qcs_problem *P)
 {
-    cudaFree(P->dC32); cudaFree(P->dCq); cudaFree(P->dU); cudaFree(P->dCoef); cudaFree(P->dTable); cudaFree(P->dQueue); cudaFree(P->dQhead);
+    cudaFree(P->dC32); cudaFree(P->dCq); cudaFree(P->dCm); cudaFree(P->dU); cudaFree(P->dCoef); cudaFree(P->dTable); cudaFree(P->dQueue); cudaFree(P->dQhead);
     cudaFree(P->dCands); cudaFree(P->dWalks); cudaFree(P->dCounters); cudaFree(P->dPend[0]); cudaFree(P->dPend[1]);
     cudaFreeHost(P->hCounters); cudaFreeHost(P->hCands); cudaFreeHost(P->hQhead);
 }

@@ -40,6 +40,14 @@ struct LevelCtx {
     // Q0 = sub + 2 W j and Q1 = Q0 + W, the words (a-quad Q0, b-quad Q0,
     // a-quad Q1, b-quad Q1) (W, R as above).
     const uint4 *Cq;
+    // n = 4, when every entry of C^ fits in int8: C^ for the tensor-core
+    // contraction (launch shape 3 of k_walks<4>), else null.  K = 512 rows
+    // (the a-parts of rows 0..255, then the b-parts), N = 256 columns, each
+    // entry stored as the byte entry + 128.  Column n takes 512 bytes at
+    // n * 512: 16-byte chunk c = 4 s + q (s = K-block of 64, q = 0..3),
+    // stored at chunk c ^ (4 (n & 1)), holds for the four 16-row K-blocks
+    // kb = 4 s .. 4 s + 3 the bytes of rows 16 kb + 2q, 2q + 1, 2q + 8, 2q + 9.
+    const uint4 *Cm;
     const uint2 *U;    // fingerprint weights (Ua, Ub) per row, 4^n
     // The weights after the first adjoint stage of a side (index 0: V, 1: W),
     // mod 2^16, for every Pauli: entry e = q_a - 1, where q_a is the side's
@@ -318,6 +326,7 @@ struct qcs_problem {
     // device data
     uint2 *dC32 = nullptr, *dU = nullptr;
     uint32_t *dCq = nullptr; // n >= 3, when every entry of C^ fits in int8
+    uint32_t *dCm = nullptr; // n = 4, when every entry fits in int8: the tensor-core layout (LevelCtx::Cm)
     const uint32_t *dT1[2] = {nullptr, nullptr}; // shared stage tables
     uint32_t *dCoef = nullptr;
     qcs::Slot *dTable = nullptr;

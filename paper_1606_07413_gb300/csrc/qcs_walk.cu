@@ -24,6 +24,7 @@
 // one contraction of the transformed weights with C^, staged in shared memory
 // as signed byte quads and contracted by byte-plane dp4a.  The result is
 // bit-identical to hashing the explicitly formed product.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -71,7 +72,11 @@ constexpr int kGemvUnroll = QCS_GEMV_UNROLL;
 //   n <= 2: 8 warps
 //   n = 3 : (16, 2) (8, 4) (32, 1) (16, 1)
 //   n = 4 : (16, 1) (24, 1) (32, 1)   (one CTA per SM: C^ takes 128 KB)
-__host__ __device__ constexpr int shape_count(int nq) { return nq <= 2 ? 1 : nq == 3 ? 4 : 3; }
+//           and shape 3: 16 warps, two walks each, with the W side's
+//           contraction on the tensor cores (k_walks_mma4; the level walk
+//           only, and only when C^ is held in int8; elsewhere shape 3 runs
+//           shape 0)
+__host__ __device__ constexpr int shape_count(int nq) { return nq <= 2 ? 1 : 4; }
 __host__ __device__ constexpr int shape_warps(int nq, int s)
 {
     return nq <= 2 ? kWarps : nq == 3 ? (s == 1 ? 8 : s == 2 ? 32 : kWarps3) : (s == 1 ? 24 : s == 2 ? 32 : 16);
@@ -282,13 +287,15 @@ __device__ __forceinline__ Decoded decode(uint64_t x, const LevelCtx &lv)
     return d;
 }
 
-// nu and h of one decoded point: the exact product of side `side` (0: V,
-// 1: W) for the rotations in qpack (and the chunk, odd k), its column
-// fingerprints and their multiset hash with hash base `base`, as a
-// full 64-bit value.  All lanes of the group call it with the same point.
+// The fingerprint weights of one decoded point pushed through its side's
+// adjoint stages (row j = sub + LPW t in ua, ub): for V (side 0) the result is
+// already the column fingerprints, L(V e_Q) = ua[Q]; for W (side 1) it still
+// has to be contracted with C^.  All lanes of the group call it with the
+// same point.
 template <int NQ>
-__device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_t base, const LevelCtx &lv,
-                               const Smem<NQ> &sm, Lanes g)
+__device__ __forceinline__ void side_weights(int side, uint64_t qpack, uint32_t chunk, const LevelCtx &lv,
+                                             const Smem<NQ> &sm, Lanes g, uint32_t (&ua)[Geo<NQ>::RPL],
+                                             uint32_t (&ub)[Geo<NQ>::RPL])
 {
     using G = Geo<NQ>;
     const Decoded dx{side, qpack};
@@ -309,7 +316,6 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
         e = qa - 1;
         s0 = 1;
     }
-    uint32_t ua[G::RPL], ub[G::RPL];
 #pragma unroll
     for (int t = 0; t < G::RPL; t++) {
         const int j = lane + G::LPW * t;
@@ -324,7 +330,6 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
         }
     }
 
-    uint32_t Lc[G::RPL];
     if (dx.side == 0) {
         // V side at exponent K: S R^(q_h)..R^(q_1) with S = multiply by
         // sqrt2^ev.  Weights go through S^* and R^(q_h)^* .. R^(q_1)^*; S^*
@@ -339,14 +344,61 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
         }
         for (int j = h - 1 - s0; j >= 0; j--)
             adj_stage<NQ, false>((uint32_t)(dx.qpack >> (8 * j)) & 0xFFu, ua, ub, sm, g);
-#pragma unroll
-        for (int t = 0; t < G::RPL; t++) Lc[t] = ua[t]; // L(V e_Q) = (U~)_a[Q]
     } else {
         // W side: R^(q_1)^T .. R^(q_h)^T [R^(c)^T] C^; weights go through
         // (R^(q_1)^T)^* first, ..., (R^(q_h)^T)^*, then (R^(c)^T)^*.
         for (int j = s0; j < h; j++)
             adj_stage<NQ, true>((uint32_t)(dx.qpack >> (8 * j)) & 0xFFu, ua, ub, sm, g);
         if (lv.k & 1) adj_stage<NQ, true>(chunk, ua, ub, sm, g);
+    }
+}
+
+// The lane's share of the multiset hash: the sum mod 2^64 of
+// smix(base ^ phi_Q) over the lane's columns Q = sub + LPW t >= 1, phi_Q the
+// sign-folded 16-bit fingerprint of column Q (column 0, the identity, does
+// not enter).
+template <int NQ>
+__device__ __forceinline__ uint64_t lane_column_sum(const uint32_t (&Lc)[Geo<NQ>::RPL], uint64_t base, int lane)
+{
+    uint64_t acc = 0;
+#pragma unroll
+    for (int t = 0; t < Geo<NQ>::RPL; t++) {
+        const int Q = lane + Geo<NQ>::LPW * t;
+        const uint32_t l = Lc[t] & 0xFFFFu, nl = (0u - l) & 0xFFFFu;
+        const uint64_t e = smix(base ^ (uint64_t)min(l, nl));
+        acc += (Q >= 1) ? e : 0ull;
+    }
+    return acc;
+}
+
+// sum mod 2^64 over the lane group from three 32-bit reductions: the high
+// words (mod 2^32) and the two 16-bit halves of the low words (no overflow:
+// at most 32 terms)
+__device__ __forceinline__ uint64_t group_sum64(uint64_t acc, unsigned mask)
+{
+    const uint32_t lo = (uint32_t)acc, hi = (uint32_t)(acc >> 32);
+    const uint32_t s_hi = __reduce_add_sync(mask, hi);
+    const uint32_t s_l0 = __reduce_add_sync(mask, lo & 0xFFFFu);
+    const uint32_t s_l1 = __reduce_add_sync(mask, lo >> 16);
+    return ((uint64_t)s_hi << 32) + ((uint64_t)s_l1 << 16) + (uint64_t)s_l0;
+}
+
+// nu and h of one decoded point: the exact product of side `side` (0: V,
+// 1: W) for the rotations in qpack (and the chunk, odd k), its column
+// fingerprints and their multiset hash with hash base `base`, as a
+// full 64-bit value.  All lanes of the group call it with the same point.
+template <int NQ>
+__device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_t base, const LevelCtx &lv,
+                               const Smem<NQ> &sm, Lanes g)
+{
+    using G = Geo<NQ>;
+    const int lane = g.sub;
+    uint32_t ua[G::RPL], ub[G::RPL], Lc[G::RPL];
+    side_weights<NQ>(side, qpack, chunk, lv, sm, g, ua, ub);
+    if (side == 0) {
+#pragma unroll
+        for (int t = 0; t < G::RPL; t++) Lc[t] = ua[t]; // L(V e_Q) = (U~)_a[Q]
+    } else {
         uint2 *su = sm.xchg;
 #pragma unroll
         for (int t = 0; t < G::RPL; t++) {
@@ -407,26 +459,10 @@ __device__ uint64_t coset_hash(int side, uint64_t qpack, uint32_t chunk, uint64_
         __syncwarp(g.mask);
     }
 
-    // sign-invariant 16-bit column fingerprints phi_Q of the columns Q >= 1
-    // (column 0, the identity, does not enter), hashed as a multiset: the sum
-    // mod 2^64 of smix(base ^ phi_Q), a function of the multiset alone.  This
-    // lane holds the columns sub + LPW t.
-    uint64_t acc = 0;
-#pragma unroll
-    for (int t = 0; t < G::RPL; t++) {
-        const int Q = lane + G::LPW * t;
-        const uint32_t l = Lc[t] & 0xFFFFu, nl = (0u - l) & 0xFFFFu;
-        const uint64_t e = smix(base ^ (uint64_t)min(l, nl));
-        acc += (Q >= 1) ? e : 0ull;
-    }
-    // warp sum mod 2^64 from three 32-bit reductions: the high words (mod
-    // 2^32) and the two 16-bit halves of the low words (no overflow: 32 terms)
-    const uint32_t lo = (uint32_t)acc, hi = (uint32_t)(acc >> 32);
-    const uint32_t s_hi = __reduce_add_sync(g.mask, hi);
-    const uint32_t s_l0 = __reduce_add_sync(g.mask, lo & 0xFFFFu);
-    const uint32_t s_l1 = __reduce_add_sync(g.mask, lo >> 16);
-    acc = ((uint64_t)s_hi << 32) + ((uint64_t)s_l1 << 16) + (uint64_t)s_l0;
-    return smix(acc);
+    // sign-invariant 16-bit column fingerprints phi_Q of the columns Q >= 1,
+    // hashed as a multiset: the sum mod 2^64 of smix(base ^ phi_Q), a
+    // function of the multiset alone
+    return smix(group_sum64(lane_column_sum<NQ>(Lc, base, lane), g.mask));
 }
 
 // f(x): all lanes of the group call it with the same x; each gets the result.
@@ -673,6 +709,303 @@ __global__ void __launch_bounds__(Shape<NQ, S>::THREADS, Shape<NQ, S>::MIN_BLOCK
         if (walk < sw.n_walks) walk_one<NQ>(sw, sm, walk, g, t);
     }
     if (cur >= 0) flush_tally(sw.counters, t, g);
+}
+
+// ---- n = 4, launch shape 3: the W side's contraction on the tensor cores ----
+//
+// 32 walks per CTA (16 warps, two walks each) step in lockstep.  Each step:
+//  A. each warp evaluates its two walks' adjoint stages (side_weights).  A V
+//     walk's weights are already its column fingerprints: it hashes them into
+//     its shared sum at once.  A W walk takes the next row of the CTA's
+//     matrix product and writes its weights there as two byte planes in f16
+//     (bytes 0..255 are exact in f16);
+//  B. (barrier) each warp multiplies the W rows by its 16 columns of C^ with
+//     mma.sync m16n8k16 (f16 x f16, f32 accumulation), converting C^'s int8
+//     entries (exact in f16) fragment by fragment from shared memory, and
+//     hashes those columns of every W walk into the walk's shared sum;
+//  C. (barrier) each walk finishes its hash and takes its step.
+// Exactness: every product is an integer of magnitude below 2^15 (a byte
+// times an int8 entry), and every partial sum of a 512-term dot product is
+// below 512 x 255 x 128 < 2^24, so the f32 accumulation is exact and the
+// result converts back to the integer dot product; the fingerprint is then
+// L = P0 + 2^8 P1 (mod 2^16) from the two planes, as in the dp4a path.
+namespace mma4 {
+
+constexpr int kCtaWarps = 16, kThreads = kCtaWarps * 32, kWalks = 32; // two walks per warp
+constexpr int kDim = 256, kK = 2 * kDim;
+// shared memory: weights | rotation masks | chunk bases | 32 exchange
+// buffers (2 KB each; a W walk's two f16 planes after its stages) | C^ in
+// the tensor-core layout (128 KB) | per-step bookkeeping (two buffers)
+constexpr size_t off_coef = sizeof(uint2) * kDim;
+constexpr size_t off_base = off_coef + sizeof(uint32_t) * Geo<4>::COEF_WORDS;
+constexpr size_t off_xchg = off_base + sizeof(uint64_t) * Geo<4>::MAX_CHUNKS;
+constexpr size_t off_cm = off_xchg + (size_t)2048 * kWalks;
+constexpr size_t off_book = off_cm + (size_t)kK * kDim;
+struct Book {
+    unsigned long long sum[2][kWalks]; // per walk slot: the multiset hash's sum
+    uint64_t wbase[2][kWalks];         // per matrix row: the W walk's hash base
+    uint32_t wslot[2][kWalks];         // per matrix row: the W walk's slot
+    uint32_t nrows[2];                 // W walks (matrix rows) this step
+};
+constexpr size_t smem_bytes = off_book + sizeof(Book);
+static_assert(smem_bytes <= 227 * 1024, "shared memory of the tensor-core walk kernel");
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Two bytes to an f16 pair, exactly: the byte permute `sel` picks from
+// (lo16 & 0xFFFF) | hi16 << 16 the two bytes b and sets each half to 0x64b
+// (= 1024 + b in f16), then `bias` is subtracted (1024 for an unsigned byte;
+// 1152 for a signed byte stored with 128 added).
+__device__ __forceinline__ uint32_t bytes_to_f16x2(uint32_t lo16, uint32_t hi16, uint32_t sel, float bias)
+{
+    const uint32_t v = __byte_perm((lo16 & 0xFFFFu) | (hi16 << 16), 0x64646464u, sel);
+    __half2 h = *reinterpret_cast<const __half2 *>(&v);
+    h = __hsub2(h, __float2half2_rn(bias));
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&a)[4], uint32_t addr)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+                 : "r"(addr));
+}
+
+} // namespace mma4
+
+__global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
+{
+    using mma4::Book;
+    using mma4::kWalks;
+    using mma4::kK;
+    using mma4::kDim;
+    using G = Geo<4>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // weights, rotation masks and chunk bases as the other walk kernels stage them
+    Smem<4> sm = stage<4, false>(w.lv, smem_raw);
+    unsigned char *xchg = smem_raw + mma4::off_xchg;
+    unsigned char *cm = smem_raw + mma4::off_cm;
+    Book &bk = *reinterpret_cast<Book *>(smem_raw + mma4::off_book);
+    {
+        const uint4 *src = w.lv.Cm;
+        uint4 *dst = reinterpret_cast<uint4 *>(cm);
+        for (int i = threadIdx.x; i < kK * kDim / 16; i += blockDim.x) dst[i] = src[i];
+        for (int i = threadIdx.x; i < 2 * kWalks; i += blockDim.x) (&bk.sum[0][0])[i] = 0;
+        if (threadIdx.x < 2) bk.nrows[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Lanes g{lane, 0xFFFFFFFFu};
+    const int gq = lane >> 2, q = lane & 3; // MMA fragment coordinates
+    const LevelCtx &lv = w.lv;
+    const uint32_t steps = w.steps, max_len = w.max_len;
+    const int dshift = lv.dshift;
+    Tally t;
+    const int n_groups = (w.n_walks + kWalks - 1) / kWalks;
+    for (int grp = blockIdx.x; grp < n_groups; grp += gridDim.x) {
+        // this warp's two walks: slots 2 warp, 2 warp + 1 of the group
+        WalkState st[2];
+        bool live[2];
+        uint32_t gw[2];
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const int local = grp * kWalks + 2 * warp + i;
+            live[i] = local < w.n_walks;
+            gw[i] = w.walk_base + (uint32_t)local;
+            if (live[i]) st[i] = w.walks[local];
+        }
+        for (uint32_t step = 0; step < steps; step++) {
+            const int buf = step & 1;
+            // A. stages; V walks hash, W walks become matrix rows
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                if (!live[i]) continue;
+                const int slot = 2 * warp + i;
+                unsigned char *region = xchg + (size_t)2048 * slot;
+                sm.xchg = reinterpret_cast<uint2 *>(region);
+                const Decoded dx = decode(st[i].cur, lv);
+                const uint64_t base = sm.base[st[i].chunk];
+                uint32_t ua[G::RPL], ub[G::RPL];
+                side_weights<4>(dx.side, dx.qpack, st[i].chunk, lv, sm, g, ua, ub);
+                if (dx.side == 0) {
+                    const uint64_t sum = group_sum64(lane_column_sum<4>(ua, base, lane), 0xFFFFFFFFu);
+                    if (lane == 0) bk.sum[buf][slot] = sum;
+                    continue;
+                }
+                uint32_t row = 0;
+                if (lane == 0) {
+                    row = atomicAdd(&bk.nrows[buf], 1u);
+                    bk.wslot[buf][row] = (uint32_t)slot;
+                    bk.wbase[buf][row] = base;
+                }
+                row = __shfl_sync(0xFFFFFFFFu, row, 0);
+                // rows j = lane + 32 t of the weights to the region, then each
+                // lane converts rows 8 lane .. 8 lane + 7 into one 16-byte chunk
+                // per plane and part: plane p, K index k (a: j, b: 256 + j),
+                // chunk k / 8 stored at chunk (k / 8) ^ (row & 7)
+                uint2 *su = reinterpret_cast<uint2 *>(region);
+#pragma unroll
+                for (int tt = 0; tt < G::RPL; tt++) su[lane + 32 * tt] = make_uint2(ua[tt], ub[tt]);
+                __syncwarp();
+                const uint4 *s4 = reinterpret_cast<const uint4 *>(region) + 4 * lane;
+                const uint4 r0 = s4[0], r1 = s4[1], r2 = s4[2], r3 = s4[3]; // rows 8 lane .. 8 lane + 7
+                __syncwarp();
+                const uint32_t va[8] = {r0.x, r0.z, r1.x, r1.z, r2.x, r2.z, r3.x, r3.z};
+                const uint32_t vb[8] = {r0.y, r0.w, r1.y, r1.w, r2.y, r2.w, r3.y, r3.w};
+                uint4 out[4]; // (plane 0, a), (plane 1, a), (plane 0, b), (plane 1, b)
+                uint32_t *o = reinterpret_cast<uint32_t *>(out);
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    o[0 * 4 + e] = mma4::bytes_to_f16x2(va[2 * e], va[2 * e + 1], 0x7240, 1024.f);
+                    o[1 * 4 + e] = mma4::bytes_to_f16x2(va[2 * e], va[2 * e + 1], 0x7341, 1024.f);
+                    o[2 * 4 + e] = mma4::bytes_to_f16x2(vb[2 * e], vb[2 * e + 1], 0x7240, 1024.f);
+                    o[3 * 4 + e] = mma4::bytes_to_f16x2(vb[2 * e], vb[2 * e + 1], 0x7341, 1024.f);
+                }
+                const uint32_t swz = row & 7;
+                uint4 *d4 = reinterpret_cast<uint4 *>(region);
+                d4[0 * 64 + ((uint32_t)lane ^ swz)] = out[0];
+                d4[1 * 64 + ((uint32_t)lane ^ swz)] = out[1];
+                d4[0 * 64 + ((uint32_t)(32 + lane) ^ swz)] = out[2];
+                d4[1 * 64 + ((uint32_t)(32 + lane) ^ swz)] = out[3];
+            }
+            __syncthreads();
+            // B. the W rows times this warp's columns 16 warp .. 16 warp + 15
+            const uint32_t nrows = bk.nrows[buf];
+            if (nrows > 0) {
+                const int tiles = (int)(nrows + 15) / 16;
+                float acc[2][2][2][4]; // [row tile][plane][column tile][fragment]
+#pragma unroll
+                for (int a = 0; a < 2; a++)
+#pragma unroll
+                    for (int b = 0; b < 2; b++)
+#pragma unroll
+                        for (int c = 0; c < 2; c++)
+#pragma unroll
+                            for (int d = 0; d < 4; d++) acc[a][b][c][d] = 0.f;
+                // ldmatrix rows: lane l addresses row (l & 7) + 8 ((l >> 3) & 1) of
+                // the tile and K offset 8 (l >> 4)
+                const int mrow = (lane & 7) + 8 * ((lane >> 3) & 1), mkof = lane >> 4;
+                uint32_t arow[2], aswz[2];
+#pragma unroll
+                for (int tile = 0; tile < 2; tile++) {
+                    const uint32_t r = (uint32_t)(16 * tile + mrow);
+                    const uint32_t rr = r < nrows ? r : 0; // rows past the W walks read row 0 (results unused)
+                    arow[tile] = mma4::smem_u32(xchg + (size_t)2048 * bk.wslot[buf][rr]);
+                    aswz[tile] = rr & 7;
+                }
+                const unsigned char *ccol[2];
+#pragma unroll
+                for (int ct = 0; ct < 2; ct++) ccol[ct] = cm + (size_t)(16 * warp + 8 * ct + gq) * 512;
+                for (int s4i = 0; s4i < kK / 64; s4i++) {
+                    uint4 braw[2];
+#pragma unroll
+                    for (int ct = 0; ct < 2; ct++) {
+                        const int ncol = 16 * warp + 8 * ct + gq;
+                        const int chunk = (4 * s4i + q) ^ (4 * (ncol & 1));
+                        braw[ct] = *reinterpret_cast<const uint4 *>(ccol[ct] + 16 * chunk);
+                    }
+#pragma unroll
+                    for (int kk4 = 0; kk4 < 4; kk4++) {
+                        const int kb = 4 * s4i + kk4; // K-block of 16
+                        uint32_t b0[2], b1[2];
+#pragma unroll
+                        for (int ct = 0; ct < 2; ct++) {
+                            const uint32_t wd = kk4 == 0 ? braw[ct].x : kk4 == 1 ? braw[ct].y : kk4 == 2 ? braw[ct].z
+                                                                                                     : braw[ct].w;
+                            b0[ct] = mma4::bytes_to_f16x2(wd & 0xFFFFu, 0, 0x5140, 1152.f);
+                            b1[ct] = mma4::bytes_to_f16x2(wd >> 16, 0, 0x5140, 1152.f);
+                        }
+#pragma unroll
+                        for (int tile = 0; tile < 2; tile++) {
+                            if (tile < tiles) {
+#pragma unroll
+                                for (int p = 0; p < 2; p++) {
+                                    const uint32_t chunk = ((uint32_t)(2 * kb + mkof)) ^ aswz[tile];
+                                    uint32_t af[4];
+                                    mma4::ldmatrix_x4(af, arow[tile] + 1024 * p + 16 * chunk);
+#pragma unroll
+                                    for (int ct = 0; ct < 2; ct++)
+                                        mma4::mma16816(acc[tile][p][ct], af, b0[ct], b1[ct]);
+                                }
+                            }
+                        }
+                    }
+                }
+                // fingerprints of this warp's columns for every W row, hashed
+                // into the row's walk: rows gq and gq + 8 of each tile
+#pragma unroll
+                for (int tile = 0; tile < 2; tile++) {
+                    if (tile < tiles) {
+#pragma unroll
+                        for (int hh = 0; hh < 2; hh++) {
+                            const uint32_t r = (uint32_t)(16 * tile + gq + 8 * hh);
+                            const bool valid = r < nrows;
+                            const uint64_t base = valid ? bk.wbase[buf][r] : 0;
+                            uint64_t part = 0;
+#pragma unroll
+                            for (int ct = 0; ct < 2; ct++)
+#pragma unroll
+                                for (int c = 0; c < 2; c++) {
+                                    const int Q = 16 * warp + 8 * ct + 2 * q + c;
+                                    const int p0 = __float2int_rn(acc[tile][0][ct][2 * hh + c]);
+                                    const int p1 = __float2int_rn(acc[tile][1][ct][2 * hh + c]);
+                                    const uint32_t l = ((uint32_t)p0 + ((uint32_t)p1 << 8)) & 0xFFFFu;
+                                    const uint32_t nl = (0u - l) & 0xFFFFu;
+                                    const uint64_t e = smix(base ^ (uint64_t)min(l, nl));
+                                    part += (valid && Q >= 1) ? e : 0ull;
+                                }
+                            part += __shfl_xor_sync(0xFFFFFFFFu, part, 1);
+                            part += __shfl_xor_sync(0xFFFFFFFFu, part, 2);
+                            if (valid && q == 0) atomicAdd(&bk.sum[buf][bk.wslot[buf][r]], part);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // C. each walk's step
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                if (!live[i]) continue;
+                const int slot = 2 * warp + i;
+                const uint64_t y = smix(bk.sum[buf][slot]) & lv.maskL;
+                WalkState &S = st[i];
+                t.steps++;
+                t.w += S.cur & 1;
+                S.len++;
+                if ((y >> dshift) == 0) {
+                    t.dp++;
+                    if (lane == 0) dp_insert(w, y, make_ref(gw[i], S.seq, S.len), t);
+                    __syncwarp();
+                    new_trail(S, gw[i], lv);
+                } else if (S.len >= max_len) {
+                    t.ab++;
+                    new_trail(S, gw[i], lv);
+                } else {
+                    S.cur = y;
+                }
+            }
+            // clear this buffer for the step after next (the next step uses the other one)
+            __syncwarp();
+            if (lane < 2) bk.sum[buf][2 * warp + lane] = 0;
+            if (threadIdx.x == 0) bk.nrows[buf] = 0;
+        }
+        __syncthreads(); // the next group's first step may reuse this group's last buffer
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+            if (live[i] && lane == 0) w.walks[grp * kWalks + 2 * warp + i] = st[i];
+    }
+    flush_tally(w.counters, t, g);
 }
 
 __global__ void k_init_walks(WalkLaunch w)
@@ -1112,6 +1445,24 @@ cudaError_t walks_ns(const WalkLaunch &w, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// the tensor-core level walk (n = 4, launch shape 3): one CTA per SM
+cudaError_t walks_mma4(const WalkLaunch &w, cudaStream_t s)
+{
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaFuncSetAttribute(k_walks_mma4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mma4::smem_bytes);
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walks_mma4, mma4::kThreads, mma4::smem_bytes);
+        per_sm = b > 0 ? b : 1;
+    }
+    const size_t groups = ((size_t)w.n_walks + mma4::kWalks - 1) / mma4::kWalks;
+    size_t grid = (size_t)num_sms() * (size_t)per_sm;
+    if (grid > groups) grid = groups;
+    if (grid == 0) grid = 1;
+    k_walks_mma4<<<(unsigned)grid, mma4::kThreads, mma4::smem_bytes, s>>>(w);
+    return cudaGetLastError();
+}
+
 template <int NQ>
 cudaError_t walks_n(const WalkLaunch &w, cudaStream_t s)
 {
@@ -1119,7 +1470,10 @@ cudaError_t walks_n(const WalkLaunch &w, cudaStream_t s)
     case 0: return walks_ns<NQ, 0>(w, s);
     case 1: if constexpr (shape_count(NQ) > 1) return walks_ns<NQ, 1>(w, s); break;
     case 2: if constexpr (shape_count(NQ) > 2) return walks_ns<NQ, 2>(w, s); break;
-    case 3: if constexpr (shape_count(NQ) > 3) return walks_ns<NQ, 3>(w, s); break;
+    case 3:
+        if constexpr (NQ == 4) return w.lv.Cm ? walks_mma4(w, s) : walks_ns<4, 0>(w, s);
+        else if constexpr (shape_count(NQ) > 3) return walks_ns<NQ, 3>(w, s);
+        break;
     }
     return cudaErrorInvalidValue;
 }
@@ -1154,7 +1508,10 @@ cudaError_t walks_batch_n(int shape, const BatchArgs &a, cudaStream_t s)
     case 0: return walks_batch_ns<NQ, 0>(a, s);
     case 1: if constexpr (shape_count(NQ) > 1) return walks_batch_ns<NQ, 1>(a, s); break;
     case 2: if constexpr (shape_count(NQ) > 2) return walks_batch_ns<NQ, 2>(a, s); break;
-    case 3: if constexpr (shape_count(NQ) > 3) return walks_batch_ns<NQ, 3>(a, s); break;
+    case 3:
+        if constexpr (NQ == 4) return walks_batch_ns<4, 0>(a, s); // no batched tensor-core form
+        else if constexpr (shape_count(NQ) > 3) return walks_batch_ns<NQ, 3>(a, s);
+        break;
     }
     return cudaErrorInvalidValue;
 }

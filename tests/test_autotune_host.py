@@ -91,7 +91,7 @@ class ShapedBatch(FakeBatch):
     on the C^ layout of its jobs: n = 3 is fastest with shape 2 and int8
     quads, n = 4 with shape 1 and 32-bit words."""
 
-    COST = {2: [1.0], 3: [3.0, 2.5, 1.0, 4.0], 4: [5.0, 4.0, 6.0]}
+    COST = {2: [1.0], 3: [3.0, 2.5, 1.0, 4.0], 4: [5.0, 4.0, 6.0, 4.5]}
 
     def add(self, p):
         p.layout = p.params_layout
@@ -120,6 +120,6 @@ def test_tuner_picks_each_qubit_counts_fastest_shape_and_layout(monkeypatch):
     grid = {"walks_per_job": (512,), "steps_per_round": (16,), "theta_min_bits": (1,), "queue_capacity": (4096,)}
     best, trials = autotune.tune_batch(targets, rounds=4, grid=grid)
     assert best["launch_shape"] == {3: 2, 4: 1} and best["c_layout"] == {3: 0, 4: 1}
-    # one host trial, then every (shape, layout) pair of n = 3 (4 x 2) and n = 4 (3 x 2)
-    assert len(trials) == 1 + 8 + 6
+    # one host trial, then every (shape, layout) pair of n = 3 (4 x 2) and n = 4 (4 x 2)
+    assert len(trials) == 1 + 8 + 8
     assert [s["shape"] for s in Q.launch_shapes(3)] == [0, 1, 2, 3]
