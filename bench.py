@@ -40,10 +40,11 @@ sys.path.insert(0, ROOT)
 CFG = 3
 K_LEVEL = 7
 STEPS_PER_LAUNCH = 64
-# evaluations of f one merge's re-walk may take per bench step; longer
-# re-walks continue in the next step (the level walk's pipeline), so a step
-# is not held up by the one longest trail pair
-REWALK_BUDGET = 1024
+# evaluations of f one merge's re-walk may take per bench step (0: none).
+# The headline re-walks every merge of a step to its end within that step, so
+# no classification work is carried past the timed steps; the budgeted,
+# carried re-walk (params.rewalk_budget) is the library's option for long runs.
+REWALK_BUDGET = 0
 FLUSH_BYTES = 256 << 20
 LEVELS = {1: 3, 2: 5, 3: 7}  # the level each configuration's construction T-count puts its claw on
 
@@ -471,7 +472,7 @@ TTO_TABLES = {1: (16, 20), 2: (22, 20), 3: (30, 24)}
 
 
 def time_to_optimal(Q, W, stream, cfg, mode="walk", table_log2=None, queue_log2=None, limit_s=900, unitary=None,
-                    dp_bits=None):
+                    dp_bits=None, seed=None):
     """Time to the optimal T-count of a configuration's seeded target (or of
     the given n-qubit unitary, Z[omega] coefficients over sqrt2^0), through
     the public API (qcs_create_problem_circuit, qcs_run_walks, qcs_wait).
@@ -489,6 +490,8 @@ def time_to_optimal(Q, W, stream, cfg, mode="walk", table_log2=None, queue_log2=
         p = Q.default_params(n, exhaustive_first=1, exhaustive_log2=34)
     else:
         extra = {"theta_policy": 0, "dp_bits": dp_bits} if dp_bits else {}
+        if seed is not None:
+            extra["seed"] = seed
         p = Q.default_params(n, table_log2=table_log2, queue_capacity=1 << queue_log2, exhaustive_log2=0, **extra)
     t0 = time.perf_counter()
     if unitary is None:
@@ -946,10 +949,14 @@ def run_tto_sweep(args):
     B.build()
     stream = torch.cuda.Stream()
     out = []
-    for table_log2, dp_bits in ((30, None), (30, 2), (30, 3), (28, None), (32, None), (33, None)):
-        r = time_to_optimal(Q, W, stream, 3, "walk", table_log2, limit_s=240, dp_bits=dp_bits)
-        out.append(r)
-        print(json.dumps(r), file=sys.stderr)
+    # each (table, theta) with three walk seeds: one seeded trajectory is a
+    # single draw of a random search's time
+    for table_log2, dp_bits in ((28, None), (30, None), (30, 2), (32, None)):
+        for seed in (0x2545F4914F6CDD1D, 11, 12):
+            r = time_to_optimal(Q, W, stream, 3, "walk", table_log2, limit_s=240, dp_bits=dp_bits, seed=seed)
+            r["seed"] = seed
+            out.append(r)
+            print(json.dumps(r), file=sys.stderr)
     print(json.dumps({"tto_walk_cfg3_sweep": out}))
 
 
