@@ -468,7 +468,7 @@ def table1_circuits(Q, W, stream, trials=10):
 
 # table of the collision walk for time-to-optimal runs per configuration:
 # (table_log2, queue_log2); the level-7 walk at n = 4 gets 16 GiB of table
-TTO_TABLES = {1: (16, 20), 2: (22, 20), 3: (30, 24)}
+TTO_TABLES = {1: (16, 20), 2: (22, 20), 3: (28, 24)}
 
 
 def time_to_optimal(Q, W, stream, cfg, mode="walk", table_log2=None, queue_log2=None, limit_s=900, unitary=None,
