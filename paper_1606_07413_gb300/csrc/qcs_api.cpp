@@ -248,8 +248,12 @@ int upload_problem(qcs_problem *P)
             if (n == 4) {
                 // the tensor-core layout (LevelCtx::Cm): biased bytes, K-blocks of 16 rows
                 cm.assign((size_t)D * 2 * D / 4, 0);
+                // K index k = part * 256 + 8 l + t holds row 32 t + l of the a-part
+                // (part 0) or b-part (part 1): the eight rows one lane of the
+                // walk kernel holds form one K chunk of eight
                 auto entry = [&](int k, int col) -> uint32_t {
-                    const size_t src = (size_t)(k & (D - 1)) * D + col;
+                    const int kk = k & (D - 1), row = (kk % 8) * 32 + kk / 8;
+                    const size_t src = (size_t)row * D + col;
                     return (uint32_t)(uint8_t)((k < D ? P->C.a[src] : P->C.b[src]) + 128);
                 };
                 for (int col = 0; col < D; col++)

@@ -42,8 +42,9 @@ struct LevelCtx {
     const uint4 *Cq;
     // n = 4, when every entry of C^ fits in int8: C^ for the tensor-core
     // contraction (launch shape 3 of k_walks<4>), else null.  K = 512 rows
-    // (the a-parts of rows 0..255, then the b-parts), N = 256 columns, each
-    // entry stored as the byte entry + 128.  Column n takes 512 bytes at
+    // (the a-parts of the 256 rows, then the b-parts; within a part, K index
+    // 8 l + t is row 32 t + l), N = 256 columns, each entry stored as the
+    // byte entry + 128.  Column n takes 512 bytes at
     // n * 512: 16-byte chunk c = 4 s + q (s = K-block of 64, q = 0..3),
     // stored at chunk c ^ (4 (n & 1)), holds for the four 16-row K-blocks
     // kb = 4 s .. 4 s + 3 the bytes of rows 16 kb + 2q, 2q + 1, 2q + 8, 2q + 9.

@@ -755,13 +755,13 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Two bytes to an f16 pair, exactly: the byte permute `sel` picks from
-// (lo16 & 0xFFFF) | hi16 << 16 the two bytes b and sets each half to 0x64b
-// (= 1024 + b in f16), then `bias` is subtracted (1024 for an unsigned byte;
-// 1152 for a signed byte stored with 128 added).
-__device__ __forceinline__ uint32_t bytes_to_f16x2(uint32_t lo16, uint32_t hi16, uint32_t sel, float bias)
+// Two bytes of `word` to an f16 pair, exactly: the byte permute `sel` puts
+// them in the low bytes of the two halves under 0x64 (0x64b = 1024 + b in
+// f16), then `bias` is subtracted (1024 for an unsigned byte; 1152 for a
+// signed byte stored with 128 added).
+__device__ __forceinline__ uint32_t bytes_to_f16x2(uint32_t word, uint32_t sel, float bias)
 {
-    const uint32_t v = __byte_perm((lo16 & 0xFFFFu) | (hi16 << 16), 0x64646464u, sel);
+    const uint32_t v = __byte_perm(word, 0x64646464u, sel);
     __half2 h = *reinterpret_cast<const __half2 *>(&v);
     h = __hsub2(h, __float2half2_rn(bias));
     return *reinterpret_cast<const uint32_t *>(&h);
@@ -850,27 +850,21 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
                     bk.wbase[buf][row] = base;
                 }
                 row = __shfl_sync(0xFFFFFFFFu, row, 0);
-                // rows j = lane + 32 t of the weights to the region, then each
-                // lane converts rows 8 lane .. 8 lane + 7 into one 16-byte chunk
-                // per plane and part: plane p, K index k (a: j, b: 256 + j),
-                // chunk k / 8 stored at chunk (k / 8) ^ (row & 7)
-                uint2 *su = reinterpret_cast<uint2 *>(region);
-#pragma unroll
-                for (int tt = 0; tt < G::RPL; tt++) su[lane + 32 * tt] = make_uint2(ua[tt], ub[tt]);
-                __syncwarp();
-                const uint4 *s4 = reinterpret_cast<const uint4 *>(region) + 4 * lane;
-                const uint4 r0 = s4[0], r1 = s4[1], r2 = s4[2], r3 = s4[3]; // rows 8 lane .. 8 lane + 7
-                __syncwarp();
-                const uint32_t va[8] = {r0.x, r0.z, r1.x, r1.z, r2.x, r2.z, r3.x, r3.z};
-                const uint32_t vb[8] = {r0.y, r0.w, r1.y, r1.w, r2.y, r2.w, r3.y, r3.w};
+                // The K order of the product (as C^ is stored for it) makes the
+                // lane's own rows j = lane + 32 t, t = 0..7, the 16-byte chunk
+                // `lane` of each part (a: chunk lane, b: chunk 32 + lane) and
+                // plane; chunk c is stored at c ^ (row & 7).  The region's
+                // stage exchange is done (side_weights ends with a warp sync).
                 uint4 out[4]; // (plane 0, a), (plane 1, a), (plane 0, b), (plane 1, b)
                 uint32_t *o = reinterpret_cast<uint32_t *>(out);
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
-                    o[0 * 4 + e] = mma4::bytes_to_f16x2(va[2 * e], va[2 * e + 1], 0x7240, 1024.f);
-                    o[1 * 4 + e] = mma4::bytes_to_f16x2(va[2 * e], va[2 * e + 1], 0x7341, 1024.f);
-                    o[2 * 4 + e] = mma4::bytes_to_f16x2(vb[2 * e], vb[2 * e + 1], 0x7240, 1024.f);
-                    o[3 * 4 + e] = mma4::bytes_to_f16x2(vb[2 * e], vb[2 * e + 1], 0x7341, 1024.f);
+                    const uint32_t wa = (ua[2 * e] & 0xFFFFu) | (ua[2 * e + 1] << 16);
+                    const uint32_t wb = (ub[2 * e] & 0xFFFFu) | (ub[2 * e + 1] << 16);
+                    o[0 * 4 + e] = mma4::bytes_to_f16x2(wa, 0x7240, 1024.f);
+                    o[1 * 4 + e] = mma4::bytes_to_f16x2(wa, 0x7341, 1024.f);
+                    o[2 * 4 + e] = mma4::bytes_to_f16x2(wb, 0x7240, 1024.f);
+                    o[3 * 4 + e] = mma4::bytes_to_f16x2(wb, 0x7341, 1024.f);
                 }
                 const uint32_t swz = row & 7;
                 uint4 *d4 = reinterpret_cast<uint4 *>(region);
@@ -907,6 +901,7 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
                 const unsigned char *ccol[2];
 #pragma unroll
                 for (int ct = 0; ct < 2; ct++) ccol[ct] = cm + (size_t)(16 * warp + 8 * ct + gq) * 512;
+#pragma unroll 2
                 for (int s4i = 0; s4i < kK / 64; s4i++) {
                     uint4 braw[2];
 #pragma unroll
@@ -923,8 +918,8 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
                         for (int ct = 0; ct < 2; ct++) {
                             const uint32_t wd = kk4 == 0 ? braw[ct].x : kk4 == 1 ? braw[ct].y : kk4 == 2 ? braw[ct].z
                                                                                                      : braw[ct].w;
-                            b0[ct] = mma4::bytes_to_f16x2(wd & 0xFFFFu, 0, 0x5140, 1152.f);
-                            b1[ct] = mma4::bytes_to_f16x2(wd >> 16, 0, 0x5140, 1152.f);
+                            b0[ct] = mma4::bytes_to_f16x2(wd, 0x4140, 1152.f); // rows 2q, 2q + 1
+                            b1[ct] = mma4::bytes_to_f16x2(wd, 0x4342, 1152.f); // rows 2q + 8, 2q + 9
                         }
 #pragma unroll
                         for (int tile = 0; tile < 2; tile++) {
