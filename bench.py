@@ -103,15 +103,17 @@ def workload_config(c, k=None, steps=None, rewalk_budget=None):
 # holds only for the kernel source it was captured on (hash of the walk
 # kernel's source files, comments and layout removed); otherwise its figures
 # are reported as null.
-# k_walks<4,0>: `ncu --set full` of `bench.py --level-only n4_level7 --steps 2`
-# (2^20 walks x 16 steps: 3.2367e10 warp instructions, 34.57 MB read and
-# 0.47 MB written).  The launch's DRAM traffic is the walk states and the
-# staged tables, which do not grow with the steps, plus 32 bytes per
-# distinguished point (0.5 MB at the headline's 64 steps), so the figure
-# stands for the headline launch (profiles/k_walks_n4_level7_walks1048576.md).
+# Each n = 4 record: `ncu --set full` of `bench.py --level-only n4_level7
+# --steps 2 --shape S` (2^20 walks x 16 steps; profiles/k_walks_n4_level7_walks1048576.md
+# and profiles/k_walks_mma4_n4_level7_walks1048576.md).  The launch's DRAM
+# traffic is the walk states and the staged tables, which do not grow with
+# the steps, plus 32 bytes per distinguished point (0.5 MB at the headline's
+# 64 steps), so the figure stands for the headline launch.
 WALK_NCU = {
-    "k_walks<4,0>": {"source_sha256_16": "7fcffe814850e398", "dram_bytes_per_launch": 35037184,
-                     "warp_inst_per_step": 1929.2},
+    "k_walks<4,3>": {"source_sha256_16": "4e8df376b16b6e50", "dram_bytes_per_launch": 34637824,
+                     "warp_inst_per_step": 1365.6},
+    "k_walks<4,0>": {"source_sha256_16": "4e8df376b16b6e50", "dram_bytes_per_launch": 35011072,
+                     "warp_inst_per_step": 1939.1},
     "k_walks<3,0>": {"source_sha256_16": None, "dram_bytes_per_launch": None, "warp_inst_per_step": None},
 }
 
@@ -154,7 +156,7 @@ def ncu_record(kernel: str):
     return rec
 
 
-def walk_roofline(kernel, n, w_steps, steps, walk_s, launches, dp4a_per_s, clock_mhz, num_sms):
+def walk_roofline(kernel, n, w_steps, steps, walk_s, launches, dp4a_per_s, clock_mhz, num_sms, hmma_per_s=None):
     """Roofline of a walk kernel ("bound": "alu").  achieved = the W side's
     contraction multiply-adds (W-side steps x 2 d^2, d = 4^n - 1: 16-bit
     fingerprint weights times C^) per second of the kernel's CUDA-event time;
@@ -180,8 +182,15 @@ def walk_roofline(kernel, n, w_steps, steps, walk_s, launches, dp4a_per_s, clock
         issue = {"warp_inst_per_step": rec["warp_inst_per_step"], "achieved_per_s": issue_rate,
                  "peak_per_s": issue_peak, "frac": issue_rate / issue_peak,
                  "peak_source": f"{num_sms} SMs x 4 schedulers x {clock_mhz:.0f} MHz (median sampled SM clock)"}
+    tensor = None
+    if hmma_per_s and kernel == "k_walks<4,3>":
+        # the tensor-core shape: each 16-bit-weight multiply-add is two f16
+        # byte-plane multiply-adds on the MMA pipe
+        tensor = {"achieved_mac_per_s": 2 * achieved, "peak_mac_per_s": hmma_per_s,
+                  "frac": 2 * achieved / hmma_per_s,
+                  "peak_source": "measured mma.sync m16n8k16 f16 -> f32 rate (qcs_peak_hmma, this run)"}
     return {"bound": "alu", "unit": "Gop/s", "kernel": kernel,
-            "achieved": achieved / 1e9, "peak": peak / 1e9, "frac": achieved / peak,
+            "achieved": achieved / 1e9, "peak": peak / 1e9, "frac": achieved / peak, "tensor": tensor,
             "traffic": traffic, "traffic_unit": "bytes per launch", "hbm": hbm, "issue_slots": issue,
             "peak_source": "2 x measured dp4a rate (qcs_peak_idp4a, this run: "
                            f"{dp4a_per_s / 1e9:.0f} G dp4a/s)",
@@ -752,6 +761,7 @@ def run_ours(args):
     Q.measure_int_peak("imad", 8, 512)
     imad_per_s, _ = Q.measure_int_peak("imad", 8, 4096)
     dp4a_per_s, _ = Q.measure_int_peak("idp4a", 8, 4096)
+    hmma_per_s, _ = Q.measure_int_peak("hmma", 4, 512)
 
     # launch shape and C^ layout of the level walk, chosen by the autotuner on
     # this level (the walks are the same under every choice)
@@ -790,7 +800,7 @@ def run_ours(args):
     value = steps_all / t_all
     walk_s = sum(walk_ms) / 1e3 if walk_ms else t_local  # sharded rounds time the whole round
     roof = walk_roofline(f"k_walks<{c['n']},{shape['launch_shape']}>", c["n"], w_steps, steps_done, walk_s,
-                         args.steps, dp4a_per_s, clk.get("sm_mhz"), num_sms)
+                         args.steps, dp4a_per_s, clk.get("sm_mhz"), num_sms, hmma_per_s)
     roof["walk_kernel_share"] = walk_s / t_local
     step_split = getattr(timed_level, "split", None) if world == 1 else None
     roof["imad_measured_gops"] = imad_per_s / 1e9

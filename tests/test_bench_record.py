@@ -1,15 +1,15 @@
-"""The committed benchmark record (profiles/bench_n3_level5_walks65536.json)
+"""The committed benchmark record (profiles/bench_n4_level7_walks1048576.json)
 is one JSON line of bench.py's contract, internally consistent: the
 roofline fraction is achieved / peak, the reported DRAM traffic belongs to
-the walk-kernel source it was captured on, the clocks saw no throttling, and
-the end-to-end figure moved bytes each step."""
+the walk-kernel source it was captured on, the clocks saw no throttling, the
+end-to-end figure moved bytes each step, and the step's split adds up."""
 import json
 import os
 
 import bench
 
 RECORD = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "profiles",
-                      "bench_n3_level5_walks65536.json")
+                      "bench_n4_level7_walks1048576.json")
 
 
 def load():
@@ -27,7 +27,8 @@ def test_record_has_the_contract_keys():
         assert key in r, key
     assert r["metric"] == "walk_steps_per_sec" and r["unit"] == "walk_steps/s" and r["higher_is_better"]
     assert r["warmup"] >= 3 and r["steps"] >= 1 and r["gpu_launches"] > 0
-    assert r["config"]["workload"].startswith("n3_t5_level5")
+    assert r["config"]["workload"].startswith("n4_t7_level7_walks1048576_L64")
+    assert r["config"]["workload"].split("_")[2] == "level7" and r["config"]["dp_bits"] == 12
 
 
 def test_roofline_and_timing_are_consistent():
@@ -52,3 +53,15 @@ def test_clocks_and_e2e():
     assert e2e["unit"] == r["unit"] and e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
     cpu = r["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] > 0
+
+
+def test_step_split_and_extras():
+    r = load()
+    sp = r["step_split_ms"]
+    assert abs(sp["walk_ms"] + sp["rewalk_ms"] + sp["collect_ms"] - r["ms_per_step"]) / r["ms_per_step"] < 0.02
+    for key in ("tto_walk_cfg1", "tto_walk_cfg2", "tto_walk_cfg3"):
+        t = r[key]
+        assert t["mode"] == "walk" and t["status"] == "found" and t["exhaustive_points"] == 0
+    s = r["serving"]
+    assert 0 <= s["miss_rate"] < 1 and s["p99_all_s"] >= s["p50_all_s"]
+    assert sum(s["status_counts"].values()) == 2000
