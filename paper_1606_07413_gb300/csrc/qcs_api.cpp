@@ -298,7 +298,7 @@ int ensure_search_buffers(qcs_problem *P)
     const size_t slots = (size_t)1 << P->p.table_log2;
     CK(cudaMalloc(&P->dTable, sizeof(Slot) * slots));
     CK(cudaMalloc(&P->dQueue, sizeof(Pair) * (size_t)P->p.queue_capacity));
-    CK(cudaMalloc(&P->dQhead, 3 * sizeof(uint32_t)));
+    CK(cudaMalloc(&P->dQhead, 4 * sizeof(uint32_t))); // merges, candidates, carried re-walks, re-walk cursor
     if (P->p.rewalk_budget > 0)
         for (int i = 0; i < 2; i++) CK(cudaMalloc(&P->dPend[i], sizeof(Pending) * (size_t)P->p.queue_capacity));
     CK(cudaMalloc(&P->dCands, sizeof(Cand) * kCandCap));
@@ -464,6 +464,8 @@ int level_rewalk(qcs_problem *P, cudaStream_t s)
         w.pend_cap = (uint32_t)P->p.queue_capacity;
         CK(cudaMemsetAsync(P->dQhead + 2, 0, sizeof(uint32_t), s));
     }
+    w.rw_next = P->dQhead + 3;
+    CK(cudaMemsetAsync(P->dQhead + 3, 0, sizeof(uint32_t), s));
     CK(launch_rewalk_pairs(w, s));
     CK(cudaMemcpyAsync(P->hCounters, P->dCounters, sizeof(unsigned long long) * C_NCOUNTERS,
                        cudaMemcpyDeviceToHost, s));

@@ -164,6 +164,9 @@ struct WalkLaunch {
     uint32_t ocap;
     Slot *outbox;
     uint32_t *ohead;
+    // single-target re-walk: merges are claimed from this device counter
+    // (zeroed before the launch); null: a fixed stride (the batched re-walk)
+    uint32_t *rw_next;
 };
 
 // Many jobs in one launch: per qubit count, the device list of tasks
@@ -332,7 +335,7 @@ struct qcs_problem {
     uint32_t *dCoef = nullptr;
     qcs::Slot *dTable = nullptr;
     qcs::Pair *dQueue = nullptr;
-    uint32_t *dQhead = nullptr; // [0] queued merges, [1] claw candidates, [2] carried re-walks
+    uint32_t *dQhead = nullptr; // [0] queued merges, [1] claw candidates, [2] carried re-walks, [3] re-walk cursor
     qcs::Pending *dPend[2] = {nullptr, nullptr}; // carried re-walks (params.rewalk_budget > 0)
     qcs::Cand *dCands = nullptr;
     qcs::WalkState *dWalks = nullptr;

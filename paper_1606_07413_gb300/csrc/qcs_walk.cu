@@ -97,7 +97,6 @@ __device__ __forceinline__ uint64_t smix(uint64_t z)
 template <int NQ>
 struct Geo {
     static constexpr int DIM = 1 << (2 * NQ);            // 4^n rows and columns
-    static constexpr int D = DIM - 1;                    // non-identity Paulis
     // one walk is evaluated by LPW consecutive lanes of a warp (4^n lanes for
     // n <= 2, QCS_LPW3 at n = 3, the whole warp at n = 4), GROUPS walks per warp
     static constexpr int LPW = DIM < 32 ? DIM : (NQ == 3 ? QCS_LPW3 : 32);
@@ -111,7 +110,6 @@ struct Geo {
     static constexpr int WARPS = NQ == 4 ? 16 : NQ == 3 ? kWarps3 : kWarps; // warps per CTA
     static constexpr int THREADS = WARPS * 32;
     static constexpr int WALKS = WARPS * GROUPS;         // walks (lane groups) per CTA
-    static constexpr int MIN_BLOCKS = NQ == 3 ? QCS_MIN_BLOCKS3 : 1;
     static constexpr int QUAD_UNROLL = NQ == 4 ? QCS_QUAD_UNROLL4 : QCS_QUAD_UNROLL3;
     static constexpr int COEF_WORDS = DIM * 2 * RPL;     // rotation coefficient bits
     static constexpr int MAX_CHUNKS = 256;               // hash bases, one per chunk
@@ -1161,13 +1159,21 @@ __device__ RewalkOut rewalk_one(const LevelCtx &lv, uint32_t chunk, uint64_t sa,
 
 // Re-walk this CTA's share of one job's queued merges; classes are counted
 // per lane group and claw candidates appended to the job's candidate list.
+// With `cursor` set, the lane groups take merges one at a time from that
+// device counter instead of by a fixed stride, so that a few long trail
+// pairs do not leave the rest of the grid idle.
 template <int NQ, typename WL>
 __device__ __forceinline__ void rewalk_job(const WL &w, const Smem<NQ> &sm, uint32_t p_begin, uint32_t p_end,
-                                           uint32_t p_stride, Lanes g)
+                                           uint32_t p_stride, Lanes g, uint32_t *cursor = nullptr)
 {
     unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0; // per class, in registers
     unsigned long long fev = 0;
-    for (uint32_t p = p_begin; p < p_end; p += p_stride) {
+    auto claim = [&]() -> uint32_t {
+        uint32_t v = 0;
+        if (g.sub == 0) v = atomicAdd(cursor, 1u);
+        return __shfl_sync(g.mask, v, 0, Geo<NQ>::LPW);
+    };
+    for (uint32_t p = cursor ? claim() : p_begin; p < p_end; p = cursor ? claim() : p + p_stride) {
         // the job's work list: first the re-walks carried from the previous
         // round (batched search), then this launch's queued merges
         uint64_t xa, xb;
@@ -1245,7 +1251,7 @@ __global__ void __launch_bounds__(Geo<NQ>::THREADS) k_rewalk_pairs(WalkLaunch w)
     if (cnt <= blockIdx.x * Geo<NQ>::WALKS) return; // no pair for this CTA (uniform)
     const Smem<NQ> sm = stage<NQ>(w.lv, smem_raw);
     rewalk_job<NQ>(w, sm, blockIdx.x * Geo<NQ>::WALKS + group_in_cta<NQ>(), cnt, gridDim.x * Geo<NQ>::WALKS,
-                   thread_lanes<NQ>());
+                   thread_lanes<NQ>(), w.rw_next);
 }
 
 // The batched re-walk: the queued merges of all jobs of this qubit count
