@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--adder-walk", type=int, default=0, metavar="TABLE_LOG2",
                     help="only time the 4-qubit full adder's search by the collision walk alone with a "
                          "2^TABLE_LOG2-slot table, print its JSON and exit")
+    ap.add_argument("--sharded", action="store_true",
+                    help="walk the headline level sharded by distinguished-point owner even on one rank "
+                         "(the form N > 1 ranks always use; under torchrun)")
     ap.add_argument("--shape", type=int, default=0, help="launch shape of the --level-only walk kernel")
     ap.add_argument("--c-layout", type=int, default=0, help="C^ layout of the --level-only walk (0 int8, 1 words)")
     ap.add_argument("--tto-sweep", action="store_true",
@@ -734,8 +737,9 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
+    sharded = world > 1 or args.sharded
+    if sharded:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
@@ -784,7 +788,7 @@ def run_ours(args):
     barrier()
     t_wall = time.perf_counter()
     lost = None
-    if world > 1:
+    if sharded:
         # one level over every rank, distinguished points exchanged with their owners
         step_ms, walk_ms, r0, r1, lost = timed_sharded_level(Q, torch, prob, stream, K_LEVEL, c["dtheta"],
                                                              STEPS_PER_LAUNCH, args.warmup, args.steps, flush,
@@ -805,20 +809,21 @@ def run_ours(args):
     roof = walk_roofline(f"k_walks<{c['n']},{shape['launch_shape']}>", c["n"], w_steps, steps_done, walk_s,
                          args.steps, dp4a_per_s, clk.get("sm_mhz"), num_sms, hmma_per_s)
     roof["walk_kernel_share"] = walk_s / t_local
-    step_split = getattr(timed_level, "split", None) if world == 1 else None
+    step_split = getattr(timed_level, "split", None) if not sharded else None
     roof["imad_measured_gops"] = imad_per_s / 1e9
 
     e2e = None
     extra = {}
     if rank == 0:
         e2e = e2e_run(Q, torch, c, gates, K_LEVEL, STEPS_PER_LAUNCH, args.steps, stream, 0xE2E, shape)
-        if not args.no_tts:
+        # the other workloads run once, on one GPU (N > 1 holds every GPU only for the sharded headline)
+        if not args.no_tts and world == 1:
             extra["tto_walk_cfg1"] = time_to_optimal(Q, W, stream, 1, "walk")
             extra["tto_walk_cfg2"] = time_to_optimal(Q, W, stream, 2, "walk")
             extra["tto_walk_cfg3"] = time_to_optimal(Q, W, stream, 3, "walk", limit_s=300)
             extra["tto_exhaustive_cfg2"] = time_to_optimal(Q, W, stream, 2, "exhaustive")
             extra["tto_exhaustive_cfg3"] = time_to_optimal(Q, W, stream, 3, "exhaustive")
-        if not args.no_extra:
+        if not args.no_extra and world == 1:
             c2 = W.CONFIGS[2]
             g2, _ = W.config_target(2)
             p2 = Q.default_params(c2["n"], walks=c2["walks"], state_bits=c2["L"], dp_bits=c2["dtheta"],
@@ -859,21 +864,21 @@ def run_ours(args):
             "config": dict(workload_config(c), launch_shape=Q.launch_shapes(c["n"])[shape["launch_shape"]],
                            c_layout=["int8 byte quads (dp4a)", "32-bit words (IMAD)"][shape["c_layout"]]),
             "autotuned_level_shape": shape_trials, "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e, "clocks": clk,
-            "gpu_launches": (5 if world > 1 else 2) * args.steps, "wall_s": wall,
+            "gpu_launches": (5 if sharded else 2) * args.steps, "wall_s": wall,
             "step_split_ms": dict(step_split or {}, note="per bench step: walk kernel; re-walk kernel and the "
                                                          "reads of its results; host wait and exact checks of "
                                                          "claw candidates"),
             "headline_counts": {k: r1[k] - r0[k] for k in ("steps", "w_steps", "dps", "merges", "claws",
                                                             "false_hash", "robin_hood", "rewalk_steps")},
         }
-        if world > 1:
+        if sharded:
             line["config"]["parallelism"] = (f"DP-owner sharding over {world} ranks: one level, every rank walks "
                                              f"{c['walks']} walks and owns a hash share of the distinguished points "
                                              "(all-to-all exchange per round)")
             line["points_lost_to_outbox"] = lost
         line.update(extra)
         print(json.dumps(line))
-    if world > 1:
+    if sharded:
         dist.destroy_process_group()
 
 
