@@ -713,15 +713,14 @@ __global__ void __launch_bounds__(Shape<NQ, S>::THREADS, Shape<NQ, S>::MIN_BLOCK
 //
 // 32 walks per CTA (16 warps, two walks each) step in lockstep.  Each step:
 //  A. each warp evaluates its two walks' adjoint stages (side_weights).  A V
-//     walk's weights are already its column fingerprints: it stores them
-//     (16 bits each) in its exchange buffer.  A W walk takes the next row of
-//     the CTA's matrix product and writes its weights there as two byte
-//     planes in f16 (bytes 0..255 are exact in f16);
+//     walk's weights are already its column fingerprints: it hashes them into
+//     its shared sum at once.  A W walk takes the next row of the CTA's
+//     matrix product and writes its weights there as two byte planes in f16
+//     (bytes 0..255 are exact in f16);
 //  B. (barrier) each warp multiplies the W rows by its 16 columns of C^ with
 //     mma.sync m16n8k16 (f16 x f16, f32 accumulation), converting C^'s int8
 //     entries (exact in f16) fragment by fragment from shared memory, and
-//     hashes those 16 columns of every walk of the step, W and V alike, into
-//     the walk's shared sum (so every warp does the same share of hashing);
+//     hashes those columns of every W walk into the walk's shared sum;
 //  C. (barrier) each walk finishes its hash and takes its step.
 // Exactness: every product is an integer of magnitude below 2^15 (a byte
 // times an int8 entry), and every partial sum of a 512-term dot product is
@@ -745,9 +744,6 @@ struct Book {
     uint64_t wbase[2][kWalks];         // per matrix row: the W walk's hash base
     uint32_t wslot[2][kWalks];         // per matrix row: the W walk's slot
     uint32_t nrows[2];                 // W walks (matrix rows) this step
-    uint64_t vbase[2][kWalks];         // per V walk of the step: its hash base
-    uint32_t vslot[2][kWalks];         // per V walk of the step: its slot
-    uint32_t nv[2];                    // V walks this step
 };
 constexpr size_t smem_bytes = off_book + sizeof(Book);
 static_assert(smem_bytes <= 227 * 1024, "shared memory of the tensor-core walk kernel");
@@ -804,7 +800,7 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
         uint4 *dst = reinterpret_cast<uint4 *>(cm);
         for (int i = threadIdx.x; i < kK * kDim / 16; i += blockDim.x) dst[i] = src[i];
         for (int i = threadIdx.x; i < 2 * kWalks; i += blockDim.x) (&bk.sum[0][0])[i] = 0;
-        if (threadIdx.x < 2) bk.nrows[threadIdx.x] = bk.nv[threadIdx.x] = 0;
+        if (threadIdx.x < 2) bk.nrows[threadIdx.x] = 0;
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -841,17 +837,8 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
                 uint32_t ua[G::RPL], ub[G::RPL];
                 side_weights<4>(dx.side, dx.qpack, st[i].chunk, lv, sm, g, ua, ub);
                 if (dx.side == 0) {
-                    // V: the fingerprints L_Q = ua of the columns Q = lane + 32 t,
-                    // stored as 16-bit values at region[Q]; the stage exchange is
-                    // done (side_weights ends with a warp sync)
-                    uint16_t *lq = reinterpret_cast<uint16_t *>(region);
-#pragma unroll
-                    for (int tt = 0; tt < G::RPL; tt++) lq[lane + 32 * tt] = (uint16_t)ua[tt];
-                    if (lane == 0) {
-                        const uint32_t vi = atomicAdd(&bk.nv[buf], 1u);
-                        bk.vslot[buf][vi] = (uint32_t)slot;
-                        bk.vbase[buf][vi] = base;
-                    }
+                    const uint64_t sum = group_sum64(lane_column_sum<4>(ua, base, lane), 0xFFFFFFFFu);
+                    if (lane == 0) bk.sum[buf][slot] = sum;
                     continue;
                 }
                 uint32_t row = 0;
@@ -978,27 +965,6 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
                     }
                 }
             }
-            {
-                // this warp's 16 columns of every V walk: two walks per pass,
-                // a half-warp each, one column per lane
-                const uint32_t nv = bk.nv[buf];
-                const int Q = 16 * warp + (lane & 15);
-                for (uint32_t i0 = 0; i0 < nv; i0 += 2) {
-                    const uint32_t i = i0 + (uint32_t)(lane >> 4);
-                    const bool valid = i < nv;
-                    const uint32_t slot = valid ? bk.vslot[buf][i] : 0;
-                    uint64_t part = 0;
-                    if (valid && Q >= 1) {
-                        const uint32_t l =
-                            reinterpret_cast<const uint16_t *>(xchg + (size_t)2048 * slot)[Q];
-                        const uint32_t nl = (0u - l) & 0xFFFFu;
-                        part = smix(bk.vbase[buf][i] ^ (uint64_t)min(l, nl));
-                    }
-#pragma unroll
-                    for (int o = 8; o >= 1; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
-                    if (valid && (lane & 15) == 0) atomicAdd(&bk.sum[buf][slot], part);
-                }
-            }
             __syncthreads();
             // C. each walk's step
 #pragma unroll
@@ -1025,7 +991,7 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
             // clear this buffer for the step after next (the next step uses the other one)
             __syncwarp();
             if (lane < 2) bk.sum[buf][2 * warp + lane] = 0;
-            if (threadIdx.x == 0) bk.nrows[buf] = bk.nv[buf] = 0;
+            if (threadIdx.x == 0) bk.nrows[buf] = 0;
         }
         __syncthreads(); // the next group's first step may reuse this group's last buffer
 #pragma unroll
