@@ -207,18 +207,21 @@ int upload_problem(qcs_problem *P)
         uint64_t wb = smix_host(kSeedU + (2ull * i + 2) * kGamma);
         u[i] = make_uint2((uint32_t)wa, (uint32_t)wb);
     }
-    // rotation coefficients per Pauli p: word t, bit l: row l + Wl t
-    // anticommutes with p; word R + t, bit l: s(p, row) = +1 (lambda = 1)
-    std::vector<uint32_t> coef((size_t)D * 2 * R, 0);
+    // rotation masks per Pauli p and lane l (LevelCtx::coef): a 16-bit word
+    // whose bit t says that row l + Wl t anticommutes with p and bit 8 + t
+    // that s(p, row) = +1 (lambda = 1); two words to a uint32
+    std::vector<uint16_t> coef16((size_t)D * Wl, 0);
     const uint32_t m = (1u << n) - 1;
     for (uint32_t p = 0; p < (uint32_t)D; p++)
         for (uint32_t j = 0; j < (uint32_t)D; j++) {
             const uint32_t t = j / (uint32_t)Wl, l = j % (uint32_t)Wl;
             const bool anti = (__builtin_popcount(((p >> n) & (j & m)) ^ ((p & m) & (j >> n))) & 1) != 0;
             const bool plus = pauli_phase(n, p, j) == 1;
-            if (anti) coef[(size_t)p * 2 * R + t] |= 1u << l;
-            if (plus) coef[(size_t)p * 2 * R + R + t] |= 1u << l;
+            if (anti) coef16[(size_t)p * Wl + l] |= (uint16_t)(1u << t);
+            if (plus) coef16[(size_t)p * Wl + l] |= (uint16_t)(1u << (8 + t));
         }
+    std::vector<uint32_t> coef(coef16.size() / 2);
+    memcpy(coef.data(), coef16.data(), sizeof(uint32_t) * coef.size());
     // n >= 3: also C^ as signed byte quads (rows 4q .. 4q+3 of a column in
     // one word) when every entry fits in int8, laid out for the walk
     // kernel's byte-plane contraction (LevelCtx::Cq)

@@ -54,9 +54,10 @@ struct LevelCtx {
     // mod 2^16, for every Pauli: entry e = q_a - 1, where q_a is the side's
     // first stage rotation (V: q_h; W: q_1); word e 4^n + row = Ua | Ub << 16.
     const uint32_t *T1[2];
-    // rotation coefficients: for Pauli p, 2R words; word t (t < R) has bit
-    // sub set when row sub + W t anticommutes with p, word R + t when the
-    // sign s(p, row) is +1.  4^n x 2R uint32.
+    // rotation masks: for Pauli p and lane sub, the 16-bit word at index
+    // p W + sub has bit t set when row sub + W t anticommutes with p and bit
+    // 8 + t when the sign s(p, row) is +1 (t < R <= 8).  4^n x W uint16,
+    // read as 4^n W / 2 uint32.
     const uint32_t *coef;
     uint64_t xi_h;     // xi^h, the number of rotation tuples per side
     int32_t ell;       // bits of one rotation's field in the state: min(16, (L - 1) / h)

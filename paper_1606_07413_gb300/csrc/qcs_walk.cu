@@ -94,6 +94,17 @@ __device__ __forceinline__ uint64_t smix(uint64_t z)
     return z ^ (z >> 31);
 }
 
+// smix(base ^ phi) for phi < 2^30, given pre = base ^ (base >> 30): the
+// first xorshift of the finaliser cannot see phi (it shifts by 30), so
+// (base ^ phi) ^ ((base ^ phi) >> 30) = pre ^ phi, and the rest follows.
+// The same value as smix(base ^ phi), one 64-bit xorshift cheaper per column.
+__device__ __forceinline__ uint64_t smix_pre(uint64_t pre, uint32_t phi)
+{
+    uint64_t z = (pre ^ (uint64_t)phi) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 template <int NQ>
 struct Geo {
     static constexpr int DIM = 1 << (2 * NQ);            // 4^n rows and columns
@@ -111,7 +122,7 @@ struct Geo {
     static constexpr int THREADS = WARPS * 32;
     static constexpr int WALKS = WARPS * GROUPS;         // walks (lane groups) per CTA
     static constexpr int QUAD_UNROLL = NQ == 4 ? QCS_QUAD_UNROLL4 : QCS_QUAD_UNROLL3;
-    static constexpr int COEF_WORDS = DIM * 2 * RPL;     // rotation coefficient bits
+    static constexpr int COEF_WORDS = DIM * LPW / 2; // rotation masks: a 16-bit word per Pauli and lane
     static constexpr int MAX_CHUNKS = 256;               // hash bases, one per chunk
     // shared memory: weights | C^ | coefficients | chunk bases | exchange buffers
     static constexpr size_t off_C = sizeof(uint2) * DIM;
@@ -194,24 +205,13 @@ __device__ __forceinline__ void adj_stage(uint32_t p, uint32_t (&ua)[Geo<NQ>::RP
 #pragma unroll
     for (int t = 0; t < G::RPL; t++) su[g.sub + G::LPW * t] = make_uint2(ua[t], ub[t]);
     __syncwarp(g.mask);
-    const uint32_t *cwp = sm.coef + p * (2 * G::RPL);
-    uint32_t cw[2 * G::RPL];
-    if ((2 * G::RPL) % 4 == 0) {
-#pragma unroll
-        for (int t = 0; t < 2 * G::RPL; t += 4) {
-            const uint4 v4 = *reinterpret_cast<const uint4 *>(cwp + t);
-            cw[t] = v4.x; cw[(t + 1) % (2 * G::RPL)] = v4.y;
-            cw[(t + 2) % (2 * G::RPL)] = v4.z; cw[(t + 3) % (2 * G::RPL)] = v4.w;
-        }
-    } else {
-#pragma unroll
-        for (int t = 0; t < 2 * G::RPL; t++) cw[t] = cwp[t];
-    }
+    // this lane's rows of Pauli p: bit t anticommutes, bit 8 + t sign +1
+    const uint32_t bits = reinterpret_cast<const uint16_t *>(sm.coef)[p * G::LPW + g.sub];
 #pragma unroll
     for (int t = 0; t < G::RPL; t++) {
         const int j = g.sub + G::LPW * t;
-        const bool anti = (cw[t] >> g.sub) & 1u;
-        const bool plus = (cw[G::RPL + t] >> g.sub) & 1u;
+        const bool anti = (bits >> t) & 1u;
+        const bool plus = (bits >> (8 + t)) & 1u;
         const uint2 v = su[j ^ (int)p];
         const bool add = (plus != ADJ_OF_TRANSPOSE);
         const uint32_t na = add ? ua[t] + v.x : ua[t] - v.x;
@@ -359,11 +359,12 @@ template <int NQ>
 __device__ __forceinline__ uint64_t lane_column_sum(const uint32_t (&Lc)[Geo<NQ>::RPL], uint64_t base, int lane)
 {
     uint64_t acc = 0;
+    const uint64_t pre = base ^ (base >> 30);
 #pragma unroll
     for (int t = 0; t < Geo<NQ>::RPL; t++) {
         const int Q = lane + Geo<NQ>::LPW * t;
         const uint32_t l = Lc[t] & 0xFFFFu, nl = (0u - l) & 0xFFFFu;
-        const uint64_t e = smix(base ^ (uint64_t)min(l, nl));
+        const uint64_t e = smix_pre(pre, min(l, nl));
         acc += (Q >= 1) ? e : 0ull;
     }
     return acc;
@@ -945,6 +946,7 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
                             const uint32_t r = (uint32_t)(16 * tile + gq + 8 * hh);
                             const bool valid = r < nrows;
                             const uint64_t base = valid ? bk.wbase[buf][r] : 0;
+                            const uint64_t pre = base ^ (base >> 30);
                             uint64_t part = 0;
 #pragma unroll
                             for (int ct = 0; ct < 2; ct++)
@@ -955,7 +957,7 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
                                     const int p1 = __float2int_rn(acc[tile][1][ct][2 * hh + c]);
                                     const uint32_t l = ((uint32_t)p0 + ((uint32_t)p1 << 8)) & 0xFFFFu;
                                     const uint32_t nl = (0u - l) & 0xFFFFu;
-                                    const uint64_t e = smix(base ^ (uint64_t)min(l, nl));
+                                    const uint64_t e = smix_pre(pre, min(l, nl));
                                     part += (valid && Q >= 1) ? e : 0ull;
                                 }
                             part += __shfl_xor_sync(0xFFFFFFFFu, part, 1);

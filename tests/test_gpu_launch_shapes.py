@@ -61,16 +61,16 @@ def test_every_shape_and_layout_walks_the_same_trails(orc, cfg, k, walks, steps,
 def test_reported_copies_match_the_uploads_and_reads():
     """A second n = 3 problem (the shared stage tables are already on the
     device) uploads C^ as 64 x 64 (a, b) words, the 64 fingerprint weights,
-    the 64 x 2R rotation masks (R = 64 / 32 lanes) and, with every entry in
-    int8, the byte quads; each walk launch reads back the 15 counters and
+    the rotation masks (a 16-bit word per Pauli and lane, 32 lanes) and, with
+    every entry in int8, the byte quads; each walk launch reads back the 15 counters and
     three queue heads, plus 24 bytes per claw candidate."""
     from paper_1606_07413_gb300 import build
 
     build.build()
     c = W.CONFIGS[2]
     gates, _ = W.config_target(2)
-    D, R = 64, 2
-    want_up = D * D * 8 + D * 8 + D * 2 * R * 4 + D * D // 2 * 4
+    D, lanes = 64, 32
+    want_up = D * D * 8 + D * 8 + D * lanes * 2 + D * D // 2 * 4
     with Q.Problem.from_circuit(3, gates, 5, Q.default_params(3, walks=4096)) as first:
         pass
     with Q.Problem.from_circuit(3, gates, 5, Q.default_params(3, walks=4096)) as prob:
