@@ -113,14 +113,14 @@ def workload_config(c, k=None, steps=None, rewalk_budget=None):
 # the steps, plus 32 bytes per distinguished point (0.5 MB at the headline's
 # 64 steps), so the figure stands for the headline launch.
 WALK_NCU = {
-    "k_walks<4,3>": {"source_sha256_16": "f4569fadfc8e6402", "dram_bytes_per_launch": 34657024,
-                     "warp_inst_per_step": 1365.6},
-    "k_walks<4,0>": {"source_sha256_16": "f4569fadfc8e6402", "dram_bytes_per_launch": 35019008,
-                     "warp_inst_per_step": 1939.2},
+    "k_walks<4,3>": {"source_sha256_16": "2e76870690a393b4", "dram_bytes_per_launch": 34905344,
+                     "warp_inst_per_step": 1356.1},
+    "k_walks<4,0>": {"source_sha256_16": "2e76870690a393b4", "dram_bytes_per_launch": 34978304,
+                     "warp_inst_per_step": 1937.6},
     # n = 3, level 5: `bench.py --level-only n3_level5 --steps 2`, one launch of 2^16 walks x 512 steps,
     # the launch of the n3_level5 record (profiles/k_walks_n3_level5_walks65536.md)
-    "k_walks<3,0>": {"source_sha256_16": "f4569fadfc8e6402", "dram_bytes_per_launch": 2175488,
-                     "warp_inst_per_step": 376.3},
+    "k_walks<3,0>": {"source_sha256_16": "2e76870690a393b4", "dram_bytes_per_launch": 2184192,
+                     "warp_inst_per_step": 379.3},
 }
 
 
