@@ -306,7 +306,8 @@ QCS_API int qcs_level_begin_shard(qcs_problem *prob, int k, uint32_t version, in
 
 /* qcs_level_walk for a sharded level: the distinguished points reached go to
  * `outbox` (DEVICE, cap pairs {point, trail reference} of uint64) instead of
- * the local table; *count (DEVICE uint32, zeroed by the call) counts every
+ * the local table (outbox must not be NULL: QCS_ERR_ARG); *count (DEVICE
+ * uint32, zeroed by the call) counts every
  * point reached, also those past cap (which are lost: size the outbox for
  * walks x steps x theta with room to spare).  Resets the launch counters and
  * the merge queue like qcs_level_walk.  Asynchronous on `stream`. */

@@ -1128,7 +1128,7 @@ int qcs_level_begin_shard(qcs_problem *P, int k, uint32_t version, int dp_bits, 
 int qcs_level_walk_out(qcs_problem *P, uint32_t steps, uint64_t *outbox, uint32_t cap, uint32_t *count,
                        void *stream)
 {
-    if (!P || !count || (cap && !outbox)) return QCS_ERR_ARG;
+    if (!P || !count || !outbox) return QCS_ERR_ARG; // a null outbox would send the points to the local table
     if (busy(P)) return QCS_ERR_BUSY;
     if (!P->lvl.active || steps == 0) return QCS_ERR_ARG;
     const cudaStream_t s = (cudaStream_t)stream;
