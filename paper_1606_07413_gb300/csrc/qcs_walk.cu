@@ -22,8 +22,15 @@
 // stages) instead of pushing all 4^n - 1 columns through them.  The V side is
 // then read off directly (its right factor is the identity), and the W side is
 // one contraction of the transformed weights with C^, staged in shared memory
-// as signed byte quads and contracted by byte-plane dp4a.  The result is
-// bit-identical to hashing the explicitly formed product.
+// as signed byte quads and contracted by byte-plane dp4a, or, at n = 4 in
+// launch shape 3, by f16 tensor-core MMAs over 32 walks at a time
+// (k_walks_mma4).  The result is bit-identical to hashing the explicitly
+// formed product.
+//
+// Also here: the distinguished-point table insert and the re-walk of merged
+// trails (Sec. 3, Fig. 2), the batched forms of both, the exhaustive level
+// pass (Eq. mitm), and the owner binning and insertion of distinguished
+// points for a level sharded across ranks.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
