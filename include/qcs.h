@@ -329,8 +329,9 @@ QCS_API int qcs_shard_bin(const uint64_t *points, uint32_t count, uint32_t n_own
  * before qcs_level_rewalk of the same round.  Asynchronous on `stream`. */
 QCS_API int qcs_level_insert(qcs_problem *prob, const uint64_t *points, uint32_t count, void *stream);
 
-/* Copy the merges queued by the last qcs_level_walk / qcs_level_insert to
- * HOST memory: up to cap triples {trail ref a, trail ref b, distinguished
+/* Copy the merges queued by the last qcs_level_walk / qcs_level_insert
+ * (Sec. 3: pairs of trails that reached one distinguished point, each to be
+ * re-walked as in Fig. 2) to HOST memory: up to cap triples {trail ref a, trail ref b, distinguished
  * point} into out (3 cap uint64), *n_out = the number copied.  Waits for the
  * problem's queue on `stream` first.  For inspection and tests: the search
  * itself re-walks the queue on the device (qcs_level_rewalk). */
