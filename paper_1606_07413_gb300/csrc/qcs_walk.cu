@@ -726,10 +726,15 @@ __global__ void __launch_bounds__(Shape<NQ, S>::THREADS, Shape<NQ, S>::MIN_BLOCK
 //     matrix product and writes its weights there as two byte planes in f16
 //     (bytes 0..255 are exact in f16);
 //  B. (barrier) each warp multiplies the W rows by its 16 columns of C^ with
-//     mma.sync m16n8k16 (f16 x f16, f32 accumulation), converting C^'s int8
-//     entries (exact in f16) fragment by fragment from shared memory, and
-//     hashes those columns of every W walk into the walk's shared sum;
+//     mma.sync m16n8k16 (f16 x f16, f32 accumulation) and hashes those
+//     columns of every W walk into the walk's shared sum;
 //  C. (barrier) each walk finishes its hash and takes its step.
+// C^'s entries are small integers, exact in f16.  In f16 C^ is 256 KB: more
+// than a CTA's shared memory, and exactly an SM's tensor memory (128 lanes x
+// 512 columns of 32 bits).  So at the start each warp converts its own
+// columns' MMA fragments once and stores them in tensor memory (tcgen05.st);
+// step B reloads them with tcgen05.ld, and shared memory holds only the
+// weights, the exchange buffers and the bookkeeping.
 // Exactness: every product is an integer of magnitude below 2^15 (a byte
 // times an int8 entry), and every partial sum of a 512-term dot product is
 // below 512 x 255 x 128 < 2^24, so the f32 accumulation is exact and the
@@ -740,19 +745,24 @@ namespace mma4 {
 constexpr int kCtaWarps = 16, kThreads = kCtaWarps * 32, kWalks = 32; // two walks per warp
 constexpr int kDim = 256, kK = 2 * kDim;
 // shared memory: weights | rotation masks | chunk bases | 32 exchange
-// buffers (2 KB each; a W walk's two f16 planes after its stages) | C^ in
-// the tensor-core layout (128 KB) | per-step bookkeeping (two buffers)
+// buffers (2 KB each; a W walk's two f16 planes after its stages) |
+// per-step bookkeeping (two buffers)
 constexpr size_t off_coef = sizeof(uint2) * kDim;
 constexpr size_t off_base = off_coef + sizeof(uint32_t) * Geo<4>::COEF_WORDS;
 constexpr size_t off_xchg = off_base + sizeof(uint64_t) * Geo<4>::MAX_CHUNKS;
-constexpr size_t off_cm = off_xchg + (size_t)2048 * kWalks;
-constexpr size_t off_book = off_cm + (size_t)kK * kDim;
+constexpr size_t off_book = off_xchg + (size_t)2048 * kWalks;
 struct Book {
     unsigned long long sum[2][kWalks]; // per walk slot: the multiset hash's sum
     uint64_t wbase[2][kWalks];         // per matrix row: the W walk's hash base
     uint32_t wslot[2][kWalks];         // per matrix row: the W walk's slot
     uint32_t nrows[2];                 // W walks (matrix rows) this step
+    uint32_t tmem;                     // base address of the CTA's tensor memory
 };
+// tensor memory: warp u of the 16 holds the fragments of C^'s columns
+// 16 u .. 16 u + 15 in lanes 32 (u % 4) .. + 31 (the lanes a warp may access)
+// and columns 128 (u / 4) .. + 127; column 16 s + 8 ct + 2 kk + h of a lane
+// is the B fragment register h of K-block 4 s + kk and column tile ct.
+constexpr uint32_t kTmemCols = 512;
 constexpr size_t smem_bytes = off_book + sizeof(Book);
 static_assert(smem_bytes <= 227 * 1024, "shared memory of the tensor-core walk kernel");
 
@@ -788,6 +798,56 @@ __device__ __forceinline__ void ldmatrix_x4(uint32_t (&a)[4], uint32_t addr)
                  : "r"(addr));
 }
 
+// Tensor memory (whole-warp instructions).  A load is asynchronous: its
+// registers are valid after tmem_wait_ld, which takes them as operands so
+// that no use can be scheduled before it.
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                 "%15,%16};" ::"r"(taddr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+                 "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t (&v)[16], uint32_t taddr)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                 "[%16];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                   "=r"(v[15])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]),
+                   "+r"(v[15])
+                 :
+                 : "memory");
+}
+
 } // namespace mma4
 
 __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
@@ -801,19 +861,39 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
     // weights, rotation masks and chunk bases as the other walk kernels stage them
     Smem<4> sm = stage<4, false>(w.lv, smem_raw);
     unsigned char *xchg = smem_raw + mma4::off_xchg;
-    unsigned char *cm = smem_raw + mma4::off_cm;
     Book &bk = *reinterpret_cast<Book *>(smem_raw + mma4::off_book);
-    {
-        const uint4 *src = w.lv.Cm;
-        uint4 *dst = reinterpret_cast<uint4 *>(cm);
-        for (int i = threadIdx.x; i < kK * kDim / 16; i += blockDim.x) dst[i] = src[i];
-        for (int i = threadIdx.x; i < 2 * kWalks; i += blockDim.x) (&bk.sum[0][0])[i] = 0;
-        if (threadIdx.x < 2) bk.nrows[threadIdx.x] = 0;
-    }
-    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Lanes g{lane, 0xFFFFFFFFu};
     const int gq = lane >> 2, q = lane & 3; // MMA fragment coordinates
+    for (int i = threadIdx.x; i < 2 * kWalks; i += blockDim.x) (&bk.sum[0][0])[i] = 0;
+    if (threadIdx.x < 2) bk.nrows[threadIdx.x] = 0;
+    if (warp == 0) mma4::tmem_alloc(&bk.tmem, mma4::kTmemCols);
+    mma4::tmem_fence_before();
+    __syncthreads();
+    mma4::tmem_fence_after();
+    // this warp's fragments of C^ (columns 16 warp .. 16 warp + 15), from the
+    // biased int8 layout: column `col` is 512 bytes, its 16-byte chunk
+    // (4 s + q) ^ (4 (col & 1)) holds the four words of K-blocks 4 s .. 4 s + 3
+    // that lane (., q) of an MMA fragment takes
+    const uint32_t tw = bk.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 128u * (uint32_t)(warp >> 2);
+#pragma unroll 1
+    for (int s4i = 0; s4i < kK / 64; s4i++) {
+        uint32_t v[16];
+#pragma unroll
+        for (int ct = 0; ct < 2; ct++) {
+            const int ncol = 16 * warp + 8 * ct + gq;
+            const int chunk = (4 * s4i + q) ^ (4 * (ncol & 1));
+            const uint4 raw = w.lv.Cm[(size_t)ncol * 32 + chunk];
+            const uint32_t wd[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+            for (int kk4 = 0; kk4 < 4; kk4++) {
+                v[8 * ct + 2 * kk4] = mma4::bytes_to_f16x2(wd[kk4], 0x4140, 1152.f);     // rows 2q, 2q + 1
+                v[8 * ct + 2 * kk4 + 1] = mma4::bytes_to_f16x2(wd[kk4], 0x4342, 1152.f); // rows 2q + 8, 2q + 9
+            }
+        }
+        mma4::tmem_st16(tw + 16u * (uint32_t)s4i, v);
+    }
+    mma4::tmem_wait_st();
     const LevelCtx &lv = w.lv;
     const uint32_t steps = w.steps, max_len = w.max_len;
     const int dshift = lv.dshift;
@@ -904,28 +984,22 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
                     arow[tile] = mma4::smem_u32(xchg + (size_t)2048 * bk.wslot[buf][rr]);
                     aswz[tile] = rr & 7;
                 }
-                const unsigned char *ccol[2];
+                // C^'s fragments from tensor memory, 16 registers per four
+                // K-blocks, the next four loading while these are used
+                uint32_t bq[2][16];
+                mma4::tmem_ld16(bq[0], tw);
 #pragma unroll
-                for (int ct = 0; ct < 2; ct++) ccol[ct] = cm + (size_t)(16 * warp + 8 * ct + gq) * 512;
-#pragma unroll 2
                 for (int s4i = 0; s4i < kK / 64; s4i++) {
-                    uint4 braw[2];
-#pragma unroll
-                    for (int ct = 0; ct < 2; ct++) {
-                        const int ncol = 16 * warp + 8 * ct + gq;
-                        const int chunk = (4 * s4i + q) ^ (4 * (ncol & 1));
-                        braw[ct] = *reinterpret_cast<const uint4 *>(ccol[ct] + 16 * chunk);
-                    }
+                    mma4::tmem_wait_ld(bq[s4i & 1]);
+                    if (s4i + 1 < kK / 64) mma4::tmem_ld16(bq[(s4i + 1) & 1], tw + 16u * (uint32_t)(s4i + 1));
 #pragma unroll
                     for (int kk4 = 0; kk4 < 4; kk4++) {
                         const int kb = 4 * s4i + kk4; // K-block of 16
                         uint32_t b0[2], b1[2];
 #pragma unroll
                         for (int ct = 0; ct < 2; ct++) {
-                            const uint32_t wd = kk4 == 0 ? braw[ct].x : kk4 == 1 ? braw[ct].y : kk4 == 2 ? braw[ct].z
-                                                                                                     : braw[ct].w;
-                            b0[ct] = mma4::bytes_to_f16x2(wd, 0x4140, 1152.f); // rows 2q, 2q + 1
-                            b1[ct] = mma4::bytes_to_f16x2(wd, 0x4342, 1152.f); // rows 2q + 8, 2q + 9
+                            b0[ct] = bq[s4i & 1][8 * ct + 2 * kk4];
+                            b1[ct] = bq[s4i & 1][8 * ct + 2 * kk4 + 1];
                         }
 #pragma unroll
                         for (int tile = 0; tile < 2; tile++) {
@@ -1008,6 +1082,13 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
             if (live[i] && lane == 0) w.walks[grp * kWalks + 2 * warp + i] = st[i];
     }
     flush_tally(w.counters, t, g);
+    // every warp's tensor-memory loads have completed (each was waited for)
+    mma4::tmem_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        mma4::tmem_fence_after();
+        mma4::tmem_dealloc(bk.tmem, mma4::kTmemCols);
+    }
 }
 
 __global__ void k_init_walks(WalkLaunch w)
