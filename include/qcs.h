@@ -365,7 +365,9 @@ QCS_API int qcs_level_merges(qcs_problem *prob, uint64_t *out, uint32_t cap, uin
  * [2] distinguished points, [3] abandoned trails, [4] overwritten points,
  * [5] duplicate inserts, [6] merges found, [7] merges pushed (low 32 bits;
  * it counts pushes past merge_cap too, so the valid triples number
- * min(counts[7], merge_cap)).  k, version, dp_bits (0 = params.dp_bits) as
+ * min(counts[7], merge_cap)); the high 32 bits of [7] are nonzero only if a
+ * bounded wait inside the n = 4 tensor-core walk (launch_shape 3) ran out,
+ * and then nothing the call wrote is valid.  k, version, dp_bits (0 = params.dp_bits) as
  * in qcs_level_begin; n_walks <= 2^24.  Asynchronous on `stream` after the
  * set-up. */
 QCS_API int qcs_level_walk_static(qcs_problem *prob, int k, uint32_t version, int dp_bits, int begin,

@@ -427,6 +427,7 @@ int level_begin(qcs_problem *P, int k, uint32_t version, int dp_bits, uint32_t n
     w.ccount = P->dQhead + 1;
     w.ccap = kCandCap;
     w.counters = P->dCounters;
+    w.stall = reinterpret_cast<uint32_t *>(P->dCounters + C_STALLED); // its low word
     w.shape = P->p.launch_shape;
     w.walk_base = walk_base;
     L.pp = 0;
@@ -485,6 +486,7 @@ int level_collect(qcs_problem *P, cudaStream_t s, bool *got, uint64_t *steps)
     const auto &L = P->lvl;
     const int k = L.k, h = L.h;
     const unsigned long long *c = P->hCounters;
+    if (c[C_STALLED]) return QCS_ERR_DEVICE; // a bounded wait of the walk kernel ran out: nothing here is valid
     const uint32_t npairs = std::min(P->hQhead[0], L.w.qcap);
     const uint32_t ncand = std::min(P->hQhead[1], kCandCap);
     int64_t d2h = (int64_t)(sizeof(unsigned long long) * C_NCOUNTERS + 3 * sizeof(uint32_t));

@@ -129,7 +129,8 @@ enum Counter {
     C_CANDS,       // claw candidates found by the re-walk (including overflowed ones)
     C_RSTEPS,      // walk steps taken by the re-walk (evaluations of f)
     C_CLS0,        // re-walk classes QCS_MERGE_ROBIN_HOOD .. QCS_MERGE_NO_MERGE at C_CLS0 + class
-    C_NCOUNTERS = C_CLS0 + 6
+    C_STALLED = C_CLS0 + 6, // warps of the tensor-core walk whose bounded wait ran out (low word)
+    C_NCOUNTERS
 };
 
 struct WalkLaunch {
@@ -168,6 +169,10 @@ struct WalkLaunch {
     // single-target re-walk: merges are claimed from this device counter
     // (zeroed before the launch); null: a fixed stride (the batched re-walk)
     uint32_t *rw_next;
+    // the tensor-core walk (n = 4, launch shape 3) counts here the warps
+    // whose bounded wait ran out (the launch's results are then invalid);
+    // it refuses to launch without it
+    uint32_t *stall;
 };
 
 // Many jobs in one launch: per qubit count, the device list of tasks

@@ -86,6 +86,7 @@ extern "C" int qcs_level_walk_static(qcs_problem *prob, int k, uint32_t version,
     w.qhead = reinterpret_cast<uint32_t *>(counts + 7); // low word of counts[7]
     w.qcap = merge_cap;
     w.counters = reinterpret_cast<unsigned long long *>(counts);
+    w.stall = reinterpret_cast<uint32_t *>(counts + 7) + 1; // high word of counts[7]
     w.shape = prob->p.launch_shape;
     e = cudaMemsetAsync(counts, 0, 8 * sizeof(uint64_t), s);
     if (e == cudaSuccess && begin) {

@@ -578,12 +578,17 @@ __device__ __forceinline__ void new_trail(WalkState &st, uint32_t walk, const Le
     st.chunk = trail_chunk(lv, st.start);
 }
 
-// per-walk-group tallies, added to the job's counters by the group's first lane
-struct Tally {
-    unsigned long long steps = 0, w = 0, dp = 0, ab = 0, evicted = 0, duplicate = 0, pairs = 0;
+// per-walk-group tallies, added to the job's counters by the group's first
+// lane (the tensor-core kernel keeps them in 32 bits and flushes them before
+// they could overflow)
+template <typename T>
+struct TallyOf {
+    T steps = 0, w = 0, dp = 0, ab = 0, evicted = 0, duplicate = 0, pairs = 0;
 };
+using Tally = TallyOf<unsigned long long>;
 
-__device__ __forceinline__ void flush_tally(unsigned long long *counters, Tally &t, Lanes g)
+template <typename T>
+__device__ __forceinline__ void flush_tally(unsigned long long *counters, TallyOf<T> &t, Lanes g)
 {
     if (g.sub == 0) {
         if (t.steps) atomicAdd(&counters[C_STEPS], t.steps);
@@ -594,15 +599,15 @@ __device__ __forceinline__ void flush_tally(unsigned long long *counters, Tally 
         if (t.duplicate) atomicAdd(&counters[C_DUPLICATE], t.duplicate);
         if (t.pairs) atomicAdd(&counters[C_PAIRS], t.pairs);
     }
-    t = Tally();
+    t = TallyOf<T>();
 }
 
 // Store the distinguished point (Sec. 3: the triple start, end, length) in
 // the slot its value hashes to, keeping the newest trail there (one 128-bit
 // atomic exchange, never a wait).  If the slot held the same point from
 // another trail the two trails merged: queue them for the re-walk.
-template <typename WL>
-__device__ void dp_insert(const WL &w, uint64_t dp, uint64_t ref, Tally &c)
+template <typename WL, typename T>
+__device__ void dp_insert(const WL &w, uint64_t dp, uint64_t ref, TallyOf<T> &c)
 {
     if (w.outbox) {
         // DP-owner sharding: the point goes to its owner's table after the exchange
@@ -719,22 +724,30 @@ __global__ void __launch_bounds__(Shape<NQ, S>::THREADS, Shape<NQ, S>::MIN_BLOCK
 
 // ---- n = 4, launch shape 3: the W side's contraction on the tensor cores ----
 //
-// 32 walks per CTA (16 warps, two walks each) step in lockstep.  Each step:
-//  A. each warp evaluates its two walks' adjoint stages (side_weights).  A V
+// Warp-specialised: 12 stage warps and 8 MMA warps per CTA, one CTA per SM.
+// A CTA steps 48 walks as two sets of 24; each stage warp owns two walks of
+// each set.  For set X, step s:
+//  A. the stage warps evaluate the set's adjoint stages (side_weights).  A V
 //     walk's weights are already its column fingerprints: it hashes them into
-//     its shared sum at once.  A W walk takes the next row of the CTA's
-//     matrix product and writes its weights there as two byte planes in f16
-//     (bytes 0..255 are exact in f16);
-//  B. (barrier) each warp multiplies the W rows by its 16 columns of C^ with
-//     mma.sync m16n8k16 (f16 x f16, f32 accumulation) and hashes those
-//     columns of every W walk into the walk's shared sum;
-//  C. (barrier) each walk finishes its hash and takes its step.
+//     its shared sum at once.  A W walk writes its weights as two byte planes
+//     in f16 (bytes 0..255 are exact in f16) into its row buffer and flags
+//     its slot; then every stage warp signals "rows of X ready";
+//  B. the MMA warps multiply the flagged rows (compacted, up to 24: one M
+//     tile, rarely two) by C^ with mma.sync m16n8k16 (f16 x f16, f32
+//     accumulation), 32 columns per warp (8 accumulator chains; two MMA
+//     warps per scheduler keep the tensor pipe busy), hash those columns of
+//     every W walk into the walk's shared sum and signal "sums of X ready";
+//  C. the stage warps finish each walk's hash and take its step.
+// The stage warps run C and A of one set while the MMA warps run B of the
+// other (C_0(s) A_0(s+1) beside B_1(s); C_1(s) A_1(s+1) beside B_0(s+1)), so
+// the stages' integer work and the contraction overlap.  The hand-offs are
+// four mbarriers; every wait on them is bounded, and a wait that runs out
+// stops its warp and is counted in *w.stall (the results are then invalid).
 // C^'s entries are small integers, exact in f16.  In f16 C^ is 256 KB: more
 // than a CTA's shared memory, and exactly an SM's tensor memory (128 lanes x
-// 512 columns of 32 bits).  So at the start each warp converts its own
-// columns' MMA fragments once and stores them in tensor memory (tcgen05.st);
-// step B reloads them with tcgen05.ld, and shared memory holds only the
-// weights, the exchange buffers and the bookkeeping.
+// 512 columns of 32 bits).  So at the start each MMA warp converts the MMA
+// fragments of its columns once and stores them in tensor memory
+// (tcgen05.st); it reloads them with tcgen05.ld, one K-block at a time.
 // Exactness: every product is an integer of magnitude below 2^15 (a byte
 // times an int8 entry), and every partial sum of a 512-term dot product is
 // below 512 x 255 x 128 < 2^24, so the f32 accumulation is exact and the
@@ -742,29 +755,51 @@ __global__ void __launch_bounds__(Shape<NQ, S>::THREADS, Shape<NQ, S>::MIN_BLOCK
 // L = P0 + 2^8 P1 (mod 2^16) from the two planes, as in the dp4a path.
 namespace mma4 {
 
-constexpr int kCtaWarps = 16, kThreads = kCtaWarps * 32, kWalks = 32; // two walks per warp
+#ifndef QCS_WS_STAGE
+#define QCS_WS_STAGE 12 // stage warps
+#endif
+#ifndef QCS_WS_MMA
+#define QCS_WS_MMA 8 // MMA warps (two per scheduler keep the legacy tensor pipe busy)
+#endif
+#ifndef QCS_WS_WPW
+#define QCS_WS_WPW 2 // walks of each set per stage warp
+#endif
+constexpr int kStageWarps = QCS_WS_STAGE, kMmaWarps = QCS_WS_MMA, kWPW = QCS_WS_WPW;
+constexpr int kCtaWarps = kStageWarps + kMmaWarps, kThreads = kCtaWarps * 32;
+static_assert(kStageWarps % 4 == 0, "MMA warp m must be warp m % 4 of its warpgroup (tensor-memory lanes 32 (m % 4) ..)");
+static_assert(kMmaWarps == 4 || kMmaWarps == 8, "C^'s 256 columns split over 4 or 8 MMA warps");
+constexpr int kSets = 2, kWalks = kWPW * kStageWarps; // walks per set
+static_assert(kWalks <= 32, "a set's rows are compacted by one warp ballot");
+constexpr int kCT = 32 / kMmaWarps; // column tiles of 8 per MMA warp
 constexpr int kDim = 256, kK = 2 * kDim;
-// shared memory: weights | rotation masks | chunk bases | 32 exchange
-// buffers (2 KB each; a W walk's two f16 planes after its stages) |
-// per-step bookkeeping (two buffers)
+// shared memory: weights | rotation masks | chunk bases | 2 x 24 row buffers
+// (2 KB each: a W walk's two f16 planes, and its stage exchanges) | per set,
+// the bookkeeping | the walks' states | the MMA warps' row lists | mbarriers
+// | tensor-memory address
 constexpr size_t off_coef = sizeof(uint2) * kDim;
 constexpr size_t off_base = off_coef + sizeof(uint32_t) * Geo<4>::COEF_WORDS;
 constexpr size_t off_xchg = off_base + sizeof(uint64_t) * Geo<4>::MAX_CHUNKS;
-constexpr size_t off_book = off_xchg + (size_t)2048 * kWalks;
+static_assert(off_coef == Geo<4>::off_coef_v && off_base == Geo<4>::off_base_v, "layout of stage<4, false>");
+constexpr size_t off_book = off_xchg + (size_t)2048 * kWalks * kSets;
 struct Book {
-    unsigned long long sum[2][kWalks]; // per walk slot: the multiset hash's sum
-    uint64_t wbase[2][kWalks];         // per matrix row: the W walk's hash base
-    uint32_t wslot[2][kWalks];         // per matrix row: the W walk's slot
-    uint32_t nrows[2];                 // W walks (matrix rows) this step
-    uint32_t tmem;                     // base address of the CTA's tensor memory
+    unsigned long long sum[kWalks]; // per walk slot: the multiset hash's sum
+    uint64_t wbase[kWalks];         // per walk slot: the hash base (W walks)
+    uint32_t isw[kWalks];           // per walk slot: 1 if it is a W walk with a row this step
 };
-// tensor memory: warp u of the 16 holds the fragments of C^'s columns
-// 16 u .. 16 u + 15 in lanes 32 (u % 4) .. + 31 (the lanes a warp may access)
-// and columns 128 (u / 4) .. + 127; column 16 s + 8 ct + 2 kk + h of a lane
-// is the B fragment register h of K-block 4 s + kk and column tile ct.
-constexpr uint32_t kTmemCols = 512;
-constexpr size_t smem_bytes = off_book + sizeof(Book);
+constexpr size_t off_wst = off_book + kSets * sizeof(Book);              // WalkState [set][slot]
+constexpr size_t off_rows = off_wst + sizeof(WalkState) * kSets * kWalks; // per MMA warp: slots of the compacted rows
+constexpr size_t off_bar = (off_rows + kMmaWarps * kWalks + 7) & ~(size_t)7;
+constexpr size_t off_tmem = off_bar + 4 * sizeof(uint64_t); // rows ready [2], sums ready [2]
+constexpr size_t smem_bytes = off_tmem + 16;
 static_assert(smem_bytes <= 227 * 1024, "shared memory of the tensor-core walk kernel");
+// tensor memory: MMA warp m (the warp m % 4 of its warpgroup, so lanes
+// 32 (m % 4) .. + 31 are the ones it may access) holds C^'s columns
+// 8 kCT m .. 8 kCT (m + 1) - 1 in columns 64 kCT (m / 4) .. of those lanes;
+// column 2 kCT kb + 2 ct + h there is the B fragment register h of K-block
+// kb and column tile ct (columns 8 kCT m + 8 ct ..).
+constexpr uint32_t kTmemCols = 512;
+// a bounded wait gives up after this many SM clock cycles (about two seconds)
+constexpr long long kWaitCycles = 1ll << 32;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -817,6 +852,13 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 __device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
 {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
@@ -838,6 +880,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t (&v)[16], uint32_t taddr)
                  : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t (&v)[8], uint32_t taddr)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7])
+                 :
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld(uint32_t (&v)[16], uint32_t taddr) { tmem_ld16(v, taddr); }
+__device__ __forceinline__ void tmem_ld(uint32_t (&v)[8], uint32_t taddr) { tmem_ld8(v, taddr); }
+__device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t (&v)[16]) { tmem_st16(taddr, v); }
+__device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t (&v)[8]) { tmem_st8(taddr, v); }
+
 __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[16])
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
@@ -848,6 +910,38 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[16])
                  : "memory");
 }
 
+
+// mbarriers (shared memory): arrive has release and try_wait acquire
+// semantics at CTA scope.
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *b)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(b))
+                 : "memory");
+}
+
+// Wait until the phase of parity `ph` has completed; false if the wait ran
+// out (kWaitCycles).
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t ph)
+{
+    const uint32_t a = smem_u32(b);
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(a), "r"(ph)
+                     : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
 } // namespace mma4
 
 __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
@@ -855,239 +949,306 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
     using mma4::Book;
     using mma4::kWalks;
     using mma4::kK;
-    using mma4::kDim;
     using G = Geo<4>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // weights, rotation masks and chunk bases as the other walk kernels stage them
     Smem<4> sm = stage<4, false>(w.lv, smem_raw);
-    unsigned char *xchg = smem_raw + mma4::off_xchg;
-    Book &bk = *reinterpret_cast<Book *>(smem_raw + mma4::off_book);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Book *books = reinterpret_cast<Book *>(smem_raw + mma4::off_book);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + mma4::off_bar); // rows ready [2], sums ready [2]
+    uint32_t *tmem_addr = reinterpret_cast<uint32_t *>(smem_raw + mma4::off_tmem);
     const Lanes g{lane, 0xFFFFFFFFu};
     const int gq = lane >> 2, q = lane & 3; // MMA fragment coordinates
-    for (int i = threadIdx.x; i < 2 * kWalks; i += blockDim.x) (&bk.sum[0][0])[i] = 0;
-    if (threadIdx.x < 2) bk.nrows[threadIdx.x] = 0;
-    if (warp == 0) mma4::tmem_alloc(&bk.tmem, mma4::kTmemCols);
+    for (int i = threadIdx.x; i < mma4::kSets * kWalks; i += blockDim.x) {
+        books[i / kWalks].sum[i % kWalks] = 0;
+        books[i / kWalks].isw[i % kWalks] = 0;
+    }
+    if (threadIdx.x == 0) {
+        mma4::mbar_init(&bars[0], mma4::kStageWarps);
+        mma4::mbar_init(&bars[1], mma4::kStageWarps);
+        mma4::mbar_init(&bars[2], mma4::kMmaWarps);
+        mma4::mbar_init(&bars[3], mma4::kMmaWarps);
+    }
+    if (warp == 0) mma4::tmem_alloc(tmem_addr, mma4::kTmemCols);
     mma4::tmem_fence_before();
     __syncthreads();
     mma4::tmem_fence_after();
-    // this warp's fragments of C^ (columns 16 warp .. 16 warp + 15), from the
-    // biased int8 layout: column `col` is 512 bytes, its 16-byte chunk
-    // (4 s + q) ^ (4 (col & 1)) holds the four words of K-blocks 4 s .. 4 s + 3
-    // that lane (., q) of an MMA fragment takes
-    const uint32_t tw = bk.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 128u * (uint32_t)(warp >> 2);
+    const uint32_t tmem = *tmem_addr;
+    if (warp >= mma4::kStageWarps) {
+        // MMA warp m: the fragments of its C^ columns, from the biased int8
+        // layout: column `col` is 512 bytes, its 16-byte chunk
+        // (4 (kb / 4) + q) ^ (4 (col & 1)) holds in word kb % 4 the four
+        // entries of K-block kb that lane (., q) of an MMA fragment takes
+        using mma4::kCT;
+        const int m = warp - mma4::kStageWarps;
+        const uint32_t tq = tmem + ((uint32_t)(32 * (m & 3)) << 16) + (uint32_t)(64 * kCT * (m >> 2));
+        const uint32_t *cm = reinterpret_cast<const uint32_t *>(w.lv.Cm);
 #pragma unroll 1
-    for (int s4i = 0; s4i < kK / 64; s4i++) {
-        uint32_t v[16];
+        for (int kb = 0; kb < kK / 16; kb++) {
+            uint32_t v[2 * kCT];
 #pragma unroll
-        for (int ct = 0; ct < 2; ct++) {
-            const int ncol = 16 * warp + 8 * ct + gq;
-            const int chunk = (4 * s4i + q) ^ (4 * (ncol & 1));
-            const uint4 raw = w.lv.Cm[(size_t)ncol * 32 + chunk];
-            const uint32_t wd[4] = {raw.x, raw.y, raw.z, raw.w};
-#pragma unroll
-            for (int kk4 = 0; kk4 < 4; kk4++) {
-                v[8 * ct + 2 * kk4] = mma4::bytes_to_f16x2(wd[kk4], 0x4140, 1152.f);     // rows 2q, 2q + 1
-                v[8 * ct + 2 * kk4 + 1] = mma4::bytes_to_f16x2(wd[kk4], 0x4342, 1152.f); // rows 2q + 8, 2q + 9
+            for (int ct = 0; ct < kCT; ct++) {
+                const int ncol = 8 * kCT * m + 8 * ct + gq;
+                const int chunk = (4 * (kb >> 2) + q) ^ (4 * (ncol & 1));
+                const uint32_t wd = cm[((size_t)ncol * 32 + chunk) * 4 + (kb & 3)];
+                v[2 * ct] = mma4::bytes_to_f16x2(wd, 0x4140, 1152.f);     // rows 2q, 2q + 1
+                v[2 * ct + 1] = mma4::bytes_to_f16x2(wd, 0x4342, 1152.f); // rows 2q + 8, 2q + 9
             }
+            mma4::tmem_st(tq + (uint32_t)(2 * kCT * kb), v);
         }
-        mma4::tmem_st16(tw + 16u * (uint32_t)s4i, v);
+        mma4::tmem_wait_st();
     }
-    mma4::tmem_wait_st();
+    mma4::tmem_fence_before();
+    __syncthreads(); // the units are stored; the barriers are initialised
+    mma4::tmem_fence_after();
+
     const LevelCtx &lv = w.lv;
     const uint32_t steps = w.steps, max_len = w.max_len;
     const int dshift = lv.dshift;
-    Tally t;
-    const int n_groups = (w.n_walks + kWalks - 1) / kWalks;
-    for (int grp = blockIdx.x; grp < n_groups; grp += gridDim.x) {
-        // this warp's two walks: slots 2 warp, 2 warp + 1 of the group
-        WalkState st[2];
-        bool live[2];
-        uint32_t gw[2];
+    const int n_groups = (w.n_walks + mma4::kSets * kWalks - 1) / (mma4::kSets * kWalks);
+    bool stalled = false;
+    if (warp < mma4::kStageWarps) {
+        // ---- stage warp: walks kWPW warp .. kWPW warp + kWPW - 1 of each set ----
+        using mma4::kWPW;
+        // The walks' states live in shared memory (lane 0 writes them);
+        // a trail's start is only written (at a new trail), never read.
+        WalkState *wst = reinterpret_cast<WalkState *>(smem_raw + mma4::off_wst); // [set][slot]
+        TallyOf<uint32_t> t; // 32-bit tallies (fewer registers), flushed before they could overflow
+        uint32_t ph[2] = {0, 0}; // parity of the next "sums ready" phase of each set
+        for (int grp = blockIdx.x; grp < n_groups && !stalled; grp += gridDim.x) {
+            const int local0 = grp * mma4::kSets * kWalks + kWPW * warp; // + X kWalks + i
+            uint32_t live = 0; // bit kWPW X + i: walk i of set X exists
 #pragma unroll
-        for (int i = 0; i < 2; i++) {
-            const int local = grp * kWalks + 2 * warp + i;
-            live[i] = local < w.n_walks;
-            gw[i] = w.walk_base + (uint32_t)local;
-            if (live[i]) st[i] = w.walks[local];
-        }
-        for (uint32_t step = 0; step < steps; step++) {
-            const int buf = step & 1;
-            // A. stages; V walks hash, W walks become matrix rows
+            for (int X = 0; X < 2; X++)
 #pragma unroll
-            for (int i = 0; i < 2; i++) {
-                if (!live[i]) continue;
-                const int slot = 2 * warp + i;
-                unsigned char *region = xchg + (size_t)2048 * slot;
-                sm.xchg = reinterpret_cast<uint2 *>(region);
-                const Decoded dx = decode(st[i].cur, lv);
-                const uint64_t base = sm.base[st[i].chunk];
-                uint32_t ua[G::RPL], ub[G::RPL];
-                side_weights<4>(dx.side, dx.qpack, st[i].chunk, lv, sm, g, ua, ub);
-                if (dx.side == 0) {
-                    const uint64_t sum = group_sum64(lane_column_sum<4>(ua, base, lane), 0xFFFFFFFFu);
-                    if (lane == 0) bk.sum[buf][slot] = sum;
-                    continue;
-                }
-                uint32_t row = 0;
-                if (lane == 0) {
-                    row = atomicAdd(&bk.nrows[buf], 1u);
-                    bk.wslot[buf][row] = (uint32_t)slot;
-                    bk.wbase[buf][row] = base;
-                }
-                row = __shfl_sync(0xFFFFFFFFu, row, 0);
-                // The K order of the product (as C^ is stored for it) makes the
-                // lane's own rows j = lane + 32 t, t = 0..7, the 16-byte chunk
-                // `lane` of each part (a: chunk lane, b: chunk 32 + lane) and
-                // plane; chunk c is stored at c ^ (row & 7).  The region's
-                // stage exchange is done (side_weights ends with a warp sync).
-                uint4 out[4]; // (plane 0, a), (plane 1, a), (plane 0, b), (plane 1, b)
-                uint32_t *o = reinterpret_cast<uint32_t *>(out);
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    const uint32_t wa = (ua[2 * e] & 0xFFFFu) | (ua[2 * e + 1] << 16);
-                    const uint32_t wb = (ub[2 * e] & 0xFFFFu) | (ub[2 * e + 1] << 16);
-                    o[0 * 4 + e] = mma4::bytes_to_f16x2(wa, 0x7240, 1024.f);
-                    o[1 * 4 + e] = mma4::bytes_to_f16x2(wa, 0x7341, 1024.f);
-                    o[2 * 4 + e] = mma4::bytes_to_f16x2(wb, 0x7240, 1024.f);
-                    o[3 * 4 + e] = mma4::bytes_to_f16x2(wb, 0x7341, 1024.f);
-                }
-                const uint32_t swz = row & 7;
-                uint4 *d4 = reinterpret_cast<uint4 *>(region);
-                d4[0 * 64 + ((uint32_t)lane ^ swz)] = out[0];
-                d4[1 * 64 + ((uint32_t)lane ^ swz)] = out[1];
-                d4[0 * 64 + ((uint32_t)(32 + lane) ^ swz)] = out[2];
-                d4[1 * 64 + ((uint32_t)(32 + lane) ^ swz)] = out[3];
-            }
-            __syncthreads();
-            // B. the W rows times this warp's columns 16 warp .. 16 warp + 15
-            const uint32_t nrows = bk.nrows[buf];
-            if (nrows > 0) {
-                const int tiles = (int)(nrows + 15) / 16;
-                float acc[2][2][2][4]; // [row tile][plane][column tile][fragment]
-#pragma unroll
-                for (int a = 0; a < 2; a++)
-#pragma unroll
-                    for (int b = 0; b < 2; b++)
-#pragma unroll
-                        for (int c = 0; c < 2; c++)
-#pragma unroll
-                            for (int d = 0; d < 4; d++) acc[a][b][c][d] = 0.f;
-                // ldmatrix rows: lane l addresses row (l & 7) + 8 ((l >> 3) & 1) of
-                // the tile and K offset 8 (l >> 4)
-                const int mrow = (lane & 7) + 8 * ((lane >> 3) & 1), mkof = lane >> 4;
-                uint32_t arow[2], aswz[2];
-#pragma unroll
-                for (int tile = 0; tile < 2; tile++) {
-                    const uint32_t r = (uint32_t)(16 * tile + mrow);
-                    const uint32_t rr = r < nrows ? r : 0; // rows past the W walks read row 0 (results unused)
-                    arow[tile] = mma4::smem_u32(xchg + (size_t)2048 * bk.wslot[buf][rr]);
-                    aswz[tile] = rr & 7;
-                }
-                // C^'s fragments from tensor memory, 16 registers per four
-                // K-blocks, the next four loading while these are used
-                uint32_t bq[2][16];
-                mma4::tmem_ld16(bq[0], tw);
-#pragma unroll
-                for (int s4i = 0; s4i < kK / 64; s4i++) {
-                    mma4::tmem_wait_ld(bq[s4i & 1]);
-                    if (s4i + 1 < kK / 64) mma4::tmem_ld16(bq[(s4i + 1) & 1], tw + 16u * (uint32_t)(s4i + 1));
-#pragma unroll
-                    for (int kk4 = 0; kk4 < 4; kk4++) {
-                        const int kb = 4 * s4i + kk4; // K-block of 16
-                        uint32_t b0[2], b1[2];
-#pragma unroll
-                        for (int ct = 0; ct < 2; ct++) {
-                            b0[ct] = bq[s4i & 1][8 * ct + 2 * kk4];
-                            b1[ct] = bq[s4i & 1][8 * ct + 2 * kk4 + 1];
-                        }
-#pragma unroll
-                        for (int tile = 0; tile < 2; tile++) {
-                            if (tile < tiles) {
-#pragma unroll
-                                for (int p = 0; p < 2; p++) {
-                                    const uint32_t chunk = ((uint32_t)(2 * kb + mkof)) ^ aswz[tile];
-                                    uint32_t af[4];
-                                    mma4::ldmatrix_x4(af, arow[tile] + 1024 * p + 16 * chunk);
-#pragma unroll
-                                    for (int ct = 0; ct < 2; ct++)
-                                        mma4::mma16816(acc[tile][p][ct], af, b0[ct], b1[ct]);
-                                }
-                            }
-                        }
+                for (int i = 0; i < kWPW; i++) {
+                    const int local = local0 + X * kWalks + i;
+                    if (local < w.n_walks) {
+                        live |= 1u << (kWPW * X + i);
+                        if (lane == 0) wst[X * kWalks + kWPW * warp + i] = w.walks[local];
                     }
                 }
-                // fingerprints of this warp's columns for every W row, hashed
-                // into the row's walk: rows gq and gq + 8 of each tile
+            __syncwarp();
+            // A of set X: stages; V walks hash, W walks become matrix rows
+            auto phase_a = [&](int X) {
+                Book &bk = books[X];
 #pragma unroll
-                for (int tile = 0; tile < 2; tile++) {
-                    if (tile < tiles) {
+                for (int i = 0; i < kWPW; i++) {
+                    const int slot = kWPW * warp + i;
+                    unsigned char *region = smem_raw + mma4::off_xchg + (size_t)2048 * (X * kWalks + slot);
+                    uint32_t isw = 0;
+                    if ((live >> (kWPW * X + i)) & 1u) {
+                        const uint64_t cur = wst[X * kWalks + slot].cur;
+                        const uint32_t chunk = wst[X * kWalks + slot].chunk;
+                        sm.xchg = reinterpret_cast<uint2 *>(region);
+                        const Decoded dx = decode(cur, lv);
+                        const uint64_t base = sm.base[chunk];
+                        uint32_t ua[G::RPL], ub[G::RPL];
+                        side_weights<4>(dx.side, dx.qpack, chunk, lv, sm, g, ua, ub);
+                        if (dx.side == 0) {
+                            const uint64_t sum = group_sum64(lane_column_sum<4>(ua, base, lane), 0xFFFFFFFFu);
+                            if (lane == 0) bk.sum[slot] = sum;
+                        } else {
+                            isw = 1;
+                            if (lane == 0) bk.wbase[slot] = base;
+                            // The K order of the product (as C^ is stored for it)
+                            // makes the lane's own rows j = lane + 32 t, t = 0..7,
+                            // the 16-byte chunk `lane` of each part (a: chunk lane,
+                            // b: chunk 32 + lane) and plane; chunk c is stored at
+                            // c ^ (slot & 7).  The region's stage exchange is done
+                            // (side_weights ends with a warp sync).
+                            uint4 out[4]; // (plane 0, a), (plane 1, a), (plane 0, b), (plane 1, b)
+                            uint32_t *o = reinterpret_cast<uint32_t *>(out);
+#pragma unroll
+                            for (int e = 0; e < 4; e++) {
+                                const uint32_t wa = (ua[2 * e] & 0xFFFFu) | (ua[2 * e + 1] << 16);
+                                const uint32_t wb = (ub[2 * e] & 0xFFFFu) | (ub[2 * e + 1] << 16);
+                                o[0 * 4 + e] = mma4::bytes_to_f16x2(wa, 0x7240, 1024.f);
+                                o[1 * 4 + e] = mma4::bytes_to_f16x2(wa, 0x7341, 1024.f);
+                                o[2 * 4 + e] = mma4::bytes_to_f16x2(wb, 0x7240, 1024.f);
+                                o[3 * 4 + e] = mma4::bytes_to_f16x2(wb, 0x7341, 1024.f);
+                            }
+                            const uint32_t swz = (uint32_t)slot & 7;
+                            uint4 *d4 = reinterpret_cast<uint4 *>(region);
+                            d4[0 * 64 + ((uint32_t)lane ^ swz)] = out[0];
+                            d4[1 * 64 + ((uint32_t)lane ^ swz)] = out[1];
+                            d4[0 * 64 + ((uint32_t)(32 + lane) ^ swz)] = out[2];
+                            d4[1 * 64 + ((uint32_t)(32 + lane) ^ swz)] = out[3];
+                        }
+                    }
+                    if (lane == 0) bk.isw[slot] = isw;
+                }
+                __syncwarp();
+                if (lane == 0) mma4::mbar_arrive(&bars[X]); // rows of X ready (this warp's part)
+            };
+            // C of set X: each walk's step
+            auto phase_c = [&](int X) {
+                Book &bk = books[X];
+#pragma unroll
+                for (int i = 0; i < kWPW; i++) {
+                    if (!((live >> (kWPW * X + i)) & 1u)) continue;
+                    const int slot = kWPW * warp + i;
+                    const uint64_t y = smix(bk.sum[slot]) & lv.maskL;
+                    WalkState S = wst[X * kWalks + slot];
+                    const int local = local0 + X * kWalks + i;
+                    const uint32_t gw = w.walk_base + (uint32_t)local;
+                    t.steps++;
+                    t.w += (uint32_t)(S.cur & 1);
+                    S.len++;
+                    if ((y >> dshift) == 0) {
+                        t.dp++;
+                        if (lane == 0) dp_insert(w, y, make_ref(gw, S.seq, S.len), t);
+                        __syncwarp();
+                        new_trail(S, gw, lv);
+                        if (lane == 0) w.walks[local].start = S.start;
+                    } else if (S.len >= max_len) {
+                        t.ab++;
+                        new_trail(S, gw, lv);
+                        if (lane == 0) w.walks[local].start = S.start;
+                    } else {
+                        S.cur = y;
+                    }
+                    __syncwarp(); // every lane has read the old state
+                    if (lane == 0) wst[X * kWalks + slot] = S;
+                }
+                // the sums start again from zero for the set's next products
+                __syncwarp();
+                if (lane < kWPW) bk.sum[kWPW * warp + lane] = 0;
+                __syncwarp();
+            };
+            if (steps > 0) {
+                phase_a(0);
+                phase_a(1);
+            }
+            for (uint32_t step = 0; step < steps && !stalled; step++) {
+#pragma unroll
+                for (int X = 0; X < 2; X++) {
+                    if (stalled) break;
+                    if (!mma4::mbar_wait(&bars[2 + X], ph[X])) {
+                        stalled = true;
+                        break;
+                    }
+                    ph[X] ^= 1u;
+                    phase_c(X);
+                    if (step + 1 < steps) phase_a(X);
+                }
+                if (t.steps >= 0x40000000u) flush_tally(w.counters, t, g); // every tally is at most t.steps
+            }
+            // the states back to global memory (every lane has written its last update)
+#pragma unroll
+            for (int X = 0; X < 2; X++)
+#pragma unroll
+                for (int i = 0; i < kWPW; i++)
+                    if (((live >> (kWPW * X + i)) & 1u) && lane == 0) {
+                        const WalkState &S = wst[X * kWalks + kWPW * warp + i];
+                        WalkState *d = &w.walks[local0 + X * kWalks + i];
+                        d->cur = S.cur;
+                        d->len = S.len;
+                        d->chunk = S.chunk;
+                        d->seq = S.seq;
+                    }
+            __syncwarp();
+        }
+        flush_tally(w.counters, t, g);
+    } else {
+        // ---- MMA warp m: C^'s columns 8 kCT m .. 8 kCT (m + 1) - 1 ----
+        using mma4::kCT;
+        const int m = warp - mma4::kStageWarps;
+        const uint32_t tq = tmem + ((uint32_t)(32 * (m & 3)) << 16) + (uint32_t)(64 * kCT * (m >> 2));
+        uint8_t *rows = smem_raw + mma4::off_rows + kWalks * m; // slots of the compacted rows
+        uint32_t ph[2] = {0, 0}; // parity of the next "rows ready" phase of each set
+        const int mrow = (lane & 7) + 8 * ((lane >> 3) & 1), mkof = lane >> 4; // ldmatrix row, K offset
+        for (int grp = blockIdx.x; grp < n_groups && !stalled; grp += gridDim.x)
+            for (uint32_t step = 0; step < steps && !stalled; step++)
+#pragma unroll 1
+                for (int X = 0; X < 2; X++) {
+                    if (!mma4::mbar_wait(&bars[X], ph[X])) {
+                        stalled = true;
+                        break;
+                    }
+                    ph[X] ^= 1u;
+                    Book &bk = books[X];
+                    // the W rows, compacted in slot order
+                    const bool flagged = lane < kWalks && bk.isw[lane < kWalks ? lane : 0] != 0;
+                    const uint32_t mask = __ballot_sync(0xFFFFFFFFu, flagged);
+                    const uint32_t nrows = (uint32_t)__popc(mask);
+                    if (flagged) rows[__popc(mask & ((1u << lane) - 1u))] = (uint8_t)lane;
+                    __syncwarp();
+#pragma unroll 1
+                    for (int tile = 0; tile < (int)(nrows + 15) / 16; tile++) {
+                        const uint32_t r0 = (uint32_t)(16 * tile + mrow);
+                        const uint32_t sl0 = rows[r0 < nrows ? r0 : 0]; // rows past the W walks read row 0 (unused)
+                        const uint32_t arow =
+                            mma4::smem_u32(smem_raw + mma4::off_xchg + (size_t)2048 * (X * kWalks + sl0));
+                        const uint32_t aswz = sl0 & 7;
+                        float acc[2][kCT][4]; // [plane][column tile][fragment]
+#pragma unroll
+                        for (int b = 0; b < 2; b++)
+#pragma unroll
+                            for (int c = 0; c < kCT; c++)
+#pragma unroll
+                                for (int d = 0; d < 4; d++) acc[b][c][d] = 0.f;
+                        // one K-block: both planes' A fragments times the 8 column tiles
+                        auto kblock = [&](int kb, const uint32_t(&f)[2 * kCT]) {
+#pragma unroll
+                            for (int p = 0; p < 2; p++) {
+                                uint32_t af[4];
+                                mma4::ldmatrix_x4(af, arow + 1024 * p + 16 * (((uint32_t)(2 * kb + mkof)) ^ aswz));
+#pragma unroll
+                                for (int ct = 0; ct < kCT; ct++) mma4::mma16816(acc[p][ct], af, f[2 * ct], f[2 * ct + 1]);
+                            }
+                        };
+                        // C^'s fragments from tensor memory, one K-block (2 kCT
+                        // registers) at a time, the next loading while one is used
+                        uint32_t f0[2 * kCT], f1[2 * kCT];
+                        mma4::tmem_ld(f0, tq);
+#pragma unroll 1
+                        for (int kb2 = 0; kb2 < kK / 32; kb2++) {
+                            mma4::tmem_wait_ld(f0);
+                            mma4::tmem_ld(f1, tq + (uint32_t)(2 * kCT * (2 * kb2 + 1)));
+                            kblock(2 * kb2, f0);
+                            mma4::tmem_wait_ld(f1);
+                            if (kb2 + 1 < kK / 32) mma4::tmem_ld(f0, tq + (uint32_t)(2 * kCT * (2 * kb2 + 2)));
+                            kblock(2 * kb2 + 1, f1);
+                        }
+                        // fingerprints of the warp's columns for the tile's rows gq
+                        // and gq + 8, hashed into each row's walk
 #pragma unroll
                         for (int hh = 0; hh < 2; hh++) {
                             const uint32_t r = (uint32_t)(16 * tile + gq + 8 * hh);
                             const bool valid = r < nrows;
-                            const uint64_t base = valid ? bk.wbase[buf][r] : 0;
+                            const uint32_t sl = rows[valid ? r : 0];
+                            const uint64_t base = valid ? bk.wbase[sl] : 0;
                             const uint64_t pre = base ^ (base >> 30);
                             uint64_t part = 0;
 #pragma unroll
-                            for (int ct = 0; ct < 2; ct++)
+                            for (int ct = 0; ct < kCT; ct++)
 #pragma unroll
                                 for (int c = 0; c < 2; c++) {
-                                    const int Q = 16 * warp + 8 * ct + 2 * q + c;
-                                    const int p0 = __float2int_rn(acc[tile][0][ct][2 * hh + c]);
-                                    const int p1 = __float2int_rn(acc[tile][1][ct][2 * hh + c]);
+                                    const int Q = 8 * kCT * m + 8 * ct + 2 * q + c;
+                                    const int p0 = __float2int_rn(acc[0][ct][2 * hh + c]);
+                                    const int p1 = __float2int_rn(acc[1][ct][2 * hh + c]);
                                     const uint32_t l = ((uint32_t)p0 + ((uint32_t)p1 << 8)) & 0xFFFFu;
                                     const uint32_t nl = (0u - l) & 0xFFFFu;
                                     const uint64_t e = smix_pre(pre, min(l, nl));
-                                    part += (valid && Q >= 1) ? e : 0ull;
+                                    part += (Q >= 1) ? e : 0ull;
                                 }
                             part += __shfl_xor_sync(0xFFFFFFFFu, part, 1);
                             part += __shfl_xor_sync(0xFFFFFFFFu, part, 2);
-                            if (valid && q == 0) atomicAdd(&bk.sum[buf][bk.wslot[buf][r]], part);
+                            if (valid && q == 0) atomicAdd(&bk.sum[sl], part);
                         }
                     }
-                }
-            }
-            __syncthreads();
-            // C. each walk's step
-#pragma unroll
-            for (int i = 0; i < 2; i++) {
-                if (!live[i]) continue;
-                const int slot = 2 * warp + i;
-                const uint64_t y = smix(bk.sum[buf][slot]) & lv.maskL;
-                WalkState &S = st[i];
-                t.steps++;
-                t.w += S.cur & 1;
-                S.len++;
-                if ((y >> dshift) == 0) {
-                    t.dp++;
-                    if (lane == 0) dp_insert(w, y, make_ref(gw[i], S.seq, S.len), t);
                     __syncwarp();
-                    new_trail(S, gw[i], lv);
-                } else if (S.len >= max_len) {
-                    t.ab++;
-                    new_trail(S, gw[i], lv);
-                } else {
-                    S.cur = y;
+                    if (lane == 0) mma4::mbar_arrive(&bars[2 + X]); // sums of X ready (this warp's part)
                 }
-            }
-            // clear this buffer for the step after next (the next step uses the other one)
-            __syncwarp();
-            if (lane < 2) bk.sum[buf][2 * warp + lane] = 0;
-            if (threadIdx.x == 0) bk.nrows[buf] = 0;
-        }
-        __syncthreads(); // the next group's first step may reuse this group's last buffer
-#pragma unroll
-        for (int i = 0; i < 2; i++)
-            if (live[i] && lane == 0) w.walks[grp * kWalks + 2 * warp + i] = st[i];
     }
-    flush_tally(w.counters, t, g);
+    if (stalled && lane == 0) atomicAdd(w.stall, 1u);
     // every warp's tensor-memory loads have completed (each was waited for)
     mma4::tmem_fence_before();
     __syncthreads();
     if (warp == 0) {
         mma4::tmem_fence_after();
-        mma4::tmem_dealloc(bk.tmem, mma4::kTmemCols);
+        mma4::tmem_dealloc(tmem, mma4::kTmemCols);
     }
 }
 
@@ -1546,7 +1707,8 @@ cudaError_t walks_mma4(const WalkLaunch &w, cudaStream_t s)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walks_mma4, mma4::kThreads, mma4::smem_bytes);
         per_sm = b > 0 ? b : 1;
     }
-    const size_t groups = ((size_t)w.n_walks + mma4::kWalks - 1) / mma4::kWalks;
+    if (!w.stall) return cudaErrorInvalidValue; // a stalled wait must have somewhere to be counted
+    const size_t groups = ((size_t)w.n_walks + mma4::kSets * mma4::kWalks - 1) / (mma4::kSets * mma4::kWalks);
     size_t grid = (size_t)num_sms() * (size_t)per_sm;
     if (grid > groups) grid = groups;
     if (grid == 0) grid = 1;

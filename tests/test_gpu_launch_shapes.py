@@ -62,7 +62,7 @@ def test_reported_copies_match_the_uploads_and_reads():
     """A second n = 3 problem (the shared stage tables are already on the
     device) uploads C^ as 64 x 64 (a, b) words, the 64 fingerprint weights,
     the rotation masks (a 16-bit word per Pauli and lane, 32 lanes) and, with
-    every entry in int8, the byte quads; each walk launch reads back the 15 counters and
+    every entry in int8, the byte quads; each walk launch reads back the 16 counters and
     three queue heads, plus 24 bytes per claw candidate."""
     from paper_1606_07413_gb300 import build
 
@@ -83,7 +83,7 @@ def test_reported_copies_match_the_uploads_and_reads():
             r = prob.level_collect()
         checked = r["claws"] + r["false_hash"]  # the host stops checking a launch's list at its first claw
         assert r["h2d_bytes"] == want_up
-        read_cands = r["d2h_bytes"] - launches * (15 * 8 + 3 * 4)
+        read_cands = r["d2h_bytes"] - launches * (16 * 8 + 3 * 4)
         assert read_cands % 24 == 0 and read_cands // 24 >= checked
     with Q.Problem.from_circuit(3, gates, 5, Q.default_params(3, walks=4096, c_layout=1)) as wide:
         assert wide.poll()["h2d_bytes"] == want_up - D * D // 2 * 4  # no byte quads
