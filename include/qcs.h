@@ -167,8 +167,9 @@ typedef struct qcs_problem qcs_problem;
 /* Launch shapes of the walk kernels for n qubits (the autotuner's space; not
  * a passage of the paper: how walks map onto the GPU).  Returns the number
  * of shapes (>= 1) and fills, for shape i < max_shapes, warps[i] (warps per
- * CTA, each warp evaluating 32 / min(32, 4^n) walks; two at n = 4, shape 3)
- * and min_blocks[i] (the
+ * CTA of the level walk, each warp evaluating 32 / min(32, 4^n) walks; at
+ * n = 4, shape 3 is the tensor-core walk: 12 warps evaluating two walks of
+ * each of two sets, and 8 warps doing the contraction) and min_blocks[i] (the
  * resident CTAs per SM the kernel is compiled for, capping its registers at
  * 65536 / (32 warps[i] min_blocks[i])).  Either pointer may be NULL.
  * QCS_ERR_ARG if n is not in 1..4. */

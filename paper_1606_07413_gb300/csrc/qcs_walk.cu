@@ -79,10 +79,10 @@ constexpr int kGemvUnroll = QCS_GEMV_UNROLL;
 //   n <= 2: 8 warps
 //   n = 3 : (16, 2) (8, 4) (32, 1) (16, 1)
 //   n = 4 : (16, 1) (24, 1) (32, 1)   (one CTA per SM: C^ takes 128 KB)
-//           and shape 3: 16 warps, two walks each, with the W side's
-//           contraction on the tensor cores (k_walks_mma4; the level walk
-//           only, and only when C^ is held in int8; elsewhere shape 3 runs
-//           shape 0)
+//           and shape 3: the W side's contraction on the tensor cores
+//           (k_walks_mma4, 12 stage and 8 MMA warps; the level walk only,
+//           and only when C^ is held in int8; elsewhere shape 3 runs shape
+//           0, whose figures shape_warps gives for it)
 __host__ __device__ constexpr int shape_count(int nq) { return nq <= 2 ? 1 : 4; }
 __host__ __device__ constexpr int shape_warps(int nq, int s)
 {
@@ -820,8 +820,8 @@ __device__ __forceinline__ uint32_t bytes_to_f16x2(uint32_t word, uint32_t sel, 
 
 __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
 {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};"
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
                  : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
@@ -887,7 +887,7 @@ __device__ __forceinline__ void tmem_ld8(uint32_t (&v)[8], uint32_t taddr)
                  : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[8])
+[[maybe_unused]] __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[8])
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7])
@@ -895,12 +895,13 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[8])
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld(uint32_t (&v)[16], uint32_t taddr) { tmem_ld16(v, taddr); }
-__device__ __forceinline__ void tmem_ld(uint32_t (&v)[8], uint32_t taddr) { tmem_ld8(v, taddr); }
-__device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t (&v)[16]) { tmem_st16(taddr, v); }
-__device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t (&v)[8]) { tmem_st8(taddr, v); }
+// (the 16-register forms serve 4 MMA warps, the 8-register ones 8)
+[[maybe_unused]] __device__ __forceinline__ void tmem_ld(uint32_t (&v)[16], uint32_t taddr) { tmem_ld16(v, taddr); }
+[[maybe_unused]] __device__ __forceinline__ void tmem_ld(uint32_t (&v)[8], uint32_t taddr) { tmem_ld8(v, taddr); }
+[[maybe_unused]] __device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t (&v)[16]) { tmem_st16(taddr, v); }
+[[maybe_unused]] __device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t (&v)[8]) { tmem_st8(taddr, v); }
 
-__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[16])
+[[maybe_unused]] __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[16])
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
@@ -1198,18 +1199,24 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
                                 for (int ct = 0; ct < kCT; ct++) mma4::mma16816(acc[p][ct], af, f[2 * ct], f[2 * ct + 1]);
                             }
                         };
-                        // C^'s fragments from tensor memory, one K-block (2 kCT
-                        // registers) at a time, the next loading while one is used
-                        uint32_t f0[2 * kCT], f1[2 * kCT];
-                        mma4::tmem_ld(f0, tq);
+                        // C^'s fragments from tensor memory, two K-blocks (16
+                        // registers) at a time, the next two loading while these are used
+                        static_assert(kCT == 4, "two K-blocks per 16-register load");
+                        uint32_t f0[16], f1[16];
+                        auto half = [](const uint32_t(&f)[16], int i) -> const uint32_t(&)[8] {
+                            return *reinterpret_cast<const uint32_t(*)[8]>(&f[8 * i]);
+                        };
+                        mma4::tmem_ld16(f0, tq);
 #pragma unroll 1
-                        for (int kb2 = 0; kb2 < kK / 32; kb2++) {
+                        for (int kb4 = 0; kb4 < kK / 64; kb4++) {
                             mma4::tmem_wait_ld(f0);
-                            mma4::tmem_ld(f1, tq + (uint32_t)(2 * kCT * (2 * kb2 + 1)));
-                            kblock(2 * kb2, f0);
+                            mma4::tmem_ld16(f1, tq + 16u * (uint32_t)(2 * kb4 + 1));
+                            kblock(4 * kb4, half(f0, 0));
+                            kblock(4 * kb4 + 1, half(f0, 1));
                             mma4::tmem_wait_ld(f1);
-                            if (kb2 + 1 < kK / 32) mma4::tmem_ld(f0, tq + (uint32_t)(2 * kCT * (2 * kb2 + 2)));
-                            kblock(2 * kb2 + 1, f1);
+                            if (kb4 + 1 < kK / 64) mma4::tmem_ld16(f0, tq + 16u * (uint32_t)(2 * kb4 + 2));
+                            kblock(4 * kb4 + 2, half(f1, 0));
+                            kblock(4 * kb4 + 3, half(f1, 1));
                         }
                         // fingerprints of the warp's columns for the tile's rows gq
                         // and gq + 8, hashed into each row's walk
@@ -1858,7 +1865,7 @@ int lanes_per_walk(int n) { return n == 4 ? Geo<4>::LPW : n == 3 ? Geo<3>::LPW :
 
 int launch_shapes(int n) { return n == 4 ? shape_count(4) : n == 3 ? shape_count(3) : shape_count(2); }
 
-int shape_warps_of(int n, int shape) { return shape_warps(n, shape); }
+int shape_warps_of(int n, int shape) { return n == 4 && shape == 3 ? mma4::kCtaWarps : shape_warps(n, shape); }
 
 int shape_min_blocks_of(int n, int shape) { return shape_min_blocks(n, shape); }
 
