@@ -113,13 +113,13 @@ def workload_config(c, k=None, steps=None, rewalk_budget=None):
 # the steps, plus 32 bytes per distinguished point (0.5 MB at the headline's
 # 64 steps), so the figure stands for the headline launch.
 WALK_NCU = {
-    "k_walks<4,3>": {"source_sha256_16": "2e76870690a393b4", "dram_bytes_per_launch": 34905344,
-                     "warp_inst_per_step": 1356.1},
-    "k_walks<4,0>": {"source_sha256_16": "2e76870690a393b4", "dram_bytes_per_launch": 34978304,
+    "k_walks<4,3>": {"source_sha256_16": "1ad60f80ab027ebf", "dram_bytes_per_launch": 34744576,
+                     "warp_inst_per_step": 1059.8},
+    "k_walks<4,0>": {"source_sha256_16": "1ad60f80ab027ebf", "dram_bytes_per_launch": 35051520,
                      "warp_inst_per_step": 1937.6},
     # n = 3, level 5: `bench.py --level-only n3_level5 --steps 2`, one launch of 2^16 walks x 512 steps,
     # the launch of the n3_level5 record (profiles/k_walks_n3_level5_walks65536.md)
-    "k_walks<3,0>": {"source_sha256_16": "2e76870690a393b4", "dram_bytes_per_launch": 2184192,
+    "k_walks<3,0>": {"source_sha256_16": "1ad60f80ab027ebf", "dram_bytes_per_launch": 2178560,
                      "warp_inst_per_step": 379.3},
 }
 
@@ -141,6 +141,20 @@ def walk_source_hash() -> str:
         code = re.sub(r"//[^\n]*", " ", code)
         h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
+
+
+def measured_tensor_tflops(sustained: bool = True):
+    """Dense bf16 tensor throughput measured on the GB300s
+    (MEASURED_PEAKS.json beside this file; the sustained figure for a kernel
+    timed inside a long step), else the fallback figure.  f16 has the same
+    nominal dense rate as bf16."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+    try:
+        with open(path) as f:
+            return float(json.load(f)[key]), f"measured dense bf16 ({key}, MEASURED_PEAKS.json; f16 = bf16 nominal)"
+    except (OSError, KeyError, ValueError):
+        return (1700.0 if sustained else 1900.0), "fallback (no measured peaks file)"
 
 
 def measured_hbm_gbs():
@@ -188,15 +202,28 @@ def walk_roofline(kernel, n, w_steps, steps, walk_s, launches, dp4a_per_s, clock
         issue = {"warp_inst_per_step": rec["warp_inst_per_step"], "achieved_per_s": issue_rate,
                  "peak_per_s": issue_peak, "frac": issue_rate / issue_peak,
                  "peak_source": f"{num_sms} SMs x 4 schedulers x {clock_mhz:.0f} MHz (median sampled SM clock)"}
-    tensor = None
-    if hmma_per_s and kernel == "k_walks<4,3>":
-        # the tensor-core shape: each 16-bit-weight multiply-add is two f16
-        # byte-plane multiply-adds on the MMA pipe
-        tensor = {"achieved_mac_per_s": 2 * achieved, "peak_mac_per_s": hmma_per_s,
-                  "frac": 2 * achieved / hmma_per_s,
-                  "peak_source": "measured mma.sync m16n8k16 f16 -> f32 rate (qcs_peak_hmma, this run)"}
+    if kernel == "k_walks<4,3>":
+        # The tensor-core shape: each 16-bit-weight multiply-add is two f16
+        # byte-plane multiply-adds (4 flops) on the tensor cores, against the
+        # measured dense f16/bf16 peak; beside it the same work against the
+        # legacy mma.sync rate this kernel issues on, and the issue slots.
+        peak_tf, peak_src = measured_tensor_tflops(sustained=True)
+        flops = 4 * achieved
+        mma_sync = None
+        if hmma_per_s:
+            mma_sync = {"achieved_mac_per_s": 2 * achieved, "peak_mac_per_s": hmma_per_s,
+                        "frac": 2 * achieved / hmma_per_s,
+                        "peak_source": "measured mma.sync m16n8k16 f16 -> f32 rate (qcs_peak_hmma, this run)"}
+        return {"bound": "tensor", "unit": "TFLOP/s", "kernel": kernel,
+                "achieved": flops / 1e12, "peak": peak_tf, "frac": flops / 1e12 / peak_tf,
+                "peak_source": peak_src, "mma_sync": mma_sync,
+                "dp4a_equivalent": {"achieved_gops": achieved / 1e9, "peak_gops": peak / 1e9, "frac": achieved / peak,
+                                    "peak_source": "2 x measured dp4a rate (the other shapes' contraction pipe)"},
+                "traffic": traffic, "traffic_unit": "bytes per launch", "hbm": hbm, "issue_slots": issue,
+                "algorithmic_ops": f"2*d^2 = {2 * d * d} 16-bit-weight multiply-adds per W-side walk step, "
+                                   "each two f16 byte-plane multiply-adds (4 flops) on the tensor cores"}
     return {"bound": "alu", "unit": "Gop/s", "kernel": kernel,
-            "achieved": achieved / 1e9, "peak": peak / 1e9, "frac": achieved / peak, "tensor": tensor,
+            "achieved": achieved / 1e9, "peak": peak / 1e9, "frac": achieved / peak,
             "traffic": traffic, "traffic_unit": "bytes per launch", "hbm": hbm, "issue_slots": issue,
             "peak_source": "2 x measured dp4a rate (qcs_peak_idp4a, this run: "
                            f"{dp4a_per_s / 1e9:.0f} G dp4a/s)",

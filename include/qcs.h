@@ -114,10 +114,11 @@ typedef struct qcs_params {
     int32_t exhaustive_first; /* 1: qcs_run_walks settles such levels by qcs_certify_level alone,
                                  without walking them (0: walk first) */
     int32_t launch_shape;     /* launch shape of the level-walk kernel, 0 .. qcs_launch_shapes(n) - 1
-                                 (0 = default); the walks and results do not depend on it.  n = 4,
-                                 shape 3: the W side's contraction on the tensor cores (f16 byte
-                                 planes, exact f32 sums), two walks per warp, when C^ is held in int8
-                                 (c_layout 0); otherwise, and in a batch, it runs shape 0 */
+                                 (default 3 at n = 4, else 0); the walks and results do not depend on
+                                 it.  n = 4, shape 3: the W side's contraction on the tensor cores
+                                 (f16 byte planes, exact f32 sums) in warps of its own, beside the
+                                 warps that evaluate the stages, when C^ is held in int8 (c_layout
+                                 0); otherwise, and in a batch, it runs shape 0 */
     int32_t c_layout;         /* device layout of C^ for the W side's contraction (n >= 3): 0 = signed
                                  byte quads when every entry fits in int8 (dp4a), else 32-bit words;
                                  1 = 32-bit words always (IMAD).  Results do not depend on it */

@@ -937,7 +937,10 @@ void qcs_default_params(int n_qubits, qcs_params *p)
     case 1:
     case 2: p->state_bits = 32; p->dp_bits = 6; p->walks = 4096; p->table_log2 = 16; break;
     case 3: p->state_bits = 48; p->dp_bits = 10; p->walks = 1 << 16; p->table_log2 = 22; break;
-    default: p->state_bits = 64; p->dp_bits = 12; p->walks = 1 << 20; p->table_log2 = 26; break;
+    default:
+        p->state_bits = 64; p->dp_bits = 12; p->walks = 1 << 20; p->table_log2 = 26;
+        p->launch_shape = 3; // the tensor-core walk (shape 0 where C^ does not fit int8)
+        break;
     }
     p->steps_per_launch = 64;
     p->max_trail_factor = 20;

@@ -789,7 +789,22 @@ struct Book {
 constexpr size_t off_wst = off_book + kSets * sizeof(Book);              // WalkState [set][slot]
 constexpr size_t off_rows = off_wst + sizeof(WalkState) * kSets * kWalks; // per MMA warp: slots of the compacted rows
 constexpr size_t off_bar = (off_rows + kMmaWarps * kWalks + 7) & ~(size_t)7;
-constexpr size_t off_tmem = off_bar + 4 * sizeof(uint64_t); // rows ready [2], sums ready [2]
+// The MMA warps are also the CTA's collectors (Sec. 4.2's role): they store
+// the distinguished points the stage warps hand them, while they wait for a
+// set's rows and after their last product, so that no stage warp waits on
+// the table's atomics.  One ring per stage warp (its lane 0 the only
+// producer; lane r / 8 of MMA warp r % 8 the only consumer of ring r); a
+// full ring makes the producer store the point itself.
+constexpr uint32_t kRing = 64;
+constexpr int kCollectBits = 8;
+struct Rings {
+    uint64_t dp[kStageWarps][kRing], ref[kStageWarps][kRing];
+    uint32_t tail[kStageWarps]; // points pushed (producer)
+    uint32_t head[kStageWarps]; // points stored (collector)
+    uint32_t done[kStageWarps]; // the stage warp has pushed its last point
+};
+constexpr size_t off_rings = off_bar + 4 * sizeof(uint64_t); // after: rows ready [2], sums ready [2]
+constexpr size_t off_tmem = off_rings + sizeof(Rings);
 constexpr size_t smem_bytes = off_tmem + 16;
 static_assert(smem_bytes <= 227 * 1024, "shared memory of the tensor-core walk kernel");
 // tensor memory: MMA warp m (the warp m % 4 of its warpgroup, so lanes
@@ -925,6 +940,31 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *b)
                  : "memory");
 }
 
+// Whether the phase of parity `ph` has completed (no waiting).
+__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t ph)
+{
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done)
+                 : "r"(smem_u32(b)), "r"(ph)
+                 : "memory");
+    return done != 0;
+}
+
+// One bounded try: whether the phase of parity `ph` has completed, waiting
+// (suspended) for at most a system-dependent time.
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t ph)
+{
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done)
+                 : "r"(smem_u32(b)), "r"(ph)
+                 : "memory");
+    return done != 0;
+}
+
 // Wait until the phase of parity `ph` has completed; false if the wait ran
 // out (kWaitCycles).
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t ph)
@@ -945,6 +985,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t ph)
 
 } // namespace mma4
 
+// COLLECT: the MMA warps store the distinguished points (launched where
+// theta >= 2^-kCollectBits); otherwise the stage warps store their own and
+// the collecting code is not compiled in.
+template <bool COLLECT>
 __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
 {
     using mma4::Book;
@@ -963,6 +1007,12 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
     for (int i = threadIdx.x; i < mma4::kSets * kWalks; i += blockDim.x) {
         books[i / kWalks].sum[i % kWalks] = 0;
         books[i / kWalks].isw[i % kWalks] = 0;
+    }
+    mma4::Rings &rings = *reinterpret_cast<mma4::Rings *>(smem_raw + mma4::off_rings);
+    if (threadIdx.x < mma4::kStageWarps) {
+        rings.tail[threadIdx.x] = 0;
+        rings.head[threadIdx.x] = 0;
+        rings.done[threadIdx.x] = 0;
     }
     if (threadIdx.x == 0) {
         mma4::mbar_init(&bars[0], mma4::kStageWarps);
@@ -1008,6 +1058,7 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
     const int dshift = lv.dshift;
     const int n_groups = (w.n_walks + mma4::kSets * kWalks - 1) / (mma4::kSets * kWalks);
     bool stalled = false;
+    constexpr bool collect = COLLECT;
     if (warp < mma4::kStageWarps) {
         // ---- stage warp: walks kWPW warp .. kWPW warp + kWPW - 1 of each set ----
         using mma4::kWPW;
@@ -1098,7 +1149,19 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
                     S.len++;
                     if ((y >> dshift) == 0) {
                         t.dp++;
-                        if (lane == 0) dp_insert(w, y, make_ref(gw, S.seq, S.len), t);
+                        if (lane == 0) {
+                            // to the collector, or stored here if its ring is full
+                            volatile uint32_t *vt = rings.tail, *vh = rings.head;
+                            const uint32_t tl = vt[warp];
+                            if (collect && tl - vh[warp] < mma4::kRing) {
+                                rings.dp[warp][tl % mma4::kRing] = y;
+                                rings.ref[warp][tl % mma4::kRing] = make_ref(gw, S.seq, S.len);
+                                __threadfence_block();
+                                vt[warp] = tl + 1;
+                            } else {
+                                dp_insert(w, y, make_ref(gw, S.seq, S.len), t);
+                            }
+                        }
                         __syncwarp();
                         new_trail(S, gw, lv);
                         if (lane == 0) w.walks[local].start = S.start;
@@ -1151,6 +1214,12 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
             __syncwarp();
         }
         flush_tally(w.counters, t, g);
+        // every point this warp pushed is in its ring: the collector may stop once they are stored
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            reinterpret_cast<volatile uint32_t *>(rings.done)[warp] = 1;
+        }
     } else {
         // ---- MMA warp m: C^'s columns 8 kCT m .. 8 kCT (m + 1) - 1 ----
         using mma4::kCT;
@@ -1158,12 +1227,49 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
         const uint32_t tq = tmem + ((uint32_t)(32 * (m & 3)) << 16) + (uint32_t)(64 * kCT * (m >> 2));
         uint8_t *rows = smem_raw + mma4::off_rows + kWalks * m; // slots of the compacted rows
         uint32_t ph[2] = {0, 0}; // parity of the next "rows ready" phase of each set
+        // collecting: lane c < 2 consumes ring m + kMmaWarps c (if there is one)
+        TallyOf<uint32_t> tc;
+        volatile uint32_t *vt = rings.tail, *vd = rings.done;
+        const int ring = m + mma4::kMmaWarps * lane;
+        const bool owner = lane < 2 && ring < mma4::kStageWarps;
+        uint32_t rhead = 0;
+        // store up to `most` pushed points of the owned ring (one at a time
+        // while rows may become ready)
+        auto drain = [&](uint32_t most) -> bool {
+            bool moved = false;
+            if (owner) {
+                volatile uint32_t *vh = rings.head;
+                const uint32_t tl = vt[ring];
+                if (tl != rhead) {
+                    __threadfence_block(); // the entries before tail are written
+                    const uint32_t stop = tl - rhead > most ? rhead + most : tl;
+                    for (; rhead != stop; rhead++)
+                        dp_insert(w, rings.dp[ring][rhead % mma4::kRing], rings.ref[ring][rhead % mma4::kRing], tc);
+                    __threadfence_block();
+                    vh[ring] = rhead; // their slots may be reused
+                    moved = true;
+                }
+            }
+            return __any_sync(0xFFFFFFFFu, moved);
+        };
+        // wait for a set's rows, storing distinguished points meanwhile (with
+        // nothing to store, the warp sleeps on the barrier itself)
+        auto wait_rows = [&](int X) -> bool {
+            const long long t0 = clock64();
+            for (;;) {
+                if (__all_sync(0xFFFFFFFFu, mma4::mbar_test(&bars[X], ph[X]))) return true;
+                if (!drain(1)) {
+                    if (__all_sync(0xFFFFFFFFu, mma4::mbar_try(&bars[X], ph[X]))) return true;
+                    if (clock64() - t0 > mma4::kWaitCycles) return false;
+                }
+            }
+        };
         const int mrow = (lane & 7) + 8 * ((lane >> 3) & 1), mkof = lane >> 4; // ldmatrix row, K offset
         for (int grp = blockIdx.x; grp < n_groups && !stalled; grp += gridDim.x)
             for (uint32_t step = 0; step < steps && !stalled; step++)
 #pragma unroll 1
                 for (int X = 0; X < 2; X++) {
-                    if (!mma4::mbar_wait(&bars[X], ph[X])) {
+                    if (!(collect ? wait_rows(X) : mma4::mbar_wait(&bars[X], ph[X]))) {
                         stalled = true;
                         break;
                     }
@@ -1248,6 +1354,32 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
                     __syncwarp();
                     if (lane == 0) mma4::mbar_arrive(&bars[2 + X]); // sums of X ready (this warp's part)
                 }
+        // the stage warps' last steps come after the last product: store
+        // their points until each owned ring's producer is done and drained
+        long long last = clock64();
+        for (; collect;) {
+            const bool moved = drain(mma4::kRing);
+            bool fin = true;
+            if (owner) {
+                const bool d = vd[ring] != 0;
+                __threadfence_block(); // the final tail, read after its done flag
+                fin = d && vt[ring] == rhead;
+            }
+            if (__all_sync(0xFFFFFFFFu, fin)) break;
+            if (moved) {
+                last = clock64();
+            } else {
+                if (clock64() - last > mma4::kWaitCycles) {
+                    stalled = true; // a stage warp neither pushed nor finished for too long
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        tc.evicted = __reduce_add_sync(0xFFFFFFFFu, tc.evicted);
+        tc.duplicate = __reduce_add_sync(0xFFFFFFFFu, tc.duplicate);
+        tc.pairs = __reduce_add_sync(0xFFFFFFFFu, tc.pairs);
+        flush_tally(w.counters, tc, g);
     }
     if (stalled && lane == 0) atomicAdd(w.stall, 1u);
     // every warp's tensor-memory loads have completed (each was waited for)
@@ -1709,9 +1841,10 @@ cudaError_t walks_mma4(const WalkLaunch &w, cudaStream_t s)
 {
     static int per_sm = 0;
     if (!per_sm) {
-        cudaFuncSetAttribute(k_walks_mma4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mma4::smem_bytes);
+        cudaFuncSetAttribute(k_walks_mma4<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mma4::smem_bytes);
+        cudaFuncSetAttribute(k_walks_mma4<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mma4::smem_bytes);
         int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walks_mma4, mma4::kThreads, mma4::smem_bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walks_mma4<false>, mma4::kThreads, mma4::smem_bytes);
         per_sm = b > 0 ? b : 1;
     }
     if (!w.stall) return cudaErrorInvalidValue; // a stalled wait must have somewhere to be counted
@@ -1719,7 +1852,12 @@ cudaError_t walks_mma4(const WalkLaunch &w, cudaStream_t s)
     size_t grid = (size_t)num_sms() * (size_t)per_sm;
     if (grid > groups) grid = groups;
     if (grid == 0) grid = 1;
-    k_walks_mma4<<<(unsigned)grid, mma4::kThreads, mma4::smem_bytes, s>>>(w);
+    // d_theta = L - dshift: the MMA warps collect where theta >= 2^-kCollectBits
+    const int dtheta = __builtin_popcountll(w.lv.maskL) - w.lv.dshift;
+    if (dtheta <= mma4::kCollectBits)
+        k_walks_mma4<true><<<(unsigned)grid, mma4::kThreads, mma4::smem_bytes, s>>>(w);
+    else
+        k_walks_mma4<false><<<(unsigned)grid, mma4::kThreads, mma4::smem_bytes, s>>>(w);
     return cudaGetLastError();
 }
 

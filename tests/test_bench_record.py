@@ -34,8 +34,15 @@ def test_record_has_the_contract_keys():
 def test_roofline_and_timing_are_consistent():
     r = load()
     roof = r["roofline"]
-    assert roof["bound"] == "alu" and roof["peak"] > 0
+    assert roof["bound"] in ("alu", "tensor") and roof["peak"] > 0
     assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-9
+    if roof["bound"] == "tensor":
+        # the tensor-core shape: f16 flops against the measured dense peak, and
+        # the same multiply-adds against the mma.sync rate it issues on
+        assert roof["kernel"] == "k_walks<4,3>" and roof["unit"] == "TFLOP/s"
+        ms = roof["mma_sync"]
+        assert abs(ms["achieved_mac_per_s"] / 2 - roof["achieved"] * 1e12 / 4) / ms["achieved_mac_per_s"] < 1e-9
+        assert abs(ms["frac"] - ms["achieved_mac_per_s"] / ms["peak_mac_per_s"]) < 1e-9
     # steps per bench step / seconds per bench step = the headline value
     steps_per_step = r["config"]["walks"] * r["config"]["steps_per_walk_per_step"]
     assert abs(r["value"] - steps_per_step / (r["ms_per_step"] / 1e3)) / r["value"] < 0.02
