@@ -76,6 +76,9 @@ def parse():
                          "(the form N > 1 ranks always use; under torchrun)")
     ap.add_argument("--shape", type=int, default=0, help="launch shape of the --level-only walk kernel")
     ap.add_argument("--c-layout", type=int, default=0, help="C^ layout of the --level-only walk (0 int8, 1 words)")
+    ap.add_argument("--theta-shapes", action="store_true",
+                    help="only time one n = 4 level-7 walk launch (2^20 walks x 16 steps) of launch shapes 0 "
+                         "and 3 at several distinguished fractions, print its JSON and exit")
     ap.add_argument("--tto-sweep", action="store_true",
                     help="only time the n = 4 seeded target's collision walk over a grid of table sizes and "
                          "distinguished fractions, print its JSON and exit")
@@ -113,13 +116,13 @@ def workload_config(c, k=None, steps=None, rewalk_budget=None):
 # the steps, plus 32 bytes per distinguished point (0.5 MB at the headline's
 # 64 steps), so the figure stands for the headline launch.
 WALK_NCU = {
-    "k_walks<4,3>": {"source_sha256_16": "1ad60f80ab027ebf", "dram_bytes_per_launch": 34744576,
-                     "warp_inst_per_step": 1059.8},
-    "k_walks<4,0>": {"source_sha256_16": "1ad60f80ab027ebf", "dram_bytes_per_launch": 35051520,
+    "k_walks<4,3>": {"source_sha256_16": "b265cae77d341701", "dram_bytes_per_launch": 34822400,
+                     "warp_inst_per_step": 1059.5},
+    "k_walks<4,0>": {"source_sha256_16": "b265cae77d341701", "dram_bytes_per_launch": 35005184,
                      "warp_inst_per_step": 1937.6},
     # n = 3, level 5: `bench.py --level-only n3_level5 --steps 2`, one launch of 2^16 walks x 512 steps,
     # the launch of the n3_level5 record (profiles/k_walks_n3_level5_walks65536.md)
-    "k_walks<3,0>": {"source_sha256_16": "1ad60f80ab027ebf", "dram_bytes_per_launch": 2178560,
+    "k_walks<3,0>": {"source_sha256_16": "b265cae77d341701", "dram_bytes_per_launch": 2178048,
                      "warp_inst_per_step": 379.3},
 }
 
@@ -1005,6 +1008,26 @@ def run_tto_sweep(args):
     print(json.dumps({"tto_walk_cfg3_sweep": out}))
 
 
+def run_theta_shapes(args):
+    """Walk steps/s of the dp4a shape (0) and the tensor-core shape (3) at
+    theta = 2^-2, 2^-4, 2^-8 and 2^-12 (one warm-up and four timed 16-step
+    launches of 2^20 walks at n = 4, level 7)."""
+    import torch
+
+    import paper_1606_07413_gb300 as Q
+    from paper_1606_07413_gb300 import build as B
+    from paper_1606_07413_gb300 import workloads as W
+
+    B.build()
+    stream = torch.cuda.Stream()
+    out = {}
+    for dp_bits in (2, 4, 8, 12):
+        for shape in (0, 3):
+            r = level_throughput(Q, W, torch, 3, 7, 16, stream, launches=4, dp_bits=dp_bits, shape=shape)
+            out[f"theta2^-{dp_bits}_shape{shape}"] = r["walk_steps_per_s"]
+    print(json.dumps({"n4_level7_theta_shapes": out}))
+
+
 def run_exhaustive_only(args):
     import torch
 
@@ -1024,6 +1047,8 @@ if __name__ == "__main__":
         run_exhaustive_only(a)
     elif a.tto_sweep:
         run_tto_sweep(a)
+    elif a.theta_shapes:
+        run_theta_shapes(a)
     elif a.config3_walk or a.adder_walk:
         run_config3_walk(a)
     elif a.level_only:

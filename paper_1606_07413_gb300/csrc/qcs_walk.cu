@@ -23,9 +23,9 @@
 // then read off directly (its right factor is the identity), and the W side is
 // one contraction of the transformed weights with C^, staged in shared memory
 // as signed byte quads and contracted by byte-plane dp4a, or, at n = 4 in
-// launch shape 3, by f16 tensor-core MMAs over 32 walks at a time
-// (k_walks_mma4).  The result is bit-identical to hashing the explicitly
-// formed product.
+// launch shape 3, by f16 tensor-core MMAs in warps of their own, beside the
+// warps that run the stages of another set of walks (k_walks_mma4).  The
+// result is bit-identical to hashing the explicitly formed product.
 //
 // Also here: the distinguished-point table insert and the re-walk of merged
 // trails (Sec. 3, Fig. 2), the batched forms of both, the exhaustive level
