@@ -81,3 +81,36 @@ def test_a_full_merge_queue_counts_and_stays_in_bounds():
     found, stored = int(counts[6]), int(counts[7]) & 0xFFFFFFFF
     assert found > cap and min(stored, cap) == cap
     assert np.all(m[cap] == np.uint64(M64))  # nothing written past the capacity
+
+
+@pytest.mark.parametrize("dp_bits,samples", [(6, 16), (9, 4)])
+def test_tensor_core_walk_queues_real_merges(orc, dp_bits, samples):
+    """The n = 4 tensor-core walk (launch shape 3) at a theta where its MMA
+    warps store the distinguished points the stage warps hand them (2^-6),
+    and at one where each stage warp stores its own (2^-9): sampled queued
+    merges name two trails that both reach the stored point."""
+    from paper_1606_07413_gb300 import build
+
+    build.build()
+    dev = torch.device("cuda:0")
+    c = W.CONFIGS[3]
+    gates, _ = W.config_target(3)
+    k, version = 7, 2
+    params = Q.default_params(4, walks=1 << 14, state_bits=c["L"], dp_bits=dp_bits, table_log2=18, launch_shape=3)
+    C = orc.channel_from_circuit(4, gates)
+    with Q.Problem.from_circuit(4, gates, k, params) as prob:
+        m, counts = run_static(prob, dev, 1 << 14, k, version, dp_bits, 48, 1 << 16)
+    assert int(counts[7]) >> 32 == 0  # no bounded wait ran out
+    assert int(counts[0]) == (1 << 14) * 48 and int(counts[2]) > 0
+    stored = min(int(counts[7]) & 0xFFFFFFFF, 1 << 16)
+    assert stored >= samples
+    rng = np.random.default_rng(dp_bits)
+    for i in rng.choice(stored, samples, replace=False):
+        ref_a, ref_b, dp = (int(v) for v in m[i])
+        assert ref_a != ref_b and dp >> (c["L"] - dp_bits) == 0
+        for ref in (ref_a, ref_b):
+            start, chunk, length = trail(ref, params.seed, version, c["L"], 255)
+            x = np.array([start], np.uint64)
+            for _ in range(length):
+                x = orc.walk_step(C, k, chunk, version, c["L"], x)
+            assert int(x[0]) == dp, (i, ref)
