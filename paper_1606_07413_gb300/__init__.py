@@ -356,9 +356,11 @@ class Problem:
     def level_walk_static(self, k, version, dp_bits, begin, walk_states, steps, merges, counts, stream=None):
         """qcs_level_walk_static: the level walk without any device allocation.
         walk_states: int64 tensor of 4 * n_walks entries; merges: int64 tensor
-        of 3 * cap entries; counts: int64 tensor of 8 entries.  All three
-        must be contiguous int64 CUDA tensors: their sizes become the
-        kernel's bounds."""
+        of 3 * cap entries; counts: int64 tensor of 8 entries (the counters of
+        include/qcs.h; the high 32 bits of counts[7] are nonzero only if a
+        bounded wait of the n = 4 tensor-core walk ran out, and then nothing
+        the call wrote is valid).  All three must be contiguous int64 CUDA
+        tensors: their sizes become the kernel's bounds."""
         import torch
 
         for name, t in (("walk_states", walk_states), ("merges", merges), ("counts", counts)):
