@@ -120,3 +120,49 @@ def test_carried_rewalks_account_for_every_merge():
             runs[budget] = (hist, seen_carried)
     assert runs[0][1] == 0 and runs[4][1] > 0
     assert runs[0][0] == runs[4][0]  # same walks, distinguished points and merges
+
+
+@pytest.mark.parametrize("walks,steps,dpb", [(1, 3, 3), (23, 1, 3), (25, 5, 3), (48, 2, 12), (49, 7, 3),
+                                             (97, 4, 12), (1000, 9, 3)])
+def test_tensor_core_walk_ragged_launches(walks, steps, dpb):
+    """The n = 4 tensor-core walk (launch shape 3) at ragged and tiny sizes.
+    The cases cover fewer walks than one set (24), a half-empty second set, a
+    group boundary (48) and single steps.  Both instantiations run: the one
+    whose MMA warps store the distinguished points (theta = 2^-3) and the
+    plain one (2^-12).  Every walk's record and the order-independent
+    counters equal the dp4a shape's, and no bounded wait runs out."""
+    from paper_1606_07413_gb300 import build
+
+    build.build()
+    dev = torch.device("cuda:0")
+    gates, _ = W.config_target(3)
+    runs = {}
+    for shape in (0, 3):
+        p = Q.default_params(4, walks=walks, table_log2=16, launch_shape=shape)
+        with Q.Problem.from_circuit(4, gates, 7, p) as prob:
+            ws = torch.zeros(4 * walks, dtype=torch.int64, device=dev)
+            merges = torch.zeros(3 * 4096, dtype=torch.int64, device=dev)
+            counts = torch.zeros(8, dtype=torch.int64, device=dev)
+            prob.level_walk_static(7, 1, dpb, 1, ws, steps, merges, counts)
+            torch.cuda.synchronize()
+            c = counts.cpu().numpy()
+            runs[shape] = (ws.cpu().numpy(), c[:4].tolist(), int(c[7]) >> 32)
+    assert runs[3][2] == 0
+    assert runs[0][1][0] == walks * steps
+    assert np.array_equal(runs[3][0], runs[0][0])
+    assert runs[3][1] == runs[0][1]
+
+
+def test_static_walk_rejects_an_empty_launch():
+    """n_walks = 0 is an argument error, not an empty launch."""
+    from paper_1606_07413_gb300 import build
+
+    build.build()
+    dev = torch.device("cuda:0")
+    gates, _ = W.config_target(3)
+    with Q.Problem.from_circuit(4, gates, 7, Q.default_params(4, walks=64, table_log2=16)) as prob:
+        ws = torch.zeros(0, dtype=torch.int64, device=dev)
+        merges = torch.zeros(3, dtype=torch.int64, device=dev)
+        counts = torch.zeros(8, dtype=torch.int64, device=dev)
+        with pytest.raises(Q.QcsError):
+            prob.level_walk_static(7, 1, 6, 1, ws, 4, merges, counts)
