@@ -747,7 +747,9 @@ __global__ void __launch_bounds__(Shape<NQ, S>::THREADS, Shape<NQ, S>::MIN_BLOCK
 // than a CTA's shared memory, and exactly an SM's tensor memory (128 lanes x
 // 512 columns of 32 bits).  So at the start each MMA warp converts the MMA
 // fragments of its columns once and stores them in tensor memory
-// (tcgen05.st); it reloads them with tcgen05.ld, one K-block at a time.
+// (tcgen05.st); it reloads them with tcgen05.ld, two K-blocks at a time.
+// Where theta is large the MMA warps also store the distinguished points the
+// stage warps find (the instantiation COLLECT; see Rings below).
 // Exactness: every product is an integer of magnitude below 2^15 (a byte
 // times an int8 entry), and every partial sum of a 512-term dot product is
 // below 512 x 255 x 128 < 2^24, so the f32 accumulation is exact and the
