@@ -116,13 +116,13 @@ def workload_config(c, k=None, steps=None, rewalk_budget=None):
 # the steps, plus 32 bytes per distinguished point (0.5 MB at the headline's
 # 64 steps), so the figure stands for the headline launch.
 WALK_NCU = {
-    "k_walks<4,3>": {"source_sha256_16": "b265cae77d341701", "dram_bytes_per_launch": 34822400,
-                     "warp_inst_per_step": 1059.5},
-    "k_walks<4,0>": {"source_sha256_16": "b265cae77d341701", "dram_bytes_per_launch": 35005184,
+    "k_walks<4,3>": {"source_sha256_16": "80027283cc3dbf3c", "dram_bytes_per_launch": 34747136,
+                     "warp_inst_per_step": 1073.2},
+    "k_walks<4,0>": {"source_sha256_16": "80027283cc3dbf3c", "dram_bytes_per_launch": 35021312,
                      "warp_inst_per_step": 1937.6},
     # n = 3, level 5: `bench.py --level-only n3_level5 --steps 2`, one launch of 2^16 walks x 512 steps,
     # the launch of the n3_level5 record (profiles/k_walks_n3_level5_walks65536.md)
-    "k_walks<3,0>": {"source_sha256_16": "b265cae77d341701", "dram_bytes_per_launch": 2178048,
+    "k_walks<3,0>": {"source_sha256_16": "80027283cc3dbf3c", "dram_bytes_per_launch": 2178304,
                      "warp_inst_per_step": 379.3},
 }
 

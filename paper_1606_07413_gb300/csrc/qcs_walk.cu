@@ -985,6 +985,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t ph)
     }
 }
 
+// The bounded wait, made warp-uniform: true only if every lane saw the phase
+// complete (lanes that time out at different moments must not leave the warp
+// split before its next warp-wide operation).
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *b, uint32_t ph)
+{
+    return __all_sync(0xFFFFFFFFu, mbar_wait(b, ph));
+}
+
 } // namespace mma4
 
 // COLLECT: the MMA warps store the distinguished points (launched where
@@ -1190,7 +1198,7 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
 #pragma unroll
                 for (int X = 0; X < 2; X++) {
                     if (stalled) break;
-                    if (!mma4::mbar_wait(&bars[2 + X], ph[X])) {
+                    if (!mma4::mbar_wait_warp(&bars[2 + X], ph[X])) {
                         stalled = true;
                         break;
                     }
@@ -1271,7 +1279,7 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
             for (uint32_t step = 0; step < steps && !stalled; step++)
 #pragma unroll 1
                 for (int X = 0; X < 2; X++) {
-                    if (!(collect ? wait_rows(X) : mma4::mbar_wait(&bars[X], ph[X]))) {
+                    if (!(collect ? wait_rows(X) : mma4::mbar_wait_warp(&bars[X], ph[X]))) {
                         stalled = true;
                         break;
                     }
