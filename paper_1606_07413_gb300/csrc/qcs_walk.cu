@@ -1060,7 +1060,7 @@ __global__ void __launch_bounds__(mma4::kThreads, 1) k_walks_mma4(WalkLaunch w)
         mma4::tmem_wait_st();
     }
     mma4::tmem_fence_before();
-    __syncthreads(); // the units are stored; the barriers are initialised
+    __syncthreads(); // the fragments are in tensor memory; the barriers are initialised
     mma4::tmem_fence_after();
 
     const LevelCtx &lv = w.lv;
