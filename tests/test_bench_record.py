@@ -72,3 +72,23 @@ def test_step_split_and_extras():
     s = r["serving"]
     assert 0 <= s["miss_rate"] < 1 and s["p99_all_s"] >= s["p50_all_s"]
     assert sum(s["status_counts"].values()) == 2000
+
+
+def test_tensor_roofline_arithmetic():
+    """bench.walk_roofline for the tensor-core shape on made-up inputs: the
+    achieved flops are 4 per 16-bit-weight multiply-add (two f16 byte-plane
+    multiply-adds), against the measured dense bf16 peak; the mma.sync
+    fraction counts the same multiply-adds twice against the given rate; the
+    dp4a shapes stay ALU-bound against twice the dp4a rate."""
+    n, w_steps, steps, walk_s = 4, 1_000_000, 2_000_000, 0.5
+    d = 4 ** n - 1
+    macs = w_steps * 2 * d * d / walk_s
+    r = bench.walk_roofline("k_walks<4,3>", n, w_steps, steps, walk_s, 1, 1e13, 2070.0, 152, hmma_per_s=3e14)
+    peak, _ = bench.measured_tensor_tflops(sustained=True)
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - 4 * macs / 1e12) < 1e-9 and r["peak"] == peak
+    assert abs(r["frac"] - r["achieved"] / peak) < 1e-12
+    assert abs(r["mma_sync"]["frac"] - 2 * macs / 3e14) < 1e-12
+    assert abs(r["dp4a_equivalent"]["frac"] - macs / 2e13) < 1e-12
+    r0 = bench.walk_roofline("k_walks<4,0>", n, w_steps, steps, walk_s, 1, 1e13, 2070.0, 152)
+    assert r0["bound"] == "alu" and abs(r0["frac"] - macs / 2e13) < 1e-12
