@@ -3,7 +3,7 @@
 
 The model mirrors the kernel's control flow:
 - 12 stage warps and 8 MMA warps;
-- two walk sets, whose "rows ready" and "sums ready" mbarriers complete a
+- the walk sets (the kernel runs two; three are checked too), whose "rows ready" and "sums ready" mbarriers complete a
   phase when every expected warp has arrived, and whose waiters wait on a
   phase parity;
 - the stage warps' single-producer rings of distinguished points, drained by
@@ -21,7 +21,7 @@ import random
 
 import pytest
 
-STAGE, MMA, SETS = 12, 8, 2
+STAGE, MMA = 12, 8
 
 
 class Barrier:
@@ -47,7 +47,8 @@ class Ring:
 
 def stage_warp(wi, st, groups, steps, dp_prob, rng):
     """Generator of one stage warp: yields ("wait", predicate) to block."""
-    ph = [0, 0]
+    SETS = st["sets"]
+    ph = [0] * SETS
     ring = st["rings"][wi]
     for _ in range(groups):
         def phase_a(x):
@@ -63,10 +64,9 @@ def stage_warp(wi, st, groups, steps, dp_prob, rng):
                     else:
                         st["stored"].append(pid)  # the ring is full: store it here
         if steps > 0:
-            phase_a(0)
-            yield ("run", None)
-            phase_a(1)
-            yield ("run", None)
+            for x in range(SETS):
+                phase_a(x)
+                yield ("run", None)
         for step in range(steps):
             for x in range(SETS):
                 b = st["sums"][x]
@@ -84,7 +84,8 @@ def stage_warp(wi, st, groups, steps, dp_prob, rng):
 
 
 def mma_warp(m, st, groups, steps):
-    ph = [0, 0]
+    SETS = st["sets"]
+    ph = [0] * SETS
     owned = [st["rings"][r] for r in (m, m + MMA) if r < STAGE]
 
     def drain(most):
@@ -118,11 +119,16 @@ def mma_warp(m, st, groups, steps):
                    or any(r.head != r.tail for r in owned))
 
 
-def run_model(seed, groups, steps, dp_prob, ring_cap, max_events=2_000_000):
+def model_state(sets, ring_cap, rows_count=STAGE):
+    return {"sets": sets, "rows": [Barrier(rows_count) for _ in range(sets)],
+            "sums": [Barrier(MMA) for _ in range(sets)], "rings": [Ring(ring_cap) for _ in range(STAGE)],
+            "found": 0, "stored": [], "ahead": 0, "sums_seen": [[0] * sets for _ in range(STAGE)],
+            "rows_seen": [[0] * sets for _ in range(MMA)]}
+
+
+def run_model(seed, sets, groups, steps, dp_prob, ring_cap, max_events=2_000_000):
     rng = random.Random(seed)
-    st = {"rows": [Barrier(STAGE) for _ in range(SETS)], "sums": [Barrier(MMA) for _ in range(SETS)],
-          "rings": [Ring(ring_cap) for _ in range(STAGE)], "found": 0, "stored": [], "ahead": 0,
-          "sums_seen": [[0, 0] for _ in range(STAGE)], "rows_seen": [[0, 0] for _ in range(MMA)]}
+    st = model_state(sets, ring_cap)
     warps = [stage_warp(i, st, groups, steps, dp_prob, random.Random(rng.random())) for i in range(STAGE)]
     warps += [mma_warp(m, st, groups, steps) for m in range(MMA)]
     blocked = {}  # warp index -> predicate
@@ -145,14 +151,15 @@ def run_model(seed, groups, steps, dp_prob, ring_cap, max_events=2_000_000):
     return st
 
 
+@pytest.mark.parametrize("sets", [2, 3])
 @pytest.mark.parametrize("seed", range(12))
-def test_protocol_finishes_and_stores_every_point_once(seed):
+def test_protocol_finishes_and_stores_every_point_once(seed, sets):
     rng = random.Random(1000 + seed)
     groups = rng.choice([0, 1, 2, 3])
     steps = rng.choice([0, 1, 2, 5, 9])
     dp_prob = rng.choice([0.0, 0.05, 0.25, 0.5, 1.0])
     ring_cap = rng.choice([1, 2, 64])
-    st = run_model(seed, groups, steps, dp_prob, ring_cap)
+    st = run_model(seed, sets, groups, steps, dp_prob, ring_cap)
     # every phase every waiter waited for completed exactly once per step and set
     for b in st["rows"] + st["sums"]:
         assert b.phase == groups * steps
@@ -165,9 +172,7 @@ def test_a_missing_arrival_is_a_deadlock_the_model_sees():
     rows barrier never completes and the model reports the deadlock (on the
     GPU, the bounded waits would give up and the launch report a stall)."""
     rng = random.Random(5)
-    st = {"rows": [Barrier(STAGE + 1) for _ in range(SETS)], "sums": [Barrier(MMA) for _ in range(SETS)],
-          "rings": [Ring(64) for _ in range(STAGE)], "found": 0, "stored": [], "ahead": 0,
-          "sums_seen": [[0, 0] for _ in range(STAGE)], "rows_seen": [[0, 0] for _ in range(MMA)]}
+    st = model_state(3, 64, rows_count=STAGE + 1)
     warps = [stage_warp(i, st, 1, 2, 0.1, random.Random(i)) for i in range(STAGE)]
     warps += [mma_warp(m, st, 1, 2) for m in range(MMA)]
     blocked, live = {}, set(range(len(warps)))
